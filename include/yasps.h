@@ -1,0 +1,265 @@
+/*
+ * yasps.h -- C ABI of the B300-native IPC Newton hot path.
+ *
+ * What is computed follows YASPS (arxiv 2605.23088): per-element energy,
+ * gradient and PSD-projected Hessian of elastic and contact-barrier terms,
+ * scatter into a duplicate-free upper-triangular 3x3 block-sparse Hessian
+ * (App. B), block-Jacobi PCG on H p = g with a BSR SpMV (Sec. 8, App. C, D),
+ * and the contact-pair broadphase and CCD step bound that feed the line search
+ * of the incremental-potential Newton step (Sec. 3, "System Overview").
+ *
+ * Conventions shared by every entry point
+ *  - All entry points are C, take plain pointers and sizes, and never throw.
+ *  - Return value: YASPS_OK (0) or a negative yasps_status.  On failure the
+ *    system stays valid and yasps_last_error() holds a message.
+ *  - "_dev" pointers are CUDA device pointers on the system's device; "_host"
+ *    pointers are host memory.  The caller owns every pointer it passes; the
+ *    library never frees caller memory and keeps no caller pointer after the
+ *    call returns (yasps_build_system copies the scene).
+ *  - The DOF vector x is an array of n_nodes nodes, 3 values each (node-major,
+ *    x[3*i + k]).  Nodes are: every free vertex (not fixed, not in an affine
+ *    body) in increasing vertex order, then 4 nodes per affine body:
+ *    t (translation) and the three columns of A, so that a body vertex with
+ *    body-relative rest position r sits at p = t + r1 A_1 + r2 A_2 + r3 A_3
+ *    (App. A "Gradient Size Computation": 3N + 9 + 3 DOF for one body).
+ *  - x, v, gradients and energies are FP64 in both precisions.  Hessian
+ *    values and PCG vectors are FP64 (precision 0) or FP32 (precision 1,
+ *    "FP32-mixed").
+ *  - All work is issued on the stream given at build time.  Calls that
+ *    return host scalars synchronise that stream; the others are asynchronous.
+ */
+#ifndef YASPS_H
+#define YASPS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct yasps_system yasps_system; /* opaque; owned by the library */
+typedef int yasps_status;
+
+#define YASPS_OK 0
+#define YASPS_E_INVAL (-1)      /* bad argument or scene */
+#define YASPS_E_NOMEM (-2)      /* device allocation failed */
+#define YASPS_E_CUDA (-3)       /* a CUDA call failed */
+#define YASPS_E_CAPACITY (-4)   /* a bounded buffer overflowed */
+#define YASPS_E_NOCONV (-5)     /* PCG or Newton hit its iteration cap */
+#define YASPS_E_LINESEARCH (-6) /* no decreasing step within ls_max_iter halvings */
+#define YASPS_E_TIMEOUT (-7)    /* a bounded device-side wait gave up */
+#define YASPS_E_NAN (-8)        /* a NaN/Inf appeared in the gradient, the solve or the energy */
+
+/* Device allocator used for every library workspace.  alloc returns a device
+ * pointer of at least `bytes` (256-byte aligned) or NULL; free releases it.
+ * Both are called on the host with the system's stream.  Pass NULL to
+ * yasps_build_system to use cudaMallocAsync / cudaFreeAsync on that stream. */
+typedef struct {
+  void* ctx;
+  void* (*alloc)(void* ctx, size_t bytes, void* cuda_stream);
+  void (*free)(void* ctx, void* ptr, void* cuda_stream);
+} yasps_allocator;
+
+/* Solver and step parameters. */
+typedef struct {
+  int precision;      /* 0: FP64 plain; 1: FP32-mixed (FP32 local Hessians, SpMV and PCG
+                         vectors with FP64 residual refinement; FP64 kept for positions,
+                         gradients, distances, barrier values, CCD and energies) */
+  double dt;          /* time step h (s) */
+  double dhat;        /* barrier activation distance (m): pairs with d^2 < dhat^2 are active */
+  double kappa;       /* barrier stiffness (multiplies sum b(d^2) in the incremental potential) */
+  double gravity[3];  /* m/s^2 */
+  double newton_tol;  /* stop when ||p||_inf <= newton_tol (m) */
+  double pcg_rel_tol; /* stop PCG when r^T z <= tol^2 r0^T z0 */
+  int pcg_max_iter;   /* <= 0: 10 * number of DOF */
+  int newton_max_iter;
+  int ls_max_iter;    /* maximum halvings in the line search */
+  int barrier_form;   /* 0: -(s - sh)^2 ln(s/sh) (IPC); 1: (s - sh)^2 ln^2(s/sh) (the paper's listing) */
+  double ccd_gap;     /* additive CCD keeps at least ccd_gap times the starting distance */
+  int ccd_max_iter;   /* cap on additive-CCD advancement steps per pair */
+  int refine_sweeps;  /* FP32-mixed only: maximum FP64 residual-refinement sweeps */
+} yasps_params;
+
+/* Scene, host pointers, copied at build.  Index arrays are int32, 0-based.
+ * Elastic elements (tets, cloth triangles, hinges) may reference free or
+ * fixed vertices; affine-body vertices take part in contact and inertia. */
+typedef struct {
+  int n_verts;
+  const double* rest_pos;   /* [n_verts][3] undeformed world positions (also the initial state) */
+  const int* vert_body;     /* [n_verts] -1 or affine body id */
+  int n_fixed;
+  const int* fixed_verts;   /* [n_fixed] vertices with prescribed positions */
+  const double* fixed_vel;  /* [n_fixed][3] prescribed velocity, applied at the start of each step */
+  int n_tets;
+  const int* tet2v;         /* [n_tets][4], positively oriented */
+  const double* tet_E;      /* [n_tets] Young's modulus (Pa) */
+  const double* tet_nu;     /* [n_tets] Poisson ratio */
+  const double* tet_rho;    /* [n_tets] density (kg/m^3) */
+  int n_tris;
+  const int* tri2v;         /* [n_tris][3] membrane (cloth) triangles */
+  const double* tri_E;
+  const double* tri_nu;
+  const double* tri_thick;
+  const double* tri_rho;
+  int n_hinges;
+  const int* hinge2v;       /* [n_hinges][4] (e0, e1, a, b): triangles (e0,e1,a) and (e1,e0,b) */
+  const double* hinge_kb;   /* [n_hinges] bending stiffness */
+  int n_bodies;
+  const double* body_mass;  /* [n_bodies] kg, lumped uniformly over the body's vertices */
+  const double* body_vol;   /* [n_bodies] m^3 */
+  const double* body_kappa; /* [n_bodies] orthogonality stiffness (Pa) */
+  int n_surf_tris;
+  const int* surf_tri2v;    /* [n_surf_tris][3] collision triangles */
+  int n_surf_edges;
+  const int* surf_edge2v;   /* [n_surf_edges][2] collision edges */
+  int n_surf_verts;
+  const int* surf_verts;    /* [n_surf_verts] collision vertices, strictly increasing */
+  int n_planes;
+  const double* planes;     /* [n_planes][4] (n, c): the half-space n.x >= c is free space */
+} yasps_scene_desc;
+
+/* Per-call statistics of yasps_step (the paper's counters, Sec. "Simulation
+ * Time Comparison": Newton and CG iterations, pair counts by type). */
+typedef struct {
+  int newton_iters;
+  int pcg_iters_total;
+  int n_pt, n_ee, n_pg; /* active pairs at the last Newton iteration */
+  int status;
+  double alpha_last;    /* last accepted line-search step */
+  double p_inf;         /* ||p||_inf at exit */
+  double t_eval_ms, t_pcg_ms, t_ccd_ms, t_ls_ms; /* stage times (CUDA events) */
+} yasps_step_stats;
+
+/* Fill *p with defaults (FP64, dt 0.01, dhat 1e-3, kappa 1e4, g = (0,-9.81,0),
+ * newton_tol 1e-6, pcg_rel_tol 1e-4, newton_max_iter 100, ls_max_iter 30,
+ * barrier_form 0, ccd_gap 0.1, ccd_max_iter 100000, refine_sweeps 4). */
+void yasps_default_params(yasps_params* p);
+
+/* Build a system: uploads the scene, computes rest-shape quantities
+ * (Dm^-1, volumes, Lame constants, lumped masses, body frames), the DOF layout
+ * and the static BSR sparsity of H (App. B: upper blocks of every elastic and
+ * inertia contribution, sorted by (row, col), duplicates removed).
+ * cuda_stream: a cudaStream_t (NULL = legacy default stream).
+ * allocator: NULL for cudaMallocAsync/cudaFreeAsync.
+ * Errors: E_INVAL (bad sizes/indices, degenerate rest element, elastic element
+ * on an affine-body vertex), E_NOMEM, E_CUDA.  *out is NULL on failure and
+ * the message is then available from yasps_build_error(). */
+yasps_status yasps_build_system(const yasps_scene_desc* scene, const yasps_params* params,
+                                const yasps_allocator* allocator, void* cuda_stream, yasps_system** out);
+const char* yasps_build_error(void);
+
+/* Release every device buffer (on the system's stream) and the handle. */
+void yasps_destroy(yasps_system* sys);
+
+/* Message of the last failing call on this system (never NULL). */
+const char* yasps_last_error(const yasps_system* sys);
+
+/* Replace the solver parameters.  Switching precision re-lays out the
+ * Hessian storage. */
+yasps_status yasps_set_params(yasps_system* sys, const yasps_params* params);
+
+/* Sizes: n_nodes (3 DOF each), n_free (free-vertex nodes), n_verts. */
+yasps_status yasps_get_sizes(const yasps_system* sys, int* n_nodes, int* n_free, int* n_verts);
+
+/* Initial node state from the rest pose and per-vertex initial velocities
+ * vel0_host [n_verts][3] (may be NULL: zero).  x_dev, v_dev: [n_nodes][3] FP64.
+ * A body gets the mean velocity of its vertices as its translation velocity. */
+yasps_status yasps_initial_state(yasps_system* sys, const double* vel0_host, double* x_dev, double* v_dev);
+
+/* World positions of all vertices, P_dev [n_verts][3] FP64, from x_dev (the
+ * UNION of free, affine and fixed parameterisations, Sec. "UNION"). */
+yasps_status yasps_vertex_positions(yasps_system* sys, const double* x_dev, double* P_dev);
+
+/* x_tilde = x_t + h v_t + h^2 M^-1 f_gravity into xtilde_dev [n_nodes][3]. */
+yasps_status yasps_xtilde(yasps_system* sys, const double* xt_dev, const double* vt_dev, double* xtilde_dev);
+
+/* Contact detection at x (Sec. "UNION" code example: collision pairs as a
+ * dynamic primitive): point-triangle, edge-edge and point-plane pairs with
+ * squared distance below dhat^2; exclusions: shared vertex, same affine body,
+ * all vertices fixed.  The lists are kept inside the system (they feed
+ * yasps_eval_local) and their counts returned (host scalars; synchronises). */
+yasps_status yasps_detect_pairs(yasps_system* sys, const double* x_dev, int* n_pt, int* n_ee, int* n_pg);
+
+/* Copy the current pair lists as (a, b, subtype) int32 triples sorted by (a, b):
+ * PT: (vertex, surface triangle, closest-feature subtype 0..6);
+ * EE: (edge i, edge j > i, subtype 0..12); PG: (vertex, plane, 0).
+ * Any output pointer may be NULL.  Host pointers sized by the counts above. */
+yasps_status yasps_export_pairs(yasps_system* sys, int* pt_host, int* ee_host, int* pg_host);
+
+/* Terms for term_mask. */
+#define YASPS_TERM_INERTIA 1
+#define YASPS_TERM_TET 2
+#define YASPS_TERM_MEMBRANE 4
+#define YASPS_TERM_BEND 8
+#define YASPS_TERM_ABD 16
+#define YASPS_TERM_BARRIER 32
+#define YASPS_TERM_ALL 63
+
+/* Incremental-potential energy E(x) = 1/2 |x - xtilde|_M^2 + h^2 (elastic +
+ * ABD) + kappa sum b(s), FP64 with compensated sums on the device, pair set
+ * detected at x (the pair lists of the system are not changed).  terms_host
+ * (nullable) receives the six term values in YASPS_TERM bit order.
+ * Synchronises. */
+yasps_status yasps_energy(yasps_system* sys, const double* x_dev, const double* xtilde_dev, double* energy_host,
+                          double* terms_host);
+
+/* Local evaluation (Sec. "Hessian Code Generation"): per element / pair
+ * gradient and PSD-projected Hessian (project != 0; exact otherwise),
+ * scattered into the system's gradient and H = H_static + H_dynamic (Sec.
+ * "Index Computation") by atomic addition (App. B "Assembly"), then the
+ * block-Jacobi inverse (App. D).  Uses the pair lists of the last
+ * yasps_detect_pairs, which must have been called at the same x.  Zeroes g and
+ * H first.  Asynchronous. */
+yasps_status yasps_eval_local(yasps_system* sys, const double* x_dev, const double* xtilde_dev, int term_mask,
+                              int project);
+
+/* Build the dynamic BSR sparsity of the contact part from the current pair
+ * lists (sort + unique of upper block keys, App. B).  yasps_detect_pairs calls
+ * it; exposed for timing. */
+yasps_status yasps_assemble(yasps_system* sys);
+
+/* Export for tests: which = 0 static / 1 dynamic upper BSR; nnzb (host),
+ * row_ptr [n_nodes+1], col [nnzb], vals [nnzb][9] FP64 and (which = 0 only)
+ * the diagonal blocks diag [n_nodes][9] FP64, all host.  NULL skips an array. */
+yasps_status yasps_export_bsr(yasps_system* sys, int which, int* nnzb, int* row_ptr_host, int* col_host,
+                              double* vals_host, double* diag_host);
+/* Gradient of the last evaluation, g_dev [n_nodes][3] FP64 (device copy). */
+yasps_status yasps_export_gradient(yasps_system* sys, double* g_dev);
+
+/* y = H x with the assembled H (symmetric upper storage, Alg. 7); FP64 in/out
+ * (in FP32-mixed the stored FP32 blocks are applied in FP64). */
+yasps_status yasps_spmv(yasps_system* sys, const double* x_dev, double* y_dev);
+
+/* Solve H p = rhs by block-Jacobi PCG (Sec. 8 "Solver", App. D), p not negated
+ * (Sec. "Solution Extraction").  rhs_dev, p_dev: [n_nodes][3] FP64.  iters and
+ * rel_res (host, nullable): iterations and final sqrt(r^T z / r0^T z0).
+ * Errors: E_NOCONV when the cap is hit (p holds the last iterate). */
+yasps_status yasps_pcg_solve(yasps_system* sys, const double* rhs_dev, double* p_dev, double rel_tol, int* iters,
+                             double* rel_res);
+
+/* Largest safe step along x - alpha p, alpha in [0, 1]: additive CCD
+ * (Li et al. 2021) for PT/EE candidates from swept boxes, exact for PG.  Host
+ * scalar (synchronises). */
+yasps_status yasps_ccd_bound(yasps_system* sys, const double* x_dev, const double* p_dev, double* alpha_host);
+
+/* One implicit time step (Sec. 3: CD -> minimise -> CCD/line search -> update):
+ * Newton iterations on the incremental potential until ||p||_inf <= newton_tol,
+ * then v = (x - x_t)/h.  x_dev, v_dev: [n_nodes][3] FP64, updated in place.
+ * stats (host, nullable).  Errors: E_LINESEARCH, E_NOCONV, E_NAN (x, v keep
+ * the last accepted iterate). */
+yasps_status yasps_step(yasps_system* sys, double* x_dev, double* v_dev, yasps_step_stats* stats);
+
+/* Prescribed positions of fixed vertices (host [n_verts][3]; only fixed rows
+ * are read / written). */
+yasps_status yasps_set_fixed_positions(yasps_system* sys, const double* P_host);
+yasps_status yasps_get_fixed_positions(yasps_system* sys, double* P_host);
+
+/* Number of kernels this system has launched since it was built (a host
+ * counter incremented at every launch). */
+long long yasps_kernel_launches(const yasps_system* sys);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* YASPS_H */

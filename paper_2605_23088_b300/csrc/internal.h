@@ -1,0 +1,166 @@
+// internal.h -- host-side state of a yasps_system and the launch wrappers that
+// the library's translation units export to each other.  Not part of the ABI.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "yasps.h"
+
+struct yasps_system;
+
+// a growable device buffer owned by the system (contents are not kept on growth)
+struct gbuf {
+  void* p = nullptr;
+  size_t cap = 0;
+};
+bool ensure(yasps_system* s, gbuf& b, size_t bytes);
+void release(yasps_system* s, gbuf& b);
+template <typename T>
+T* as(const gbuf& b) { return static_cast<T*>(b.p); }
+
+// Upper off-diagonal BSR part: rows sorted, columns strictly greater than the
+// row and increasing inside a row (App. B: unique, upper triangle, sorted).
+struct bsr_struct {
+  int nnzb = 0;
+  gbuf row_ptr;  // int [nn + 1]
+  gbuf col;      // int [nnzb]
+  gbuf row;      // int [nnzb] row of each block (block-parallel SpMV)
+  gbuf vals;     // T [nnzb][9]
+};
+
+struct yasps_system {
+  yasps_params prm{};
+  cudaStream_t stream = nullptr;
+  yasps_allocator allocator{};
+  bool have_allocator = false;
+  std::string err;
+  long long launches = 0;
+
+  // sizes
+  int nv = 0, nn = 0, nfree = 0, nb = 0, nt = 0, nc = 0, nh = 0, nst = 0, nse = 0, nsv = 0, npl = 0, nfix = 0;
+  int nbits = 1;  // bits of a node id in packed (row, col) keys; node 2^nbits - 1 is the sentinel
+
+  // scene, device
+  gbuf vnode;     // int [nv] free: node; body: first node of its body; fixed: -1
+  gbuf vbody;     // int [nv]
+  gbuf vr;        // double [nv][3] body-relative rest position (body vertices)
+  gbuf vmass;     // double [nv]
+  gbuf rest;      // double [nv][3]
+  gbuf xfix;      // double [nv][3] prescribed positions (rows of fixed vertices)
+  gbuf fixed;     // int [nfix]
+  gbuf fixvel;    // double [nfix][3]
+  gbuf nodemass;  // double [nfree] then [nb][16]
+  gbuf tet_v;     // int [nt][4] vertex ids
+  gbuf tet_n;     // int [nt][4] node ids (-1 fixed)
+  gbuf tet_rest;  // double [nt][12]: Dm^-1 (9, row-major), vol, mu, lam
+  gbuf tet_slot;  // int [nt][6] static BSR slot of local pairs (01,02,03,12,13,23), -1 none
+  gbuf tri_v, tri_n;  // int [nc][3]
+  gbuf tri_rest;      // double [nc][8]: Dm^-1 (4), area*thick, mu, lam, 0
+  gbuf tri_slot;      // int [nc][3] (01, 02, 12)
+  gbuf hinge_v, hinge_n;  // int [nh][4]
+  gbuf hinge_rest;        // double [nh][2]: theta0, kb * 3|e|^2 / (A1 + A2)
+  gbuf hinge_slot;        // int [nh][6]
+  gbuf body_kv;           // double [nb] kappa_a * vol
+  gbuf body_slot;         // int [nb][6] (01,02,03,12,13,23) among the body's 4 nodes
+  gbuf stri;   // int [nst][3]
+  gbuf sedge;  // int [nse][2]
+  gbuf svert;  // int [nsv]
+  gbuf planes; // double [npl][4]
+
+  // assembled system
+  int hess_precision = -1;  // layout of diag / vals / minv (0 FP64, 1 FP32)
+  bsr_struct Hs, Hd;        // static (elastic, inertia, ABD) and dynamic (contact) parts
+  gbuf diag;                // T [nn][9]
+  gbuf grad;                // double [nn][3]
+  gbuf minv;                // T [nfree][9] then [nb][144]
+  gbuf P;                   // double [nv][3] vertex positions at the last evaluation
+
+  // contact pairs, int [n][3] = (a, b, subtype), sorted by (a, b)
+  int npt = 0, nee = 0, npg = 0;
+  gbuf pt, ee, pg;
+  gbuf pair_key_off;  // int [npt + nee + 1] offsets of each pair's dynamic keys
+  gbuf dyn_slot;      // int [nkeys] dynamic BSR slot per key
+  int nkeys = 0;
+
+  // workspaces
+  gbuf status;    // int: latched device error bits
+  gbuf scal;      // device scalars (PCG and reductions)
+  gbuf red;       // reduction partials
+  gbuf scan_tmp;  // scan block sums
+  gbuf ws[10];    // scratch (sort keys/values, grid, counts)
+  gbuf vec[10];   // PCG vectors
+  gbuf stepv[6];  // step vectors
+  cudaEvent_t ev[8] = {};
+};
+
+#define SYS_FAIL(s, code, msg) \
+  do {                         \
+    (s)->err = (msg);          \
+    return (code);             \
+  } while (0)
+
+yasps_status cuda_check(yasps_system* s, cudaError_t e, const char* where);
+#define CK(s, call)                                    \
+  do {                                                 \
+    yasps_status _rc = cuda_check((s), (call), #call); \
+    if (_rc != YASPS_OK) return _rc;                   \
+  } while (0)
+#define RC(call)                       \
+  do {                                 \
+    yasps_status _rc = (call);         \
+    if (_rc != YASPS_OK) return _rc;   \
+  } while (0)
+// record a launch and check the launch error
+#define LAUNCH_CHECK(s, name)                                  \
+  do {                                                         \
+    (s)->launches++;                                           \
+    yasps_status _rc = cuda_check((s), cudaGetLastError(), name); \
+    if (_rc != YASPS_OK) return _rc;                           \
+  } while (0)
+#define ENSURE(s, buf, bytes)                                                   \
+  do {                                                                          \
+    if (!ensure((s), (buf), (bytes))) SYS_FAIL((s), YASPS_E_NOMEM, "device allocation failed"); \
+  } while (0)
+
+// ---------------------------------------------------------------- sort.cu
+// exclusive prefix sum of n int32 (in may alias out); *total_host (nullable) synchronises
+yasps_status scan_exclusive(yasps_system* s, const int* in, int* out, int n, int* total_host);
+// stable LSD radix sort of (uint64 key, int value) pairs on the low `bits` bits,
+// in place in keys/vals, using keys_tmp/vals_tmp as the ping-pong buffers
+yasps_status radix_sort_pairs(yasps_system* s, uint64_t* keys, int* vals, uint64_t* keys_tmp, int* vals_tmp, int n,
+                              int bits);
+// Upper BSR structure from n packed keys (row << nbits | col, row < col; the
+// sentinel row 2^nbits - 1 is dropped) with contribution ids vals: sorts,
+// removes duplicates, fills B.row_ptr / col / row / nnzb and slot_of[contrib]
+// (-1 for sentinel keys).  keys/vals are clobbered; tmp buffers from s->ws[6..8].
+yasps_status bsr_from_keys(yasps_system* s, uint64_t* keys, int* vals, int n, bsr_struct& B, int* slot_of,
+                           int n_contrib);
+
+// ---------------------------------------------------------------- elements.cu
+yasps_status setup_rest(yasps_system* s);  // rest-shape data and free-vertex masses
+yasps_status static_sparsity(yasps_system* s);
+yasps_status launch_positions(yasps_system* s, const double* x, double* P);
+yasps_status launch_xtilde(yasps_system* s, const double* xt, const double* vt, double* xtil);
+yasps_status launch_eval_static(yasps_system* s, const double* x, const double* xtil, int mask, int project);
+// five static terms (inertia, tet, membrane, bend, ABD) into out5 (host); synchronises
+yasps_status energy_static(yasps_system* s, const double* x, const double* xtil, double* out5);
+
+// ---------------------------------------------------------------- contact.cu
+yasps_status detect_pairs(yasps_system* s, const double* P);
+yasps_status build_dynamic_bsr(yasps_system* s);
+yasps_status launch_eval_barrier(yasps_system* s, int project);
+yasps_status barrier_energy(yasps_system* s, const double* P, double* E_host);
+yasps_status ccd_bound(yasps_system* s, const double* x, const double* p, double* alpha_host);
+
+// ---------------------------------------------------------------- solver.cu
+yasps_status alloc_hessian(yasps_system* s);
+yasps_status zero_system(yasps_system* s);
+yasps_status launch_bjacobi(yasps_system* s);
+yasps_status spmv64(yasps_system* s, const double* x, double* y);
+yasps_status pcg_solve(yasps_system* s, const double* rhs, double* p, double tol, int maxit, int* iters,
+                       double* rel_res);
+yasps_status inf_norm(yasps_system* s, const double* x, int n, double* out_host);
+yasps_status read_status(yasps_system* s, int* bits);  // synchronises, clears the device word
