@@ -1,0 +1,312 @@
+"""B300-native IPC Newton hot path (YASPS, arxiv 2605.23088) -- Python binding.
+
+A thin ctypes binding over the C ABI of ``libyasps.so`` (declared in
+``include/yasps.h``).  It only marshals arguments: every step of the path
+(element and barrier derivatives, projection, assembly, PCG, broadphase, CCD,
+line search) runs in the library's CUDA kernels.  PyTorch provides the device
+memory (the library's workspaces come from torch's caching allocator through
+the allocator callbacks) and the CUDA stream.  There is no CPU fallback: if
+the library or a CUDA device is missing, the calls raise.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libyasps.so")
+
+YASPS_OK = 0
+STATUS = {0: "OK", -1: "E_INVAL", -2: "E_NOMEM", -3: "E_CUDA", -4: "E_CAPACITY", -5: "E_NOCONV",
+          -6: "E_LINESEARCH", -7: "E_TIMEOUT", -8: "E_NAN"}
+TERM_INERTIA, TERM_TET, TERM_MEMBRANE, TERM_BEND, TERM_ABD, TERM_BARRIER, TERM_ALL = 1, 2, 4, 8, 16, 32, 63
+
+# every symbol include/yasps.h declares
+EXPORTS = [
+    "yasps_default_params", "yasps_build_system", "yasps_build_error", "yasps_destroy", "yasps_last_error",
+    "yasps_set_params", "yasps_get_sizes", "yasps_initial_state", "yasps_vertex_positions", "yasps_xtilde",
+    "yasps_detect_pairs", "yasps_export_pairs", "yasps_energy", "yasps_eval_local", "yasps_assemble",
+    "yasps_export_bsr", "yasps_export_gradient", "yasps_spmv", "yasps_pcg_solve", "yasps_ccd_bound", "yasps_step",
+    "yasps_set_fixed_positions", "yasps_get_fixed_positions", "yasps_kernel_launches",
+]
+
+
+class YaspsError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("dt", ctypes.c_double), ("dhat", ctypes.c_double),
+                ("kappa", ctypes.c_double), ("gravity", ctypes.c_double * 3), ("newton_tol", ctypes.c_double),
+                ("pcg_rel_tol", ctypes.c_double), ("pcg_max_iter", ctypes.c_int), ("newton_max_iter", ctypes.c_int),
+                ("ls_max_iter", ctypes.c_int), ("barrier_form", ctypes.c_int), ("ccd_gap", ctypes.c_double),
+                ("ccd_max_iter", ctypes.c_int), ("refine_sweeps", ctypes.c_int)]
+
+
+_PD = ctypes.POINTER(ctypes.c_double)
+_PI = ctypes.POINTER(ctypes.c_int)
+
+
+class SceneDesc(ctypes.Structure):
+    _fields_ = [("n_verts", ctypes.c_int), ("rest_pos", _PD), ("vert_body", _PI),
+                ("n_fixed", ctypes.c_int), ("fixed_verts", _PI), ("fixed_vel", _PD),
+                ("n_tets", ctypes.c_int), ("tet2v", _PI), ("tet_E", _PD), ("tet_nu", _PD), ("tet_rho", _PD),
+                ("n_tris", ctypes.c_int), ("tri2v", _PI), ("tri_E", _PD), ("tri_nu", _PD), ("tri_thick", _PD),
+                ("tri_rho", _PD),
+                ("n_hinges", ctypes.c_int), ("hinge2v", _PI), ("hinge_kb", _PD),
+                ("n_bodies", ctypes.c_int), ("body_mass", _PD), ("body_vol", _PD), ("body_kappa", _PD),
+                ("n_surf_tris", ctypes.c_int), ("surf_tri2v", _PI), ("n_surf_edges", ctypes.c_int),
+                ("surf_edge2v", _PI), ("n_surf_verts", ctypes.c_int), ("surf_verts", _PI),
+                ("n_planes", ctypes.c_int), ("planes", _PD)]
+
+
+class StepStats(ctypes.Structure):
+    _fields_ = [("newton_iters", ctypes.c_int), ("pcg_iters_total", ctypes.c_int), ("n_pt", ctypes.c_int),
+                ("n_ee", ctypes.c_int), ("n_pg", ctypes.c_int), ("status", ctypes.c_int),
+                ("alpha_last", ctypes.c_double), ("p_inf", ctypes.c_double), ("t_eval_ms", ctypes.c_double),
+                ("t_pcg_ms", ctypes.c_double), ("t_ccd_ms", ctypes.c_double), ("t_ls_ms", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class Allocator(ctypes.Structure):
+    _ALLOC = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+    _FREE = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p)
+    _fields_ = [("ctx", ctypes.c_void_p), ("alloc", _ALLOC), ("free", _FREE)]
+
+
+_lib = None
+
+
+def lib():
+    """Load libyasps.so (raises if it has not been built: there is no fallback)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing; build it with `python -m paper_2605_23088_b300.build`")
+        L = ctypes.CDLL(LIB_PATH)
+        L.yasps_build_error.restype = ctypes.c_char_p
+        L.yasps_last_error.restype = ctypes.c_char_p
+        L.yasps_kernel_launches.restype = ctypes.c_longlong
+        L.yasps_build_system.argtypes = [ctypes.POINTER(SceneDesc), ctypes.POINTER(Params),
+                                         ctypes.POINTER(Allocator), ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]
+        for name in EXPORTS:
+            getattr(L, name)
+        _lib = L
+    return _lib
+
+
+def default_params(**kw):
+    p = Params()
+    lib().yasps_default_params(ctypes.byref(p))
+    for k, v in kw.items():
+        if k == "gravity":
+            p.gravity[:] = list(v)
+        else:
+            setattr(p, k, v)
+    return p
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class System:
+    """A scene held on the GPU by the library (one ``yasps_system``).
+
+    ``scene`` is a dict from the ``scenes`` generators.  State tensors (x, v)
+    are torch FP64 CUDA tensors of shape (n_nodes, 3).
+    """
+
+    def __init__(self, scene, use_torch_allocator=True, stream=None, **params):
+        import torch
+
+        if not torch.cuda.is_available():
+            raise RuntimeError("paper_2605_23088_b300 needs a CUDA device (no CPU fallback)")
+        self.torch = torch
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        p = dict(dt=scene["dt"], dhat=scene["dhat"], kappa=scene["kappa"], gravity=list(scene["gravity"]),
+                 newton_tol=scene["newton_tol"])
+        p.update(params)
+        self.params = default_params(**p)
+        self._keep = []
+
+        def arr(a, dtype):
+            a = np.ascontiguousarray(np.asarray(a, dtype=dtype))
+            self._keep.append(a)
+            return a.ctypes.data_as(_PD if dtype == np.float64 else _PI)
+
+        s = scene
+        d = SceneDesc()
+        d.n_verts = len(s["rest_pos"]); d.rest_pos = arr(s["rest_pos"], np.float64); d.vert_body = arr(s["vert_body"], np.int32)
+        d.n_fixed = len(s["fixed"]); d.fixed_verts = arr(s["fixed"], np.int32); d.fixed_vel = arr(s["fixed_vel"], np.float64)
+        d.n_tets = len(s["tets"]); d.tet2v = arr(s["tets"], np.int32); d.tet_E = arr(s["tet_E"], np.float64)
+        d.tet_nu = arr(s["tet_nu"], np.float64); d.tet_rho = arr(s["tet_rho"], np.float64)
+        d.n_tris = len(s["tris"]); d.tri2v = arr(s["tris"], np.int32); d.tri_E = arr(s["tri_E"], np.float64)
+        d.tri_nu = arr(s["tri_nu"], np.float64); d.tri_thick = arr(s["tri_thick"], np.float64)
+        d.tri_rho = arr(s["tri_rho"], np.float64)
+        d.n_hinges = len(s["hinges"]); d.hinge2v = arr(s["hinges"], np.int32); d.hinge_kb = arr(s["hinge_kb"], np.float64)
+        d.n_bodies = len(s["body_mass"]); d.body_mass = arr(s["body_mass"], np.float64)
+        d.body_vol = arr(s["body_vol"], np.float64); d.body_kappa = arr(s["body_kappa"], np.float64)
+        d.n_surf_tris = len(s["surf_tris"]); d.surf_tri2v = arr(s["surf_tris"], np.int32)
+        d.n_surf_edges = len(s["surf_edges"]); d.surf_edge2v = arr(s["surf_edges"], np.int32)
+        d.n_surf_verts = len(s["surf_verts"]); d.surf_verts = arr(s["surf_verts"], np.int32)
+        d.n_planes = len(s["planes"]); d.planes = arr(s["planes"], np.float64)
+        self.scene = scene
+        self._alloc = None
+        if use_torch_allocator:
+            dev = self.device.index
+
+            def _a(ctx, nbytes, stream):
+                return torch.cuda.caching_allocator_alloc(int(nbytes), dev, int(stream or 0))
+
+            def _f(ctx, ptr, stream):
+                torch.cuda.caching_allocator_delete(int(ptr))
+
+            self._cb = (Allocator._ALLOC(_a), Allocator._FREE(_f))
+            self._alloc = Allocator(None, self._cb[0], self._cb[1])
+        h = ctypes.c_void_p()
+        rc = lib().yasps_build_system(ctypes.byref(d), ctypes.byref(self.params),
+                                      ctypes.byref(self._alloc) if self._alloc else None,
+                                      ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h))
+        if rc != YASPS_OK:
+            raise YaspsError(rc, lib().yasps_build_error().decode())
+        self.h = h
+        nn, nf, nv = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        lib().yasps_get_sizes(self.h, ctypes.byref(nn), ctypes.byref(nf), ctypes.byref(nv))
+        self.n_nodes, self.n_free, self.n_verts = nn.value, nf.value, nv.value
+
+    # ------------------------------------------------------------ plumbing
+    def _check(self, rc):
+        if rc != YASPS_OK:
+            raise YaspsError(rc, lib().yasps_last_error(self.h).decode())
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().yasps_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def zeros(self, *shape, dtype=None):
+        return self.torch.zeros(*shape, dtype=dtype or self.torch.float64, device=self.device)
+
+    # ------------------------------------------------------------ ABI calls
+    def set_params(self, **kw):
+        for k, v in kw.items():
+            if k == "gravity":
+                self.params.gravity[:] = list(v)
+            else:
+                setattr(self.params, k, v)
+        self._check(lib().yasps_set_params(self.h, ctypes.byref(self.params)))
+
+    def initial_state(self):
+        x = self.zeros(self.n_nodes, 3)
+        v = self.zeros(self.n_nodes, 3)
+        vel0 = np.ascontiguousarray(self.scene["vel0"], dtype=np.float64)
+        self._check(lib().yasps_initial_state(self.h, vel0.ctypes.data_as(_PD), _ptr(x), _ptr(v)))
+        return x, v
+
+    def vertex_positions(self, x):
+        P = self.zeros(self.n_verts, 3)
+        self._check(lib().yasps_vertex_positions(self.h, _ptr(x), _ptr(P)))
+        return P
+
+    def xtilde(self, x, v):
+        out = self.zeros(self.n_nodes, 3)
+        self._check(lib().yasps_xtilde(self.h, _ptr(x), _ptr(v), _ptr(out)))
+        return out
+
+    def detect_pairs(self, x):
+        a, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        self._check(lib().yasps_detect_pairs(self.h, _ptr(x), ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+        return a.value, b.value, c.value
+
+    def export_pairs(self, counts):
+        pt = np.zeros((counts[0], 3), np.int32)
+        ee = np.zeros((counts[1], 3), np.int32)
+        pg = np.zeros((counts[2], 3), np.int32)
+        self._check(lib().yasps_export_pairs(self.h, pt.ctypes.data_as(_PI), ee.ctypes.data_as(_PI),
+                                             pg.ctypes.data_as(_PI)))
+        return pt, ee, pg
+
+    def pairs(self, x):
+        return self.export_pairs(self.detect_pairs(x))
+
+    def energy(self, x, xtil, terms=False):
+        E = ctypes.c_double()
+        t = np.zeros(6)
+        self._check(lib().yasps_energy(self.h, _ptr(x), _ptr(xtil), ctypes.byref(E), t.ctypes.data_as(_PD)))
+        return (E.value, t) if terms else E.value
+
+    def eval_local(self, x, xtil, term_mask=TERM_ALL, project=True):
+        self._check(lib().yasps_eval_local(self.h, _ptr(x), _ptr(xtil), ctypes.c_int(term_mask),
+                                           ctypes.c_int(int(project))))
+
+    def assemble(self):
+        self._check(lib().yasps_assemble(self.h))
+
+    def export_bsr(self, which):
+        nnzb = ctypes.c_int()
+        self._check(lib().yasps_export_bsr(self.h, ctypes.c_int(which), ctypes.byref(nnzb), None, None, None, None))
+        n = nnzb.value
+        rowptr = np.zeros(self.n_nodes + 1, np.int32)
+        col = np.zeros(max(n, 1), np.int32)
+        vals = np.zeros((max(n, 1), 9))
+        diag = np.zeros((self.n_nodes, 9))
+        self._check(lib().yasps_export_bsr(self.h, ctypes.c_int(which), ctypes.byref(nnzb), rowptr.ctypes.data_as(_PI),
+                                           col.ctypes.data_as(_PI), vals.ctypes.data_as(_PD),
+                                           diag.ctypes.data_as(_PD) if which == 0 else None))
+        return rowptr, col[:n].copy(), vals[:n].reshape(n, 3, 3).copy(), diag.reshape(-1, 3, 3)
+
+    def export_gradient(self):
+        g = self.zeros(self.n_nodes, 3)
+        self._check(lib().yasps_export_gradient(self.h, _ptr(g)))
+        return g
+
+    def spmv(self, x):
+        y = self.zeros(self.n_nodes, 3)
+        self._check(lib().yasps_spmv(self.h, _ptr(x), _ptr(y)))
+        return y
+
+    def pcg_solve(self, rhs, rel_tol=1e-4):
+        p = self.zeros(self.n_nodes, 3)
+        it, rel = ctypes.c_int(), ctypes.c_double()
+        self._check(lib().yasps_pcg_solve(self.h, _ptr(rhs), _ptr(p), ctypes.c_double(rel_tol), ctypes.byref(it),
+                                          ctypes.byref(rel)))
+        return p, it.value, rel.value
+
+    def ccd_bound(self, x, p):
+        a = ctypes.c_double()
+        self._check(lib().yasps_ccd_bound(self.h, _ptr(x), _ptr(p), ctypes.byref(a)))
+        return a.value
+
+    def step(self, x, v, raise_on_error=True):
+        """One implicit time step, x and v updated in place; returns the stats dict."""
+        st = StepStats()
+        rc = lib().yasps_step(self.h, _ptr(x), _ptr(v), ctypes.byref(st))
+        if raise_on_error:
+            self._check(rc)
+        d = st.as_dict()
+        d["rc"] = rc
+        return d
+
+    def set_fixed_positions(self, P):
+        P = np.ascontiguousarray(P, dtype=np.float64)
+        self._check(lib().yasps_set_fixed_positions(self.h, P.ctypes.data_as(_PD)))
+
+    def get_fixed_positions(self):
+        P = np.zeros((self.n_verts, 3))
+        self._check(lib().yasps_get_fixed_positions(self.h, P.ctypes.data_as(_PD)))
+        return P
+
+    def kernel_launches(self):
+        return lib().yasps_kernel_launches(self.h)

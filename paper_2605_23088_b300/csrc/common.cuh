@@ -44,6 +44,9 @@ YASPS_HD v3<T> cross(v3<T> a, v3<T> b) {
   return {a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
 }
 
+template <typename T>
+YASPS_HD T comp3(v3<T> a, int i) { return i == 0 ? a.x : (i == 1 ? a.y : a.z); }
+
 YASPS_D v3<double> ld3(const double* p, int i) { return {p[3 * i], p[3 * i + 1], p[3 * i + 2]}; }
 YASPS_D void st3(double* p, int i, v3<double> a) {
   p[3 * i] = a.x;

@@ -1,0 +1,990 @@
+// contact.cu -- the dynamic (collision) part of the IPC Newton step.
+//
+//  * broadphase: a uniform grid over the boxes of one primitive set (counting
+//    sort into cells), queried by the boxes of the other; each overlapping box
+//    pair is reported once, in the cell holding the minimum corner of the
+//    boxes' intersection;
+//  * narrow phase: exact FP64 squared distances with closest-feature
+//    classification (distance.cuh); a pair is active when s < dhat^2.  Pair
+//    lists are canonical: sorted by (a, b) (Sec. "UNION": collision pairs are a
+//    dynamic primitive whose connectivity is rebuilt at run time);
+//  * the dynamic BSR layout of H_dynamic (Sec. "Index Computation"): the upper
+//    block keys of every pair's node set, sorted and made unique (App. B);
+//  * barrier evaluation: b(s), its position-space gradient and Hessian,
+//    projected in position space (the reduced-coordinate projection of Sec.
+//    "EVD and PSD Projection", valid because free and affine parameterisations
+//    are linear), then mapped to nodes through the UNION Jacobian of each
+//    vertex (I3 for a free vertex, [I3, r1 I3, r2 I3, r3 I3] for an affine one,
+//    Sec. "Differentiation of Unioned Attributes") with duplicate nodes merged
+//    (Sec. "Hessian Code Generation", local compression);
+//  * the CCD step bound: additive CCD (Li, Kaufman and Jiang 2021, ACCD) on
+//    swept-box candidates, exact for point-plane pairs.
+#include <algorithm>
+#include <cmath>
+
+#include "common.cuh"
+#include "distance.cuh"
+#include "eig.cuh"
+#include "internal.h"
+
+using dist::d3;
+
+namespace {
+
+// ---------------------------------------------------------------- boxes and grid
+struct gridp {
+  double lo[3];
+  double cell, inv;
+  int dim[3];
+};
+
+__device__ __forceinline__ int cell_coord(double v, double lo, double inv, int dim) {
+  double f = floor((v - lo) * inv);
+  int c = (f < 0.0) ? 0 : (f > (double)(dim - 1) ? dim - 1 : (int)f);
+  return c;
+}
+
+// boxes of k-vertex primitives at positions P0 (and P1 when swept), grown by infl
+__global__ void k_boxes(int n, int k, const int* __restrict__ idx, const double* __restrict__ P0,
+                        const double* __restrict__ P1, double infl, double* __restrict__ lo, double* __restrict__ hi) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n) return;
+  double l[3], h[3];
+  const int v0 = idx[k * e];
+  for (int c = 0; c < 3; ++c) l[c] = h[c] = P0[3 * v0 + c];
+  for (int a = 1; a < k; ++a) {
+    const int v = idx[k * e + a];
+    for (int c = 0; c < 3; ++c) { l[c] = fmin(l[c], P0[3 * v + c]); h[c] = fmax(h[c], P0[3 * v + c]); }
+  }
+  if (P1) {
+    double l1[3], h1[3];
+    for (int c = 0; c < 3; ++c) l1[c] = h1[c] = P1[3 * v0 + c];
+    for (int a = 1; a < k; ++a) {
+      const int v = idx[k * e + a];
+      for (int c = 0; c < 3; ++c) { l1[c] = fmin(l1[c], P1[3 * v + c]); h1[c] = fmax(h1[c], P1[3 * v + c]); }
+    }
+    for (int c = 0; c < 3; ++c) { l[c] = fmin(l[c], l1[c]); h[c] = fmax(h[c], h1[c]); }
+  }
+  for (int c = 0; c < 3; ++c) {
+    lo[3 * e + c] = l[c] - infl;
+    hi[3 * e + c] = h[c] + infl;
+  }
+}
+
+// min of lo, max of hi, max extent over n boxes -> out[7] (per-block partials first)
+__global__ void k_box_reduce(int n, const double* __restrict__ lo, const double* __restrict__ hi, double* __restrict__ part) {
+  double r[7] = {1e300, 1e300, 1e300, -1e300, -1e300, -1e300, 0.0};
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x)
+    for (int c = 0; c < 3; ++c) {
+      r[c] = fmin(r[c], lo[3 * e + c]);
+      r[3 + c] = fmax(r[3 + c], hi[3 * e + c]);
+      r[6] = fmax(r[6], hi[3 * e + c] - lo[3 * e + c]);
+    }
+  __shared__ double sh[7][32];
+  for (int q = 0; q < 7; ++q) {
+    double v = r[q];
+    for (int o = 16; o > 0; o >>= 1) {
+      double w = __shfl_xor_sync(0xffffffffu, v, o);
+      v = (q < 3) ? fmin(v, w) : fmax(v, w);
+    }
+    if ((threadIdx.x & 31) == 0) sh[q][threadIdx.x >> 5] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < 7) {
+    const int q = threadIdx.x;
+    double v = sh[q][0];
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) v = (q < 3) ? fmin(v, sh[q][w]) : fmax(v, sh[q][w]);
+    part[7 * blockIdx.x + q] = v;
+  }
+}
+
+__device__ __forceinline__ void cell_range(const gridp& G, const double* lo, const double* hi, int* c0, int* c1) {
+  for (int c = 0; c < 3; ++c) {
+    c0[c] = cell_coord(lo[c], G.lo[c], G.inv, G.dim[c]);
+    c1[c] = cell_coord(hi[c], G.lo[c], G.inv, G.dim[c]);
+  }
+}
+
+__global__ void k_grid_count(int n, const double* __restrict__ lo, const double* __restrict__ hi, gridp G,
+                             int* __restrict__ cnt) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n) return;
+  int c0[3], c1[3];
+  cell_range(G, lo + 3 * e, hi + 3 * e, c0, c1);
+  for (int z = c0[2]; z <= c1[2]; ++z)
+    for (int y = c0[1]; y <= c1[1]; ++y)
+      for (int x = c0[0]; x <= c1[0]; ++x) atomicAdd(&cnt[((long long)z * G.dim[1] + y) * G.dim[0] + x], 1);
+}
+__global__ void k_grid_fill(int n, const double* __restrict__ lo, const double* __restrict__ hi, gridp G,
+                            const int* __restrict__ start, int* __restrict__ fill, int* __restrict__ items) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n) return;
+  int c0[3], c1[3];
+  cell_range(G, lo + 3 * e, hi + 3 * e, c0, c1);
+  for (int z = c0[2]; z <= c1[2]; ++z)
+    for (int y = c0[1]; y <= c1[1]; ++y)
+      for (int x = c0[0]; x <= c1[0]; ++x) {
+        const long long id = ((long long)z * G.dim[1] + y) * G.dim[0] + x;
+        items[start[id] + atomicAdd(&fill[id], 1)] = e;
+      }
+}
+
+struct grid_dev {
+  gridp G;
+  const int* start;
+  const int* items;
+  const double *blo, *bhi;
+};
+
+// Visit every B box overlapping A box (alo, ahi) once (min-corner rule).
+template <class F>
+__device__ __forceinline__ void grid_visit(const grid_dev& g, const double* alo, const double* ahi, F&& f) {
+  int c0[3], c1[3];
+  cell_range(g.G, alo, ahi, c0, c1);
+  for (int z = c0[2]; z <= c1[2]; ++z)
+    for (int y = c0[1]; y <= c1[1]; ++y)
+      for (int x = c0[0]; x <= c1[0]; ++x) {
+        const long long id = ((long long)z * g.G.dim[1] + y) * g.G.dim[0] + x;
+        for (int q = g.start[id]; q < g.start[id + 1]; ++q) {
+          const int j = g.items[q];
+          const double* bl = g.blo + 3 * j;
+          const double* bh = g.bhi + 3 * j;
+          bool ov = true;
+          for (int c = 0; c < 3; ++c)
+            if (ahi[c] < bl[c] || bh[c] < alo[c]) ov = false;
+          if (!ov) continue;
+          // report only in the cell of the intersection's minimum corner
+          const int mx = cell_coord(fmax(alo[0], bl[0]), g.G.lo[0], g.G.inv, g.G.dim[0]);
+          const int my = cell_coord(fmax(alo[1], bl[1]), g.G.lo[1], g.G.inv, g.G.dim[1]);
+          const int mz = cell_coord(fmax(alo[2], bl[2]), g.G.lo[2], g.G.inv, g.G.dim[2]);
+          if (mx != x || my != y || mz != z) continue;
+          f(j);
+        }
+      }
+}
+
+// ---------------------------------------------------------------- exclusions
+struct topo {
+  const int *vnode, *vbody, *stri, *sedge, *svert;
+};
+__device__ __forceinline__ bool pt_excluded(const topo& T, int v, int t0, int t1, int t2) {
+  if (v == t0 || v == t1 || v == t2) return true;
+  const int bv = T.vbody[v];
+  if (bv >= 0 && bv == T.vbody[t0]) return true;
+  if (T.vnode[v] < 0 && T.vnode[t0] < 0 && T.vnode[t1] < 0 && T.vnode[t2] < 0) return true;
+  return false;
+}
+__device__ __forceinline__ bool ee_excluded(const topo& T, int e0, int e1, int f0, int f1) {
+  if (e0 == f0 || e0 == f1 || e1 == f0 || e1 == f1) return true;
+  const int be = T.vbody[e0];
+  if (be >= 0 && be == T.vbody[f0]) return true;
+  if (T.vnode[e0] < 0 && T.vnode[e1] < 0 && T.vnode[f0] < 0 && T.vnode[f1] < 0) return true;
+  return false;
+}
+
+// ---------------------------------------------------------------- barrier scalar
+struct bder {
+  double b, db, d2b;
+};
+__device__ __forceinline__ bder barrier_fn(double s, double sh, int form) {
+  if (!(s < sh)) return {0.0, 0.0, 0.0};
+  const double d = s - sh, L = log(s / sh);
+  if (form == 1)
+    return {d * d * L * L, 2.0 * d * L * L + 2.0 * d * d * L / s,
+            2.0 * L * L + 8.0 * d * L / s + 2.0 * d * d / (s * s) - 2.0 * d * d * L / (s * s)};
+  return {-d * d * L, -2.0 * d * L - d * d / s, -2.0 * L - 4.0 * d / s + d * d / (s * s)};
+}
+
+// ---------------------------------------------------------------- detection
+// mode 0: count, mode 1: write + sort segment, mode 2: accumulate kappa * b(s)
+__global__ void k_pt_query(int nsv, topo T, const double* __restrict__ P, grid_dev g, const double* __restrict__ alo,
+                           const double* __restrict__ ahi, double sh, int mode, int* __restrict__ cnt,
+                           const int* __restrict__ off, int* __restrict__ out, double kappa, int form,
+                           ksum* __restrict__ part) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  ksum acc{0.0, 0.0};
+  if (i < nsv) {
+    const int v = T.svert[i];
+    const d3 p = ld3(P, v);
+    int c = 0;
+    const int base = (mode == 1) ? off[i] : 0;
+    grid_visit(g, alo + 3 * i, ahi + 3 * i, [&](int t) {
+      const int t0 = T.stri[3 * t], t1 = T.stri[3 * t + 1], t2 = T.stri[3 * t + 2];
+      if (pt_excluded(T, v, t0, t1, t2)) return;
+      double s;
+      const int st = dist::pt_classify(p, ld3(P, t0), ld3(P, t1), ld3(P, t2), &s);
+      if (!(s < sh)) return;
+      if (mode == 1) {
+        int* o = out + 3 * (size_t)(base + c);
+        o[0] = v; o[1] = t; o[2] = st;
+      } else if (mode == 2) {
+        kadd(acc, kappa * barrier_fn(s, sh, form).b);
+      }
+      ++c;
+    });
+    if (mode == 0) cnt[i] = c;
+    if (mode == 1) {  // insertion sort of this vertex's partners by triangle id
+      int* o = out + 3 * (size_t)base;
+      for (int a = 1; a < c; ++a) {
+        const int kb = o[3 * a + 1], ks = o[3 * a + 2];
+        int q = a - 1;
+        while (q >= 0 && o[3 * q + 1] > kb) {
+          o[3 * (q + 1) + 1] = o[3 * q + 1];
+          o[3 * (q + 1) + 2] = o[3 * q + 2];
+          --q;
+        }
+        o[3 * (q + 1) + 1] = kb;
+        o[3 * (q + 1) + 2] = ks;
+      }
+    }
+  }
+  if (mode == 2) {
+    acc = block_ksum(acc);
+    if (threadIdx.x == 0) part[blockIdx.x] = acc;
+  }
+}
+
+__global__ void k_ee_query(int nse, topo T, const double* __restrict__ P, grid_dev g, const double* __restrict__ alo,
+                           const double* __restrict__ ahi, double sh, int mode, int* __restrict__ cnt,
+                           const int* __restrict__ off, int* __restrict__ out, double kappa, int form,
+                           ksum* __restrict__ part) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  ksum acc{0.0, 0.0};
+  if (i < nse) {
+    const int e0 = T.sedge[2 * i], e1 = T.sedge[2 * i + 1];
+    const d3 a0 = ld3(P, e0), a1 = ld3(P, e1);
+    int c = 0;
+    const int base = (mode == 1) ? off[i] : 0;
+    grid_visit(g, alo + 3 * i, ahi + 3 * i, [&](int j) {
+      if (j <= i) return;
+      const int f0 = T.sedge[2 * j], f1 = T.sedge[2 * j + 1];
+      if (ee_excluded(T, e0, e1, f0, f1)) return;
+      double s;
+      const int st = dist::ee_classify(a0, a1, ld3(P, f0), ld3(P, f1), &s);
+      if (!(s < sh)) return;
+      if (mode == 1) {
+        int* o = out + 3 * (size_t)(base + c);
+        o[0] = i; o[1] = j; o[2] = st;
+      } else if (mode == 2) {
+        kadd(acc, kappa * barrier_fn(s, sh, form).b);
+      }
+      ++c;
+    });
+    if (mode == 0) cnt[i] = c;
+    if (mode == 1) {
+      int* o = out + 3 * (size_t)base;
+      for (int a = 1; a < c; ++a) {
+        const int kb = o[3 * a + 1], ks = o[3 * a + 2];
+        int q = a - 1;
+        while (q >= 0 && o[3 * q + 1] > kb) {
+          o[3 * (q + 1) + 1] = o[3 * q + 1];
+          o[3 * (q + 1) + 2] = o[3 * q + 2];
+          --q;
+        }
+        o[3 * (q + 1) + 1] = kb;
+        o[3 * (q + 1) + 2] = ks;
+      }
+    }
+  }
+  if (mode == 2) {
+    acc = block_ksum(acc);
+    if (threadIdx.x == 0) part[blockIdx.x] = acc;
+  }
+}
+
+// point-plane pairs: d = n.p - c, active when d > 0 and d^2 < dhat^2
+__global__ void k_pg_query(int nsv, int npl, topo T, const double* __restrict__ P, const double* __restrict__ planes,
+                           double sh, int mode, int* __restrict__ cnt, const int* __restrict__ off,
+                           int* __restrict__ out, double kappa, int form, ksum* __restrict__ part) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  ksum acc{0.0, 0.0};
+  if (i < nsv) {
+    const int v = T.svert[i];
+    int c = 0;
+    if (T.vnode[v] >= 0) {
+      const d3 p = ld3(P, v);
+      for (int k = 0; k < npl; ++k) {
+        const double* pl = planes + 4 * k;
+        const double d = dist::sub(dist::vdot(d3{pl[0], pl[1], pl[2]}, p), pl[3]);
+        const double s = dist::mul(d, d);
+        if (!(d > 0.0 && s < sh)) continue;
+        if (mode == 1) {
+          int* o = out + 3 * (size_t)(off[i] + c);
+          o[0] = v; o[1] = k; o[2] = 0;
+        } else if (mode == 2) {
+          kadd(acc, kappa * barrier_fn(s, sh, form).b);
+        }
+        ++c;
+      }
+    }
+    if (mode == 0) cnt[i] = c;
+  }
+  if (mode == 2) {
+    acc = block_ksum(acc);
+    if (threadIdx.x == 0) part[blockIdx.x] = acc;
+  }
+}
+
+// ---------------------------------------------------------------- pair node sets
+// Nodes and weights of a vertex through its UNION branch (App. A index rules):
+// free -> 1 node (w = 1); affine -> 4 nodes (t, A1, A2, A3; w = 1, r1, r2, r3);
+// fixed -> none.
+struct vmapd {
+  int n;
+  int node[4];
+  double w[4];
+};
+__device__ __forceinline__ vmapd vertex_map(int v, const int* vnode, const int* vbody, const double* vr) {
+  vmapd m;
+  const int n = vnode[v];
+  if (n < 0) { m.n = 0; return m; }
+  if (vbody[v] < 0) { m.n = 1; m.node[0] = n; m.w[0] = 1.0; return m; }
+  m.n = 4;
+  for (int k = 0; k < 4; ++k) m.node[k] = n + k;
+  m.w[0] = 1.0; m.w[1] = vr[3 * v]; m.w[2] = vr[3 * v + 1]; m.w[3] = vr[3 * v + 2];
+  return m;
+}
+
+// sorted unique node list of up to 4 vertices (<= 16 before merging)
+struct nodeset {
+  int m;
+  int node[16];
+};
+__device__ __forceinline__ nodeset pair_nodes(const int* ids, int k, const int* vnode, const int* vbody,
+                                              const double* vr) {
+  nodeset S;
+  S.m = 0;
+  for (int a = 0; a < k; ++a) {
+    const vmapd vm = vertex_map(ids[a], vnode, vbody, vr);
+    for (int q = 0; q < vm.n; ++q) {
+      const int nd = vm.node[q];
+      int pos = 0;
+      bool dup = false;
+      for (; pos < S.m; ++pos) {
+        if (S.node[pos] == nd) { dup = true; break; }
+        if (S.node[pos] > nd) break;
+      }
+      if (dup) continue;
+      for (int r = S.m; r > pos; --r) S.node[r] = S.node[r - 1];
+      S.node[pos] = nd;
+      ++S.m;
+    }
+  }
+  return S;
+}
+// index of key (u < w) in the lexicographic enumeration of pairs of m items
+__device__ __forceinline__ int pair_rank(int u, int w, int m) { return u * (2 * m - u - 1) / 2 + (w - u - 1); }
+
+__device__ __forceinline__ void pair_vertices(int kind, int pidx, const int* pairs, const topo& T, int* ids, int* k) {
+  const int* pr = pairs + 3 * (size_t)pidx;
+  if (kind == 0) {
+    ids[0] = pr[0];
+    ids[1] = T.stri[3 * pr[1]]; ids[2] = T.stri[3 * pr[1] + 1]; ids[3] = T.stri[3 * pr[1] + 2];
+    *k = 4;
+  } else if (kind == 1) {
+    ids[0] = T.sedge[2 * pr[0]]; ids[1] = T.sedge[2 * pr[0] + 1];
+    ids[2] = T.sedge[2 * pr[1]]; ids[3] = T.sedge[2 * pr[1] + 1];
+    *k = 4;
+  } else {
+    ids[0] = pr[0];
+    *k = 1;
+  }
+}
+
+// number of upper off-diagonal keys per pair; pairs are PT, then EE, then PG
+__global__ void k_pair_nkeys(int npt, int nee, int npg, const int* __restrict__ pt, const int* __restrict__ ee,
+                             const int* __restrict__ pg, topo T, const double* __restrict__ vr, int* __restrict__ nk) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= npt + nee + npg) return;
+  const int kind = p < npt ? 0 : (p < npt + nee ? 1 : 2);
+  const int li = p - (kind == 0 ? 0 : (kind == 1 ? npt : npt + nee));
+  int ids[4], k;
+  pair_vertices(kind, li, kind == 0 ? pt : (kind == 1 ? ee : pg), T, ids, &k);
+  const nodeset S = pair_nodes(ids, k, T.vnode, T.vbody, vr);
+  nk[p] = S.m * (S.m - 1) / 2;
+}
+__global__ void k_pair_keys(int npt, int nee, int npg, const int* __restrict__ pt, const int* __restrict__ ee,
+                            const int* __restrict__ pg, topo T, const double* __restrict__ vr,
+                            const int* __restrict__ koff, int nbits, uint64_t* __restrict__ keys, int* __restrict__ vals) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= npt + nee + npg) return;
+  const int kind = p < npt ? 0 : (p < npt + nee ? 1 : 2);
+  const int li = p - (kind == 0 ? 0 : (kind == 1 ? npt : npt + nee));
+  int ids[4], k;
+  pair_vertices(kind, li, kind == 0 ? pt : (kind == 1 ? ee : pg), T, ids, &k);
+  const nodeset S = pair_nodes(ids, k, T.vnode, T.vbody, vr);
+  int o = koff[p];
+  for (int u = 0; u < S.m; ++u)
+    for (int w = u + 1; w < S.m; ++w) {
+      keys[o] = ((uint64_t)S.node[u] << nbits) | (uint64_t)S.node[w];
+      vals[o] = o;
+      ++o;
+    }
+}
+
+// ---------------------------------------------------------------- barrier evaluation
+template <int N, typename T>
+__device__ __forceinline__ void project_n(T* H) {
+  project_psd<N, T>(H);
+}
+
+// kind 0 = PT, 1 = EE; one thread per pair
+template <typename T>
+__global__ void __launch_bounds__(128) k_barrier(int kind, int npairs, int pair_base, const int* __restrict__ pairs,
+                                                 topo Tp, const double* __restrict__ vr, const double* __restrict__ P,
+                                                 double sh, double kappa, int form, int project,
+                                                 const int* __restrict__ koff, const int* __restrict__ dslot,
+                                                 double* __restrict__ g, T* __restrict__ diag, T* __restrict__ vals,
+                                                 int* status) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= npairs) return;
+  int ids[4], k;
+  pair_vertices(kind, p, pairs, Tp, ids, &k);
+  d3 y[4];
+  for (int a = 0; a < 4; ++a) y[a] = ld3(P, ids[a]);
+  double s;
+  dist::dclass dc;
+  if (kind == 0) dc = dist::pt_dclass(dist::pt_classify(y[0], y[1], y[2], y[3], &s));
+  else dc = dist::ee_dclass(dist::ee_classify(y[0], y[1], y[2], y[3], &s));
+  if (!(s < sh) || !(s > 0.0)) return;
+  const bder bd = barrier_fn(s, sh, form);
+  d3 yl[4];
+  for (int q = 0; q < dc.n; ++q) yl[q] = y[dc.loc[q]];
+  double gs[12], Hs[144];
+  switch (dc.dtype) {
+    case dist::PP: dist::ds_pp(yl, gs, Hs); break;
+    case dist::PE: dist::ds_pe(yl, gs, Hs); break;
+    case dist::PT: dist::ds_pt(yl, gs, Hs); break;
+    default: dist::ds_ee(yl, gs, Hs); break;
+  }
+  const int n3 = 3 * dc.n;
+  T H[144];
+  for (int r = 0; r < n3; ++r)
+    for (int c = 0; c < n3; ++c) H[r * n3 + c] = (T)(kappa * (bd.d2b * gs[r] * gs[c] + bd.db * Hs[r * n3 + c]));
+  if (project) {
+    if (dc.n == 2) project_n<6, T>(H);
+    else if (dc.n == 3) project_n<9, T>(H);
+    else project_n<12, T>(H);
+  }
+  // UNION Jacobians of the classified vertices, merged over the pair's node set
+  const nodeset S = pair_nodes(ids, k, Tp.vnode, Tp.vbody, vr);
+  double W[4][16];
+  for (int q = 0; q < dc.n; ++q) {
+    for (int u = 0; u < S.m; ++u) W[q][u] = 0.0;
+    const vmapd vm = vertex_map(ids[dc.loc[q]], Tp.vnode, Tp.vbody, vr);
+    for (int a = 0; a < vm.n; ++a) {
+      int u = 0;
+      while (S.node[u] != vm.node[a]) ++u;
+      W[q][u] += vm.w[a];
+    }
+  }
+  for (int u = 0; u < S.m; ++u) {
+    double gu[3] = {0, 0, 0};
+    bool any = false;
+    for (int q = 0; q < dc.n; ++q)
+      if (W[q][u] != 0.0) {
+        any = true;
+        for (int i = 0; i < 3; ++i) gu[i] += W[q][u] * kappa * bd.db * gs[3 * q + i];
+      }
+    if (any)
+      for (int i = 0; i < 3; ++i) atomicAdd(&g[3 * S.node[u] + i], gu[i]);
+  }
+  const int kbase = koff[pair_base + p];
+  for (int u = 0; u < S.m; ++u)
+    for (int w = u; w < S.m; ++w) {
+      T B[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+      bool any = false;
+      for (int q = 0; q < dc.n; ++q) {
+        if (W[q][u] == 0.0) continue;
+        for (int r = 0; r < dc.n; ++r) {
+          const double f = W[q][u] * W[r][w];
+          if (f == 0.0) continue;
+          any = true;
+          for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) B[3 * i + j] += (T)f * H[(3 * q + i) * n3 + 3 * r + j];
+        }
+      }
+      if (!any) continue;
+      T* d;
+      if (u == w) d = diag + 9 * (size_t)S.node[u];
+      else {
+        const int sl = dslot[kbase + pair_rank(u, w, S.m)];
+        if (sl < 0) { dev_flag(status, DEV_BADINDEX); continue; }
+        d = vals + 9 * (size_t)sl;
+      }
+      for (int t = 0; t < 9; ++t) atomicAdd(d + t, B[t]);
+    }
+}
+
+// point-plane pairs: s = d^2, grad s = 2 d n, hess s = 2 n n^T; the position-
+// space Hessian kappa (4 d^2 b'' + 2 b') n n^T is rank one: its projection
+// keeps it when the eigenvalue kappa (4 d^2 b'' + 2 b') |n|^2 is positive.
+template <typename T>
+__global__ void k_barrier_pg(int npg, int pair_base, const int* __restrict__ pg, topo Tp, const double* __restrict__ vr,
+                             const double* __restrict__ P, const double* __restrict__ planes, double sh, double kappa,
+                             int form, int project, const int* __restrict__ koff, const int* __restrict__ dslot,
+                             double* __restrict__ g, T* __restrict__ diag, T* __restrict__ vals, int* status) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= npg) return;
+  const int v = pg[3 * p], k = pg[3 * p + 1];
+  const double* pl = planes + 4 * k;
+  const d3 x = ld3(P, v);
+  const double d = dist::sub(dist::vdot(d3{pl[0], pl[1], pl[2]}, x), pl[3]);
+  const double s = dist::mul(d, d);
+  if (!(s < sh) || !(d > 0.0)) return;
+  const bder bd = barrier_fn(s, sh, form);
+  const double nv[3] = {pl[0], pl[1], pl[2]};
+  const double lam = kappa * (4.0 * d * d * bd.d2b + 2.0 * bd.db);
+  const double hc = (project && lam < 0.0) ? 0.0 : lam;
+  const vmapd vm = vertex_map(v, Tp.vnode, Tp.vbody, vr);
+  for (int a = 0; a < vm.n; ++a)
+    for (int i = 0; i < 3; ++i) atomicAdd(&g[3 * vm.node[a] + i], vm.w[a] * kappa * bd.db * 2.0 * d * nv[i]);
+  const int kbase = koff[pair_base + p];
+  for (int a = 0; a < vm.n; ++a)
+    for (int b = a; b < vm.n; ++b) {
+      const double f = vm.w[a] * vm.w[b] * hc;
+      if (f == 0.0) continue;
+      T* dst;
+      if (a == b) dst = diag + 9 * (size_t)vm.node[a];
+      else {
+        const int sl = dslot[kbase + pair_rank(a, b, vm.n)];
+        if (sl < 0) { dev_flag(status, DEV_BADINDEX); continue; }
+        dst = vals + 9 * (size_t)sl;
+      }
+      for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) atomicAdd(dst + 3 * i + j, (T)(f * nv[i] * nv[j]));
+    }
+}
+
+// ---------------------------------------------------------------- CCD
+__device__ double pair_dist2(int kind, const d3* x) {
+  double s;
+  if (kind == 0) dist::pt_classify(x[0], x[1], x[2], x[3], &s);
+  else dist::ee_classify(x[0], x[1], x[2], x[3], &s);
+  return s;
+}
+// additive CCD along x + t dx, t in [0, tmax]: advance by (1 - gap) d / l_p,
+// where l_p bounds the relative motion; stop before the distance falls below
+// gap * (starting distance).  Explicitly rounded like the reference arithmetic.
+__device__ double accd(int kind, d3* x, d3* dx, double gap, double tmax, int max_iter, bool* capped) {
+  using namespace dist;
+  double m[3] = {0.0, 0.0, 0.0};
+  for (int i = 0; i < 4; ++i) {
+    m[0] = add(m[0], mul(0.25, dx[i].x));
+    m[1] = add(m[1], mul(0.25, dx[i].y));
+    m[2] = add(m[2], mul(0.25, dx[i].z));
+  }
+  double nrm[4];
+  for (int i = 0; i < 4; ++i) {
+    dx[i] = d3{sub(dx[i].x, m[0]), sub(dx[i].y, m[1]), sub(dx[i].z, m[2])};
+    nrm[i] = sqrt(vdot(dx[i], dx[i]));
+  }
+  const double lp = (kind == 0) ? add(nrm[0], fmax(nrm[1], fmax(nrm[2], nrm[3])))
+                                : add(fmax(nrm[0], nrm[1]), fmax(nrm[2], nrm[3]));
+  if (lp == 0.0) return tmax;
+  double d = sqrt(pair_dist2(kind, x));
+  const double g = mul(gap, d);
+  double t = 0.0, tl = dv(mul(sub(1.0, gap), d), lp);
+  for (int it = 0; it < max_iter; ++it) {
+    for (int i = 0; i < 4; ++i)
+      x[i] = d3{add(x[i].x, mul(tl, dx[i].x)), add(x[i].y, mul(tl, dx[i].y)), add(x[i].z, mul(tl, dx[i].z))};
+    d = sqrt(pair_dist2(kind, x));
+    if (t > 0.0 && d < g) return t;
+    t = add(t, tl);
+    if (t > tmax) return tmax;
+    tl = dv(mul(sub(1.0, gap), d), lp);
+  }
+  *capped = true;
+  return t;
+}
+
+__device__ __forceinline__ void atomic_min_pos(double* addr, double v) {
+  // non-negative doubles order like their bit patterns
+  atomicMin(reinterpret_cast<unsigned long long*>(addr), (unsigned long long)__double_as_longlong(v));
+}
+
+__global__ void k_ccd_pt(int nsv, topo T, const double* __restrict__ P0, const double* __restrict__ D, grid_dev g,
+                         const double* __restrict__ alo, const double* __restrict__ ahi, double gap, int max_iter,
+                         double* __restrict__ tmin, int* status) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nsv) return;
+  const int v = T.svert[i];
+  double best = 1.0;
+  bool capped = false;
+  grid_visit(g, alo + 3 * i, ahi + 3 * i, [&](int t) {
+    const int t0 = T.stri[3 * t], t1 = T.stri[3 * t + 1], t2 = T.stri[3 * t + 2];
+    if (pt_excluded(T, v, t0, t1, t2)) return;
+    d3 x[4] = {ld3(P0, v), ld3(P0, t0), ld3(P0, t1), ld3(P0, t2)};
+    d3 dx[4] = {ld3(D, v), ld3(D, t0), ld3(D, t1), ld3(D, t2)};
+    const double tk = accd(0, x, dx, gap, 1.0, max_iter, &capped);
+    best = fmin(best, tk);
+  });
+  if (capped) dev_flag(status, DEV_ITERCAP);
+  if (best < 1.0) atomic_min_pos(tmin, best);
+}
+__global__ void k_ccd_ee(int nse, topo T, const double* __restrict__ P0, const double* __restrict__ D, grid_dev g,
+                         const double* __restrict__ alo, const double* __restrict__ ahi, double gap, int max_iter,
+                         double* __restrict__ tmin, int* status) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nse) return;
+  const int e0 = T.sedge[2 * i], e1 = T.sedge[2 * i + 1];
+  double best = 1.0;
+  bool capped = false;
+  grid_visit(g, alo + 3 * i, ahi + 3 * i, [&](int j) {
+    if (j <= i) return;
+    const int f0 = T.sedge[2 * j], f1 = T.sedge[2 * j + 1];
+    if (ee_excluded(T, e0, e1, f0, f1)) return;
+    d3 x[4] = {ld3(P0, e0), ld3(P0, e1), ld3(P0, f0), ld3(P0, f1)};
+    d3 dx[4] = {ld3(D, e0), ld3(D, e1), ld3(D, f0), ld3(D, f1)};
+    const double tk = accd(1, x, dx, gap, 1.0, max_iter, &capped);
+    best = fmin(best, tk);
+  });
+  if (capped) dev_flag(status, DEV_ITERCAP);
+  if (best < 1.0) atomic_min_pos(tmin, best);
+}
+__global__ void k_ccd_pg(int nsv, int npl, topo T, const double* __restrict__ P0, const double* __restrict__ D,
+                         const double* __restrict__ planes, double gap, double* __restrict__ tmin) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nsv) return;
+  const int v = T.svert[i];
+  if (T.vnode[v] < 0) return;
+  using namespace dist;
+  double best = 1.0;
+  const d3 p = ld3(P0, v), dp = ld3(D, v);
+  for (int k = 0; k < npl; ++k) {
+    const d3 n = d3{planes[4 * k], planes[4 * k + 1], planes[4 * k + 2]};
+    const double d0 = sub(vdot(n, p), planes[4 * k + 3]);
+    const double vel = vdot(n, dp);
+    if (vel >= 0.0) continue;
+    const double t = dv(mul(sub(1.0, gap), d0), -vel);
+    best = fmin(best, t);
+  }
+  if (best < 1.0) atomic_min_pos(tmin, best);
+}
+
+__global__ void k_sub(int n, const double* __restrict__ a, const double* __restrict__ b, double* __restrict__ out) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = a[i] - b[i];
+}
+
+__global__ void k_reduce_ksum(const ksum* __restrict__ part, int n, double* __restrict__ out) {
+  ksum k{0.0, 0.0};
+  for (int i = threadIdx.x; i < n; i += blockDim.x) kmerge(k, part[i]);
+  k = block_ksum(k);
+  if (threadIdx.x == 0) *out = k.s + k.c;
+}
+
+// ======================================================================== host
+topo make_topo(yasps_system* s) {
+  return topo{as<int>(s->vnode), as<int>(s->vbody), as<int>(s->stri), as<int>(s->sedge), as<int>(s->svert)};
+}
+
+// Build a grid on boxes (blo, bhi) of n primitives.  Buffers: ws[3] start,
+// ws[4] fill, ws[5] items, red for the box reduction.
+yasps_status build_grid(yasps_system* s, int n, const double* blo, const double* bhi, grid_dev* out) {
+  const int nblk = std::min(148 * 2, std::max(1, (n + 255) / 256));
+  ENSURE(s, s->red, sizeof(double) * 7 * nblk + 64);
+  double* part = as<double>(s->red);
+  k_box_reduce<<<nblk, 256, 0, s->stream>>>(n, blo, bhi, part);
+  LAUNCH_CHECK(s, "k_box_reduce");
+  std::vector<double> hp(7 * (size_t)nblk);
+  CK(s, cudaMemcpyAsync(hp.data(), part, sizeof(double) * 7 * nblk, cudaMemcpyDeviceToHost, s->stream));
+  CK(s, cudaStreamSynchronize(s->stream));
+  double r[7] = {1e300, 1e300, 1e300, -1e300, -1e300, -1e300, 0.0};
+  for (int b = 0; b < nblk; ++b)
+    for (int q = 0; q < 7; ++q) r[q] = (q < 3) ? std::min(r[q], hp[7 * b + q]) : std::max(r[q], hp[7 * b + q]);
+  for (int q = 0; q < 7; ++q)
+    if (!std::isfinite(r[q])) SYS_FAIL(s, YASPS_E_NAN, "non-finite primitive box in the broadphase");
+  gridp G;
+  double span = 0.0;
+  for (int c = 0; c < 3; ++c) span = std::max(span, r[3 + c] - r[c]);
+  double cell = std::max(r[6], 1e-12);
+  if (span / cell > 512.0) cell = span / 512.0;
+  long long ncell;
+  for (;;) {
+    ncell = 1;
+    for (int c = 0; c < 3; ++c) {
+      G.dim[c] = (int)((r[3 + c] - r[c]) / cell) + 1;
+      ncell *= G.dim[c];
+    }
+    if (ncell <= (1LL << 23)) break;
+    cell *= 1.25;
+  }
+  for (int c = 0; c < 3; ++c) G.lo[c] = r[c];
+  G.cell = cell;
+  G.inv = 1.0 / cell;
+  ENSURE(s, s->ws[3], sizeof(int) * (ncell + 1));
+  ENSURE(s, s->ws[4], sizeof(int) * (ncell + 1));
+  int* start = as<int>(s->ws[3]);
+  int* fill = as<int>(s->ws[4]);
+  CK(s, cudaMemsetAsync(start, 0, sizeof(int) * (ncell + 1), s->stream));
+  k_grid_count<<<blocks_for(n, 256), 256, 0, s->stream>>>(n, blo, bhi, G, start);
+  LAUNCH_CHECK(s, "k_grid_count");
+  int total = 0;
+  RC(scan_exclusive(s, start, start, (int)(ncell + 1), &total));
+  ENSURE(s, s->ws[5], sizeof(int) * (total + 1));
+  CK(s, cudaMemsetAsync(fill, 0, sizeof(int) * (ncell + 1), s->stream));
+  k_grid_fill<<<blocks_for(n, 256), 256, 0, s->stream>>>(n, blo, bhi, G, start, fill, as<int>(s->ws[5]));
+  LAUNCH_CHECK(s, "k_grid_fill");
+  out->G = G;
+  out->start = start;
+  out->items = as<int>(s->ws[5]);
+  out->blo = blo;
+  out->bhi = bhi;
+  return YASPS_OK;
+}
+
+// box buffers: vec slots are not used here; ws[0..2] (A lo/hi, B lo/hi packed)
+struct boxbufs {
+  double *alo, *ahi, *blo, *bhi;
+};
+yasps_status alloc_boxes(yasps_system* s, boxbufs* b) {
+  const size_t nmax = std::max({s->nsv, s->nst, s->nse, 1});
+  ENSURE(s, s->ws[0], sizeof(double) * 6 * nmax);
+  ENSURE(s, s->ws[1], sizeof(double) * 6 * nmax);
+  b->alo = as<double>(s->ws[0]);
+  b->ahi = b->alo + 3 * nmax;
+  b->blo = as<double>(s->ws[1]);
+  b->bhi = b->blo + 3 * nmax;
+  return YASPS_OK;
+}
+
+// run a count / write pair (or energy) query of kind 0 (PT) or 1 (EE)
+template <typename Launch>
+yasps_status two_pass(yasps_system* s, int nA, Launch&& launch, gbuf& outbuf, int* nout) {
+  ENSURE(s, s->ws[2], sizeof(int) * (nA + 1));
+  int* cnt = as<int>(s->ws[2]);
+  RC(launch(0, cnt, (const int*)nullptr, (int*)nullptr));
+  int total = 0;
+  RC(scan_exclusive(s, cnt, cnt, nA, &total));
+  ENSURE(s, outbuf, sizeof(int) * 3 * ((size_t)total + 1));
+  if (total > 0) RC(launch(1, (int*)nullptr, cnt, as<int>(outbuf)));
+  *nout = total;
+  return YASPS_OK;
+}
+
+template <typename T>
+yasps_status eval_barrier_t(yasps_system* s, int project) {
+  const topo Tp = make_topo(s);
+  const double sh = s->prm.dhat * s->prm.dhat;
+  int* st = as<int>(s->status);
+  T* diag = as<T>(s->diag);
+  T* vals = as<T>(s->Hd.vals);
+  double* g = as<double>(s->grad);
+  const double* P = as<double>(s->P);
+  const int* koff = as<int>(s->pair_key_off);
+  const int* dslot = as<int>(s->dyn_slot);
+  if (s->npt) {
+    k_barrier<T><<<blocks_for(s->npt, 128), 128, 0, s->stream>>>(0, s->npt, 0, as<int>(s->pt), Tp, as<double>(s->vr), P,
+                                                                sh, s->prm.kappa, s->prm.barrier_form, project, koff,
+                                                                dslot, g, diag, vals, st);
+    LAUNCH_CHECK(s, "k_barrier(PT)");
+  }
+  if (s->nee) {
+    k_barrier<T><<<blocks_for(s->nee, 128), 128, 0, s->stream>>>(1, s->nee, s->npt, as<int>(s->ee), Tp,
+                                                                as<double>(s->vr), P, sh, s->prm.kappa,
+                                                                s->prm.barrier_form, project, koff, dslot, g, diag,
+                                                                vals, st);
+    LAUNCH_CHECK(s, "k_barrier(EE)");
+  }
+  if (s->npg) {
+    k_barrier_pg<T><<<blocks_for(s->npg, 128), 128, 0, s->stream>>>(s->npg, s->npt + s->nee, as<int>(s->pg), Tp,
+                                                                   as<double>(s->vr), P, as<double>(s->planes), sh,
+                                                                   s->prm.kappa, s->prm.barrier_form, project, koff,
+                                                                   dslot, g, diag, vals, st);
+    LAUNCH_CHECK(s, "k_barrier_pg");
+  }
+  return YASPS_OK;
+}
+
+}  // namespace
+
+// ======================================================================== API
+yasps_status detect_pairs(yasps_system* s, const double* P) {
+  const topo Tp = make_topo(s);
+  const double sh = s->prm.dhat * s->prm.dhat;
+  s->npt = s->nee = s->npg = 0;
+  if (s->nsv > 0 && s->npl > 0) {
+    RC(two_pass(s, s->nsv, [&](int mode, int* cnt, const int* off, int* out) -> yasps_status {
+      k_pg_query<<<blocks_for(s->nsv, 128), 128, 0, s->stream>>>(s->nsv, s->npl, Tp, P, as<double>(s->planes), sh, mode,
+                                                                cnt, off, out, 0.0, 0, nullptr);
+      LAUNCH_CHECK(s, "k_pg_query");
+      return YASPS_OK;
+    }, s->pg, &s->npg));
+  }
+  if (s->nst > 0 && s->nsv > 0) {
+    boxbufs bb;
+    RC(alloc_boxes(s, &bb));
+    k_boxes<<<blocks_for(s->nsv, 256), 256, 0, s->stream>>>(s->nsv, 1, as<int>(s->svert), P, nullptr, s->prm.dhat,
+                                                           bb.alo, bb.ahi);
+    LAUNCH_CHECK(s, "k_boxes");
+    k_boxes<<<blocks_for(s->nst, 256), 256, 0, s->stream>>>(s->nst, 3, as<int>(s->stri), P, nullptr, 0.0, bb.blo, bb.bhi);
+    LAUNCH_CHECK(s, "k_boxes");
+    grid_dev g;
+    RC(build_grid(s, s->nst, bb.blo, bb.bhi, &g));
+    RC(two_pass(s, s->nsv, [&](int mode, int* cnt, const int* off, int* out) -> yasps_status {
+      k_pt_query<<<blocks_for(s->nsv, 128), 128, 0, s->stream>>>(s->nsv, Tp, P, g, bb.alo, bb.ahi, sh, mode, cnt, off,
+                                                                out, 0.0, 0, nullptr);
+      LAUNCH_CHECK(s, "k_pt_query");
+      return YASPS_OK;
+    }, s->pt, &s->npt));
+  }
+  if (s->nse > 1) {
+    boxbufs bb;
+    RC(alloc_boxes(s, &bb));
+    k_boxes<<<blocks_for(s->nse, 256), 256, 0, s->stream>>>(s->nse, 2, as<int>(s->sedge), P, nullptr, s->prm.dhat,
+                                                           bb.alo, bb.ahi);
+    LAUNCH_CHECK(s, "k_boxes");
+    k_boxes<<<blocks_for(s->nse, 256), 256, 0, s->stream>>>(s->nse, 2, as<int>(s->sedge), P, nullptr, 0.0, bb.blo, bb.bhi);
+    LAUNCH_CHECK(s, "k_boxes");
+    grid_dev g;
+    RC(build_grid(s, s->nse, bb.blo, bb.bhi, &g));
+    RC(two_pass(s, s->nse, [&](int mode, int* cnt, const int* off, int* out) -> yasps_status {
+      k_ee_query<<<blocks_for(s->nse, 128), 128, 0, s->stream>>>(s->nse, Tp, P, g, bb.alo, bb.ahi, sh, mode, cnt, off,
+                                                                out, 0.0, 0, nullptr);
+      LAUNCH_CHECK(s, "k_ee_query");
+      return YASPS_OK;
+    }, s->ee, &s->nee));
+  }
+  return build_dynamic_bsr(s);
+}
+
+yasps_status build_dynamic_bsr(yasps_system* s) {
+  const topo Tp = make_topo(s);
+  const int np = s->npt + s->nee + s->npg;
+  ENSURE(s, s->pair_key_off, sizeof(int) * (np + 1));
+  int* koff = as<int>(s->pair_key_off);
+  int nkeys = 0;
+  if (np > 0) {
+    k_pair_nkeys<<<blocks_for(np, 128), 128, 0, s->stream>>>(s->npt, s->nee, s->npg, as<int>(s->pt), as<int>(s->ee),
+                                                            as<int>(s->pg), Tp, as<double>(s->vr), koff);
+    LAUNCH_CHECK(s, "k_pair_nkeys");
+    RC(scan_exclusive(s, koff, koff, np, &nkeys));
+  }
+  s->nkeys = nkeys;
+  ENSURE(s, s->dyn_slot, sizeof(int) * (nkeys + 1));
+  ENSURE(s, s->ws[0], sizeof(uint64_t) * (nkeys + 1));
+  ENSURE(s, s->ws[1], sizeof(int) * (nkeys + 1));
+  if (nkeys > 0) {
+    k_pair_keys<<<blocks_for(np, 128), 128, 0, s->stream>>>(s->npt, s->nee, s->npg, as<int>(s->pt), as<int>(s->ee),
+                                                           as<int>(s->pg), Tp, as<double>(s->vr), koff, s->nbits,
+                                                           as<uint64_t>(s->ws[0]), as<int>(s->ws[1]));
+    LAUNCH_CHECK(s, "k_pair_keys");
+  }
+  RC(bsr_from_keys(s, as<uint64_t>(s->ws[0]), as<int>(s->ws[1]), nkeys, s->Hd, as<int>(s->dyn_slot), nkeys));
+  const size_t es = (s->hess_precision == 1) ? sizeof(float) : sizeof(double);
+  ENSURE(s, s->Hd.vals, es * 9 * ((size_t)s->Hd.nnzb + 1));
+  return YASPS_OK;
+}
+
+yasps_status launch_eval_barrier(yasps_system* s, int project) {
+  if (s->hess_precision == 1) return eval_barrier_t<float>(s, project);
+  return eval_barrier_t<double>(s, project);
+}
+
+yasps_status barrier_energy(yasps_system* s, const double* P, double* E_host) {
+  const topo Tp = make_topo(s);
+  const double sh = s->prm.dhat * s->prm.dhat;
+  const int nblk_v = blocks_for(std::max(s->nsv, 1), 128), nblk_e = blocks_for(std::max(s->nse, 1), 128);
+  const int npart = 2 * nblk_v + nblk_e;
+  gbuf& pb = s->ws[9];
+  ENSURE(s, pb, sizeof(ksum) * (npart + 4));
+  ksum* part = as<ksum>(pb);
+  CK(s, cudaMemsetAsync(part, 0, sizeof(ksum) * (npart + 4), s->stream));
+  if (s->nsv > 0 && s->npl > 0) {
+    k_pg_query<<<nblk_v, 128, 0, s->stream>>>(s->nsv, s->npl, Tp, P, as<double>(s->planes), sh, 2, nullptr, nullptr,
+                                              nullptr, s->prm.kappa, s->prm.barrier_form, part);
+    LAUNCH_CHECK(s, "k_pg_query(E)");
+  }
+  if (s->nst > 0 && s->nsv > 0) {
+    boxbufs bb;
+    RC(alloc_boxes(s, &bb));
+    k_boxes<<<blocks_for(s->nsv, 256), 256, 0, s->stream>>>(s->nsv, 1, as<int>(s->svert), P, nullptr, s->prm.dhat,
+                                                           bb.alo, bb.ahi);
+    LAUNCH_CHECK(s, "k_boxes");
+    k_boxes<<<blocks_for(s->nst, 256), 256, 0, s->stream>>>(s->nst, 3, as<int>(s->stri), P, nullptr, 0.0, bb.blo, bb.bhi);
+    LAUNCH_CHECK(s, "k_boxes");
+    grid_dev g;
+    RC(build_grid(s, s->nst, bb.blo, bb.bhi, &g));
+    k_pt_query<<<nblk_v, 128, 0, s->stream>>>(s->nsv, Tp, P, g, bb.alo, bb.ahi, sh, 2, nullptr, nullptr, nullptr,
+                                              s->prm.kappa, s->prm.barrier_form, part + nblk_v);
+    LAUNCH_CHECK(s, "k_pt_query(E)");
+  }
+  if (s->nse > 1) {
+    boxbufs bb;
+    RC(alloc_boxes(s, &bb));
+    k_boxes<<<blocks_for(s->nse, 256), 256, 0, s->stream>>>(s->nse, 2, as<int>(s->sedge), P, nullptr, s->prm.dhat,
+                                                           bb.alo, bb.ahi);
+    LAUNCH_CHECK(s, "k_boxes");
+    k_boxes<<<blocks_for(s->nse, 256), 256, 0, s->stream>>>(s->nse, 2, as<int>(s->sedge), P, nullptr, 0.0, bb.blo, bb.bhi);
+    LAUNCH_CHECK(s, "k_boxes");
+    grid_dev g;
+    RC(build_grid(s, s->nse, bb.blo, bb.bhi, &g));
+    k_ee_query<<<nblk_e, 128, 0, s->stream>>>(s->nse, Tp, P, g, bb.alo, bb.ahi, sh, 2, nullptr, nullptr, nullptr,
+                                              s->prm.kappa, s->prm.barrier_form, part + 2 * nblk_v);
+    LAUNCH_CHECK(s, "k_ee_query(E)");
+  }
+  double* out = reinterpret_cast<double*>(part + npart + 2);
+  k_reduce_ksum<<<1, 256, 0, s->stream>>>(part, npart, out);
+  LAUNCH_CHECK(s, "k_reduce_ksum");
+  CK(s, cudaMemcpyAsync(E_host, out, sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+  CK(s, cudaStreamSynchronize(s->stream));
+  return YASPS_OK;
+}
+
+yasps_status ccd_bound(yasps_system* s, const double* x, const double* p, double* alpha_host) {
+  const topo Tp = make_topo(s);
+  const size_t nv3 = 3 * (size_t)s->nv;
+  ENSURE(s, s->stepv[3], sizeof(double) * (3 * (size_t)s->nn + 1));  // x - p
+  ENSURE(s, s->stepv[4], sizeof(double) * (2 * nv3 + 2));           // P1, D
+  double* x1 = as<double>(s->stepv[3]);
+  double* P1 = as<double>(s->stepv[4]);
+  double* D = P1 + nv3;
+  double* tmin = D + nv3;  // one double
+  double* P0 = as<double>(s->P);
+  RC(launch_positions(s, x, P0));
+  k_sub<<<blocks_for(3LL * s->nn, 256), 256, 0, s->stream>>>(3 * s->nn, x, p, x1);
+  LAUNCH_CHECK(s, "k_sub");
+  RC(launch_positions(s, x1, P1));
+  k_sub<<<blocks_for((long long)nv3, 256), 256, 0, s->stream>>>((int)nv3, P1, P0, D);
+  LAUNCH_CHECK(s, "k_sub");
+  const double one = 1.0;
+  CK(s, cudaMemcpyAsync(tmin, &one, sizeof(double), cudaMemcpyHostToDevice, s->stream));
+  int* st = as<int>(s->status);
+  if (s->nsv > 0 && s->npl > 0) {
+    k_ccd_pg<<<blocks_for(s->nsv, 128), 128, 0, s->stream>>>(s->nsv, s->npl, Tp, P0, D, as<double>(s->planes),
+                                                            s->prm.ccd_gap, tmin);
+    LAUNCH_CHECK(s, "k_ccd_pg");
+  }
+  if (s->nst > 0 && s->nsv > 0) {
+    boxbufs bb;
+    RC(alloc_boxes(s, &bb));
+    k_boxes<<<blocks_for(s->nsv, 256), 256, 0, s->stream>>>(s->nsv, 1, as<int>(s->svert), P0, P1, s->prm.dhat, bb.alo,
+                                                           bb.ahi);
+    LAUNCH_CHECK(s, "k_boxes");
+    k_boxes<<<blocks_for(s->nst, 256), 256, 0, s->stream>>>(s->nst, 3, as<int>(s->stri), P0, P1, 0.0, bb.blo, bb.bhi);
+    LAUNCH_CHECK(s, "k_boxes");
+    grid_dev g;
+    RC(build_grid(s, s->nst, bb.blo, bb.bhi, &g));
+    k_ccd_pt<<<blocks_for(s->nsv, 64), 64, 0, s->stream>>>(s->nsv, Tp, P0, D, g, bb.alo, bb.ahi, s->prm.ccd_gap,
+                                                          s->prm.ccd_max_iter, tmin, st);
+    LAUNCH_CHECK(s, "k_ccd_pt");
+  }
+  if (s->nse > 1) {
+    boxbufs bb;
+    RC(alloc_boxes(s, &bb));
+    k_boxes<<<blocks_for(s->nse, 256), 256, 0, s->stream>>>(s->nse, 2, as<int>(s->sedge), P0, P1, s->prm.dhat, bb.alo,
+                                                           bb.ahi);
+    LAUNCH_CHECK(s, "k_boxes");
+    k_boxes<<<blocks_for(s->nse, 256), 256, 0, s->stream>>>(s->nse, 2, as<int>(s->sedge), P0, P1, 0.0, bb.blo, bb.bhi);
+    LAUNCH_CHECK(s, "k_boxes");
+    grid_dev g;
+    RC(build_grid(s, s->nse, bb.blo, bb.bhi, &g));
+    k_ccd_ee<<<blocks_for(s->nse, 64), 64, 0, s->stream>>>(s->nse, Tp, P0, D, g, bb.alo, bb.ahi, s->prm.ccd_gap,
+                                                          s->prm.ccd_max_iter, tmin, st);
+    LAUNCH_CHECK(s, "k_ccd_ee");
+  }
+  CK(s, cudaMemcpyAsync(alpha_host, tmin, sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+  CK(s, cudaStreamSynchronize(s->stream));
+  return YASPS_OK;
+}

@@ -41,6 +41,7 @@ struct yasps_system {
 
   // sizes
   int nv = 0, nn = 0, nfree = 0, nb = 0, nt = 0, nc = 0, nh = 0, nst = 0, nse = 0, nsv = 0, npl = 0, nfix = 0;
+  double bbox_diag = 1.0;
   int nbits = 1;  // bits of a node id in packed (row, col) keys; node 2^nbits - 1 is the sentinel
 
   // scene, device
@@ -140,11 +141,15 @@ yasps_status bsr_from_keys(yasps_system* s, uint64_t* keys, int* vals, int n, bs
                            int n_contrib);
 
 // ---------------------------------------------------------------- elements.cu
-yasps_status setup_rest(yasps_system* s);  // rest-shape data and free-vertex masses
+// rest-shape data (Dm^-1, volumes, Lame constants) and free-vertex lumped masses
+yasps_status setup_rest(yasps_system* s, const double* tE, const double* tnu, const double* trho, const double* cE,
+                        const double* cnu, const double* cth, const double* crho, const double* hkb);
 yasps_status static_sparsity(yasps_system* s);
 yasps_status launch_positions(yasps_system* s, const double* x, double* P);
 yasps_status launch_xtilde(yasps_system* s, const double* xt, const double* vt, double* xtil);
 yasps_status launch_eval_static(yasps_system* s, const double* x, const double* xtil, int mask, int project);
+// bend.cu: discrete-shell hinges (gradient + projected Hessian), precision by s->hess_precision
+yasps_status launch_bend(yasps_system* s, int project);
 // five static terms (inertia, tet, membrane, bend, ABD) into out5 (host); synchronises
 yasps_status energy_static(yasps_system* s, const double* x, const double* xtil, double* out5);
 

@@ -1,0 +1,591 @@
+// system.cu -- the C ABI (include/yasps.h): system build, state helpers, and
+// the implicit time step of the incremental potential (Sec. 3 "System
+// Overview": collision detection -> minimise (assemble H, g; solve H p = g) ->
+// CCD step bound and line search -> update).
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "internal.h"
+
+static thread_local std::string g_build_error;
+
+// ---------------------------------------------------------------- memory
+void* sys_alloc(yasps_system* s, size_t bytes) {
+  if (bytes == 0) bytes = 256;
+  if (s->have_allocator) return s->allocator.alloc(s->allocator.ctx, bytes, (void*)s->stream);
+  void* p = nullptr;
+  if (cudaMallocAsync(&p, bytes, s->stream) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return p;
+}
+void sys_free(yasps_system* s, void* p) {
+  if (!p) return;
+  if (s->have_allocator) s->allocator.free(s->allocator.ctx, p, (void*)s->stream);
+  else cudaFreeAsync(p, s->stream);
+}
+bool ensure(yasps_system* s, gbuf& b, size_t bytes) {
+  if (bytes <= b.cap && b.p) return true;
+  size_t cap = std::max<size_t>(bytes + bytes / 4, 256);
+  sys_free(s, b.p);
+  b.p = sys_alloc(s, cap);
+  b.cap = b.p ? cap : 0;
+  return b.p != nullptr;
+}
+void release(yasps_system* s, gbuf& b) {
+  sys_free(s, b.p);
+  b.p = nullptr;
+  b.cap = 0;
+}
+
+yasps_status cuda_check(yasps_system* s, cudaError_t e, const char* where) {
+  if (e == cudaSuccess) return YASPS_OK;
+  s->err = std::string(where) + ": " + cudaGetErrorString(e);
+  cudaGetLastError();
+  return e == cudaErrorMemoryAllocation ? YASPS_E_NOMEM : YASPS_E_CUDA;
+}
+
+template <typename T>
+static yasps_status upload(yasps_system* s, gbuf& b, const T* host, size_t count) {
+  ENSURE(s, b, sizeof(T) * (count + 1));
+  if (count) CK(s, cudaMemcpyAsync(b.p, host, sizeof(T) * count, cudaMemcpyHostToDevice, s->stream));
+  return YASPS_OK;
+}
+
+static void all_bufs(yasps_system* s, std::vector<gbuf*>& v) {
+  gbuf* one[] = {&s->vnode, &s->vbody, &s->vr, &s->vmass, &s->rest, &s->xfix, &s->fixed, &s->fixvel, &s->nodemass,
+                 &s->tet_v, &s->tet_n, &s->tet_rest, &s->tet_slot, &s->tri_v, &s->tri_n, &s->tri_rest, &s->tri_slot,
+                 &s->hinge_v, &s->hinge_n, &s->hinge_rest, &s->hinge_slot, &s->body_kv, &s->body_slot, &s->stri,
+                 &s->sedge, &s->svert, &s->planes, &s->Hs.row_ptr, &s->Hs.col, &s->Hs.row, &s->Hs.vals,
+                 &s->Hd.row_ptr, &s->Hd.col, &s->Hd.row, &s->Hd.vals, &s->diag, &s->grad, &s->minv, &s->P, &s->pt,
+                 &s->ee, &s->pg, &s->pair_key_off, &s->dyn_slot, &s->status, &s->scal, &s->red, &s->scan_tmp};
+  for (gbuf* b : one) v.push_back(b);
+  for (auto& b : s->ws) v.push_back(&b);
+  for (auto& b : s->vec) v.push_back(&b);
+  for (auto& b : s->stepv) v.push_back(&b);
+}
+
+// ======================================================================== ABI
+extern "C" {
+
+void yasps_default_params(yasps_params* p) {
+  std::memset(p, 0, sizeof(*p));
+  p->precision = 0;
+  p->dt = 0.01;
+  p->dhat = 1e-3;
+  p->kappa = 1e4;
+  p->gravity[1] = -9.81;
+  p->newton_tol = 1e-6;
+  p->pcg_rel_tol = 1e-4;
+  p->pcg_max_iter = 0;
+  p->newton_max_iter = 100;
+  p->ls_max_iter = 30;
+  p->barrier_form = 0;
+  p->ccd_gap = 0.1;
+  p->ccd_max_iter = 100000;
+  p->refine_sweeps = 4;
+}
+
+const char* yasps_build_error(void) { return g_build_error.c_str(); }
+const char* yasps_last_error(const yasps_system* s) { return s ? s->err.c_str() : "null system"; }
+long long yasps_kernel_launches(const yasps_system* s) { return s ? s->launches : 0; }
+
+static yasps_status build_impl(yasps_system* s, const yasps_scene_desc* d) {
+  const int nv = d->n_verts;
+  if (nv < 0 || d->n_tets < 0 || d->n_tris < 0 || d->n_hinges < 0 || d->n_bodies < 0 || d->n_fixed < 0 ||
+      d->n_surf_tris < 0 || d->n_surf_edges < 0 || d->n_surf_verts < 0 || d->n_planes < 0)
+    SYS_FAIL(s, YASPS_E_INVAL, "negative size in the scene");
+  if (nv > 0 && (!d->rest_pos || !d->vert_body)) SYS_FAIL(s, YASPS_E_INVAL, "rest_pos / vert_body missing");
+  auto bad_idx = [&](const int* a, long long n, int hi) {
+    for (long long i = 0; i < n; ++i)
+      if (a[i] < 0 || a[i] >= hi) return true;
+    return false;
+  };
+  if (bad_idx(d->tet2v, 4LL * d->n_tets, nv) || bad_idx(d->tri2v, 3LL * d->n_tris, nv) ||
+      bad_idx(d->hinge2v, 4LL * d->n_hinges, nv) || bad_idx(d->fixed_verts, d->n_fixed, nv) ||
+      bad_idx(d->surf_tri2v, 3LL * d->n_surf_tris, nv) || bad_idx(d->surf_edge2v, 2LL * d->n_surf_edges, nv) ||
+      bad_idx(d->surf_verts, d->n_surf_verts, nv))
+    SYS_FAIL(s, YASPS_E_INVAL, "vertex index out of range in the scene");
+  for (int i = 1; i < d->n_surf_verts; ++i)
+    if (d->surf_verts[i] <= d->surf_verts[i - 1]) SYS_FAIL(s, YASPS_E_INVAL, "surf_verts must be strictly increasing");
+  for (int v = 0; v < nv; ++v)
+    if (d->vert_body[v] < -1 || d->vert_body[v] >= d->n_bodies) SYS_FAIL(s, YASPS_E_INVAL, "vert_body out of range");
+
+  s->nv = nv; s->nt = d->n_tets; s->nc = d->n_tris; s->nh = d->n_hinges; s->nb = d->n_bodies;
+  s->nst = d->n_surf_tris; s->nse = d->n_surf_edges; s->nsv = d->n_surf_verts; s->npl = d->n_planes;
+  s->nfix = d->n_fixed;
+
+  // DOF layout (App. A "Gradient Size Computation"): free vertices, then 4 nodes per body
+  std::vector<int> isfixed(nv, 0), vnode(nv, -1);
+  for (int i = 0; i < d->n_fixed; ++i) isfixed[d->fixed_verts[i]] = 1;
+  for (int v = 0; v < nv; ++v)
+    if (isfixed[v] && d->vert_body[v] >= 0) SYS_FAIL(s, YASPS_E_INVAL, "a fixed vertex cannot belong to an affine body");
+  int nf = 0;
+  for (int v = 0; v < nv; ++v)
+    if (!isfixed[v] && d->vert_body[v] < 0) vnode[v] = nf++;
+  s->nfree = nf;
+  s->nn = nf + 4 * s->nb;
+  for (int v = 0; v < nv; ++v)
+    if (d->vert_body[v] >= 0) vnode[v] = nf + 4 * d->vert_body[v];
+  int nbits = 1;
+  while (((1LL << nbits) - 1) < (long long)s->nn + 1) ++nbits;
+  if (nbits > 31) SYS_FAIL(s, YASPS_E_INVAL, "too many nodes");
+  s->nbits = nbits;
+
+  // affine bodies: body-centred rest coordinates r, uniformly lumped masses,
+  // node mass matrix M_ab = sum_v m_v w_a w_b with w = (1, r1, r2, r3)
+  std::vector<double> vr(3 * (size_t)nv, 0.0), bcen(3 * (size_t)s->nb, 0.0), bvm(nv, 0.0), Mb(16 * (size_t)s->nb, 0.0);
+  std::vector<int> bcnt(s->nb, 0);
+  for (int v = 0; v < nv; ++v)
+    if (d->vert_body[v] >= 0) {
+      const int b = d->vert_body[v];
+      bcnt[b]++;
+      for (int c = 0; c < 3; ++c) bcen[3 * b + c] += d->rest_pos[3 * v + c];
+    }
+  for (int b = 0; b < s->nb; ++b) {
+    if (bcnt[b] == 0) SYS_FAIL(s, YASPS_E_INVAL, "affine body without vertices");
+    for (int c = 0; c < 3; ++c) bcen[3 * b + c] /= bcnt[b];
+  }
+  for (int v = 0; v < nv; ++v)
+    if (d->vert_body[v] >= 0) {
+      const int b = d->vert_body[v];
+      for (int c = 0; c < 3; ++c) vr[3 * v + c] = d->rest_pos[3 * v + c] - bcen[3 * b + c];
+      bvm[v] = d->body_mass[b] / bcnt[b];
+      const double w[4] = {1.0, vr[3 * v], vr[3 * v + 1], vr[3 * v + 2]};
+      for (int a = 0; a < 4; ++a)
+        for (int q = 0; q < 4; ++q) Mb[16 * b + 4 * a + q] += bvm[v] * w[a] * w[q];
+    }
+  std::vector<double> kv(s->nb);
+  for (int b = 0; b < s->nb; ++b) kv[b] = d->body_kappa[b] * d->body_vol[b];
+  double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+  for (int v = 0; v < nv; ++v)
+    for (int c = 0; c < 3; ++c) {
+      lo[c] = std::min(lo[c], d->rest_pos[3 * v + c]);
+      hi[c] = std::max(hi[c], d->rest_pos[3 * v + c]);
+    }
+  s->bbox_diag = nv ? std::sqrt((hi[0] - lo[0]) * (hi[0] - lo[0]) + (hi[1] - lo[1]) * (hi[1] - lo[1]) +
+                                (hi[2] - lo[2]) * (hi[2] - lo[2]))
+                    : 1.0;
+
+  RC(upload(s, s->rest, d->rest_pos, 3 * (size_t)nv));
+  RC(upload(s, s->xfix, d->rest_pos, 3 * (size_t)nv));
+  RC(upload(s, s->vnode, vnode.data(), nv));
+  RC(upload(s, s->vbody, d->vert_body, nv));
+  RC(upload(s, s->vr, vr.data(), 3 * (size_t)nv));
+  RC(upload(s, s->vmass, bvm.data(), nv));
+  RC(upload(s, s->fixed, d->fixed_verts, d->n_fixed));
+  RC(upload(s, s->fixvel, d->fixed_vel, 3 * (size_t)d->n_fixed));
+  ENSURE(s, s->nodemass, sizeof(double) * ((size_t)nf + 16 * (size_t)s->nb + 1));
+  CK(s, cudaMemsetAsync(s->nodemass.p, 0, sizeof(double) * nf, s->stream));
+  if (s->nb)
+    CK(s, cudaMemcpyAsync(as<double>(s->nodemass) + nf, Mb.data(), sizeof(double) * 16 * s->nb, cudaMemcpyHostToDevice,
+                          s->stream));
+  RC(upload(s, s->tet_v, d->tet2v, 4 * (size_t)s->nt));
+  ENSURE(s, s->tet_n, sizeof(int) * (4 * (size_t)s->nt + 4));
+  ENSURE(s, s->tet_rest, sizeof(double) * (12 * (size_t)s->nt + 1));
+  ENSURE(s, s->tet_slot, sizeof(int) * (6 * (size_t)s->nt + 1));
+  RC(upload(s, s->tri_v, d->tri2v, 3 * (size_t)s->nc));
+  ENSURE(s, s->tri_n, sizeof(int) * (3 * (size_t)s->nc + 1));
+  ENSURE(s, s->tri_rest, sizeof(double) * (8 * (size_t)s->nc + 1));
+  ENSURE(s, s->tri_slot, sizeof(int) * (3 * (size_t)s->nc + 1));
+  RC(upload(s, s->hinge_v, d->hinge2v, 4 * (size_t)s->nh));
+  ENSURE(s, s->hinge_n, sizeof(int) * (4 * (size_t)s->nh + 1));
+  ENSURE(s, s->hinge_rest, sizeof(double) * (2 * (size_t)s->nh + 1));
+  ENSURE(s, s->hinge_slot, sizeof(int) * (6 * (size_t)s->nh + 1));
+  RC(upload(s, s->body_kv, kv.data(), s->nb));
+  ENSURE(s, s->body_slot, sizeof(int) * (6 * (size_t)s->nb + 1));
+  RC(upload(s, s->stri, d->surf_tri2v, 3 * (size_t)s->nst));
+  RC(upload(s, s->sedge, d->surf_edge2v, 2 * (size_t)s->nse));
+  RC(upload(s, s->svert, d->surf_verts, s->nsv));
+  RC(upload(s, s->planes, d->planes, 4 * (size_t)s->npl));
+  ENSURE(s, s->status, 64);
+  CK(s, cudaMemsetAsync(s->status.p, 0, 64, s->stream));
+  ENSURE(s, s->P, sizeof(double) * (3 * (size_t)nv + 1));
+
+  // per-element material inputs (temporaries)
+  gbuf tmp[8];
+  struct { const double* p; size_t n; } mats[8] = {{d->tet_E, (size_t)s->nt},     {d->tet_nu, (size_t)s->nt},
+                                                  {d->tet_rho, (size_t)s->nt},   {d->tri_E, (size_t)s->nc},
+                                                  {d->tri_nu, (size_t)s->nc},    {d->tri_thick, (size_t)s->nc},
+                                                  {d->tri_rho, (size_t)s->nc},   {d->hinge_kb, (size_t)s->nh}};
+  yasps_status rc = YASPS_OK;
+  for (int k = 0; k < 8 && rc == YASPS_OK; ++k) rc = upload(s, tmp[k], mats[k].p, mats[k].n);
+  if (rc == YASPS_OK)
+    rc = setup_rest(s, as<double>(tmp[0]), as<double>(tmp[1]), as<double>(tmp[2]), as<double>(tmp[3]),
+                    as<double>(tmp[4]), as<double>(tmp[5]), as<double>(tmp[6]), as<double>(tmp[7]));
+  for (auto& b : tmp) release(s, b);
+  RC(rc);
+  int bits = 0;
+  RC(read_status(s, &bits));
+  if (bits) SYS_FAIL(s, YASPS_E_INVAL, "degenerate rest element or elastic element on an affine-body vertex");
+  RC(static_sparsity(s));
+  RC(alloc_hessian(s));
+  // no contact pairs yet
+  s->npt = s->nee = s->npg = 0;
+  RC(build_dynamic_bsr(s));
+  CK(s, cudaStreamSynchronize(s->stream));
+  return YASPS_OK;
+}
+
+yasps_status yasps_build_system(const yasps_scene_desc* scene, const yasps_params* params,
+                                const yasps_allocator* allocator, void* cuda_stream, yasps_system** out) {
+  if (!out || !scene || !params) {
+    g_build_error = "null argument";
+    return YASPS_E_INVAL;
+  }
+  *out = nullptr;
+  yasps_system* s = new yasps_system();
+  s->prm = *params;
+  s->stream = (cudaStream_t)cuda_stream;
+  if (allocator && allocator->alloc && allocator->free) {
+    s->allocator = *allocator;
+    s->have_allocator = true;
+  }
+  for (auto& e : s->ev) cudaEventCreate(&e);
+  yasps_status rc = build_impl(s, scene);
+  if (rc != YASPS_OK) {
+    g_build_error = s->err;
+    yasps_destroy(s);
+    return rc;
+  }
+  *out = s;
+  return YASPS_OK;
+}
+
+void yasps_destroy(yasps_system* s) {
+  if (!s) return;
+  std::vector<gbuf*> bufs;
+  all_bufs(s, bufs);
+  for (gbuf* b : bufs) release(s, *b);
+  cudaStreamSynchronize(s->stream);
+  for (auto& e : s->ev)
+    if (e) cudaEventDestroy(e);
+  delete s;
+}
+
+yasps_status yasps_set_params(yasps_system* s, const yasps_params* p) {
+  if (!s || !p) return YASPS_E_INVAL;
+  const int old = s->hess_precision;
+  s->prm = *p;
+  if ((p->precision == 1 ? 1 : 0) != old) {
+    release(s, s->diag); release(s, s->Hs.vals); release(s, s->Hd.vals); release(s, s->minv);
+    RC(alloc_hessian(s));
+  }
+  return YASPS_OK;
+}
+
+yasps_status yasps_get_sizes(const yasps_system* s, int* n_nodes, int* n_free, int* n_verts) {
+  if (!s) return YASPS_E_INVAL;
+  if (n_nodes) *n_nodes = s->nn;
+  if (n_free) *n_free = s->nfree;
+  if (n_verts) *n_verts = s->nv;
+  return YASPS_OK;
+}
+
+yasps_status yasps_initial_state(yasps_system* s, const double* vel0, double* x_dev, double* v_dev) {
+  if (!s || !x_dev || !v_dev) return YASPS_E_INVAL;
+  std::vector<double> rest(3 * (size_t)s->nv), vr(3 * (size_t)s->nv);
+  std::vector<int> vnode(s->nv), vbody(s->nv);
+  CK(s, cudaMemcpyAsync(rest.data(), s->rest.p, sizeof(double) * rest.size(), cudaMemcpyDeviceToHost, s->stream));
+  CK(s, cudaMemcpyAsync(vr.data(), s->vr.p, sizeof(double) * vr.size(), cudaMemcpyDeviceToHost, s->stream));
+  CK(s, cudaMemcpyAsync(vnode.data(), s->vnode.p, sizeof(int) * s->nv, cudaMemcpyDeviceToHost, s->stream));
+  CK(s, cudaMemcpyAsync(vbody.data(), s->vbody.p, sizeof(int) * s->nv, cudaMemcpyDeviceToHost, s->stream));
+  CK(s, cudaStreamSynchronize(s->stream));
+  std::vector<double> x(3 * (size_t)s->nn, 0.0), v(3 * (size_t)s->nn, 0.0);
+  std::vector<int> cnt(s->nb, 0);
+  for (int i = 0; i < s->nv; ++i) {
+    const int n = vnode[i];
+    if (n < 0) continue;
+    if (vbody[i] < 0) {
+      for (int c = 0; c < 3; ++c) {
+        x[3 * n + c] = rest[3 * i + c];
+        v[3 * n + c] = vel0 ? vel0[3 * i + c] : 0.0;
+      }
+    } else {
+      const int b = vbody[i];
+      for (int c = 0; c < 3; ++c) {
+        x[3 * n + c] = rest[3 * i + c] - vr[3 * i + c];  // t = body centre
+        if (vel0) v[3 * n + c] += vel0[3 * i + c];
+      }
+      for (int k = 0; k < 3; ++k) x[3 * (n + 1 + k) + k] = 1.0;  // A = I
+      cnt[b]++;
+    }
+  }
+  for (int b = 0; b < s->nb; ++b) {
+    const int n = s->nfree + 4 * b;
+    for (int c = 0; c < 3; ++c) v[3 * n + c] /= std::max(cnt[b], 1);
+  }
+  CK(s, cudaMemcpyAsync(x_dev, x.data(), sizeof(double) * x.size(), cudaMemcpyHostToDevice, s->stream));
+  CK(s, cudaMemcpyAsync(v_dev, v.data(), sizeof(double) * v.size(), cudaMemcpyHostToDevice, s->stream));
+  CK(s, cudaStreamSynchronize(s->stream));
+  return YASPS_OK;
+}
+
+yasps_status yasps_vertex_positions(yasps_system* s, const double* x_dev, double* P_dev) {
+  if (!s || !x_dev || !P_dev) return YASPS_E_INVAL;
+  return launch_positions(s, x_dev, P_dev);
+}
+
+yasps_status yasps_xtilde(yasps_system* s, const double* xt, const double* vt, double* xtil) {
+  if (!s || !xt || !vt || !xtil) return YASPS_E_INVAL;
+  return launch_xtilde(s, xt, vt, xtil);
+}
+
+yasps_status yasps_detect_pairs(yasps_system* s, const double* x_dev, int* n_pt, int* n_ee, int* n_pg) {
+  if (!s || !x_dev) return YASPS_E_INVAL;
+  RC(launch_positions(s, x_dev, as<double>(s->P)));
+  RC(detect_pairs(s, as<double>(s->P)));
+  if (n_pt) *n_pt = s->npt;
+  if (n_ee) *n_ee = s->nee;
+  if (n_pg) *n_pg = s->npg;
+  return YASPS_OK;
+}
+
+yasps_status yasps_export_pairs(yasps_system* s, int* pt, int* ee, int* pg) {
+  if (!s) return YASPS_E_INVAL;
+  if (pt && s->npt) CK(s, cudaMemcpyAsync(pt, s->pt.p, sizeof(int) * 3 * s->npt, cudaMemcpyDeviceToHost, s->stream));
+  if (ee && s->nee) CK(s, cudaMemcpyAsync(ee, s->ee.p, sizeof(int) * 3 * s->nee, cudaMemcpyDeviceToHost, s->stream));
+  if (pg && s->npg) CK(s, cudaMemcpyAsync(pg, s->pg.p, sizeof(int) * 3 * s->npg, cudaMemcpyDeviceToHost, s->stream));
+  CK(s, cudaStreamSynchronize(s->stream));
+  return YASPS_OK;
+}
+
+static yasps_status energy_impl(yasps_system* s, const double* x, const double* xtil, double* E, double* terms) {
+  RC(launch_positions(s, x, as<double>(s->P)));
+  double t[6] = {0, 0, 0, 0, 0, 0};
+  RC(energy_static(s, x, xtil, t));
+  RC(barrier_energy(s, as<double>(s->P), &t[5]));
+  // compensated total
+  ksum k{0.0, 0.0};
+  for (int i = 0; i < 6; ++i) kadd(k, t[i]);
+  *E = k.s + k.c;
+  if (terms) std::memcpy(terms, t, sizeof t);
+  if (!std::isfinite(*E)) SYS_FAIL(s, YASPS_E_NAN, "non-finite energy");
+  return YASPS_OK;
+}
+
+yasps_status yasps_energy(yasps_system* s, const double* x_dev, const double* xtilde_dev, double* E, double* terms) {
+  if (!s || !x_dev || !xtilde_dev || !E) return YASPS_E_INVAL;
+  return energy_impl(s, x_dev, xtilde_dev, E, terms);
+}
+
+yasps_status yasps_assemble(yasps_system* s) {
+  if (!s) return YASPS_E_INVAL;
+  return build_dynamic_bsr(s);
+}
+
+static yasps_status eval_impl(yasps_system* s, const double* x, const double* xtil, int mask, int project) {
+  RC(launch_positions(s, x, as<double>(s->P)));
+  const size_t es = (s->hess_precision == 1) ? sizeof(float) : sizeof(double);
+  ENSURE(s, s->Hd.vals, es * 9 * ((size_t)s->Hd.nnzb + 1));
+  RC(zero_system(s));
+  RC(launch_eval_static(s, x, xtil, mask, project));
+  if (mask & YASPS_TERM_BARRIER) RC(launch_eval_barrier(s, project));
+  RC(launch_bjacobi(s));
+  return YASPS_OK;
+}
+
+yasps_status yasps_eval_local(yasps_system* s, const double* x_dev, const double* xtilde_dev, int mask, int project) {
+  if (!s || !x_dev || !xtilde_dev) return YASPS_E_INVAL;
+  RC(eval_impl(s, x_dev, xtilde_dev, mask, project));
+  int bits = 0;
+  RC(read_status(s, &bits));
+  if (bits & (DEV_NAN | DEV_BADINDEX)) SYS_FAIL(s, YASPS_E_NAN, "device error during local evaluation");
+  return YASPS_OK;
+}
+
+yasps_status yasps_export_bsr(yasps_system* s, int which, int* nnzb, int* row_ptr, int* col, double* vals,
+                              double* diag) {
+  if (!s || !nnzb) return YASPS_E_INVAL;
+  bsr_struct& B = which ? s->Hd : s->Hs;
+  *nnzb = B.nnzb;
+  if (row_ptr) CK(s, cudaMemcpyAsync(row_ptr, B.row_ptr.p, sizeof(int) * (s->nn + 1), cudaMemcpyDeviceToHost, s->stream));
+  if (col && B.nnzb) CK(s, cudaMemcpyAsync(col, B.col.p, sizeof(int) * B.nnzb, cudaMemcpyDeviceToHost, s->stream));
+  const bool f32 = s->hess_precision == 1;
+  const size_t es = f32 ? sizeof(float) : sizeof(double);
+  std::vector<char> tmpv, tmpd;
+  if (vals && B.nnzb) {
+    tmpv.resize(es * 9 * B.nnzb);
+    CK(s, cudaMemcpyAsync(tmpv.data(), B.vals.p, tmpv.size(), cudaMemcpyDeviceToHost, s->stream));
+  }
+  if (diag && which == 0) {
+    tmpd.resize(es * 9 * s->nn);
+    CK(s, cudaMemcpyAsync(tmpd.data(), s->diag.p, tmpd.size(), cudaMemcpyDeviceToHost, s->stream));
+  }
+  CK(s, cudaStreamSynchronize(s->stream));
+  auto conv = [&](const std::vector<char>& src, double* dst, size_t n) {
+    for (size_t i = 0; i < n; ++i)
+      dst[i] = f32 ? (double)reinterpret_cast<const float*>(src.data())[i] : reinterpret_cast<const double*>(src.data())[i];
+  };
+  if (vals && B.nnzb) conv(tmpv, vals, 9 * (size_t)B.nnzb);
+  if (diag && which == 0) conv(tmpd, diag, 9 * (size_t)s->nn);
+  return YASPS_OK;
+}
+
+yasps_status yasps_export_gradient(yasps_system* s, double* g_dev) {
+  if (!s || !g_dev) return YASPS_E_INVAL;
+  CK(s, cudaMemcpyAsync(g_dev, s->grad.p, sizeof(double) * 3 * s->nn, cudaMemcpyDeviceToDevice, s->stream));
+  return YASPS_OK;
+}
+
+yasps_status yasps_spmv(yasps_system* s, const double* x_dev, double* y_dev) {
+  if (!s || !x_dev || !y_dev) return YASPS_E_INVAL;
+  return spmv64(s, x_dev, y_dev);
+}
+
+yasps_status yasps_pcg_solve(yasps_system* s, const double* rhs, double* p, double tol, int* iters, double* rel) {
+  if (!s || !rhs || !p) return YASPS_E_INVAL;
+  return pcg_solve(s, rhs, p, tol, s->prm.pcg_max_iter, iters, rel);
+}
+
+yasps_status yasps_ccd_bound(yasps_system* s, const double* x_dev, const double* p_dev, double* alpha) {
+  if (!s || !x_dev || !p_dev || !alpha) return YASPS_E_INVAL;
+  return ccd_bound(s, x_dev, p_dev, alpha);
+}
+
+yasps_status yasps_set_fixed_positions(yasps_system* s, const double* P) {
+  if (!s || !P) return YASPS_E_INVAL;
+  std::vector<int> fx(s->nfix);
+  if (s->nfix) {
+    CK(s, cudaMemcpyAsync(fx.data(), s->fixed.p, sizeof(int) * s->nfix, cudaMemcpyDeviceToHost, s->stream));
+    CK(s, cudaStreamSynchronize(s->stream));
+  }
+  for (int v : fx)
+    CK(s, cudaMemcpyAsync(as<double>(s->xfix) + 3 * (size_t)v, P + 3 * (size_t)v, sizeof(double) * 3,
+                          cudaMemcpyHostToDevice, s->stream));
+  CK(s, cudaStreamSynchronize(s->stream));
+  return YASPS_OK;
+}
+
+yasps_status yasps_get_fixed_positions(yasps_system* s, double* P) {
+  if (!s || !P) return YASPS_E_INVAL;
+  CK(s, cudaMemcpyAsync(P, s->xfix.p, sizeof(double) * 3 * s->nv, cudaMemcpyDeviceToHost, s->stream));
+  CK(s, cudaStreamSynchronize(s->stream));
+  return YASPS_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------- time step
+namespace {
+__global__ void k_fixed_advance(int nfix, const int* __restrict__ fixed, const double* __restrict__ fv, double h,
+                                double* __restrict__ xfix) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nfix) return;
+  const int v = fixed[i];
+  for (int c = 0; c < 3; ++c) xfix[3 * v + c] += h * fv[3 * i + c];
+}
+__global__ void k_axpy_out(int n, const double* __restrict__ x, double a, const double* __restrict__ p,
+                           double* __restrict__ out) {  // out = x - a p
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = x[i] - a * p[i];
+}
+__global__ void k_velocity(int n, const double* __restrict__ x, const double* __restrict__ xt, double inv_h,
+                           double* __restrict__ v) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) v[i] = (x[i] - xt[i]) * inv_h;
+}
+}  // namespace
+
+static float elapsed(cudaEvent_t a, cudaEvent_t b) {
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, a, b);
+  return ms;
+}
+
+extern "C" yasps_status yasps_step(yasps_system* s, double* x, double* v, yasps_step_stats* stats) {
+  if (!s || !x || !v) return YASPS_E_INVAL;
+  const int n3 = 3 * s->nn;
+  const double h = s->prm.dt;
+  yasps_step_stats st{};
+  for (int k = 0; k < 4; ++k) ENSURE(s, s->stepv[k], sizeof(double) * (n3 + 4));
+  double* xt = as<double>(s->stepv[0]);
+  double* xtil = as<double>(s->stepv[1]);
+  double* p = as<double>(s->stepv[2]);
+  gbuf& trial = s->vec[7];
+  ENSURE(s, trial, sizeof(double) * (n3 + 4));
+  double* xtrial = as<double>(trial);
+  if (s->nfix) {
+    k_fixed_advance<<<blocks_for(s->nfix, 128), 128, 0, s->stream>>>(s->nfix, as<int>(s->fixed), as<double>(s->fixvel),
+                                                                    h, as<double>(s->xfix));
+    LAUNCH_CHECK(s, "k_fixed_advance");
+  }
+  CK(s, cudaMemcpyAsync(xt, x, sizeof(double) * n3, cudaMemcpyDeviceToDevice, s->stream));
+  RC(launch_xtilde(s, x, v, xtil));
+  yasps_status rc = YASPS_OK;
+  int it = 0;
+  double pinf = 0.0, alpha = 0.0;
+  for (it = 0; it < s->prm.newton_max_iter; ++it) {
+    cudaEventRecord(s->ev[0], s->stream);
+    RC(launch_positions(s, x, as<double>(s->P)));
+    RC(detect_pairs(s, as<double>(s->P)));
+    RC(eval_impl(s, x, xtil, YASPS_TERM_ALL, 1));
+    cudaEventRecord(s->ev[1], s->stream);
+    int pit = 0;
+    double rel = 0.0;
+    rc = pcg_solve(s, as<double>(s->grad), p, s->prm.pcg_rel_tol, s->prm.pcg_max_iter, &pit, &rel);
+    st.pcg_iters_total += pit;
+    if (rc == YASPS_E_NOCONV) rc = YASPS_OK;  // inexact Newton: keep the last iterate
+    if (rc != YASPS_OK) break;
+    cudaEventRecord(s->ev[2], s->stream);
+    int bits = 0;
+    RC(read_status(s, &bits));
+    if (bits & (DEV_NAN | DEV_BADINDEX)) {
+      s->err = "device error during evaluation";
+      rc = YASPS_E_NAN;
+      break;
+    }
+    RC(inf_norm(s, p, n3, &pinf));
+    if (!std::isfinite(pinf)) {
+      s->err = "non-finite Newton direction";
+      rc = YASPS_E_NAN;
+      break;
+    }
+    st.t_eval_ms += elapsed(s->ev[0], s->ev[1]);
+    st.t_pcg_ms += elapsed(s->ev[1], s->ev[2]);
+    st.n_pt = s->npt; st.n_ee = s->nee; st.n_pg = s->npg;
+    if (pinf <= s->prm.newton_tol) break;
+    cudaEventRecord(s->ev[3], s->stream);
+    RC(ccd_bound(s, x, p, &alpha));
+    cudaEventRecord(s->ev[4], s->stream);
+    double E0 = 0.0, E1 = 0.0;
+    RC(energy_impl(s, x, xtil, &E0, nullptr));
+    int ls = 0;
+    for (ls = 0; ls < s->prm.ls_max_iter; ++ls) {
+      k_axpy_out<<<blocks_for(n3, 256), 256, 0, s->stream>>>(n3, x, alpha, p, xtrial);
+      LAUNCH_CHECK(s, "k_axpy_out");
+      RC(energy_impl(s, xtrial, xtil, &E1, nullptr));
+      if (E1 <= E0) break;
+      alpha *= 0.5;
+    }
+    cudaEventRecord(s->ev[5], s->stream);
+    cudaEventSynchronize(s->ev[5]);
+    st.t_ccd_ms += elapsed(s->ev[3], s->ev[4]);
+    st.t_ls_ms += elapsed(s->ev[4], s->ev[5]);
+    if (ls == s->prm.ls_max_iter) {
+      s->err = "line search found no decreasing step";
+      rc = YASPS_E_LINESEARCH;
+      break;
+    }
+    CK(s, cudaMemcpyAsync(x, xtrial, sizeof(double) * n3, cudaMemcpyDeviceToDevice, s->stream));
+    st.alpha_last = alpha;
+  }
+  if (rc == YASPS_OK && it == s->prm.newton_max_iter) {
+    s->err = "Newton hit its iteration cap";
+    rc = YASPS_E_NOCONV;
+  }
+  k_velocity<<<blocks_for(n3, 256), 256, 0, s->stream>>>(n3, x, xt, 1.0 / h, v);
+  LAUNCH_CHECK(s, "k_velocity");
+  CK(s, cudaStreamSynchronize(s->stream));
+  st.newton_iters = it;
+  st.p_inf = pinf;
+  st.status = rc;
+  if (stats) *stats = st;
+  return rc;
+}
