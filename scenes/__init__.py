@@ -372,7 +372,7 @@ def mixed_scene(sphere_r=0.1, sphere_h=0.0108, cloth_n=101, cloth_size=1.0, n_bo
     """Soft sphere + StVK cloth + 16 affine boxes (every cross-parameterisation pair)."""
     parts = _empty_parts()
     sv, st = sphere_mesh(sphere_r, sphere_h)
-    sv = sv + np.array([0.0, sphere_r + 1e-3 - sv[:, 1].min() - sphere_r, 0.0]) + np.array([0, sphere_r, 0])
+    sv = sv + np.array([0.0, 1e-3 - sv[:, 1].min(), 0.0])  # resting 1 mm above the ground
     _add_soft(parts, sv, st, 5e4, 0.4, 1000.0)
     top = sv[:, 1].max()
     thick = 1e-3

@@ -1,0 +1,289 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Inputs are seeded scenes from ``scenes`` and states produced by the oracle or
+by plain translations of the generated geometry; nothing here feeds a CUDA
+result back into the oracle.
+
+Tolerances (written in each test):
+  * contact-pair sets and BSR sparsity: bit-exact (integer / index work);
+  * FP64 gradients, Hessian blocks, energies: max |a - b| / max |b| <= 1e-10
+    (the element derivatives are exact formulas on both sides, so only
+    summation order differs: atomic assembly vs the oracle's sorted sums);
+  * per-step positions: within 1e-6 of the scene's bounding-box diagonal;
+  * FP32-mixed Hessians: max |a - b| / max |b| <= 2e-5 (FP32 rounding of the
+    projected blocks, a 9x9 / 12x12 Jacobi EVD in FP32).
+"""
+import numpy as np
+import pytest
+
+import oracle
+import scenes
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+RTOL = 1e-10
+
+
+def rel(a, b):
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300)) if b.size else 0.0
+
+
+def T(a):
+    return torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64), device="cuda")
+
+
+def N(t):
+    return t.detach().cpu().numpy()
+
+
+@pytest.fixture(scope="module")
+def yb():
+    import paper_2605_23088_b300 as m
+    return m
+
+
+# ---------------------------------------------------------------- scenes
+@pytest.fixture(scope="module")
+def cubes(yb):
+    s = scenes.cubes_scene()
+    O = oracle.OracleSystem(s, pcg_tol=1e-12)
+    x, v = O.initial_state()
+    states = [(x, v)]
+    for _ in range(3):
+        x, v, rc, st = O.step(x, v)
+        assert rc == 0
+        states.append((x, v))
+    G = yb.System(s, pcg_rel_tol=1e-12)
+    return s, O, G, states
+
+
+def mixed_contact_state(O, s):
+    """Oracle initial state of the small mixed scene, translated into contact:
+    cloth 0.3 mm above the sphere's top face, boxes 0.3 mm above the cloth, box 1
+    0.3 mm beside box 0, everything lowered so the sphere is 0.3 mm above the ground."""
+    x, v = O.initial_state()
+    vnode, vr, vm = O.vertex_info()
+    P = s["rest_pos"]
+    body = s["vert_body"]
+    nt = len(s["tets"])
+    sphere = np.unique(s["tets"])
+    cloth = np.unique(s["tris"])
+    top = P[sphere, 1].max()
+    gap = 3e-4
+    dy_cloth = (top + gap) - P[cloth, 1].min()
+    x[vnode[cloth]] += [0.0, dy_cloth, 0.0]
+    cloth_y = top + gap
+    for b in range(len(s["body_mass"])):
+        bv = np.nonzero(body == b)[0]
+        dy = (cloth_y + gap) - P[bv, 1].min()
+        x[O.nfree + 4 * b] += [0.0, dy, 0.0]
+    b0 = P[body == 0]
+    b1 = P[body == 1]
+    x[O.nfree + 4] += [(b0[:, 0].max() + gap) - b1[:, 0].min(), 0.0, 0.0]
+    drop = P[sphere, 1].min() - gap
+    for i in range(O.nfree):
+        x[i, 1] -= drop
+    for b in range(len(s["body_mass"])):
+        x[O.nfree + 4 * b, 1] -= drop
+    return x, v
+
+
+@pytest.fixture(scope="module")
+def mixed(yb):
+    s = scenes.mixed_scene(sphere_h=0.04, cloth_n=9, cloth_size=0.3, n_boxes=4)
+    O = oracle.OracleSystem(s, pcg_tol=1e-12)
+    x, v = mixed_contact_state(O, s)
+    G = yb.System(s, pcg_rel_tol=1e-12)
+    return s, O, G, x, v
+
+
+# ---------------------------------------------------------------- helpers
+def compare_assembly(G, O, x, v, project=True, tol=RTOL):
+    xt = O.xtilde(x, v)
+    g_ref = O.assemble(x, xt, project=project)
+    xg, xtg = T(x), T(xt)
+    counts = G.detect_pairs(xg)
+    G.eval_local(xg, xtg, project=project)
+    g = N(G.export_gradient())
+    assert rel(g, g_ref) <= tol, rel(g, g_ref)
+    diag_ref = None
+    for which in (0, 1):
+        rp, col, vals, diag = G.export_bsr(which)
+        rp_r, col_r, vals_r, diag_r = O.bsr(which)
+        assert np.array_equal(rp, rp_r), which
+        assert np.array_equal(col, col_r), which
+        if len(vals_r):
+            scale = max(np.abs(vals_r).max(), np.abs(diag_r).max())
+            assert np.max(np.abs(vals - vals_r)) / scale <= tol, which
+        if which == 0:
+            gdiag = diag
+            diag_ref = diag_r.copy()
+        else:
+            diag_ref += diag_r
+    assert rel(gdiag, diag_ref) <= tol
+    return counts
+
+
+# ---------------------------------------------------------------- two cubes
+def test_initial_state_and_positions(cubes):
+    s, O, G, states = cubes
+    x, v = G.initial_state()
+    xr, vr = O.initial_state()
+    assert np.array_equal(N(x), xr) and np.array_equal(N(v), vr)
+    for xs, _ in states:
+        assert np.array_equal(N(G.vertex_positions(T(xs))), O.positions(xs))
+
+
+def test_pairs_bit_exact(cubes):
+    s, O, G, states = cubes
+    seen = 0
+    for xs, _ in states:
+        got = G.pairs(T(xs))
+        ref = O.pairs(xs)
+        for a, b in zip(got, ref):
+            assert np.array_equal(a, b)
+        seen += sum(len(a) for a in ref)
+    assert seen > 0
+
+
+@pytest.mark.parametrize("project", [True, False])
+def test_assembly_parity(cubes, project):
+    s, O, G, states = cubes
+    for xs, vs in states[1:]:
+        compare_assembly(G, O, xs, vs, project=project)
+
+
+def test_spmv_and_pcg(cubes):
+    s, O, G, states = cubes
+    x, v = states[-1]
+    xt = O.xtilde(x, v)
+    g_ref = O.assemble(x, xt)
+    G.detect_pairs(T(x))
+    G.eval_local(T(x), T(xt))
+    rng = np.random.default_rng(5)
+    y = rng.normal(size=(O.nn, 3))
+    assert rel(N(G.spmv(T(y))), O.spmv(y)) <= 1e-12
+    H = O.dense_hessian()
+    ref = np.linalg.solve(H, g_ref.ravel()).reshape(-1, 3)
+    p, it, rr = G.pcg_solve(T(g_ref), rel_tol=1e-12)
+    assert rel(N(p), ref) <= 1e-8
+    assert it > 0 and rr <= 1e-12
+
+
+def test_energy_parity(cubes):
+    s, O, G, states = cubes
+    for xs, vs in states:
+        xt = O.xtilde(xs, vs)
+        E, t = G.energy(T(xs), T(xt), terms=True)
+        Er, tr = O.energy(xs, xt, terms=True)
+        assert E == pytest.approx(Er, rel=1e-12, abs=1e-300)
+        for a, b in zip(t, tr):
+            assert a == pytest.approx(b, rel=1e-11, abs=1e-18)
+
+
+def test_ccd_bound_parity(cubes):
+    s, O, G, states = cubes
+    x, v = states[1]
+    xt = O.xtilde(x, v)
+    g = O.assemble(x, xt)
+    p, _, _ = O.pcg(g, tol=1e-10)
+    for scale in (1.0, 5.0, 50.0):
+        a = G.ccd_bound(T(x), T(scale * p))
+        ar = O.ccd_bound(x, scale * p)
+        assert a == pytest.approx(ar, rel=1e-14, abs=0.0)
+
+
+def test_step_teacher_forced(cubes, yb):
+    s, O, G, states = cubes
+    for (x0, v0), (x1, v1) in zip(states[:-1], states[1:]):
+        xg, vg = T(x0), T(v0)
+        st = G.step(xg, vg)
+        assert st["rc"] == 0
+        assert np.abs(N(xg) - x1).max() <= 1e-6 * s["bbox_diag"]
+
+
+def test_mixed_precision_step(cubes, yb):
+    s, O, G, states = cubes
+    Gm = yb.System(s, precision=1, pcg_rel_tol=1e-10)
+    for (x0, v0), (x1, v1) in zip(states[:-1], states[1:]):
+        xg, vg = T(x0), T(v0)
+        st = Gm.step(xg, vg)
+        assert st["rc"] == 0
+        assert np.abs(N(xg) - x1).max() <= 1e-6 * s["bbox_diag"]
+
+
+def test_mixed_precision_hessian(cubes, yb):
+    s, O, G, states = cubes
+    Gm = yb.System(s, precision=1)
+    x, v = states[-1]
+    xt = O.xtilde(x, v)
+    g_ref = O.assemble(x, xt)
+    Gm.detect_pairs(T(x))
+    Gm.eval_local(T(x), T(xt))
+    assert rel(N(Gm.export_gradient()), g_ref) <= RTOL  # gradients stay FP64
+    rp, col, vals, diag = Gm.export_bsr(0)
+    _, _, vals_r, diag_r = O.bsr(0)
+    assert np.max(np.abs(vals - vals_r)) / np.abs(vals_r).max() <= 2e-5
+
+
+# ---------------------------------------------------------------- mixed parameterisations
+def test_mixed_scene_pairs_cover_all_parameterisations(mixed):
+    s, O, G, x, v = mixed
+    pt, ee, pg = O.pairs(x)
+    got = G.pairs(T(x))
+    for a, b in zip(got, (pt, ee, pg)):
+        assert np.array_equal(a, b)
+    body = s["vert_body"]
+    kinds = set()
+    for vtx, t, _ in pt:
+        kinds.add((body[vtx] >= 0, body[s["surf_tris"][t][0]] >= 0))
+    assert (False, False) in kinds and (True, False) in kinds and (False, True) in kinds and (True, True) in kinds
+    assert len(pg) > 0 and len(ee) > 0
+
+
+@pytest.mark.parametrize("project", [True, False])
+def test_mixed_scene_assembly(mixed, project):
+    s, O, G, x, v = mixed
+    compare_assembly(G, O, x, v, project=project)
+
+
+def test_mixed_scene_energy_ccd_step(mixed):
+    s, O, G, x, v = mixed
+    xt = O.xtilde(x, v)
+    E, t = G.energy(T(x), T(xt), terms=True)
+    Er, tr = O.energy(x, xt, terms=True)
+    assert E == pytest.approx(Er, rel=1e-12)
+    g = O.assemble(x, xt)
+    p, _, _ = O.pcg(g, tol=1e-10)
+    assert G.ccd_bound(T(x), T(p)) == pytest.approx(O.ccd_bound(x, p), rel=1e-14)
+    x1, v1, rc, st = O.step(x, v)
+    assert rc == 0
+    xg, vg = T(x), T(v)
+    stg = G.step(xg, vg)
+    assert stg["rc"] == 0
+    assert np.abs(N(xg) - x1).max() <= 1e-6 * s["bbox_diag"]
+
+
+# ---------------------------------------------------------------- edge cases
+def test_scene_without_contact_surfaces(yb):
+    s = scenes.cubes_scene(n=1)
+    for k in ("surf_tris", "surf_edges"):
+        s[k] = s[k][:0]
+    s["surf_verts"] = s["surf_verts"][:0]
+    s["planes"] = s["planes"][:0]
+    G = yb.System(s)
+    O = oracle.OracleSystem(s, pcg_tol=1e-12)
+    x, v = O.initial_state()
+    assert G.pairs(T(x)) == tuple(np.zeros((0, 3), np.int32) for _ in range(3)) or all(len(a) == 0 for a in G.pairs(T(x)))
+    compare_assembly(G, O, x + 1e-3 * np.random.default_rng(0).normal(size=x.shape), v)
+
+
+def test_bad_scene_is_rejected(yb):
+    s = scenes.cubes_scene(n=1)
+    s["tets"] = s["tets"].copy()
+    s["tets"][0, 0] = 10 ** 6
+    with pytest.raises(yb.YaspsError):
+        yb.System(s)
