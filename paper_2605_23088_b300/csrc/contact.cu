@@ -166,6 +166,7 @@ __device__ __forceinline__ void grid_visit(const grid_dev& g, const double* alo,
 // ---------------------------------------------------------------- exclusions
 struct topo {
   const int *vnode, *vbody, *stri, *sedge, *svert;
+  int* status;
 };
 __device__ __forceinline__ bool pt_excluded(const topo& T, int v, int t0, int t1, int t2) {
   if (v == t0 || v == t1 || v == t2) return true;
@@ -197,7 +198,7 @@ __device__ __forceinline__ bder barrier_fn(double s, double sh, int form) {
 
 // ---------------------------------------------------------------- detection
 // mode 0: count, mode 1: write + sort segment, mode 2: accumulate kappa * b(s)
-__global__ void k_pt_query(int nsv, topo T, const double* __restrict__ P, grid_dev g, const double* __restrict__ alo,
+__global__ void k_pt_query(int total, int nsv, topo T, const double* __restrict__ P, grid_dev g, const double* __restrict__ alo,
                            const double* __restrict__ ahi, double sh, int mode, int* __restrict__ cnt,
                            const int* __restrict__ off, int* __restrict__ out, double kappa, int form,
                            ksum* __restrict__ part) {
@@ -208,6 +209,7 @@ __global__ void k_pt_query(int nsv, topo T, const double* __restrict__ P, grid_d
     const d3 p = ld3(P, v);
     int c = 0;
     const int base = (mode == 1) ? off[i] : 0;
+    const int lim = (mode == 1) ? ((i + 1 < nsv) ? off[i + 1] : total) : 0;
     grid_visit(g, alo + 3 * i, ahi + 3 * i, [&](int t) {
       const int t0 = T.stri[3 * t], t1 = T.stri[3 * t + 1], t2 = T.stri[3 * t + 2];
       if (pt_excluded(T, v, t0, t1, t2)) return;
@@ -215,6 +217,7 @@ __global__ void k_pt_query(int nsv, topo T, const double* __restrict__ P, grid_d
       const int st = dist::pt_classify(p, ld3(P, t0), ld3(P, t1), ld3(P, t2), &s);
       if (!(s < sh)) return;
       if (mode == 1) {
+        if (base + c >= lim) { dev_flag(T.status, DEV_CAPACITY); return; }
         int* o = out + 3 * (size_t)(base + c);
         o[0] = v; o[1] = t; o[2] = st;
       } else if (mode == 2) {
@@ -224,6 +227,7 @@ __global__ void k_pt_query(int nsv, topo T, const double* __restrict__ P, grid_d
     });
     if (mode == 0) cnt[i] = c;
     if (mode == 1) {  // insertion sort of this vertex's partners by triangle id
+      c = min(c, lim - base);
       int* o = out + 3 * (size_t)base;
       for (int a = 1; a < c; ++a) {
         const int kb = o[3 * a + 1], ks = o[3 * a + 2];
@@ -244,7 +248,7 @@ __global__ void k_pt_query(int nsv, topo T, const double* __restrict__ P, grid_d
   }
 }
 
-__global__ void k_ee_query(int nse, topo T, const double* __restrict__ P, grid_dev g, const double* __restrict__ alo,
+__global__ void k_ee_query(int total, int nse, topo T, const double* __restrict__ P, grid_dev g, const double* __restrict__ alo,
                            const double* __restrict__ ahi, double sh, int mode, int* __restrict__ cnt,
                            const int* __restrict__ off, int* __restrict__ out, double kappa, int form,
                            ksum* __restrict__ part) {
@@ -255,6 +259,7 @@ __global__ void k_ee_query(int nse, topo T, const double* __restrict__ P, grid_d
     const d3 a0 = ld3(P, e0), a1 = ld3(P, e1);
     int c = 0;
     const int base = (mode == 1) ? off[i] : 0;
+    const int lim = (mode == 1) ? ((i + 1 < nse) ? off[i + 1] : total) : 0;
     grid_visit(g, alo + 3 * i, ahi + 3 * i, [&](int j) {
       if (j <= i) return;
       const int f0 = T.sedge[2 * j], f1 = T.sedge[2 * j + 1];
@@ -263,6 +268,7 @@ __global__ void k_ee_query(int nse, topo T, const double* __restrict__ P, grid_d
       const int st = dist::ee_classify(a0, a1, ld3(P, f0), ld3(P, f1), &s);
       if (!(s < sh)) return;
       if (mode == 1) {
+        if (base + c >= lim) { dev_flag(T.status, DEV_CAPACITY); return; }
         int* o = out + 3 * (size_t)(base + c);
         o[0] = i; o[1] = j; o[2] = st;
       } else if (mode == 2) {
@@ -272,6 +278,7 @@ __global__ void k_ee_query(int nse, topo T, const double* __restrict__ P, grid_d
     });
     if (mode == 0) cnt[i] = c;
     if (mode == 1) {
+      c = min(c, lim - base);
       int* o = out + 3 * (size_t)base;
       for (int a = 1; a < c; ++a) {
         const int kb = o[3 * a + 1], ks = o[3 * a + 2];
@@ -293,7 +300,7 @@ __global__ void k_ee_query(int nse, topo T, const double* __restrict__ P, grid_d
 }
 
 // point-plane pairs: d = n.p - c, active when d > 0 and d^2 < dhat^2
-__global__ void k_pg_query(int nsv, int npl, topo T, const double* __restrict__ P, const double* __restrict__ planes,
+__global__ void k_pg_query(int total, int nsv, int npl, topo T, const double* __restrict__ P, const double* __restrict__ planes,
                            double sh, int mode, int* __restrict__ cnt, const int* __restrict__ off,
                            int* __restrict__ out, double kappa, int form, ksum* __restrict__ part) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -309,6 +316,8 @@ __global__ void k_pg_query(int nsv, int npl, topo T, const double* __restrict__ 
         const double s = dist::mul(d, d);
         if (!(d > 0.0 && s < sh)) continue;
         if (mode == 1) {
+          const int lim = (i + 1 < nsv) ? off[i + 1] : total;
+          if (off[i] + c >= lim) { dev_flag(T.status, DEV_CAPACITY); break; }
           int* o = out + 3 * (size_t)(off[i] + c);
           o[0] = v; o[1] = k; o[2] = 0;
         } else if (mode == 2) {
@@ -676,7 +685,8 @@ __global__ void k_reduce_ksum(const ksum* __restrict__ part, int n, double* __re
 
 // ======================================================================== host
 topo make_topo(yasps_system* s) {
-  return topo{as<int>(s->vnode), as<int>(s->vbody), as<int>(s->stri), as<int>(s->sedge), as<int>(s->svert)};
+  return topo{as<int>(s->vnode), as<int>(s->vbody), as<int>(s->stri), as<int>(s->sedge), as<int>(s->svert),
+              as<int>(s->status)};
 }
 
 // Build a grid on boxes (blo, bhi) of n primitives.  Buffers: ws[3] start,
@@ -754,11 +764,11 @@ template <typename Launch>
 yasps_status two_pass(yasps_system* s, int nA, Launch&& launch, gbuf& outbuf, int* nout) {
   ENSURE(s, s->ws[2], sizeof(int) * (nA + 1));
   int* cnt = as<int>(s->ws[2]);
-  RC(launch(0, cnt, (const int*)nullptr, (int*)nullptr));
+  RC(launch(0, 0, cnt, (const int*)nullptr, (int*)nullptr));
   int total = 0;
   RC(scan_exclusive(s, cnt, cnt, nA, &total));
   ENSURE(s, outbuf, sizeof(int) * 3 * ((size_t)total + 1));
-  if (total > 0) RC(launch(1, (int*)nullptr, cnt, as<int>(outbuf)));
+  if (total > 0) RC(launch(1, total, (int*)nullptr, cnt, as<int>(outbuf)));
   *nout = total;
   return YASPS_OK;
 }
@@ -805,8 +815,8 @@ yasps_status detect_pairs(yasps_system* s, const double* P) {
   const double sh = s->prm.dhat * s->prm.dhat;
   s->npt = s->nee = s->npg = 0;
   if (s->nsv > 0 && s->npl > 0) {
-    RC(two_pass(s, s->nsv, [&](int mode, int* cnt, const int* off, int* out) -> yasps_status {
-      k_pg_query<<<blocks_for(s->nsv, 128), 128, 0, s->stream>>>(s->nsv, s->npl, Tp, P, as<double>(s->planes), sh, mode,
+    RC(two_pass(s, s->nsv, [&](int mode, int total, int* cnt, const int* off, int* out) -> yasps_status {
+      k_pg_query<<<blocks_for(s->nsv, 128), 128, 0, s->stream>>>(total, s->nsv, s->npl, Tp, P, as<double>(s->planes), sh, mode,
                                                                 cnt, off, out, 0.0, 0, nullptr);
       LAUNCH_CHECK(s, "k_pg_query");
       return YASPS_OK;
@@ -822,8 +832,8 @@ yasps_status detect_pairs(yasps_system* s, const double* P) {
     LAUNCH_CHECK(s, "k_boxes");
     grid_dev g;
     RC(build_grid(s, s->nst, bb.blo, bb.bhi, &g));
-    RC(two_pass(s, s->nsv, [&](int mode, int* cnt, const int* off, int* out) -> yasps_status {
-      k_pt_query<<<blocks_for(s->nsv, 128), 128, 0, s->stream>>>(s->nsv, Tp, P, g, bb.alo, bb.ahi, sh, mode, cnt, off,
+    RC(two_pass(s, s->nsv, [&](int mode, int total, int* cnt, const int* off, int* out) -> yasps_status {
+      k_pt_query<<<blocks_for(s->nsv, 128), 128, 0, s->stream>>>(total, s->nsv, Tp, P, g, bb.alo, bb.ahi, sh, mode, cnt, off,
                                                                 out, 0.0, 0, nullptr);
       LAUNCH_CHECK(s, "k_pt_query");
       return YASPS_OK;
@@ -839,8 +849,8 @@ yasps_status detect_pairs(yasps_system* s, const double* P) {
     LAUNCH_CHECK(s, "k_boxes");
     grid_dev g;
     RC(build_grid(s, s->nse, bb.blo, bb.bhi, &g));
-    RC(two_pass(s, s->nse, [&](int mode, int* cnt, const int* off, int* out) -> yasps_status {
-      k_ee_query<<<blocks_for(s->nse, 128), 128, 0, s->stream>>>(s->nse, Tp, P, g, bb.alo, bb.ahi, sh, mode, cnt, off,
+    RC(two_pass(s, s->nse, [&](int mode, int total, int* cnt, const int* off, int* out) -> yasps_status {
+      k_ee_query<<<blocks_for(s->nse, 128), 128, 0, s->stream>>>(total, s->nse, Tp, P, g, bb.alo, bb.ahi, sh, mode, cnt, off,
                                                                 out, 0.0, 0, nullptr);
       LAUNCH_CHECK(s, "k_ee_query");
       return YASPS_OK;
@@ -892,7 +902,7 @@ yasps_status barrier_energy(yasps_system* s, const double* P, double* E_host) {
   ksum* part = as<ksum>(pb);
   CK(s, cudaMemsetAsync(part, 0, sizeof(ksum) * (npart + 4), s->stream));
   if (s->nsv > 0 && s->npl > 0) {
-    k_pg_query<<<nblk_v, 128, 0, s->stream>>>(s->nsv, s->npl, Tp, P, as<double>(s->planes), sh, 2, nullptr, nullptr,
+    k_pg_query<<<nblk_v, 128, 0, s->stream>>>(0, s->nsv, s->npl, Tp, P, as<double>(s->planes), sh, 2, nullptr, nullptr,
                                               nullptr, s->prm.kappa, s->prm.barrier_form, part);
     LAUNCH_CHECK(s, "k_pg_query(E)");
   }
@@ -906,7 +916,7 @@ yasps_status barrier_energy(yasps_system* s, const double* P, double* E_host) {
     LAUNCH_CHECK(s, "k_boxes");
     grid_dev g;
     RC(build_grid(s, s->nst, bb.blo, bb.bhi, &g));
-    k_pt_query<<<nblk_v, 128, 0, s->stream>>>(s->nsv, Tp, P, g, bb.alo, bb.ahi, sh, 2, nullptr, nullptr, nullptr,
+    k_pt_query<<<nblk_v, 128, 0, s->stream>>>(0, s->nsv, Tp, P, g, bb.alo, bb.ahi, sh, 2, nullptr, nullptr, nullptr,
                                               s->prm.kappa, s->prm.barrier_form, part + nblk_v);
     LAUNCH_CHECK(s, "k_pt_query(E)");
   }
@@ -920,7 +930,7 @@ yasps_status barrier_energy(yasps_system* s, const double* P, double* E_host) {
     LAUNCH_CHECK(s, "k_boxes");
     grid_dev g;
     RC(build_grid(s, s->nse, bb.blo, bb.bhi, &g));
-    k_ee_query<<<nblk_e, 128, 0, s->stream>>>(s->nse, Tp, P, g, bb.alo, bb.ahi, sh, 2, nullptr, nullptr, nullptr,
+    k_ee_query<<<nblk_e, 128, 0, s->stream>>>(0, s->nse, Tp, P, g, bb.alo, bb.ahi, sh, 2, nullptr, nullptr, nullptr,
                                               s->prm.kappa, s->prm.barrier_form, part + 2 * nblk_v);
     LAUNCH_CHECK(s, "k_ee_query(E)");
   }
