@@ -208,7 +208,8 @@ yasps_status yasps_energy(yasps_system* sys, const double* x_dev, const double* 
  * gradient and PSD-projected Hessian (project != 0; exact otherwise),
  * scattered into the system's gradient and H = H_static + H_dynamic (Sec.
  * "Index Computation") by atomic addition (App. B "Assembly"), then the
- * block-Jacobi inverse (App. D).  Uses the pair lists of the last
+ * block-Jacobi inverse (App. D; only when YASPS_TERM_INERTIA is in the mask,
+ * since the inverse needs the mass-regularised full Hessian).  Uses the pair lists of the last
  * yasps_detect_pairs, which must have been called at the same x.  Zeroes g and
  * H first.  Asynchronous. */
 yasps_status yasps_eval_local(yasps_system* sys, const double* x_dev, const double* xtilde_dev, int term_mask,

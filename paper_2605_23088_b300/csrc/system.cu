@@ -387,7 +387,8 @@ static yasps_status eval_impl(yasps_system* s, const double* x, const double* xt
   RC(zero_system(s));
   RC(launch_eval_static(s, x, xtil, mask, project));
   if (mask & YASPS_TERM_BARRIER) RC(launch_eval_barrier(s, project));
-  RC(launch_bjacobi(s));
+  // the block-Jacobi preconditioner needs the mass-regularised full Hessian
+  if (mask & YASPS_TERM_INERTIA) RC(launch_bjacobi(s));
   return YASPS_OK;
 }
 
