@@ -260,6 +260,31 @@ yasps_status yasps_get_fixed_positions(yasps_system* sys, double* P_host);
  * counter incremented at every launch). */
 long long yasps_kernel_launches(const yasps_system* sys);
 
+/* Stage timing for measurement.  While enabled, the library brackets every
+ * instance of a stage with CUDA events recorded on its own stream and keeps,
+ * per stage, the count, the summed event time and the algorithmic bytes the
+ * stage must move (inputs read once, unique outputs written once):
+ *   YASPS_STAGE_SPMV     one H d product inside PCG: the fused direction
+ *                        update + diagonal product and the two upper BSR parts
+ *                        (bytes: nnzb (9 s + 4) + n (9 s + 4) + 4 * 3 s n,
+ *                        s = bytes per Hessian scalar, n = nodes);
+ *   YASPS_STAGE_TET      the Neo-Hookean tet gradient / projected-Hessian kernel;
+ *   YASPS_STAGE_BARRIER  the contact-barrier evaluation kernels;
+ *   YASPS_STAGE_PCG      one whole PCG solve.
+ * Enabling (enable != 0) resets the counters.  yasps_profile_get synchronises. */
+#define YASPS_STAGE_SPMV 0
+#define YASPS_STAGE_TET 1
+#define YASPS_STAGE_BARRIER 2
+#define YASPS_STAGE_PCG 3
+#define YASPS_NUM_STAGES 4
+typedef struct {
+  long long count;
+  double ms;
+  double bytes;
+} yasps_stage_stats;
+yasps_status yasps_profile_enable(yasps_system* sys, int enable);
+yasps_status yasps_profile_get(yasps_system* sys, int stage, yasps_stage_stats* out);
+
 #ifdef __cplusplus
 }
 #endif

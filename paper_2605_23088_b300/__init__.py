@@ -27,8 +27,10 @@ EXPORTS = [
     "yasps_set_params", "yasps_get_sizes", "yasps_initial_state", "yasps_vertex_positions", "yasps_xtilde",
     "yasps_detect_pairs", "yasps_export_pairs", "yasps_energy", "yasps_eval_local", "yasps_assemble",
     "yasps_export_bsr", "yasps_export_gradient", "yasps_spmv", "yasps_pcg_solve", "yasps_ccd_bound", "yasps_step",
-    "yasps_set_fixed_positions", "yasps_get_fixed_positions", "yasps_kernel_launches",
+    "yasps_set_fixed_positions", "yasps_get_fixed_positions", "yasps_kernel_launches", "yasps_profile_enable",
+    "yasps_profile_get",
 ]
+STAGE_SPMV, STAGE_TET, STAGE_BARRIER, STAGE_PCG = 0, 1, 2, 3
 
 
 class YaspsError(RuntimeError):
@@ -70,6 +72,10 @@ class StepStats(ctypes.Structure):
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class StageStats(ctypes.Structure):
+    _fields_ = [("count", ctypes.c_longlong), ("ms", ctypes.c_double), ("bytes", ctypes.c_double)]
 
 
 class Allocator(ctypes.Structure):
@@ -310,3 +316,11 @@ class System:
 
     def kernel_launches(self):
         return lib().yasps_kernel_launches(self.h)
+
+    def profile_enable(self, on=True):
+        self._check(lib().yasps_profile_enable(self.h, ctypes.c_int(int(on))))
+
+    def profile_get(self, stage):
+        st = StageStats()
+        self._check(lib().yasps_profile_get(self.h, ctypes.c_int(stage), ctypes.byref(st)))
+        return {"count": st.count, "ms": st.ms, "bytes": st.bytes}

@@ -604,10 +604,15 @@ yasps_status eval_static_t(yasps_system* s, const double* x, const double* xtil,
     LAUNCH_CHECK(s, "k_inertia_body");
   }
   if ((mask & YASPS_TERM_TET) && s->nt > 0) {
+    // algorithmic bytes: per-tet inputs once, positions once, unique outputs once
+    const double bytes = (double)s->nt * (16 + 16 + 96 + 24) + 24.0 * s->nv + 24.0 * s->nn +
+                         (double)sizeof(T) * 9.0 * ((double)s->Hs.nnzb + s->nn);
+    cudaEvent_t pa = prof_begin(s);
     k_snh<T><<<blocks_for(s->nt, 128), 128, 0, s->stream>>>(s->nt, as<int>(s->tet_v), as<int>(s->tet_n),
                                                            as<double>(s->tet_rest), as<int>(s->tet_slot), P, h2,
                                                            project, g, diag, vals);
     LAUNCH_CHECK(s, "k_snh");
+    prof_end(s, YASPS_STAGE_TET, pa, bytes);
   }
   if ((mask & YASPS_TERM_MEMBRANE) && s->nc > 0) {
     k_membrane<T><<<blocks_for(s->nc, 128), 128, 0, s->stream>>>(s->nc, as<int>(s->tri_v), as<int>(s->tri_n),

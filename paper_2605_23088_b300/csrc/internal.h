@@ -95,7 +95,24 @@ struct yasps_system {
   gbuf vec[10];   // PCG vectors
   gbuf stepv[6];  // step vectors
   cudaEvent_t ev[8] = {};
+
+  // stage profiler (yasps_profile_*)
+  bool prof_on = false;
+  struct pending {
+    int stage;
+    cudaEvent_t a, b;
+    double bytes;
+  };
+  std::vector<pending> prof_pending;
+  std::vector<cudaEvent_t> prof_pool;
+  yasps_stage_stats prof_acc[YASPS_NUM_STAGES] = {};
 };
+
+// stage profiler: prof_begin returns an event recorded on the stream (or null
+// when profiling is off); prof_end records the closing event.
+cudaEvent_t prof_begin(yasps_system* s);
+void prof_end(yasps_system* s, int stage, cudaEvent_t a, double bytes);
+void prof_resolve(yasps_system* s);  // synchronises and folds pending pairs into the counters
 
 #define SYS_FAIL(s, code, msg) \
   do {                         \

@@ -410,12 +410,17 @@ yasps_status pcg_inner(yasps_system* s, const double* rhs, double* p, double tol
   k_pcg_init<T, V><<<nblk_u, PT_, 0, s->stream>>>(s->nfree, s->nb, rhs, Mi, x, r, z, d, part, sc);
   LAUNCH_CHECK(s, "k_pcg_init");
   const int check_every = 8;
+  const double es = sizeof(T);
+  const double spmv_bytes = (double)(s->Hs.nnzb + s->Hd.nnzb) * (9 * es + 4) + (double)s->nn * (9 * es + 4) +
+                            4.0 * 3.0 * sizeof(V) * s->nn;
   int it = 0;
   for (;;) {
     for (int k = 0; k < check_every; ++k) {
+      cudaEvent_t pa = prof_begin(s);
       k_pcg_dir<T, V><<<blocks_for(s->nn, PT_), PT_, 0, s->stream>>>(s->nn, D, z, d, q, sc);
       LAUNCH_CHECK(s, "k_pcg_dir");
       RC((spmv_t<T, V>(s, d, q, &sc->done)));
+      prof_end(s, YASPS_STAGE_SPMV, pa, spmv_bytes);
       k_pcg_alpha<V><<<nblk_dot, PT_, 0, s->stream>>>(n3, d, q, part, sc);
       LAUNCH_CHECK(s, "k_pcg_alpha");
       k_pcg_update<T, V><<<nblk_u, PT_, 0, s->stream>>>(s->nfree, s->nb, Mi, x, r, z, d, q, part, sc);
@@ -425,6 +430,17 @@ yasps_status pcg_inner(yasps_system* s, const double* rhs, double* p, double tol
     CK(s, cudaMemcpyAsync(&h, sc, sizeof(pcg_dev), cudaMemcpyDeviceToHost, s->stream));
     CK(s, cudaStreamSynchronize(s->stream));
     if (h.done || h.iters >= maxit || it >= maxit) break;
+  }
+  if (s->prof_on) {
+    // the iterations launched after convergence returned at once: drop their
+    // SpMV samples so the stage average covers real products only
+    prof_resolve(s);
+    const long long wasted = (long long)it - h.iters;
+    if (wasted > 0) {
+      auto& a = s->prof_acc[YASPS_STAGE_SPMV];
+      a.count -= wasted;
+      a.bytes -= wasted * spmv_bytes;
+    }
   }
   k_add_to<V><<<blocks_for(n3, 256), 256, 0, s->stream>>>(n3, p, x);
   LAUNCH_CHECK(s, "k_add_to");
@@ -454,6 +470,9 @@ yasps_status rz64(yasps_system* s, const double* r, double* out) {
 }  // namespace
 
 // ======================================================================== API
+yasps_status pcg_solve_impl(yasps_system* s, const double* rhs, double* p, double tol, int maxit, int* iters,
+                            double* rel_res);
+
 yasps_status alloc_hessian(yasps_system* s) {
   const size_t es = (s->prm.precision == 1) ? sizeof(float) : sizeof(double);
   s->hess_precision = (s->prm.precision == 1) ? 1 : 0;
@@ -501,6 +520,14 @@ yasps_status spmv64(yasps_system* s, const double* x, double* y) {
 
 yasps_status pcg_solve(yasps_system* s, const double* rhs, double* p, double tol, int maxit, int* iters,
                        double* rel_res) {
+  cudaEvent_t pa = prof_begin(s);
+  yasps_status rc = pcg_solve_impl(s, rhs, p, tol, maxit, iters, rel_res);
+  prof_end(s, YASPS_STAGE_PCG, pa, 0.0);
+  return rc;
+}
+
+yasps_status pcg_solve_impl(yasps_system* s, const double* rhs, double* p, double tol, int maxit, int* iters,
+                            double* rel_res) {
   const int n3 = 3 * s->nn;
   if (maxit <= 0) maxit = 10 * n3;
   CK(s, cudaMemsetAsync(p, 0, sizeof(double) * n3, s->stream));

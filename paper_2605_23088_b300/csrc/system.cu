@@ -71,8 +71,61 @@ static void all_bufs(yasps_system* s, std::vector<gbuf*>& v) {
   for (auto& b : s->stepv) v.push_back(&b);
 }
 
+// ---------------------------------------------------------------- profiler
+cudaEvent_t prof_begin(yasps_system* s) {
+  if (!s->prof_on) return nullptr;
+  cudaEvent_t e;
+  if (!s->prof_pool.empty()) {
+    e = s->prof_pool.back();
+    s->prof_pool.pop_back();
+  } else if (cudaEventCreate(&e) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  cudaEventRecord(e, s->stream);
+  return e;
+}
+void prof_end(yasps_system* s, int stage, cudaEvent_t a, double bytes) {
+  if (!a) return;
+  cudaEvent_t b = prof_begin(s);
+  if (!b) return;
+  s->prof_pending.push_back({stage, a, b, bytes});
+  if (s->prof_pending.size() >= 256) prof_resolve(s);
+}
+void prof_resolve(yasps_system* s) {
+  if (s->prof_pending.empty()) return;
+  cudaStreamSynchronize(s->stream);
+  for (auto& p : s->prof_pending) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, p.a, p.b);
+    auto& acc = s->prof_acc[p.stage];
+    acc.count += 1;
+    acc.ms += ms;
+    acc.bytes += p.bytes;
+    s->prof_pool.push_back(p.a);
+    s->prof_pool.push_back(p.b);
+  }
+  s->prof_pending.clear();
+}
+
 // ======================================================================== ABI
 extern "C" {
+
+yasps_status yasps_profile_enable(yasps_system* s, int enable) {
+  if (!s) return YASPS_E_INVAL;
+  prof_resolve(s);
+  s->prof_on = enable != 0;
+  if (enable)
+    for (auto& a : s->prof_acc) a = yasps_stage_stats{0, 0.0, 0.0};
+  return YASPS_OK;
+}
+
+yasps_status yasps_profile_get(yasps_system* s, int stage, yasps_stage_stats* out) {
+  if (!s || !out || stage < 0 || stage >= YASPS_NUM_STAGES) return YASPS_E_INVAL;
+  prof_resolve(s);
+  *out = s->prof_acc[stage];
+  return YASPS_OK;
+}
 
 void yasps_default_params(yasps_params* p) {
   std::memset(p, 0, sizeof(*p));
@@ -260,6 +313,8 @@ yasps_status yasps_build_system(const yasps_scene_desc* scene, const yasps_param
 
 void yasps_destroy(yasps_system* s) {
   if (!s) return;
+  prof_resolve(s);
+  for (auto e : s->prof_pool) cudaEventDestroy(e);
   std::vector<gbuf*> bufs;
   all_bufs(s, bufs);
   for (gbuf* b : bufs) release(s, *b);
@@ -386,7 +441,14 @@ static yasps_status eval_impl(yasps_system* s, const double* x, const double* xt
   ENSURE(s, s->Hd.vals, es * 9 * ((size_t)s->Hd.nnzb + 1));
   RC(zero_system(s));
   RC(launch_eval_static(s, x, xtil, mask, project));
-  if (mask & YASPS_TERM_BARRIER) RC(launch_eval_barrier(s, project));
+  if (mask & YASPS_TERM_BARRIER) {
+    const double es = (s->hess_precision == 1) ? 4.0 : 8.0;
+    const double bytes = (double)(s->npt + s->nee + s->npg) * (12.0 + 4 * 24.0) + (double)s->nkeys * 4.0 +
+                         es * 9.0 * ((double)s->Hd.nnzb + s->nn) + 24.0 * s->nn;
+    cudaEvent_t pa = prof_begin(s);
+    RC(launch_eval_barrier(s, project));
+    prof_end(s, YASPS_STAGE_BARRIER, pa, bytes);
+  }
   // the block-Jacobi preconditioner needs the mass-regularised full Hessian
   if (mask & YASPS_TERM_INERTIA) RC(launch_bjacobi(s));
   return YASPS_OK;

@@ -354,12 +354,12 @@ def tori_scene(nx=4, ny=4, nz=4, spacing=0.24, R=0.08, r=0.03, h=0.008, seed=0, 
     Rs = random_rotations(rng, n)
     Es = np.exp(rng.uniform(np.log(1e4), np.log(1e6), n))
     parts = _empty_parts()
-    margin = (box - spacing * (nx - 1)) / 2
+    margin = [(box - spacing * (n_ - 1)) / 2 for n_ in (nx, ny, nz)]
     idx = 0
     for k in range(nz):
         for j in range(ny):
             for i in range(nx):
-                c = np.array([margin + i * spacing, margin + j * spacing, margin + k * spacing])
+                c = np.array([margin[0] + i * spacing, margin[1] + j * spacing, margin[2] + k * spacing])
                 v = tv @ Rs[idx].T + c
                 _add_soft(parts, v, tt, Es[idx], nu, rho)
                 idx += 1

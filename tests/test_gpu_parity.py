@@ -325,7 +325,7 @@ def test_scene_without_contact_surfaces(yb):
     G = yb.System(s)
     O = oracle.OracleSystem(s, pcg_tol=1e-12)
     x, v = O.initial_state()
-    assert G.pairs(T(x)) == tuple(np.zeros((0, 3), np.int32) for _ in range(3)) or all(len(a) == 0 for a in G.pairs(T(x)))
+    assert all(len(a) == 0 for a in G.pairs(T(x)))
     compare_assembly(G, O, x + 1e-3 * np.random.default_rng(0).normal(size=x.shape), v)
 
 
