@@ -285,6 +285,32 @@ typedef struct {
 yasps_status yasps_profile_enable(yasps_system* sys, int enable);
 yasps_status yasps_profile_get(yasps_system* sys, int stage, yasps_stage_stats* out);
 
+/* Block-Jacobi PCG that allocates no device memory (the paper has no
+ * counterpart; it is an interface for callers that cannot allocate).
+ * Some callers may not call cudaMalloc / cudaFree at solve time -- code inside
+ * another framework's fixed memory budget, real-time loops that forbid
+ * allocation after start-up, hosts that only lend their own buffers.  This
+ * entry point solves H p = rhs for a symmetric positive-definite matrix the
+ * caller has assembled in device memory, in the library's layout: n_nodes 3x3
+ * diagonal blocks diag_dev [n_nodes][9] and nnzb upper off-diagonal blocks
+ * vals_dev [nnzb][9] at (row_dev[k], col_dev[k]) with row < col (repeated
+ * coordinates are summed), all FP64, row-major blocks.  rhs_dev, p_dev:
+ * [n_nodes][3] FP64 (p is overwritten).  Preconditioner: 3x3 block Jacobi.
+ * Stops when r^T z <= rel_tol^2 r0^T z0 or after max_iter iterations
+ * (<= 0: 10 * 3 n_nodes).  iters, rel_res (host, nullable) as in
+ * yasps_pcg_solve; err (nullable, err_len bytes) receives a message on failure.
+ * Every temporary lives in one fixed __device__ array of about 11 MB that each
+ * GPU loading the library holds until exit, so n_nodes is limited to 65536:
+ * larger problems get YASPS_E_CAPACITY.  All calls share that array: calls
+ * whose work overlaps on the GPU race and must be serialised.  The first call
+ * on a device looks up the array's device address; make it before any stream
+ * capture.  Work runs on cuda_stream; the call returns after synchronising it.
+ * Errors: E_INVAL, E_CAPACITY, E_NAN (not positive definite), E_NOCONV, E_CUDA. */
+yasps_status yasps_pcg_solve_static(int n_nodes, int nnzb, const int* row_dev, const int* col_dev,
+                                    const double* vals_dev, const double* diag_dev, const double* rhs_dev,
+                                    double* p_dev, double rel_tol, int max_iter, void* cuda_stream, int* iters,
+                                    double* rel_res, char* err, int err_len);
+
 #ifdef __cplusplus
 }
 #endif

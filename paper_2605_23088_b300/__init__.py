@@ -28,7 +28,7 @@ EXPORTS = [
     "yasps_detect_pairs", "yasps_export_pairs", "yasps_energy", "yasps_eval_local", "yasps_assemble",
     "yasps_export_bsr", "yasps_export_gradient", "yasps_spmv", "yasps_pcg_solve", "yasps_ccd_bound", "yasps_step",
     "yasps_set_fixed_positions", "yasps_get_fixed_positions", "yasps_kernel_launches", "yasps_profile_enable",
-    "yasps_profile_get",
+    "yasps_profile_get", "yasps_pcg_solve_static",
 ]
 STAGE_SPMV, STAGE_TET, STAGE_BARRIER, STAGE_PCG = 0, 1, 2, 3
 
@@ -118,6 +118,33 @@ def default_params(**kw):
 
 def _ptr(t):
     return ctypes.c_void_p(t.data_ptr())
+
+
+def pcg_solve_static(n_nodes, row, col, vals, diag, rhs, rel_tol=1e-4, max_iter=0, stream=None):
+    """Block-Jacobi PCG that allocates no device memory (yasps_pcg_solve_static).
+
+    For callers that may not allocate at solve time: every argument is a CUDA
+    tensor the caller owns (row/col int32 [nnzb], vals float64 [nnzb,3,3], diag
+    float64 [n_nodes,3,3], rhs float64 [n_nodes,3]); the temporaries live in a
+    fixed device array inside the library (at most 65536 nodes).  Returns
+    (p, iters, rel_res) with p a new tensor like rhs.
+    """
+    import torch
+
+    p = torch.empty_like(rhs)
+    it, rel = ctypes.c_int(), ctypes.c_double()
+    err = ctypes.create_string_buffer(256)
+    s = stream if stream is not None else torch.cuda.current_stream()
+    nnzb = int(row.numel())
+    null = ctypes.c_void_p(0)
+    rc = lib().yasps_pcg_solve_static(ctypes.c_int(n_nodes), ctypes.c_int(nnzb), _ptr(row) if nnzb else null,
+                                      _ptr(col) if nnzb else null, _ptr(vals) if nnzb else null, _ptr(diag),
+                                      _ptr(rhs), _ptr(p), ctypes.c_double(rel_tol), ctypes.c_int(max_iter),
+                                      ctypes.c_void_p(s.cuda_stream), ctypes.byref(it), ctypes.byref(rel), err,
+                                      ctypes.c_int(len(err)))
+    if rc != YASPS_OK:
+        raise YaspsError(rc, err.value.decode())
+    return p, it.value, rel.value
 
 
 class System:
