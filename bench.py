@@ -189,6 +189,7 @@ def native(args):
         status = []
         with ClockSampler(local) as clk:
             torch.cuda.synchronize()
+            torch.cuda.nvtx.range_push(f"timed_{precision_name}")
             e0.record(stream)
             for _ in range(steps):
                 st = system.step(xs, vs, raise_on_error=False)
@@ -198,9 +199,10 @@ def native(args):
                 status.append(st["rc"])
             e1.record(stream)
             torch.cuda.synchronize()
+            torch.cuda.nvtx.range_pop()
         ms = e0.elapsed_time(e1)
         launches = system.kernel_launches() - l0
-        prof = {k: system.profile_get(i) for i, k in enumerate(["spmv", "tet", "barrier", "pcg"])} if profile else None
+        prof = {k: system.profile_get(i) for i, k in enumerate(yb.STAGE_NAMES)} if profile else None
         if profile:
             system.profile_enable(False)
         barrier(world)

@@ -270,13 +270,21 @@ long long yasps_kernel_launches(const yasps_system* sys);
  *                        s = bytes per Hessian scalar, n = nodes);
  *   YASPS_STAGE_TET      the Neo-Hookean tet gradient / projected-Hessian kernel;
  *   YASPS_STAGE_BARRIER  the contact-barrier evaluation kernels;
- *   YASPS_STAGE_PCG      one whole PCG solve.
+ *   YASPS_STAGE_PCG      one whole PCG solve;
+ *   YASPS_STAGE_DETECT   contact detection + dynamic BSR layout (in yasps_step);
+ *   YASPS_STAGE_EVAL     the whole local evaluation incl. block-Jacobi (in yasps_step);
+ *   YASPS_STAGE_CCD      the CCD step bound (in yasps_step);
+ *   YASPS_STAGE_LS       the line search's energy evaluations (in yasps_step).
  * Enabling (enable != 0) resets the counters.  yasps_profile_get synchronises. */
 #define YASPS_STAGE_SPMV 0
 #define YASPS_STAGE_TET 1
 #define YASPS_STAGE_BARRIER 2
 #define YASPS_STAGE_PCG 3
-#define YASPS_NUM_STAGES 4
+#define YASPS_STAGE_DETECT 4
+#define YASPS_STAGE_EVAL 5
+#define YASPS_STAGE_CCD 6
+#define YASPS_STAGE_LS 7
+#define YASPS_NUM_STAGES 8
 typedef struct {
   long long count;
   double ms;

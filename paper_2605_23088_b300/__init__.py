@@ -30,7 +30,8 @@ EXPORTS = [
     "yasps_set_fixed_positions", "yasps_get_fixed_positions", "yasps_kernel_launches", "yasps_profile_enable",
     "yasps_profile_get", "yasps_pcg_solve_static",
 ]
-STAGE_SPMV, STAGE_TET, STAGE_BARRIER, STAGE_PCG = 0, 1, 2, 3
+STAGE_SPMV, STAGE_TET, STAGE_BARRIER, STAGE_PCG, STAGE_DETECT, STAGE_EVAL, STAGE_CCD, STAGE_LS = range(8)
+STAGE_NAMES = ["spmv", "tet", "barrier", "pcg", "detect", "eval", "ccd", "line_search"]
 
 
 class YaspsError(RuntimeError):

@@ -586,9 +586,13 @@ extern "C" yasps_status yasps_step(yasps_system* s, double* x, double* v, yasps_
   double pinf = 0.0, alpha = 0.0;
   for (it = 0; it < s->prm.newton_max_iter; ++it) {
     cudaEventRecord(s->ev[0], s->stream);
+    cudaEvent_t pd = prof_begin(s);
     RC(launch_positions(s, x, as<double>(s->P)));
     RC(detect_pairs(s, as<double>(s->P)));
+    prof_end(s, YASPS_STAGE_DETECT, pd, 0.0);
+    cudaEvent_t pe = prof_begin(s);
     RC(eval_impl(s, x, xtil, YASPS_TERM_ALL, 1));
+    prof_end(s, YASPS_STAGE_EVAL, pe, 0.0);
     cudaEventRecord(s->ev[1], s->stream);
     int pit = 0;
     double rel = 0.0;
@@ -615,8 +619,11 @@ extern "C" yasps_status yasps_step(yasps_system* s, double* x, double* v, yasps_
     st.n_pt = s->npt; st.n_ee = s->nee; st.n_pg = s->npg;
     if (pinf <= s->prm.newton_tol) break;
     cudaEventRecord(s->ev[3], s->stream);
+    cudaEvent_t pc = prof_begin(s);
     RC(ccd_bound(s, x, p, &alpha));
+    prof_end(s, YASPS_STAGE_CCD, pc, 0.0);
     cudaEventRecord(s->ev[4], s->stream);
+    cudaEvent_t pl = prof_begin(s);
     double E0 = 0.0, E1 = 0.0;
     RC(energy_impl(s, x, xtil, &E0, nullptr));
     int ls = 0;
@@ -627,6 +634,7 @@ extern "C" yasps_status yasps_step(yasps_system* s, double* x, double* v, yasps_
       if (E1 <= E0) break;
       alpha *= 0.5;
     }
+    prof_end(s, YASPS_STAGE_LS, pl, 0.0);
     cudaEventRecord(s->ev[5], s->stream);
     cudaEventSynchronize(s->ev[5]);
     st.t_ccd_ms += elapsed(s->ev[3], s->ev[4]);
