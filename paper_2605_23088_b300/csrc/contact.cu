@@ -683,6 +683,124 @@ __global__ void k_reduce_ksum(const ksum* __restrict__ part, int n, double* __re
   if (threadIdx.x == 0) *out = k.s + k.c;
 }
 
+// ---------------------------------------------------------------- swept candidates
+// Candidate pairs of one Newton iteration: query boxes swept over [x, x - p]
+// and grown by dhat, against swept (not grown) boxes of the other set.  Every
+// pair that comes within dhat anywhere on the segment, and every pair the CCD
+// must examine, is in the list.  mode 0: count per query primitive, mode 1:
+// write (a, b) sorted by b.
+__global__ void k_cand_query(int total, int kind, int nA, topo T, grid_dev g, const double* __restrict__ alo,
+                             const double* __restrict__ ahi, int mode, int* __restrict__ cnt,
+                             const int* __restrict__ off, int* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nA) return;
+  int c = 0;
+  const int base = (mode == 1) ? off[i] : 0;
+  const int lim = (mode == 1) ? ((i + 1 < nA) ? off[i + 1] : total) : 0;
+  const int a = (kind == 0) ? T.svert[i] : i;
+  grid_visit(g, alo + 3 * i, ahi + 3 * i, [&](int j) {
+    if (kind == 0) {
+      if (pt_excluded(T, a, T.stri[3 * j], T.stri[3 * j + 1], T.stri[3 * j + 2])) return;
+    } else {
+      if (j <= i) return;
+      if (ee_excluded(T, T.sedge[2 * i], T.sedge[2 * i + 1], T.sedge[2 * j], T.sedge[2 * j + 1])) return;
+    }
+    if (mode == 1) {
+      if (base + c >= lim) { dev_flag(T.status, DEV_CAPACITY); return; }
+      out[2 * (size_t)(base + c)] = a;
+      out[2 * (size_t)(base + c) + 1] = j;
+    }
+    ++c;
+  });
+  if (mode == 0) cnt[i] = c;
+  if (mode == 1) {
+    c = min(c, lim - base);
+    int* o = out + 2 * (size_t)base;
+    for (int q = 1; q < c; ++q) {
+      const int kb = o[2 * q + 1];
+      int r = q - 1;
+      while (r >= 0 && o[2 * r + 1] > kb) { o[2 * (r + 1) + 1] = o[2 * r + 1]; --r; }
+      o[2 * (r + 1) + 1] = kb;
+    }
+  }
+}
+
+__device__ __forceinline__ void cand_vertices(int kind, const int* cand, size_t k, const topo& T, int* ids) {
+  const int a = cand[2 * k], b = cand[2 * k + 1];
+  if (kind == 0) {
+    ids[0] = a; ids[1] = T.stri[3 * b]; ids[2] = T.stri[3 * b + 1]; ids[3] = T.stri[3 * b + 2];
+  } else {
+    ids[0] = T.sedge[2 * a]; ids[1] = T.sedge[2 * a + 1]; ids[2] = T.sedge[2 * b]; ids[3] = T.sedge[2 * b + 1];
+  }
+}
+
+// additive CCD over the candidate list; one atomic min per block
+__global__ void k_ccd_cand(int kind, int n, const int* __restrict__ cand, topo T, const double* __restrict__ P0,
+                           const double* __restrict__ D, double gap, int max_iter, double* __restrict__ tmin, int* status) {
+  const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  double best = 1.0;
+  bool capped = false;
+  if (k < n) {
+    int ids[4];
+    cand_vertices(kind, cand, (size_t)k, T, ids);
+    d3 x[4], dx[4];
+    for (int q = 0; q < 4; ++q) { x[q] = ld3(P0, ids[q]); dx[q] = ld3(D, ids[q]); }
+    best = accd(kind, x, dx, gap, 1.0, max_iter, &capped);
+  }
+  if (capped) dev_flag(status, DEV_ITERCAP);
+  for (int o = 16; o > 0; o >>= 1) best = fmin(best, __shfl_xor_sync(0xffffffffu, best, o));
+  __shared__ double sh[32];
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = best;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double b = sh[0];
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) b = fmin(b, sh[w]);
+    if (b < 1.0) atomic_min_pos(tmin, b);
+  }
+}
+
+// barrier energy over the candidate list at positions P (fixed grid: deterministic)
+__global__ void k_energy_cand(int kind, int n, const int* __restrict__ cand, topo T, const double* __restrict__ P,
+                              double sh, double kappa, int form, ksum* __restrict__ part) {
+  ksum acc{0.0, 0.0};
+  for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
+    int ids[4];
+    cand_vertices(kind, cand, (size_t)k, T, ids);
+    double s;
+    if (kind == 0) dist::pt_classify(ld3(P, ids[0]), ld3(P, ids[1]), ld3(P, ids[2]), ld3(P, ids[3]), &s);
+    else dist::ee_classify(ld3(P, ids[0]), ld3(P, ids[1]), ld3(P, ids[2]), ld3(P, ids[3]), &s);
+    if (s < sh) kadd(acc, kappa * barrier_fn(s, sh, form).b);
+  }
+  acc = block_ksum(acc);
+  if (threadIdx.x == 0) part[blockIdx.x] = acc;
+}
+
+// active pairs among the candidates at positions P: flag + subtype
+__global__ void k_filter_cand(int kind, int n, const int* __restrict__ cand, topo T, const double* __restrict__ P,
+                              double sh, int* __restrict__ flag, int* __restrict__ sub) {
+  const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  int ids[4];
+  cand_vertices(kind, cand, (size_t)k, T, ids);
+  double s;
+  int st;
+  if (kind == 0) st = dist::pt_classify(ld3(P, ids[0]), ld3(P, ids[1]), ld3(P, ids[2]), ld3(P, ids[3]), &s);
+  else st = dist::ee_classify(ld3(P, ids[0]), ld3(P, ids[1]), ld3(P, ids[2]), ld3(P, ids[3]), &s);
+  flag[k] = (s < sh) ? 1 : 0;
+  sub[k] = st;
+}
+__global__ void k_compact_cand(int n, const int* __restrict__ cand, const int* __restrict__ flag,
+                               const int* __restrict__ off, const int* __restrict__ sub, int* __restrict__ out) {
+  const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  const int i = off[k];
+  if (k + 1 < n ? off[k + 1] > i : flag[k]) {
+    out[3 * (size_t)i] = cand[2 * k];
+    out[3 * (size_t)i + 1] = cand[2 * k + 1];
+    out[3 * (size_t)i + 2] = sub[k];
+  }
+}
+
 // ======================================================================== host
 topo make_topo(yasps_system* s) {
   return topo{as<int>(s->vnode), as<int>(s->vbody), as<int>(s->stri), as<int>(s->sedge), as<int>(s->svert),
@@ -943,14 +1061,19 @@ yasps_status barrier_energy(yasps_system* s, const double* P, double* E_host) {
 }
 
 yasps_status ccd_bound(yasps_system* s, const double* x, const double* p, double* alpha_host) {
+  RC(swept_candidates(s, x, p));
+  return ccd_candidates(s, alpha_host);
+}
+
+// ======================================================================== candidates
+yasps_status swept_candidates(yasps_system* s, const double* x, const double* p) {
   const topo Tp = make_topo(s);
   const size_t nv3 = 3 * (size_t)s->nv;
-  ENSURE(s, s->stepv[3], sizeof(double) * (3 * (size_t)s->nn + 1));  // x - p
-  ENSURE(s, s->stepv[4], sizeof(double) * (2 * nv3 + 2));           // P1, D
+  ENSURE(s, s->stepv[3], sizeof(double) * (3 * (size_t)s->nn + 1));
+  ENSURE(s, s->stepv[4], sizeof(double) * (2 * nv3 + 2));
   double* x1 = as<double>(s->stepv[3]);
   double* P1 = as<double>(s->stepv[4]);
   double* D = P1 + nv3;
-  double* tmin = D + nv3;  // one double
   double* P0 = as<double>(s->P);
   RC(launch_positions(s, x, P0));
   k_sub<<<blocks_for(3LL * s->nn, 256), 256, 0, s->stream>>>(3 * s->nn, x, p, x1);
@@ -958,6 +1081,51 @@ yasps_status ccd_bound(yasps_system* s, const double* x, const double* p, double
   RC(launch_positions(s, x1, P1));
   k_sub<<<blocks_for((long long)nv3, 256), 256, 0, s->stream>>>((int)nv3, P1, P0, D);
   LAUNCH_CHECK(s, "k_sub");
+  s->ncpt = s->ncee = 0;
+  for (int kind = 0; kind < 2; ++kind) {
+    const int nA = kind == 0 ? s->nsv : s->nse;
+    const int nB = kind == 0 ? s->nst : s->nse;
+    if (nA == 0 || nB == 0 || (kind == 1 && nA < 2)) continue;
+    boxbufs bb;
+    RC(alloc_boxes(s, &bb));
+    if (kind == 0) {
+      k_boxes<<<blocks_for(nA, 256), 256, 0, s->stream>>>(nA, 1, as<int>(s->svert), P0, P1, s->prm.dhat, bb.alo, bb.ahi);
+      LAUNCH_CHECK(s, "k_boxes");
+      k_boxes<<<blocks_for(nB, 256), 256, 0, s->stream>>>(nB, 3, as<int>(s->stri), P0, P1, 0.0, bb.blo, bb.bhi);
+      LAUNCH_CHECK(s, "k_boxes");
+    } else {
+      k_boxes<<<blocks_for(nA, 256), 256, 0, s->stream>>>(nA, 2, as<int>(s->sedge), P0, P1, s->prm.dhat, bb.alo, bb.ahi);
+      LAUNCH_CHECK(s, "k_boxes");
+      k_boxes<<<blocks_for(nB, 256), 256, 0, s->stream>>>(nB, 2, as<int>(s->sedge), P0, P1, 0.0, bb.blo, bb.bhi);
+      LAUNCH_CHECK(s, "k_boxes");
+    }
+    grid_dev g;
+    RC(build_grid(s, nB, bb.blo, bb.bhi, &g));
+    ENSURE(s, s->ws[2], sizeof(int) * (nA + 1));
+    int* cnt = as<int>(s->ws[2]);
+    k_cand_query<<<blocks_for(nA, 128), 128, 0, s->stream>>>(0, kind, nA, Tp, g, bb.alo, bb.ahi, 0, cnt, nullptr, nullptr);
+    LAUNCH_CHECK(s, "k_cand_query");
+    int total = 0;
+    RC(scan_exclusive(s, cnt, cnt, nA, &total));
+    gbuf& out = kind == 0 ? s->cpt : s->cee;
+    ENSURE(s, out, sizeof(int) * 2 * ((size_t)total + 1));
+    if (total > 0) {
+      k_cand_query<<<blocks_for(nA, 128), 128, 0, s->stream>>>(total, kind, nA, Tp, g, bb.alo, bb.ahi, 1, nullptr, cnt,
+                                                               as<int>(out));
+      LAUNCH_CHECK(s, "k_cand_query");
+    }
+    (kind == 0 ? s->ncpt : s->ncee) = total;
+  }
+  s->cand_valid = true;
+  return YASPS_OK;
+}
+
+yasps_status ccd_candidates(yasps_system* s, double* alpha_host) {
+  const topo Tp = make_topo(s);
+  const size_t nv3 = 3 * (size_t)s->nv;
+  double* P0 = as<double>(s->P);
+  double* D = as<double>(s->stepv[4]) + nv3;
+  double* tmin = D + nv3;
   const double one = 1.0;
   CK(s, cudaMemcpyAsync(tmin, &one, sizeof(double), cudaMemcpyHostToDevice, s->stream));
   int* st = as<int>(s->status);
@@ -966,35 +1134,81 @@ yasps_status ccd_bound(yasps_system* s, const double* x, const double* p, double
                                                             s->prm.ccd_gap, tmin);
     LAUNCH_CHECK(s, "k_ccd_pg");
   }
-  if (s->nst > 0 && s->nsv > 0) {
-    boxbufs bb;
-    RC(alloc_boxes(s, &bb));
-    k_boxes<<<blocks_for(s->nsv, 256), 256, 0, s->stream>>>(s->nsv, 1, as<int>(s->svert), P0, P1, s->prm.dhat, bb.alo,
-                                                           bb.ahi);
-    LAUNCH_CHECK(s, "k_boxes");
-    k_boxes<<<blocks_for(s->nst, 256), 256, 0, s->stream>>>(s->nst, 3, as<int>(s->stri), P0, P1, 0.0, bb.blo, bb.bhi);
-    LAUNCH_CHECK(s, "k_boxes");
-    grid_dev g;
-    RC(build_grid(s, s->nst, bb.blo, bb.bhi, &g));
-    k_ccd_pt<<<blocks_for(s->nsv, 64), 64, 0, s->stream>>>(s->nsv, Tp, P0, D, g, bb.alo, bb.ahi, s->prm.ccd_gap,
-                                                          s->prm.ccd_max_iter, tmin, st);
-    LAUNCH_CHECK(s, "k_ccd_pt");
-  }
-  if (s->nse > 1) {
-    boxbufs bb;
-    RC(alloc_boxes(s, &bb));
-    k_boxes<<<blocks_for(s->nse, 256), 256, 0, s->stream>>>(s->nse, 2, as<int>(s->sedge), P0, P1, s->prm.dhat, bb.alo,
-                                                           bb.ahi);
-    LAUNCH_CHECK(s, "k_boxes");
-    k_boxes<<<blocks_for(s->nse, 256), 256, 0, s->stream>>>(s->nse, 2, as<int>(s->sedge), P0, P1, 0.0, bb.blo, bb.bhi);
-    LAUNCH_CHECK(s, "k_boxes");
-    grid_dev g;
-    RC(build_grid(s, s->nse, bb.blo, bb.bhi, &g));
-    k_ccd_ee<<<blocks_for(s->nse, 64), 64, 0, s->stream>>>(s->nse, Tp, P0, D, g, bb.alo, bb.ahi, s->prm.ccd_gap,
-                                                          s->prm.ccd_max_iter, tmin, st);
-    LAUNCH_CHECK(s, "k_ccd_ee");
+  for (int kind = 0; kind < 2; ++kind) {
+    const int n = kind == 0 ? s->ncpt : s->ncee;
+    if (n == 0) continue;
+    k_ccd_cand<<<blocks_for(n, 128), 128, 0, s->stream>>>(kind, n, as<int>(kind == 0 ? s->cpt : s->cee), Tp, P0, D,
+                                                         s->prm.ccd_gap, s->prm.ccd_max_iter, tmin, st);
+    LAUNCH_CHECK(s, "k_ccd_cand");
   }
   CK(s, cudaMemcpyAsync(alpha_host, tmin, sizeof(double), cudaMemcpyDeviceToHost, s->stream));
   CK(s, cudaStreamSynchronize(s->stream));
   return YASPS_OK;
+}
+
+yasps_status barrier_energy_candidates(yasps_system* s, const double* P, double* E_host) {
+  const topo Tp = make_topo(s);
+  const double sh = s->prm.dhat * s->prm.dhat;
+  const int nblk_v = blocks_for(std::max(s->nsv, 1), 128);
+  const int nblk_c = 148 * 2;
+  const int npart = nblk_v + 2 * nblk_c;
+  gbuf& pb = s->ws[9];
+  ENSURE(s, pb, sizeof(ksum) * (npart + 4));
+  ksum* part = as<ksum>(pb);
+  CK(s, cudaMemsetAsync(part, 0, sizeof(ksum) * (npart + 4), s->stream));
+  if (s->nsv > 0 && s->npl > 0) {
+    k_pg_query<<<nblk_v, 128, 0, s->stream>>>(0, s->nsv, s->npl, Tp, P, as<double>(s->planes), sh, 2, nullptr, nullptr,
+                                              nullptr, s->prm.kappa, s->prm.barrier_form, part);
+    LAUNCH_CHECK(s, "k_pg_query(E)");
+  }
+  for (int kind = 0; kind < 2; ++kind) {
+    const int n = kind == 0 ? s->ncpt : s->ncee;
+    if (n == 0) continue;
+    k_energy_cand<<<nblk_c, 128, 0, s->stream>>>(kind, n, as<int>(kind == 0 ? s->cpt : s->cee), Tp, P, sh, s->prm.kappa,
+                                                 s->prm.barrier_form, part + nblk_v + kind * nblk_c);
+    LAUNCH_CHECK(s, "k_energy_cand");
+  }
+  double* out = reinterpret_cast<double*>(part + npart + 2);
+  k_reduce_ksum<<<1, 256, 0, s->stream>>>(part, npart, out);
+  LAUNCH_CHECK(s, "k_reduce_ksum");
+  CK(s, cudaMemcpyAsync(E_host, out, sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+  CK(s, cudaStreamSynchronize(s->stream));
+  return YASPS_OK;
+}
+
+yasps_status detect_from_candidates(yasps_system* s, const double* P) {
+  const topo Tp = make_topo(s);
+  const double sh = s->prm.dhat * s->prm.dhat;
+  s->npt = s->nee = s->npg = 0;
+  if (s->nsv > 0 && s->npl > 0) {
+    RC(two_pass(s, s->nsv, [&](int mode, int total, int* cnt, const int* off, int* out) -> yasps_status {
+      k_pg_query<<<blocks_for(s->nsv, 128), 128, 0, s->stream>>>(total, s->nsv, s->npl, Tp, P, as<double>(s->planes), sh,
+                                                                mode, cnt, off, out, 0.0, 0, nullptr);
+      LAUNCH_CHECK(s, "k_pg_query");
+      return YASPS_OK;
+    }, s->pg, &s->npg));
+  }
+  for (int kind = 0; kind < 2; ++kind) {
+    const int n = kind == 0 ? s->ncpt : s->ncee;
+    int& nout = kind == 0 ? s->npt : s->nee;
+    gbuf& outbuf = kind == 0 ? s->pt : s->ee;
+    nout = 0;
+    if (n == 0) continue;
+    ENSURE(s, s->ws[0], sizeof(int) * (n + 1));
+    ENSURE(s, s->ws[1], sizeof(int) * (n + 1));
+    ENSURE(s, s->ws[2], sizeof(int) * (n + 1));
+    int *flag = as<int>(s->ws[0]), *sub = as<int>(s->ws[1]), *off = as<int>(s->ws[2]);
+    const int* cand = as<int>(kind == 0 ? s->cpt : s->cee);
+    k_filter_cand<<<blocks_for(n, 128), 128, 0, s->stream>>>(kind, n, cand, Tp, P, sh, flag, sub);
+    LAUNCH_CHECK(s, "k_filter_cand");
+    int total = 0;
+    RC(scan_exclusive(s, flag, off, n, &total));
+    ENSURE(s, outbuf, sizeof(int) * 3 * ((size_t)total + 1));
+    if (total > 0) {
+      k_compact_cand<<<blocks_for(n, 256), 256, 0, s->stream>>>(n, cand, flag, off, sub, as<int>(outbuf));
+      LAUNCH_CHECK(s, "k_compact_cand");
+    }
+    nout = total;
+  }
+  return build_dynamic_bsr(s);
 }

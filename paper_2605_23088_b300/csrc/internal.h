@@ -82,6 +82,10 @@ struct yasps_system {
   // contact pairs, int [n][3] = (a, b, subtype), sorted by (a, b)
   int npt = 0, nee = 0, npg = 0;
   gbuf pt, ee, pg;
+  // swept candidates of the current Newton iteration, int [n][2], sorted by (a, b)
+  int ncpt = 0, ncee = 0;
+  gbuf cpt, cee;
+  bool cand_valid = false;
   gbuf pair_key_off;  // int [npt + nee + 1] offsets of each pair's dynamic keys
   gbuf dyn_slot;      // int [nkeys] dynamic BSR slot per key
   int nkeys = 0;
@@ -176,6 +180,12 @@ yasps_status build_dynamic_bsr(yasps_system* s);
 yasps_status launch_eval_barrier(yasps_system* s, int project);
 yasps_status barrier_energy(yasps_system* s, const double* P, double* E_host);
 yasps_status ccd_bound(yasps_system* s, const double* x, const double* p, double* alpha_host);
+// candidates of the segment [x, x - p] (positions at x left in s->P, P(x - p) and
+// the displacement in s->stepv[4]); CCD, barrier energy and detection on them
+yasps_status swept_candidates(yasps_system* s, const double* x, const double* p);
+yasps_status ccd_candidates(yasps_system* s, double* alpha_host);
+yasps_status barrier_energy_candidates(yasps_system* s, const double* P, double* E_host);
+yasps_status detect_from_candidates(yasps_system* s, const double* P);
 
 // ---------------------------------------------------------------- solver.cu
 yasps_status alloc_hessian(yasps_system* s);

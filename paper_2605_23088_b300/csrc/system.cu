@@ -64,7 +64,7 @@ static void all_bufs(yasps_system* s, std::vector<gbuf*>& v) {
                  &s->hinge_v, &s->hinge_n, &s->hinge_rest, &s->hinge_slot, &s->body_kv, &s->body_slot, &s->stri,
                  &s->sedge, &s->svert, &s->planes, &s->Hs.row_ptr, &s->Hs.col, &s->Hs.row, &s->Hs.vals,
                  &s->Hd.row_ptr, &s->Hd.col, &s->Hd.row, &s->Hd.vals, &s->diag, &s->grad, &s->minv, &s->P, &s->pt,
-                 &s->ee, &s->pg, &s->pair_key_off, &s->dyn_slot, &s->status, &s->scal, &s->red, &s->scan_tmp};
+                 &s->ee, &s->pg, &s->cpt, &s->cee, &s->pair_key_off, &s->dyn_slot, &s->status, &s->scal, &s->red, &s->scan_tmp};
   for (gbuf* b : one) v.push_back(b);
   for (auto& b : s->ws) v.push_back(&b);
   for (auto& b : s->vec) v.push_back(&b);
@@ -411,11 +411,13 @@ yasps_status yasps_export_pairs(yasps_system* s, int* pt, int* ee, int* pg) {
   return YASPS_OK;
 }
 
-static yasps_status energy_impl(yasps_system* s, const double* x, const double* xtil, double* E, double* terms) {
+static yasps_status energy_impl(yasps_system* s, const double* x, const double* xtil, double* E, double* terms,
+                                bool on_candidates = false) {
   RC(launch_positions(s, x, as<double>(s->P)));
   double t[6] = {0, 0, 0, 0, 0, 0};
   RC(energy_static(s, x, xtil, t));
-  RC(barrier_energy(s, as<double>(s->P), &t[5]));
+  if (on_candidates) RC(barrier_energy_candidates(s, as<double>(s->P), &t[5]));
+  else RC(barrier_energy(s, as<double>(s->P), &t[5]));
   // compensated total
   ksum k{0.0, 0.0};
   for (int i = 0; i < 6; ++i) kadd(k, t[i]);
@@ -581,6 +583,7 @@ extern "C" yasps_status yasps_step(yasps_system* s, double* x, double* v, yasps_
   }
   CK(s, cudaMemcpyAsync(xt, x, sizeof(double) * n3, cudaMemcpyDeviceToDevice, s->stream));
   RC(launch_xtilde(s, x, v, xtil));
+  s->cand_valid = false;
   yasps_status rc = YASPS_OK;
   int it = 0;
   double pinf = 0.0, alpha = 0.0;
@@ -588,7 +591,10 @@ extern "C" yasps_status yasps_step(yasps_system* s, double* x, double* v, yasps_
     cudaEventRecord(s->ev[0], s->stream);
     cudaEvent_t pd = prof_begin(s);
     RC(launch_positions(s, x, as<double>(s->P)));
-    RC(detect_pairs(s, as<double>(s->P)));
+    // after the first iteration, x lies on the previous iteration's swept
+    // segment, so its active pairs are among that segment's candidates
+    if (it > 0 && s->cand_valid) RC(detect_from_candidates(s, as<double>(s->P)));
+    else RC(detect_pairs(s, as<double>(s->P)));
     prof_end(s, YASPS_STAGE_DETECT, pd, 0.0);
     cudaEvent_t pe = prof_begin(s);
     RC(eval_impl(s, x, xtil, YASPS_TERM_ALL, 1));
@@ -625,12 +631,12 @@ extern "C" yasps_status yasps_step(yasps_system* s, double* x, double* v, yasps_
     cudaEventRecord(s->ev[4], s->stream);
     cudaEvent_t pl = prof_begin(s);
     double E0 = 0.0, E1 = 0.0;
-    RC(energy_impl(s, x, xtil, &E0, nullptr));
+    RC(energy_impl(s, x, xtil, &E0, nullptr, true));
     int ls = 0;
     for (ls = 0; ls < s->prm.ls_max_iter; ++ls) {
       k_axpy_out<<<blocks_for(n3, 256), 256, 0, s->stream>>>(n3, x, alpha, p, xtrial);
       LAUNCH_CHECK(s, "k_axpy_out");
-      RC(energy_impl(s, xtrial, xtil, &E1, nullptr));
+      RC(energy_impl(s, xtrial, xtil, &E1, nullptr, true));
       if (E1 <= E0) break;
       alpha *= 0.5;
     }
