@@ -69,7 +69,8 @@ class StepStats(ctypes.Structure):
     _fields_ = [("newton_iters", ctypes.c_int), ("pcg_iters_total", ctypes.c_int), ("n_pt", ctypes.c_int),
                 ("n_ee", ctypes.c_int), ("n_pg", ctypes.c_int), ("status", ctypes.c_int),
                 ("alpha_last", ctypes.c_double), ("p_inf", ctypes.c_double), ("t_eval_ms", ctypes.c_double),
-                ("t_pcg_ms", ctypes.c_double), ("t_ccd_ms", ctypes.c_double), ("t_ls_ms", ctypes.c_double)]
+                ("t_pcg_ms", ctypes.c_double), ("t_ccd_ms", ctypes.c_double), ("t_ls_ms", ctypes.c_double),
+                ("n_cand_pt", ctypes.c_int), ("n_cand_ee", ctypes.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

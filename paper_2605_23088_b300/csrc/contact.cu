@@ -73,28 +73,34 @@ __global__ void k_boxes(int n, int k, const int* __restrict__ idx, const double*
 
 // min of lo, max of hi, max extent over n boxes -> out[7] (per-block partials first)
 __global__ void k_box_reduce(int n, const double* __restrict__ lo, const double* __restrict__ hi, double* __restrict__ part) {
-  double r[7] = {1e300, 1e300, 1e300, -1e300, -1e300, -1e300, 0.0};
-  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x)
+  // min lo (3), max hi (3), max extent, sum of per-box largest extents
+  double r[8] = {1e300, 1e300, 1e300, -1e300, -1e300, -1e300, 0.0, 0.0};
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+    double ext = 0.0;
     for (int c = 0; c < 3; ++c) {
       r[c] = fmin(r[c], lo[3 * e + c]);
       r[3 + c] = fmax(r[3 + c], hi[3 * e + c]);
-      r[6] = fmax(r[6], hi[3 * e + c] - lo[3 * e + c]);
+      ext = fmax(ext, hi[3 * e + c] - lo[3 * e + c]);
     }
-  __shared__ double sh[7][32];
-  for (int q = 0; q < 7; ++q) {
+    r[6] = fmax(r[6], ext);
+    r[7] += ext;
+  }
+  __shared__ double sh[8][32];
+  for (int q = 0; q < 8; ++q) {
     double v = r[q];
     for (int o = 16; o > 0; o >>= 1) {
       double w = __shfl_xor_sync(0xffffffffu, v, o);
-      v = (q < 3) ? fmin(v, w) : fmax(v, w);
+      v = (q < 3) ? fmin(v, w) : (q < 7 ? fmax(v, w) : v + w);
     }
     if ((threadIdx.x & 31) == 0) sh[q][threadIdx.x >> 5] = v;
   }
   __syncthreads();
-  if (threadIdx.x < 7) {
+  if (threadIdx.x < 8) {
     const int q = threadIdx.x;
     double v = sh[q][0];
-    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) v = (q < 3) ? fmin(v, sh[q][w]) : fmax(v, sh[q][w]);
-    part[7 * blockIdx.x + q] = v;
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
+      v = (q < 3) ? fmin(v, sh[q][w]) : (q < 7 ? fmax(v, sh[q][w]) : v + sh[q][w]);
+    part[8 * blockIdx.x + q] = v;
   }
 }
 
@@ -811,22 +817,25 @@ topo make_topo(yasps_system* s) {
 // ws[4] fill, ws[5] items, red for the box reduction.
 yasps_status build_grid(yasps_system* s, int n, const double* blo, const double* bhi, grid_dev* out) {
   const int nblk = std::min(148 * 2, std::max(1, (n + 255) / 256));
-  ENSURE(s, s->red, sizeof(double) * 7 * nblk + 64);
+  ENSURE(s, s->red, sizeof(double) * 8 * nblk + 64);
   double* part = as<double>(s->red);
   k_box_reduce<<<nblk, 256, 0, s->stream>>>(n, blo, bhi, part);
   LAUNCH_CHECK(s, "k_box_reduce");
-  std::vector<double> hp(7 * (size_t)nblk);
-  CK(s, cudaMemcpyAsync(hp.data(), part, sizeof(double) * 7 * nblk, cudaMemcpyDeviceToHost, s->stream));
+  std::vector<double> hp(8 * (size_t)nblk);
+  CK(s, cudaMemcpyAsync(hp.data(), part, sizeof(double) * 8 * nblk, cudaMemcpyDeviceToHost, s->stream));
   CK(s, cudaStreamSynchronize(s->stream));
-  double r[7] = {1e300, 1e300, 1e300, -1e300, -1e300, -1e300, 0.0};
+  double r[8] = {1e300, 1e300, 1e300, -1e300, -1e300, -1e300, 0.0, 0.0};
   for (int b = 0; b < nblk; ++b)
-    for (int q = 0; q < 7; ++q) r[q] = (q < 3) ? std::min(r[q], hp[7 * b + q]) : std::max(r[q], hp[7 * b + q]);
-  for (int q = 0; q < 7; ++q)
+    for (int q = 0; q < 8; ++q)
+      r[q] = (q < 3) ? std::min(r[q], hp[8 * b + q]) : (q < 7 ? std::max(r[q], hp[8 * b + q]) : r[q] + hp[8 * b + q]);
+  for (int q = 0; q < 8; ++q)
     if (!std::isfinite(r[q])) SYS_FAIL(s, YASPS_E_NAN, "non-finite primitive box in the broadphase");
   gridp G;
   double span = 0.0;
   for (int c = 0; c < 3; ++c) span = std::max(span, r[3 + c] - r[c]);
-  double cell = std::max(r[6], 1e-12);
+  // cells as large as the mean box: a few large (fast, swept) boxes span more
+  // cells instead of making every cell crowded
+  double cell = std::max(r[7] / std::max(n, 1), 1e-12);
   if (span / cell > 512.0) cell = span / 512.0;
   long long ncell;
   for (;;) {

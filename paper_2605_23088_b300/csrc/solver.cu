@@ -333,6 +333,96 @@ __global__ void k_pcg_update(int nfree, int nb, const T* __restrict__ Mi, V* __r
   }
 }
 
+// ---------------------------------------------------------------- fused PCG iteration
+// (1) d = z + beta d ; q = D d ; partial d^T D d
+template <typename T, typename V>
+__global__ void k_pcg_dir_dd(int nn, const T* __restrict__ D, const V* __restrict__ z, V* __restrict__ d,
+                             V* __restrict__ q, const pcg_dev* __restrict__ sc, double* __restrict__ part) {
+  if (sc->done) return;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  double acc = 0.0;
+  if (i < nn) {
+    const V beta = (V)sc->beta;
+    V dv[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      dv[a] = z[3 * i + a] + beta * d[3 * i + a];
+      d[3 * i + a] = dv[a];
+    }
+    const T* B = D + 9 * (size_t)i;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const V qa = (V)B[3 * a] * dv[0] + (V)B[3 * a + 1] * dv[1] + (V)B[3 * a + 2] * dv[2];
+      q[3 * i + a] = qa;
+      acc += (double)dv[a] * (double)qa;
+    }
+  }
+  acc = block_sum(acc);
+  if (threadIdx.x == 0) part[blockIdx.x] = acc;
+}
+
+// (2) q += U d + U^T d over both upper parts (static blocks first, then
+// dynamic), partial 2 d_r^T B d_c; the last block finishes d^T H d and alpha.
+template <typename T, typename V>
+__global__ void __launch_bounds__(256) k_spmv_both(int n_s, const int* __restrict__ row_s, const int* __restrict__ col_s,
+                                                   const T* __restrict__ val_s, int n_d, const int* __restrict__ row_d,
+                                                   const int* __restrict__ col_d, const T* __restrict__ val_d,
+                                                   const V* __restrict__ x, V* __restrict__ y, pcg_dev* sc,
+                                                   double* __restrict__ part, int n_dir_parts) {
+  if (sc->done) return;
+  const int lane = threadIdx.x & 31;
+  const long long total = (long long)n_s + n_d;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  double acc = 0.0;
+  for (long long base = (long long)blockIdx.x * blockDim.x; base < total; base += stride) {
+    const long long k = base + threadIdx.x;
+    int r = -1;
+    V a0 = 0, a1 = 0, a2 = 0;
+    if (k < total) {
+      const bool st = k < n_s;
+      const long long kk = st ? k : k - n_s;
+      r = st ? row_s[kk] : row_d[kk];
+      const int c = st ? col_s[kk] : col_d[kk];
+      const T* B = (st ? val_s : val_d) + 9 * (size_t)kk;
+      T b[9];
+#pragma unroll
+      for (int t = 0; t < 9; ++t) b[t] = B[t];
+      const V xc0 = x[3 * c], xc1 = x[3 * c + 1], xc2 = x[3 * c + 2];
+      const V xr0 = x[3 * r], xr1 = x[3 * r + 1], xr2 = x[3 * r + 2];
+      a0 = (V)b[0] * xc0 + (V)b[1] * xc1 + (V)b[2] * xc2;
+      a1 = (V)b[3] * xc0 + (V)b[4] * xc1 + (V)b[5] * xc2;
+      a2 = (V)b[6] * xc0 + (V)b[7] * xc1 + (V)b[8] * xc2;
+      acc += 2.0 * ((double)xr0 * a0 + (double)xr1 * a1 + (double)xr2 * a2);
+      atomicAdd(&y[3 * c], (V)b[0] * xr0 + (V)b[3] * xr1 + (V)b[6] * xr2);
+      atomicAdd(&y[3 * c + 1], (V)b[1] * xr0 + (V)b[4] * xr1 + (V)b[7] * xr2);
+      atomicAdd(&y[3 * c + 2], (V)b[2] * xr0 + (V)b[5] * xr1 + (V)b[8] * xr2);
+    }
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int ro = __shfl_down_sync(0xffffffffu, r, o);
+      const V b0 = shfl_down_v(a0, o), b1 = shfl_down_v(a1, o), b2 = shfl_down_v(a2, o);
+      if (lane + o < 32 && ro == r) { a0 += b0; a1 += b1; a2 += b2; }
+    }
+    const int rp = __shfl_up_sync(0xffffffffu, r, 1);
+    if (r >= 0 && (lane == 0 || rp != r)) {
+      atomicAdd(&y[3 * r], a0);
+      atomicAdd(&y[3 * r + 1], a1);
+      atomicAdd(&y[3 * r + 2], a2);
+    }
+  }
+  acc = block_sum(acc);
+  if (threadIdx.x == 0) part[n_dir_parts + blockIdx.x] = acc;
+  if (last_block(&sc->counter_dq)) {
+    const double dq = sum_partials(part, n_dir_parts + gridDim.x);
+    if (threadIdx.x == 0) {
+      sc->dq = dq;
+      sc->alpha = (dq > 0.0) ? sc->rz / dq : 0.0;
+      if (!(dq > 0.0)) sc->done = 2;
+      sc->counter_dq = 0;
+    }
+  }
+}
+
 template <typename V>
 __global__ void k_add_to(int n, double* __restrict__ p, const V* __restrict__ dx) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -397,9 +487,11 @@ yasps_status pcg_inner(yasps_system* s, const double* rhs, double* p, double tol
   V *x = as<V>(s->vec[0]), *r = as<V>(s->vec[1]), *z = as<V>(s->vec[2]), *d = as<V>(s->vec[3]), *q = as<V>(s->vec[4]);
   const int nu = s->nfree + s->nb;
   const int nblk_u = blocks_for(std::max(nu, 1), PT_);
-  const int nblk_dot = std::min(148 * 4, blocks_for(std::max(n3, 1), PT_));
+  const int nblk_dir = blocks_for(std::max(s->nn, 1), PT_);
+  const long long nup = (long long)s->Hs.nnzb + s->Hd.nnzb;
+  const int nblk_up = (int)std::min<long long>(148LL * 8, std::max<long long>(1, (nup + PT_ - 1) / PT_));
   ENSURE(s, s->scal, sizeof(pcg_dev) + 64);
-  ENSURE(s, s->red, sizeof(double) * (std::max(nblk_u, nblk_dot) + 8));
+  ENSURE(s, s->red, sizeof(double) * (std::max(nblk_u, nblk_dir + nblk_up) + 8));
   pcg_dev* sc = as<pcg_dev>(s->scal);
   double* part = as<double>(s->red);
   pcg_dev h{};
@@ -409,7 +501,7 @@ yasps_status pcg_inner(yasps_system* s, const double* rhs, double* p, double tol
   const T* D = as<T>(s->diag);
   k_pcg_init<T, V><<<nblk_u, PT_, 0, s->stream>>>(s->nfree, s->nb, rhs, Mi, x, r, z, d, part, sc);
   LAUNCH_CHECK(s, "k_pcg_init");
-  const int check_every = 8;
+  const int check_every = 16;
   const double es = sizeof(T);
   const double spmv_bytes = (double)(s->Hs.nnzb + s->Hd.nnzb) * (9 * es + 4) + (double)s->nn * (9 * es + 4) +
                             4.0 * 3.0 * sizeof(V) * s->nn;
@@ -417,12 +509,13 @@ yasps_status pcg_inner(yasps_system* s, const double* rhs, double* p, double tol
   for (;;) {
     for (int k = 0; k < check_every; ++k) {
       cudaEvent_t pa = prof_begin(s);
-      k_pcg_dir<T, V><<<blocks_for(s->nn, PT_), PT_, 0, s->stream>>>(s->nn, D, z, d, q, sc);
-      LAUNCH_CHECK(s, "k_pcg_dir");
-      RC((spmv_t<T, V>(s, d, q, &sc->done)));
+      k_pcg_dir_dd<T, V><<<nblk_dir, PT_, 0, s->stream>>>(s->nn, D, z, d, q, sc, part);
+      LAUNCH_CHECK(s, "k_pcg_dir_dd");
+      k_spmv_both<T, V><<<nblk_up, PT_, 0, s->stream>>>(
+          s->Hs.nnzb, as<int>(s->Hs.row), as<int>(s->Hs.col), as<T>(s->Hs.vals), s->Hd.nnzb, as<int>(s->Hd.row),
+          as<int>(s->Hd.col), as<T>(s->Hd.vals), d, q, sc, part, nblk_dir);
+      LAUNCH_CHECK(s, "k_spmv_both");
       prof_end(s, YASPS_STAGE_SPMV, pa, spmv_bytes);
-      k_pcg_alpha<V><<<nblk_dot, PT_, 0, s->stream>>>(n3, d, q, part, sc);
-      LAUNCH_CHECK(s, "k_pcg_alpha");
       k_pcg_update<T, V><<<nblk_u, PT_, 0, s->stream>>>(s->nfree, s->nb, Mi, x, r, z, d, q, part, sc);
       LAUNCH_CHECK(s, "k_pcg_update");
     }

@@ -628,6 +628,8 @@ extern "C" yasps_status yasps_step(yasps_system* s, double* x, double* v, yasps_
     cudaEvent_t pc = prof_begin(s);
     RC(ccd_bound(s, x, p, &alpha));
     prof_end(s, YASPS_STAGE_CCD, pc, 0.0);
+    st.n_cand_pt = s->ncpt;
+    st.n_cand_ee = s->ncee;
     cudaEventRecord(s->ev[4], s->stream);
     cudaEvent_t pl = prof_begin(s);
     double E0 = 0.0, E1 = 0.0;
