@@ -288,6 +288,121 @@ __device__ __forceinline__ int lc(int i, int j, int k) {  // Levi-Civita for i,j
   return (i == j || j == k || i == k) ? 0 : (((j - i + 3) % 3 == 1) ? 1 : -1);
 }
 
+// PSD projection of the F-space Hessian c1 I + c2 f f^T + lam g g^T + c4 d2J/dF2
+// in closed form.  With the signed SVD F = U diag(s) V^T (U, V rotations) the
+// nine eigenvectors are U E V^T for: the three "scaling" directions E = diag(w)
+// (w an eigenvector of the 3x3 matrix A_ii = c1 + c2 s_i^2 + lam g_i^2,
+// A_ij = c2 s_i s_j + lam g_i g_j + c4 s_k, g_i = s_j s_k), and for each pair
+// (i, j) a "twist" E = (e_i e_j^T - e_j e_i^T)/sqrt2 with eigenvalue c1 + c4 s_k
+// and a "flip" E = (e_i e_j^T + e_j e_i^T)/sqrt2 with eigenvalue c1 - c4 s_k
+// (d2J/dF2 is 0 / -s_k / +s_k on those subspaces).  Negative eigenvalues are
+// dropped.  The result equals the EVD projection of the assembled 9x9 matrix.
+template <typename T>
+__device__ __forceinline__ void snh_project_fspace(const T* F, T c1, T c2, T lam, T c4, T* P) {
+  // F^T F and its eigen-decomposition (descending), V a rotation
+  T C[9];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) C[3 * i + j] = F[i] * F[j] + F[3 + i] * F[3 + j] + F[6 + i] * F[6 + j];
+  T V[9];
+  eig_sym<3, T>(C, V);
+  T w[3] = {C[0], C[4], C[8]};
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int b = 0; b < 2 - a; ++b)
+      if (w[b] < w[b + 1]) {
+        const T tw = w[b]; w[b] = w[b + 1]; w[b + 1] = tw;
+#pragma unroll
+        for (int r = 0; r < 3; ++r) { const T tv = V[3 * r + b]; V[3 * r + b] = V[3 * r + b + 1]; V[3 * r + b + 1] = tv; }
+      }
+  const T detV = V[0] * (V[4] * V[8] - V[5] * V[7]) - V[1] * (V[3] * V[8] - V[5] * V[6]) + V[2] * (V[3] * V[7] - V[4] * V[6]);
+  if (detV < T(0)) { V[2] = -V[2]; V[5] = -V[5]; V[8] = -V[8]; }
+  T v[3][3], u[3][3], s[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c)
+#pragma unroll
+    for (int r = 0; r < 3; ++r) v[c][r] = V[3 * r + c];
+  s[0] = sqrt(w[0] > T(0) ? w[0] : T(0));
+  s[1] = sqrt(w[1] > T(0) ? w[1] : T(0));
+  T Fv[3][3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c)
+#pragma unroll
+    for (int r = 0; r < 3; ++r) Fv[c][r] = F[3 * r] * v[c][0] + F[3 * r + 1] * v[c][1] + F[3 * r + 2] * v[c][2];
+  {
+    T n0 = sqrt(Fv[0][0] * Fv[0][0] + Fv[0][1] * Fv[0][1] + Fv[0][2] * Fv[0][2]);
+    if (!(n0 > T(0))) { u[0][0] = 1; u[0][1] = 0; u[0][2] = 0; }
+    else { u[0][0] = Fv[0][0] / n0; u[0][1] = Fv[0][1] / n0; u[0][2] = Fv[0][2] / n0; }
+    T d = u[0][0] * Fv[1][0] + u[0][1] * Fv[1][1] + u[0][2] * Fv[1][2];
+    T x1 = Fv[1][0] - d * u[0][0], y1 = Fv[1][1] - d * u[0][1], z1 = Fv[1][2] - d * u[0][2];
+    T n1 = sqrt(x1 * x1 + y1 * y1 + z1 * z1);
+    if (!(n1 > T(1e-30))) {  // any unit vector orthogonal to u0
+      const T ax = fabs(u[0][0]) < T(0.9) ? T(1) : T(0), ay = ax > T(0) ? T(0) : T(1);
+      x1 = ay * u[0][2]; y1 = -ax * u[0][2]; z1 = ax * u[0][1] - ay * u[0][0];
+      n1 = sqrt(x1 * x1 + y1 * y1 + z1 * z1);
+    }
+    u[1][0] = x1 / n1; u[1][1] = y1 / n1; u[1][2] = z1 / n1;
+    u[2][0] = u[0][1] * u[1][2] - u[0][2] * u[1][1];
+    u[2][1] = u[0][2] * u[1][0] - u[0][0] * u[1][2];
+    u[2][2] = u[0][0] * u[1][1] - u[0][1] * u[1][0];
+  }
+  s[2] = u[2][0] * Fv[2][0] + u[2][1] * Fv[2][1] + u[2][2] * Fv[2][2];  // signed
+  const T g[3] = {s[1] * s[2], s[0] * s[2], s[0] * s[1]};
+  T A[9];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+      A[3 * i + j] = (i == j) ? c1 + c2 * s[i] * s[i] + lam * g[i] * g[i]
+                              : c2 * s[i] * s[j] + lam * g[i] * g[j] + c4 * s[3 - i - j];
+  T W[9];
+  eig_sym<3, T>(A, W);
+#pragma unroll
+  for (int k = 0; k < 81; ++k) P[k] = T(0);
+  // rank-one update with q = vec(sum_t a_t u_{i_t} v_{j_t}^T)
+  auto add_mode = [&](T lamb, const T* coef /*9: E in the SVD frame*/) {
+    if (!(lamb > T(0))) return;
+    T q[9];
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        T acc = 0;
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+          for (int b = 0; b < 3; ++b)
+            if (coef[3 * a + b] != T(0)) acc += coef[3 * a + b] * u[a][r] * v[b][c];
+        q[3 * r + c] = acc;
+      }
+#pragma unroll
+    for (int r = 0; r < 9; ++r)
+#pragma unroll
+      for (int c = r; c < 9; ++c) P[9 * r + c] += lamb * q[r] * q[c];
+  };
+#pragma unroll
+  for (int m = 0; m < 3; ++m) {
+    T coef[9] = {W[m], 0, 0, 0, W[3 + m], 0, 0, 0, W[6 + m]};
+    add_mode(A[4 * m], coef);
+  }
+  const T h = T(0.70710678118654752440);
+#pragma unroll
+  for (int pr = 0; pr < 3; ++pr) {
+    const int i = (pr == 2) ? 1 : 0, j = (pr == 0) ? 1 : 2, k = 3 - i - j;
+    T ct[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0}, cf[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    ct[3 * i + j] = h; ct[3 * j + i] = -h;
+    cf[3 * i + j] = h; cf[3 * j + i] = h;
+    add_mode(c1 + c4 * s[k], ct);
+    add_mode(c1 - c4 * s[k], cf);
+  }
+#pragma unroll
+  for (int r = 0; r < 9; ++r)
+#pragma unroll
+    for (int c = 0; c < r; ++c) P[9 * r + c] = P[9 * c + r];
+}
+
 template <typename T>
 __global__ void __launch_bounds__(128) k_snh(int nt, const int* __restrict__ tv, const int* __restrict__ tn,
                                              const double* __restrict__ trest, const int* __restrict__ tslot,
@@ -346,22 +461,28 @@ __global__ void __launch_bounds__(128) k_snh(int nt, const int* __restrict__ tv,
   // d2Psi/dF2 = c1 I + c2 f f^T + lam c c^T + c4 d2J/dF2  (f = vec F, c = vec cof F)
   const T c2 = (T)(2.0 * mu / ((Ic + 1.0) * (Ic + 1.0)));
   T Hf[81];
-  T Ft[9], Ct[9];
+  T Ft[9];
 #pragma unroll
-  for (int k = 0; k < 9; ++k) { Ft[k] = (T)F[k]; Ct[k] = (T)C[k]; }
+  for (int k = 0; k < 9; ++k) Ft[k] = (T)F[k];
+  if (project) {
+    snh_project_fspace<T>(Ft, (T)c1, c2, (T)lam, (T)c4, Hf);
+  } else {
+    T Ct[9];
 #pragma unroll
-  for (int r = 0; r < 9; ++r)
+    for (int k = 0; k < 9; ++k) Ct[k] = (T)C[k];
 #pragma unroll
-    for (int q = 0; q < 9; ++q) {
-      const int i = r / 3, j = r % 3, k = q / 3, l = q % 3;
-      T hj = 0;
-      if (i != k && j != l) {
-        const int m = 3 - i - k, nn = 3 - j - l;
-        hj = (T)(lc(i, k, m) * lc(j, l, nn)) * Ft[3 * m + nn];
+    for (int r = 0; r < 9; ++r)
+#pragma unroll
+      for (int q = 0; q < 9; ++q) {
+        const int i = r / 3, j = r % 3, k = q / 3, l = q % 3;
+        T hj = 0;
+        if (i != k && j != l) {
+          const int m = 3 - i - k, nn = 3 - j - l;
+          hj = (T)(lc(i, k, m) * lc(j, l, nn)) * Ft[3 * m + nn];
+        }
+        Hf[9 * r + q] = ((r == q) ? (T)c1 : T(0)) + c2 * Ft[r] * Ft[q] + (T)lam * Ct[r] * Ct[q] + (T)c4 * hj;
       }
-      Hf[9 * r + q] = ((r == q) ? (T)c1 : T(0)) + c2 * Ft[r] * Ft[q] + (T)lam * Ct[r] * Ct[q] + (T)c4 * hj;
-    }
-  if (project) project_psd<9, T>(Hf);
+  }
   const int* sl = tslot + 6 * (size_t)e;
   int slots[6];
 #pragma unroll

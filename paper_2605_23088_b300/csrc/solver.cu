@@ -340,7 +340,7 @@ __global__ void k_pcg_dir_dd(int nn, const T* __restrict__ D, const V* __restric
                              V* __restrict__ q, const pcg_dev* __restrict__ sc, double* __restrict__ part) {
   if (sc->done) return;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  double acc = 0.0;
+  V accv = 0;
   if (i < nn) {
     const V beta = (V)sc->beta;
     V dv[3];
@@ -354,10 +354,10 @@ __global__ void k_pcg_dir_dd(int nn, const T* __restrict__ D, const V* __restric
     for (int a = 0; a < 3; ++a) {
       const V qa = (V)B[3 * a] * dv[0] + (V)B[3 * a + 1] * dv[1] + (V)B[3 * a + 2] * dv[2];
       q[3 * i + a] = qa;
-      acc += (double)dv[a] * (double)qa;
+      accv += dv[a] * qa;
     }
   }
-  acc = block_sum(acc);
+  const double acc = block_sum((double)accv);
   if (threadIdx.x == 0) part[blockIdx.x] = acc;
 }
 
@@ -373,7 +373,7 @@ __global__ void __launch_bounds__(256) k_spmv_both(int n_s, const int* __restric
   const int lane = threadIdx.x & 31;
   const long long total = (long long)n_s + n_d;
   const long long stride = (long long)gridDim.x * blockDim.x;
-  double acc = 0.0;
+  V accv = 0;  // per-thread partial in the vector precision (FP64 ALU is scarce)
   for (long long base = (long long)blockIdx.x * blockDim.x; base < total; base += stride) {
     const long long k = base + threadIdx.x;
     int r = -1;
@@ -392,7 +392,7 @@ __global__ void __launch_bounds__(256) k_spmv_both(int n_s, const int* __restric
       a0 = (V)b[0] * xc0 + (V)b[1] * xc1 + (V)b[2] * xc2;
       a1 = (V)b[3] * xc0 + (V)b[4] * xc1 + (V)b[5] * xc2;
       a2 = (V)b[6] * xc0 + (V)b[7] * xc1 + (V)b[8] * xc2;
-      acc += 2.0 * ((double)xr0 * a0 + (double)xr1 * a1 + (double)xr2 * a2);
+      accv += (V)2 * (xr0 * a0 + xr1 * a1 + xr2 * a2);
       atomicAdd(&y[3 * c], (V)b[0] * xr0 + (V)b[3] * xr1 + (V)b[6] * xr2);
       atomicAdd(&y[3 * c + 1], (V)b[1] * xr0 + (V)b[4] * xr1 + (V)b[7] * xr2);
       atomicAdd(&y[3 * c + 2], (V)b[2] * xr0 + (V)b[5] * xr1 + (V)b[8] * xr2);
@@ -410,7 +410,7 @@ __global__ void __launch_bounds__(256) k_spmv_both(int n_s, const int* __restric
       atomicAdd(&y[3 * r + 2], a2);
     }
   }
-  acc = block_sum(acc);
+  const double acc = block_sum((double)accv);
   if (threadIdx.x == 0) part[n_dir_parts + blockIdx.x] = acc;
   if (last_block(&sc->counter_dq)) {
     const double dq = sum_partials(part, n_dir_parts + gridDim.x);
