@@ -99,6 +99,9 @@ struct yasps_system {
   gbuf vec[10];   // PCG vectors
   gbuf stepv[6];  // step vectors
   cudaEvent_t ev[8] = {};
+  cudaStream_t cstream = nullptr;  // library stream for the PCG graphs
+  cudaEvent_t fence[2] = {};
+  cudaEvent_t spmv_ev[32] = {};
 
   // stage profiler (yasps_profile_*)
   bool prof_on = false;

@@ -24,6 +24,7 @@
 namespace {
 
 constexpr int PT_ = 256;  // threads per block for vector kernels
+constexpr int kPcgChunk = 16;  // PCG iterations per CUDA graph launch
 
 struct pcg_dev {
   double rz, rz_new, dq, alpha, beta, rz0, tol2;
@@ -489,59 +490,84 @@ yasps_status pcg_inner(yasps_system* s, const double* rhs, double* p, double tol
   const int nblk_u = blocks_for(std::max(nu, 1), PT_);
   const int nblk_dir = blocks_for(std::max(s->nn, 1), PT_);
   const long long nup = (long long)s->Hs.nnzb + s->Hd.nnzb;
-  const int nblk_up = (int)std::min<long long>(148LL * 8, std::max<long long>(1, (nup + PT_ - 1) / PT_));
+  const int nblk_up = (int)std::max<long long>(1, (nup + PT_ - 1) / PT_);  // one block per thread
   ENSURE(s, s->scal, sizeof(pcg_dev) + 64);
   ENSURE(s, s->red, sizeof(double) * (std::max(nblk_u, nblk_dir + nblk_up) + 8));
   pcg_dev* sc = as<pcg_dev>(s->scal);
   double* part = as<double>(s->red);
   pcg_dev h{};
   h.tol2 = tol * tol;
-  CK(s, cudaMemcpyAsync(sc, &h, sizeof(pcg_dev), cudaMemcpyHostToDevice, s->stream));
   const T* Mi = as<T>(s->minv);
   const T* D = as<T>(s->diag);
-  k_pcg_init<T, V><<<nblk_u, PT_, 0, s->stream>>>(s->nfree, s->nb, rhs, Mi, x, r, z, d, part, sc);
+  // the iterations run on the library's own stream as CUDA graphs of
+  // check_every iterations (3 kernels each), fenced to the caller's stream
+  cudaStream_t cs = s->cstream;
+  CK(s, cudaEventRecord(s->fence[0], s->stream));
+  CK(s, cudaStreamWaitEvent(cs, s->fence[0], 0));
+  CK(s, cudaMemcpyAsync(sc, &h, sizeof(pcg_dev), cudaMemcpyHostToDevice, cs));
+  k_pcg_init<T, V><<<nblk_u, PT_, 0, cs>>>(s->nfree, s->nb, rhs, Mi, x, r, z, d, part, sc);
   LAUNCH_CHECK(s, "k_pcg_init");
-  const int check_every = 16;
+  const int check_every = kPcgChunk;
   const double es = sizeof(T);
   const double spmv_bytes = (double)(s->Hs.nnzb + s->Hd.nnzb) * (9 * es + 4) + (double)s->nn * (9 * es + 4) +
                             4.0 * 3.0 * sizeof(V) * s->nn;
+  const bool prof = s->prof_on;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  CK(s, cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+  for (int k = 0; k < check_every; ++k) {
+    if (prof) cudaEventRecord(s->spmv_ev[2 * k], cs);
+    k_pcg_dir_dd<T, V><<<nblk_dir, PT_, 0, cs>>>(s->nn, D, z, d, q, sc, part);
+    k_spmv_both<T, V><<<nblk_up, PT_, 0, cs>>>(s->Hs.nnzb, as<int>(s->Hs.row), as<int>(s->Hs.col), as<T>(s->Hs.vals),
+                                               s->Hd.nnzb, as<int>(s->Hd.row), as<int>(s->Hd.col), as<T>(s->Hd.vals),
+                                               d, q, sc, part, nblk_dir);
+    if (prof) cudaEventRecord(s->spmv_ev[2 * k + 1], cs);
+    k_pcg_update<T, V><<<nblk_u, PT_, 0, cs>>>(s->nfree, s->nb, Mi, x, r, z, d, q, part, sc);
+  }
+  cudaError_t ce = cudaStreamEndCapture(cs, &graph);
+  if (ce == cudaSuccess) ce = cudaGraphInstantiate(&exec, graph, 0);
+  if (ce != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    return cuda_check(s, ce, "PCG graph capture");
+  }
   int it = 0;
+  yasps_status rc = YASPS_OK;
   for (;;) {
-    for (int k = 0; k < check_every; ++k) {
-      cudaEvent_t pa = prof_begin(s);
-      k_pcg_dir_dd<T, V><<<nblk_dir, PT_, 0, s->stream>>>(s->nn, D, z, d, q, sc, part);
-      LAUNCH_CHECK(s, "k_pcg_dir_dd");
-      k_spmv_both<T, V><<<nblk_up, PT_, 0, s->stream>>>(
-          s->Hs.nnzb, as<int>(s->Hs.row), as<int>(s->Hs.col), as<T>(s->Hs.vals), s->Hd.nnzb, as<int>(s->Hd.row),
-          as<int>(s->Hd.col), as<T>(s->Hd.vals), d, q, sc, part, nblk_dir);
-      LAUNCH_CHECK(s, "k_spmv_both");
-      prof_end(s, YASPS_STAGE_SPMV, pa, spmv_bytes);
-      k_pcg_update<T, V><<<nblk_u, PT_, 0, s->stream>>>(s->nfree, s->nb, Mi, x, r, z, d, q, part, sc);
-      LAUNCH_CHECK(s, "k_pcg_update");
+    ce = cudaGraphLaunch(exec, cs);
+    s->launches += 3LL * check_every;
+    if (ce == cudaSuccess) ce = cudaMemcpyAsync(&h, sc, sizeof(pcg_dev), cudaMemcpyDeviceToHost, cs);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(cs);
+    if (ce != cudaSuccess) {
+      rc = cuda_check(s, ce, "PCG graph launch");
+      break;
+    }
+    if (prof) {  // only the products of iterations that really ran
+      const int real = std::min(check_every, std::max(0, h.iters - it));
+      for (int k = 0; k < real; ++k) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, s->spmv_ev[2 * k], s->spmv_ev[2 * k + 1]);
+        auto& a = s->prof_acc[YASPS_STAGE_SPMV];
+        a.count += 1;
+        a.ms += ms;
+        a.bytes += spmv_bytes;
+      }
     }
     it += check_every;
-    CK(s, cudaMemcpyAsync(&h, sc, sizeof(pcg_dev), cudaMemcpyDeviceToHost, s->stream));
-    CK(s, cudaStreamSynchronize(s->stream));
     if (h.done || h.iters >= maxit || it >= maxit) break;
   }
-  if (s->prof_on) {
-    // the iterations launched after convergence returned at once: drop their
-    // SpMV samples so the stage average covers real products only
-    prof_resolve(s);
-    const long long wasted = (long long)it - h.iters;
-    if (wasted > 0) {
-      auto& a = s->prof_acc[YASPS_STAGE_SPMV];
-      a.count -= wasted;
-      a.bytes -= wasted * spmv_bytes;
-    }
-  }
-  k_add_to<V><<<blocks_for(n3, 256), 256, 0, s->stream>>>(n3, p, x);
+  cudaGraphExecDestroy(exec);
+  cudaGraphDestroy(graph);
+  RC(rc);
+  k_add_to<V><<<blocks_for(n3, 256), 256, 0, cs>>>(n3, p, x);
   LAUNCH_CHECK(s, "k_add_to");
+  CK(s, cudaEventRecord(s->fence[1], cs));
+  CK(s, cudaStreamWaitEvent(s->stream, s->fence[1], 0));
   *iters = h.iters;
   *state = h.done;
   *rel = (h.rz0 > 0.0) ? std::sqrt(std::max(h.rz, 0.0) / h.rz0) : 0.0;
   return YASPS_OK;
 }
+
 
 template <typename T>
 yasps_status rz64(yasps_system* s, const double* r, double* out) {

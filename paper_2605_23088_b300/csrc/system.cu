@@ -301,6 +301,14 @@ yasps_status yasps_build_system(const yasps_scene_desc* scene, const yasps_param
     s->have_allocator = true;
   }
   for (auto& e : s->ev) cudaEventCreate(&e);
+  for (auto& e : s->fence) cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
+  for (auto& e : s->spmv_ev) cudaEventCreate(&e);
+  if (cudaStreamCreateWithFlags(&s->cstream, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    g_build_error = "cudaStreamCreateWithFlags failed";
+    yasps_destroy(s);
+    return YASPS_E_CUDA;
+  }
   yasps_status rc = build_impl(s, scene);
   if (rc != YASPS_OK) {
     g_build_error = s->err;
@@ -321,6 +329,14 @@ void yasps_destroy(yasps_system* s) {
   cudaStreamSynchronize(s->stream);
   for (auto& e : s->ev)
     if (e) cudaEventDestroy(e);
+  for (auto& e : s->fence)
+    if (e) cudaEventDestroy(e);
+  for (auto& e : s->spmv_ev)
+    if (e) cudaEventDestroy(e);
+  if (s->cstream) {
+    cudaStreamSynchronize(s->cstream);
+    cudaStreamDestroy(s->cstream);
+  }
   delete s;
 }
 
