@@ -253,7 +253,7 @@ def native(args):
 
     peak, peak_kind = load_peaks()
     sp = mixed["prof"]["spmv"]
-    spmv_gbs = sp["bytes"] / (sp["ms"] * 1e-3) / 1e9 if sp["count"] else None
+    spmv_gbs = sp["bytes"] / (sp["ms"] * 1e-3) / 1e9 if sp["count"] and sp["ms"] > 0 else None
     tr = traffic_record(["paper_2605_23088_b300/csrc/solver.cu"])
     roof = {"bound": "hbm", "kernel": "PCG SpMV (k_pcg_dir + k_spmv_upper x2), FP32",
             "achieved": spmv_gbs, "peak": peak, "unit": "GB/s",
@@ -287,7 +287,7 @@ def native(args):
         line["fp64_plain"] = {
             "value": fp64["passes_all"] / (fp64["ms_max"] * 1e-3), "unit": "Newton iterations/s",
             "ms_per_step": fp64["ms_max"] / args.steps, "newton_iters": fp64["newton"], "pcg_iters": fp64["pcg"],
-            "spmv_gbs": sp64["bytes"] / (sp64["ms"] * 1e-3) / 1e9 if sp64["count"] else None,
+            "spmv_gbs": sp64["bytes"] / (sp64["ms"] * 1e-3) / 1e9 if sp64["count"] and sp64["ms"] > 0 else None,
             "stages_ms": {k: (v["ms"], v["count"]) for k, v in fp64["prof"].items()},
             "gpu_launches": fp64["launches"], "clocks": fp64["clocks"]}
     if rank == 0 and world == 1 and not args.skip_cpu:

@@ -516,12 +516,12 @@ yasps_status pcg_inner(yasps_system* s, const double* rhs, double* p, double tol
   cudaGraphExec_t exec = nullptr;
   CK(s, cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
   for (int k = 0; k < check_every; ++k) {
-    if (prof) cudaEventRecord(s->spmv_ev[2 * k], cs);
+    if (prof) cudaEventRecordWithFlags(s->spmv_ev[2 * k], cs, cudaEventRecordExternal);
     k_pcg_dir_dd<T, V><<<nblk_dir, PT_, 0, cs>>>(s->nn, D, z, d, q, sc, part);
     k_spmv_both<T, V><<<nblk_up, PT_, 0, cs>>>(s->Hs.nnzb, as<int>(s->Hs.row), as<int>(s->Hs.col), as<T>(s->Hs.vals),
                                                s->Hd.nnzb, as<int>(s->Hd.row), as<int>(s->Hd.col), as<T>(s->Hd.vals),
                                                d, q, sc, part, nblk_dir);
-    if (prof) cudaEventRecord(s->spmv_ev[2 * k + 1], cs);
+    if (prof) cudaEventRecordWithFlags(s->spmv_ev[2 * k + 1], cs, cudaEventRecordExternal);
     k_pcg_update<T, V><<<nblk_u, PT_, 0, cs>>>(s->nfree, s->nb, Mi, x, r, z, d, q, part, sc);
   }
   cudaError_t ce = cudaStreamEndCapture(cs, &graph);
