@@ -322,16 +322,6 @@ __global__ void k_pcg_update(int nfree, int nb, const T* __restrict__ Mi, V* __r
   }
   acc = block_sum(acc);
   if (threadIdx.x == 0) part[blockIdx.x] = acc;
-  if (last_block(&sc->counter_rz)) {
-    const double rz = sum_partials(part, gridDim.x);
-    if (threadIdx.x == 0) {
-      sc->beta = rz / sc->rz;
-      sc->rz = rz;
-      sc->iters += 1;
-      if (rz <= sc->tol2 * sc->rz0) sc->done = 1;
-      sc->counter_rz = 0;
-    }
-  }
 }
 
 // ---------------------------------------------------------------- fused PCG iteration
@@ -413,14 +403,28 @@ __global__ void __launch_bounds__(256) k_spmv_both(int n_s, const int* __restric
   }
   const double acc = block_sum((double)accv);
   if (threadIdx.x == 0) part[n_dir_parts + blockIdx.x] = acc;
-  if (last_block(&sc->counter_dq)) {
-    const double dq = sum_partials(part, n_dir_parts + gridDim.x);
-    if (threadIdx.x == 0) {
-      sc->dq = dq;
-      sc->alpha = (dq > 0.0) ? sc->rz / dq : 0.0;
-      if (!(dq > 0.0)) sc->done = 2;
-      sc->counter_dq = 0;
-    }
+}
+
+// one block: d^T H d from the partials in order, then alpha (a separate kernel:
+// a grid-wide "last block" counter serialises thousands of same-address atomics)
+__global__ void k_pcg_alpha_fin(const double* __restrict__ part, int nparts, pcg_dev* sc) {
+  if (sc->done) return;
+  const double dq = sum_partials(part, nparts);
+  if (threadIdx.x == 0) {
+    sc->dq = dq;
+    sc->alpha = (dq > 0.0) ? sc->rz / dq : 0.0;
+    if (!(dq > 0.0)) sc->done = 2;
+  }
+}
+// one block: r^T z from the partials, beta, iteration count, convergence
+__global__ void k_pcg_beta_fin(const double* __restrict__ part, int nparts, pcg_dev* sc) {
+  if (sc->done) return;
+  const double rz = sum_partials(part, nparts);
+  if (threadIdx.x == 0) {
+    sc->beta = rz / sc->rz;
+    sc->rz = rz;
+    sc->iters += 1;
+    if (rz <= sc->tol2 * sc->rz0) sc->done = 1;
   }
 }
 
@@ -492,9 +496,10 @@ yasps_status pcg_inner(yasps_system* s, const double* rhs, double* p, double tol
   const long long nup = (long long)s->Hs.nnzb + s->Hd.nnzb;
   const int nblk_up = (int)std::max<long long>(1, (nup + PT_ - 1) / PT_);  // one block per thread
   ENSURE(s, s->scal, sizeof(pcg_dev) + 64);
-  ENSURE(s, s->red, sizeof(double) * (std::max(nblk_u, nblk_dir + nblk_up) + 8));
+  ENSURE(s, s->red, sizeof(double) * ((size_t)nblk_u + nblk_dir + nblk_up + 8));
   pcg_dev* sc = as<pcg_dev>(s->scal);
-  double* part = as<double>(s->red);
+  double* part = as<double>(s->red);          // dir + SpMV partials
+  double* part2 = part + nblk_dir + nblk_up;  // update partials
   pcg_dev h{};
   h.tol2 = tol * tol;
   const T* Mi = as<T>(s->minv);
@@ -522,7 +527,9 @@ yasps_status pcg_inner(yasps_system* s, const double* rhs, double* p, double tol
                                                s->Hd.nnzb, as<int>(s->Hd.row), as<int>(s->Hd.col), as<T>(s->Hd.vals),
                                                d, q, sc, part, nblk_dir);
     if (prof) cudaEventRecordWithFlags(s->spmv_ev[2 * k + 1], cs, cudaEventRecordExternal);
-    k_pcg_update<T, V><<<nblk_u, PT_, 0, cs>>>(s->nfree, s->nb, Mi, x, r, z, d, q, part, sc);
+    k_pcg_alpha_fin<<<1, 1024, 0, cs>>>(part, nblk_dir + nblk_up, sc);
+    k_pcg_update<T, V><<<nblk_u, PT_, 0, cs>>>(s->nfree, s->nb, Mi, x, r, z, d, q, part2, sc);
+    k_pcg_beta_fin<<<1, 1024, 0, cs>>>(part2, nblk_u, sc);
   }
   cudaError_t ce = cudaStreamEndCapture(cs, &graph);
   if (ce == cudaSuccess) ce = cudaGraphInstantiate(&exec, graph, 0);
@@ -534,7 +541,7 @@ yasps_status pcg_inner(yasps_system* s, const double* rhs, double* p, double tol
   yasps_status rc = YASPS_OK;
   for (;;) {
     ce = cudaGraphLaunch(exec, cs);
-    s->launches += 3LL * check_every;
+    s->launches += 5LL * check_every;
     if (ce == cudaSuccess) ce = cudaMemcpyAsync(&h, sc, sizeof(pcg_dev), cudaMemcpyDeviceToHost, cs);
     if (ce == cudaSuccess) ce = cudaStreamSynchronize(cs);
     if (ce != cudaSuccess) {
