@@ -129,6 +129,7 @@ typedef struct {
   double alpha_last;    /* last accepted line-search step */
   double p_inf;         /* ||p||_inf at exit */
   double t_eval_ms, t_pcg_ms, t_ccd_ms, t_ls_ms; /* stage times (CUDA events) */
+  int n_cand_pt, n_cand_ee; /* swept-box candidates of the last line search */
 } yasps_step_stats;
 
 /* Fill *p with defaults (FP64, dt 0.01, dhat 1e-3, kappa 1e4, g = (0,-9.81,0),

@@ -32,21 +32,36 @@ using dist::d3;
 namespace {
 
 // ---------------------------------------------------------------- boxes and grid
+// The grid works on FP32 copies of the boxes rounded outward (a conservative
+// superset); pairs that pass the FP32 test are confirmed on the exact FP64
+// boxes, so candidate sets are those of the FP64 boxes while the per-item work
+// stays off the (scarce) FP64 pipe.
 struct gridp {
-  double lo[3];
-  double cell, inv;
+  float lo[3];
+  float inv;
   int dim[3];
 };
 
-__device__ __forceinline__ int cell_coord(double v, double lo, double inv, int dim) {
-  double f = floor((v - lo) * inv);
-  int c = (f < 0.0) ? 0 : (f > (double)(dim - 1) ? dim - 1 : (int)f);
-  return c;
+__device__ __forceinline__ int cell_coord(float v, float lo, float inv, int dim) {
+  const float f = floorf((v - lo) * inv);
+  return (f < 0.0f) ? 0 : (f > (float)(dim - 1) ? dim - 1 : (int)f);
 }
+
+struct boxes {  // n boxes, 3 per corner, FP64 exact + FP32 outward-rounded copies
+  const double *lo, *hi;
+  const float *lof, *hif;
+};
+struct boxw {
+  double *lo, *hi;
+  float *lof, *hif;
+  operator boxes() const { return boxes{lo, hi, lof, hif}; }
+};
 
 // boxes of k-vertex primitives at positions P0 (and P1 when swept), grown by infl
 __global__ void k_boxes(int n, int k, const int* __restrict__ idx, const double* __restrict__ P0,
-                        const double* __restrict__ P1, double infl, double* __restrict__ lo, double* __restrict__ hi) {
+                        const double* __restrict__ P1, double infl, boxw out) {
+  double* __restrict__ lo = out.lo;
+  double* __restrict__ hi = out.hi;
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= n) return;
   double l[3], h[3];
@@ -66,8 +81,11 @@ __global__ void k_boxes(int n, int k, const int* __restrict__ idx, const double*
     for (int c = 0; c < 3; ++c) { l[c] = fmin(l[c], l1[c]); h[c] = fmax(h[c], h1[c]); }
   }
   for (int c = 0; c < 3; ++c) {
-    lo[3 * e + c] = l[c] - infl;
-    hi[3 * e + c] = h[c] + infl;
+    const double lc = l[c] - infl, hc = h[c] + infl;
+    lo[3 * e + c] = lc;
+    hi[3 * e + c] = hc;
+    out.lof[3 * e + c] = __double2float_rd(lc);
+    out.hif[3 * e + c] = __double2float_ru(hc);
   }
 }
 
@@ -104,14 +122,14 @@ __global__ void k_box_reduce(int n, const double* __restrict__ lo, const double*
   }
 }
 
-__device__ __forceinline__ void cell_range(const gridp& G, const double* lo, const double* hi, int* c0, int* c1) {
+__device__ __forceinline__ void cell_range(const gridp& G, const float* lo, const float* hi, int* c0, int* c1) {
   for (int c = 0; c < 3; ++c) {
     c0[c] = cell_coord(lo[c], G.lo[c], G.inv, G.dim[c]);
     c1[c] = cell_coord(hi[c], G.lo[c], G.inv, G.dim[c]);
   }
 }
 
-__global__ void k_grid_count(int n, const double* __restrict__ lo, const double* __restrict__ hi, gridp G,
+__global__ void k_grid_count(int n, const float* __restrict__ lo, const float* __restrict__ hi, gridp G,
                              int* __restrict__ cnt) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= n) return;
@@ -121,7 +139,7 @@ __global__ void k_grid_count(int n, const double* __restrict__ lo, const double*
     for (int y = c0[1]; y <= c1[1]; ++y)
       for (int x = c0[0]; x <= c1[0]; ++x) atomicAdd(&cnt[((long long)z * G.dim[1] + y) * G.dim[0] + x], 1);
 }
-__global__ void k_grid_fill(int n, const double* __restrict__ lo, const double* __restrict__ hi, gridp G,
+__global__ void k_grid_fill(int n, const float* __restrict__ lo, const float* __restrict__ hi, gridp G,
                             const int* __restrict__ start, int* __restrict__ fill, int* __restrict__ items) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= n) return;
@@ -139,31 +157,39 @@ struct grid_dev {
   gridp G;
   const int* start;
   const int* items;
-  const double *blo, *bhi;
+  boxes B;
 };
 
-// Visit every B box overlapping A box (alo, ahi) once (min-corner rule).
+// Visit every B box overlapping A box i once (min-corner rule on the FP32
+// boxes, then the exact FP64 overlap test).
 template <class F>
-__device__ __forceinline__ void grid_visit(const grid_dev& g, const double* alo, const double* ahi, F&& f) {
+__device__ __forceinline__ void grid_visit(const grid_dev& g, const boxes& A, int i, F&& f) {
+  const float* alf = A.lof + 3 * i;
+  const float* ahf = A.hif + 3 * i;
+  const double* alo = A.lo + 3 * i;
+  const double* ahi = A.hi + 3 * i;
   int c0[3], c1[3];
-  cell_range(g.G, alo, ahi, c0, c1);
+  cell_range(g.G, alf, ahf, c0, c1);
   for (int z = c0[2]; z <= c1[2]; ++z)
     for (int y = c0[1]; y <= c1[1]; ++y)
       for (int x = c0[0]; x <= c1[0]; ++x) {
         const long long id = ((long long)z * g.G.dim[1] + y) * g.G.dim[0] + x;
         for (int q = g.start[id]; q < g.start[id + 1]; ++q) {
           const int j = g.items[q];
-          const double* bl = g.blo + 3 * j;
-          const double* bh = g.bhi + 3 * j;
-          bool ov = true;
-          for (int c = 0; c < 3; ++c)
-            if (ahi[c] < bl[c] || bh[c] < alo[c]) ov = false;
-          if (!ov) continue;
-          // report only in the cell of the intersection's minimum corner
-          const int mx = cell_coord(fmax(alo[0], bl[0]), g.G.lo[0], g.G.inv, g.G.dim[0]);
-          const int my = cell_coord(fmax(alo[1], bl[1]), g.G.lo[1], g.G.inv, g.G.dim[1]);
-          const int mz = cell_coord(fmax(alo[2], bl[2]), g.G.lo[2], g.G.inv, g.G.dim[2]);
+          const float* blf = g.B.lof + 3 * j;
+          const float* bhf = g.B.hif + 3 * j;
+          if (ahf[0] < blf[0] || bhf[0] < alf[0] || ahf[1] < blf[1] || bhf[1] < alf[1] || ahf[2] < blf[2] ||
+              bhf[2] < alf[2])
+            continue;
+          // report only in the cell of the FP32 intersection's minimum corner
+          const int mx = cell_coord(fmaxf(alf[0], blf[0]), g.G.lo[0], g.G.inv, g.G.dim[0]);
+          const int my = cell_coord(fmaxf(alf[1], blf[1]), g.G.lo[1], g.G.inv, g.G.dim[1]);
+          const int mz = cell_coord(fmaxf(alf[2], blf[2]), g.G.lo[2], g.G.inv, g.G.dim[2]);
           if (mx != x || my != y || mz != z) continue;
+          const double* bl = g.B.lo + 3 * j;
+          const double* bh = g.B.hi + 3 * j;
+          if (ahi[0] < bl[0] || bh[0] < alo[0] || ahi[1] < bl[1] || bh[1] < alo[1] || ahi[2] < bl[2] || bh[2] < alo[2])
+            continue;
           f(j);
         }
       }
@@ -204,8 +230,7 @@ __device__ __forceinline__ bder barrier_fn(double s, double sh, int form) {
 
 // ---------------------------------------------------------------- detection
 // mode 0: count, mode 1: write + sort segment, mode 2: accumulate kappa * b(s)
-__global__ void k_pt_query(int total, int nsv, topo T, const double* __restrict__ P, grid_dev g, const double* __restrict__ alo,
-                           const double* __restrict__ ahi, double sh, int mode, int* __restrict__ cnt,
+__global__ void k_pt_query(int total, int nsv, topo T, const double* __restrict__ P, grid_dev g, boxes A, double sh, int mode, int* __restrict__ cnt,
                            const int* __restrict__ off, int* __restrict__ out, double kappa, int form,
                            ksum* __restrict__ part) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -216,7 +241,7 @@ __global__ void k_pt_query(int total, int nsv, topo T, const double* __restrict_
     int c = 0;
     const int base = (mode == 1) ? off[i] : 0;
     const int lim = (mode == 1) ? ((i + 1 < nsv) ? off[i + 1] : total) : 0;
-    grid_visit(g, alo + 3 * i, ahi + 3 * i, [&](int t) {
+    grid_visit(g, A, i, [&](int t) {
       const int t0 = T.stri[3 * t], t1 = T.stri[3 * t + 1], t2 = T.stri[3 * t + 2];
       if (pt_excluded(T, v, t0, t1, t2)) return;
       double s;
@@ -254,8 +279,7 @@ __global__ void k_pt_query(int total, int nsv, topo T, const double* __restrict_
   }
 }
 
-__global__ void k_ee_query(int total, int nse, topo T, const double* __restrict__ P, grid_dev g, const double* __restrict__ alo,
-                           const double* __restrict__ ahi, double sh, int mode, int* __restrict__ cnt,
+__global__ void k_ee_query(int total, int nse, topo T, const double* __restrict__ P, grid_dev g, boxes A, double sh, int mode, int* __restrict__ cnt,
                            const int* __restrict__ off, int* __restrict__ out, double kappa, int form,
                            ksum* __restrict__ part) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -266,7 +290,7 @@ __global__ void k_ee_query(int total, int nse, topo T, const double* __restrict_
     int c = 0;
     const int base = (mode == 1) ? off[i] : 0;
     const int lim = (mode == 1) ? ((i + 1 < nse) ? off[i + 1] : total) : 0;
-    grid_visit(g, alo + 3 * i, ahi + 3 * i, [&](int j) {
+    grid_visit(g, A, i, [&](int j) {
       if (j <= i) return;
       const int f0 = T.sedge[2 * j], f1 = T.sedge[2 * j + 1];
       if (ee_excluded(T, e0, e1, f0, f1)) return;
@@ -618,45 +642,6 @@ __device__ __forceinline__ void atomic_min_pos(double* addr, double v) {
   atomicMin(reinterpret_cast<unsigned long long*>(addr), (unsigned long long)__double_as_longlong(v));
 }
 
-__global__ void k_ccd_pt(int nsv, topo T, const double* __restrict__ P0, const double* __restrict__ D, grid_dev g,
-                         const double* __restrict__ alo, const double* __restrict__ ahi, double gap, int max_iter,
-                         double* __restrict__ tmin, int* status) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= nsv) return;
-  const int v = T.svert[i];
-  double best = 1.0;
-  bool capped = false;
-  grid_visit(g, alo + 3 * i, ahi + 3 * i, [&](int t) {
-    const int t0 = T.stri[3 * t], t1 = T.stri[3 * t + 1], t2 = T.stri[3 * t + 2];
-    if (pt_excluded(T, v, t0, t1, t2)) return;
-    d3 x[4] = {ld3(P0, v), ld3(P0, t0), ld3(P0, t1), ld3(P0, t2)};
-    d3 dx[4] = {ld3(D, v), ld3(D, t0), ld3(D, t1), ld3(D, t2)};
-    const double tk = accd(0, x, dx, gap, 1.0, max_iter, &capped);
-    best = fmin(best, tk);
-  });
-  if (capped) dev_flag(status, DEV_ITERCAP);
-  if (best < 1.0) atomic_min_pos(tmin, best);
-}
-__global__ void k_ccd_ee(int nse, topo T, const double* __restrict__ P0, const double* __restrict__ D, grid_dev g,
-                         const double* __restrict__ alo, const double* __restrict__ ahi, double gap, int max_iter,
-                         double* __restrict__ tmin, int* status) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= nse) return;
-  const int e0 = T.sedge[2 * i], e1 = T.sedge[2 * i + 1];
-  double best = 1.0;
-  bool capped = false;
-  grid_visit(g, alo + 3 * i, ahi + 3 * i, [&](int j) {
-    if (j <= i) return;
-    const int f0 = T.sedge[2 * j], f1 = T.sedge[2 * j + 1];
-    if (ee_excluded(T, e0, e1, f0, f1)) return;
-    d3 x[4] = {ld3(P0, e0), ld3(P0, e1), ld3(P0, f0), ld3(P0, f1)};
-    d3 dx[4] = {ld3(D, e0), ld3(D, e1), ld3(D, f0), ld3(D, f1)};
-    const double tk = accd(1, x, dx, gap, 1.0, max_iter, &capped);
-    best = fmin(best, tk);
-  });
-  if (capped) dev_flag(status, DEV_ITERCAP);
-  if (best < 1.0) atomic_min_pos(tmin, best);
-}
 __global__ void k_ccd_pg(int nsv, int npl, topo T, const double* __restrict__ P0, const double* __restrict__ D,
                          const double* __restrict__ planes, double gap, double* __restrict__ tmin) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -695,8 +680,7 @@ __global__ void k_reduce_ksum(const ksum* __restrict__ part, int n, double* __re
 // pair that comes within dhat anywhere on the segment, and every pair the CCD
 // must examine, is in the list.  mode 0: count per query primitive, mode 1:
 // write (a, b) sorted by b.
-__global__ void k_cand_query(int total, int kind, int nA, topo T, grid_dev g, const double* __restrict__ alo,
-                             const double* __restrict__ ahi, int mode, int* __restrict__ cnt,
+__global__ void k_cand_query(int total, int kind, int nA, topo T, grid_dev g, boxes A, int mode, int* __restrict__ cnt,
                              const int* __restrict__ off, int* __restrict__ out) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nA) return;
@@ -704,7 +688,7 @@ __global__ void k_cand_query(int total, int kind, int nA, topo T, grid_dev g, co
   const int base = (mode == 1) ? off[i] : 0;
   const int lim = (mode == 1) ? ((i + 1 < nA) ? off[i + 1] : total) : 0;
   const int a = (kind == 0) ? T.svert[i] : i;
-  grid_visit(g, alo + 3 * i, ahi + 3 * i, [&](int j) {
+  grid_visit(g, A, i, [&](int j) {
     if (kind == 0) {
       if (pt_excluded(T, a, T.stri[3 * j], T.stri[3 * j + 1], T.stri[3 * j + 2])) return;
     } else {
@@ -815,7 +799,9 @@ topo make_topo(yasps_system* s) {
 
 // Build a grid on boxes (blo, bhi) of n primitives.  Buffers: ws[3] start,
 // ws[4] fill, ws[5] items, red for the box reduction.
-yasps_status build_grid(yasps_system* s, int n, const double* blo, const double* bhi, grid_dev* out) {
+yasps_status build_grid(yasps_system* s, int n, boxes B, grid_dev* out) {
+  const double* blo = B.lo;
+  const double* bhi = B.hi;
   const int nblk = std::min(148 * 2, std::max(1, (n + 255) / 256));
   ENSURE(s, s->red, sizeof(double) * 8 * nblk + 64);
   double* part = as<double>(s->red);
@@ -840,49 +826,53 @@ yasps_status build_grid(yasps_system* s, int n, const double* blo, const double*
   long long ncell;
   for (;;) {
     ncell = 1;
+    // one spare cell on each side: the FP32 origin sits a cell below the boxes
     for (int c = 0; c < 3; ++c) {
-      G.dim[c] = (int)((r[3 + c] - r[c]) / cell) + 1;
+      G.dim[c] = (int)((r[3 + c] - r[c]) / cell) + 3;
       ncell *= G.dim[c];
     }
     if (ncell <= (1LL << 23)) break;
     cell *= 1.25;
   }
-  for (int c = 0; c < 3; ++c) G.lo[c] = r[c];
-  G.cell = cell;
-  G.inv = 1.0 / cell;
+  for (int c = 0; c < 3; ++c) G.lo[c] = (float)(r[c] - cell);
+  G.inv = (float)(1.0 / cell);
   ENSURE(s, s->ws[3], sizeof(int) * (ncell + 1));
   ENSURE(s, s->ws[4], sizeof(int) * (ncell + 1));
   int* start = as<int>(s->ws[3]);
   int* fill = as<int>(s->ws[4]);
   CK(s, cudaMemsetAsync(start, 0, sizeof(int) * (ncell + 1), s->stream));
-  k_grid_count<<<blocks_for(n, 256), 256, 0, s->stream>>>(n, blo, bhi, G, start);
+  k_grid_count<<<blocks_for(n, 256), 256, 0, s->stream>>>(n, B.lof, B.hif, G, start);
   LAUNCH_CHECK(s, "k_grid_count");
   int total = 0;
   RC(scan_exclusive(s, start, start, (int)(ncell + 1), &total));
   ENSURE(s, s->ws[5], sizeof(int) * (total + 1));
   CK(s, cudaMemsetAsync(fill, 0, sizeof(int) * (ncell + 1), s->stream));
-  k_grid_fill<<<blocks_for(n, 256), 256, 0, s->stream>>>(n, blo, bhi, G, start, fill, as<int>(s->ws[5]));
+  k_grid_fill<<<blocks_for(n, 256), 256, 0, s->stream>>>(n, B.lof, B.hif, G, start, fill, as<int>(s->ws[5]));
   LAUNCH_CHECK(s, "k_grid_fill");
   out->G = G;
   out->start = start;
   out->items = as<int>(s->ws[5]);
-  out->blo = blo;
-  out->bhi = bhi;
+  out->B = B;
   return YASPS_OK;
 }
 
 // box buffers: vec slots are not used here; ws[0..2] (A lo/hi, B lo/hi packed)
 struct boxbufs {
-  double *alo, *ahi, *blo, *bhi;
+  boxw a, b;
 };
-yasps_status alloc_boxes(yasps_system* s, boxbufs* b) {
+yasps_status alloc_boxes(yasps_system* s, boxbufs* bb) {
   const size_t nmax = std::max({s->nsv, s->nst, s->nse, 1});
-  ENSURE(s, s->ws[0], sizeof(double) * 6 * nmax);
-  ENSURE(s, s->ws[1], sizeof(double) * 6 * nmax);
-  b->alo = as<double>(s->ws[0]);
-  b->ahi = b->alo + 3 * nmax;
-  b->blo = as<double>(s->ws[1]);
-  b->bhi = b->blo + 3 * nmax;
+  const size_t bytes = (sizeof(double) + sizeof(float)) * 6 * nmax;
+  ENSURE(s, s->ws[0], bytes);
+  ENSURE(s, s->ws[1], bytes);
+  for (int k = 0; k < 2; ++k) {
+    boxw& w = k == 0 ? bb->a : bb->b;
+    double* d = as<double>(s->ws[k]);
+    w.lo = d;
+    w.hi = d + 3 * nmax;
+    w.lof = reinterpret_cast<float*>(d + 6 * nmax);
+    w.hif = w.lof + 3 * nmax;
+  }
   return YASPS_OK;
 }
 
@@ -953,14 +943,14 @@ yasps_status detect_pairs(yasps_system* s, const double* P) {
     boxbufs bb;
     RC(alloc_boxes(s, &bb));
     k_boxes<<<blocks_for(s->nsv, 256), 256, 0, s->stream>>>(s->nsv, 1, as<int>(s->svert), P, nullptr, s->prm.dhat,
-                                                           bb.alo, bb.ahi);
+                                                           bb.a);
     LAUNCH_CHECK(s, "k_boxes");
-    k_boxes<<<blocks_for(s->nst, 256), 256, 0, s->stream>>>(s->nst, 3, as<int>(s->stri), P, nullptr, 0.0, bb.blo, bb.bhi);
+    k_boxes<<<blocks_for(s->nst, 256), 256, 0, s->stream>>>(s->nst, 3, as<int>(s->stri), P, nullptr, 0.0, bb.b);
     LAUNCH_CHECK(s, "k_boxes");
     grid_dev g;
-    RC(build_grid(s, s->nst, bb.blo, bb.bhi, &g));
+    RC(build_grid(s, s->nst, bb.b, &g));
     RC(two_pass(s, s->nsv, [&](int mode, int total, int* cnt, const int* off, int* out) -> yasps_status {
-      k_pt_query<<<blocks_for(s->nsv, 128), 128, 0, s->stream>>>(total, s->nsv, Tp, P, g, bb.alo, bb.ahi, sh, mode, cnt, off,
+      k_pt_query<<<blocks_for(s->nsv, 128), 128, 0, s->stream>>>(total, s->nsv, Tp, P, g, bb.a, sh, mode, cnt, off,
                                                                 out, 0.0, 0, nullptr);
       LAUNCH_CHECK(s, "k_pt_query");
       return YASPS_OK;
@@ -970,14 +960,14 @@ yasps_status detect_pairs(yasps_system* s, const double* P) {
     boxbufs bb;
     RC(alloc_boxes(s, &bb));
     k_boxes<<<blocks_for(s->nse, 256), 256, 0, s->stream>>>(s->nse, 2, as<int>(s->sedge), P, nullptr, s->prm.dhat,
-                                                           bb.alo, bb.ahi);
+                                                           bb.a);
     LAUNCH_CHECK(s, "k_boxes");
-    k_boxes<<<blocks_for(s->nse, 256), 256, 0, s->stream>>>(s->nse, 2, as<int>(s->sedge), P, nullptr, 0.0, bb.blo, bb.bhi);
+    k_boxes<<<blocks_for(s->nse, 256), 256, 0, s->stream>>>(s->nse, 2, as<int>(s->sedge), P, nullptr, 0.0, bb.b);
     LAUNCH_CHECK(s, "k_boxes");
     grid_dev g;
-    RC(build_grid(s, s->nse, bb.blo, bb.bhi, &g));
+    RC(build_grid(s, s->nse, bb.b, &g));
     RC(two_pass(s, s->nse, [&](int mode, int total, int* cnt, const int* off, int* out) -> yasps_status {
-      k_ee_query<<<blocks_for(s->nse, 128), 128, 0, s->stream>>>(total, s->nse, Tp, P, g, bb.alo, bb.ahi, sh, mode, cnt, off,
+      k_ee_query<<<blocks_for(s->nse, 128), 128, 0, s->stream>>>(total, s->nse, Tp, P, g, bb.a, sh, mode, cnt, off,
                                                                 out, 0.0, 0, nullptr);
       LAUNCH_CHECK(s, "k_ee_query");
       return YASPS_OK;
@@ -1037,13 +1027,13 @@ yasps_status barrier_energy(yasps_system* s, const double* P, double* E_host) {
     boxbufs bb;
     RC(alloc_boxes(s, &bb));
     k_boxes<<<blocks_for(s->nsv, 256), 256, 0, s->stream>>>(s->nsv, 1, as<int>(s->svert), P, nullptr, s->prm.dhat,
-                                                           bb.alo, bb.ahi);
+                                                           bb.a);
     LAUNCH_CHECK(s, "k_boxes");
-    k_boxes<<<blocks_for(s->nst, 256), 256, 0, s->stream>>>(s->nst, 3, as<int>(s->stri), P, nullptr, 0.0, bb.blo, bb.bhi);
+    k_boxes<<<blocks_for(s->nst, 256), 256, 0, s->stream>>>(s->nst, 3, as<int>(s->stri), P, nullptr, 0.0, bb.b);
     LAUNCH_CHECK(s, "k_boxes");
     grid_dev g;
-    RC(build_grid(s, s->nst, bb.blo, bb.bhi, &g));
-    k_pt_query<<<nblk_v, 128, 0, s->stream>>>(0, s->nsv, Tp, P, g, bb.alo, bb.ahi, sh, 2, nullptr, nullptr, nullptr,
+    RC(build_grid(s, s->nst, bb.b, &g));
+    k_pt_query<<<nblk_v, 128, 0, s->stream>>>(0, s->nsv, Tp, P, g, bb.a, sh, 2, nullptr, nullptr, nullptr,
                                               s->prm.kappa, s->prm.barrier_form, part + nblk_v);
     LAUNCH_CHECK(s, "k_pt_query(E)");
   }
@@ -1051,13 +1041,13 @@ yasps_status barrier_energy(yasps_system* s, const double* P, double* E_host) {
     boxbufs bb;
     RC(alloc_boxes(s, &bb));
     k_boxes<<<blocks_for(s->nse, 256), 256, 0, s->stream>>>(s->nse, 2, as<int>(s->sedge), P, nullptr, s->prm.dhat,
-                                                           bb.alo, bb.ahi);
+                                                           bb.a);
     LAUNCH_CHECK(s, "k_boxes");
-    k_boxes<<<blocks_for(s->nse, 256), 256, 0, s->stream>>>(s->nse, 2, as<int>(s->sedge), P, nullptr, 0.0, bb.blo, bb.bhi);
+    k_boxes<<<blocks_for(s->nse, 256), 256, 0, s->stream>>>(s->nse, 2, as<int>(s->sedge), P, nullptr, 0.0, bb.b);
     LAUNCH_CHECK(s, "k_boxes");
     grid_dev g;
-    RC(build_grid(s, s->nse, bb.blo, bb.bhi, &g));
-    k_ee_query<<<nblk_e, 128, 0, s->stream>>>(0, s->nse, Tp, P, g, bb.alo, bb.ahi, sh, 2, nullptr, nullptr, nullptr,
+    RC(build_grid(s, s->nse, bb.b, &g));
+    k_ee_query<<<nblk_e, 128, 0, s->stream>>>(0, s->nse, Tp, P, g, bb.a, sh, 2, nullptr, nullptr, nullptr,
                                               s->prm.kappa, s->prm.barrier_form, part + 2 * nblk_v);
     LAUNCH_CHECK(s, "k_ee_query(E)");
   }
@@ -1098,28 +1088,28 @@ yasps_status swept_candidates(yasps_system* s, const double* x, const double* p)
     boxbufs bb;
     RC(alloc_boxes(s, &bb));
     if (kind == 0) {
-      k_boxes<<<blocks_for(nA, 256), 256, 0, s->stream>>>(nA, 1, as<int>(s->svert), P0, P1, s->prm.dhat, bb.alo, bb.ahi);
+      k_boxes<<<blocks_for(nA, 256), 256, 0, s->stream>>>(nA, 1, as<int>(s->svert), P0, P1, s->prm.dhat, bb.a);
       LAUNCH_CHECK(s, "k_boxes");
-      k_boxes<<<blocks_for(nB, 256), 256, 0, s->stream>>>(nB, 3, as<int>(s->stri), P0, P1, 0.0, bb.blo, bb.bhi);
+      k_boxes<<<blocks_for(nB, 256), 256, 0, s->stream>>>(nB, 3, as<int>(s->stri), P0, P1, 0.0, bb.b);
       LAUNCH_CHECK(s, "k_boxes");
     } else {
-      k_boxes<<<blocks_for(nA, 256), 256, 0, s->stream>>>(nA, 2, as<int>(s->sedge), P0, P1, s->prm.dhat, bb.alo, bb.ahi);
+      k_boxes<<<blocks_for(nA, 256), 256, 0, s->stream>>>(nA, 2, as<int>(s->sedge), P0, P1, s->prm.dhat, bb.a);
       LAUNCH_CHECK(s, "k_boxes");
-      k_boxes<<<blocks_for(nB, 256), 256, 0, s->stream>>>(nB, 2, as<int>(s->sedge), P0, P1, 0.0, bb.blo, bb.bhi);
+      k_boxes<<<blocks_for(nB, 256), 256, 0, s->stream>>>(nB, 2, as<int>(s->sedge), P0, P1, 0.0, bb.b);
       LAUNCH_CHECK(s, "k_boxes");
     }
     grid_dev g;
-    RC(build_grid(s, nB, bb.blo, bb.bhi, &g));
+    RC(build_grid(s, nB, bb.b, &g));
     ENSURE(s, s->ws[2], sizeof(int) * (nA + 1));
     int* cnt = as<int>(s->ws[2]);
-    k_cand_query<<<blocks_for(nA, 128), 128, 0, s->stream>>>(0, kind, nA, Tp, g, bb.alo, bb.ahi, 0, cnt, nullptr, nullptr);
+    k_cand_query<<<blocks_for(nA, 128), 128, 0, s->stream>>>(0, kind, nA, Tp, g, bb.a, 0, cnt, nullptr, nullptr);
     LAUNCH_CHECK(s, "k_cand_query");
     int total = 0;
     RC(scan_exclusive(s, cnt, cnt, nA, &total));
     gbuf& out = kind == 0 ? s->cpt : s->cee;
     ENSURE(s, out, sizeof(int) * 2 * ((size_t)total + 1));
     if (total > 0) {
-      k_cand_query<<<blocks_for(nA, 128), 128, 0, s->stream>>>(total, kind, nA, Tp, g, bb.alo, bb.ahi, 1, nullptr, cnt,
+      k_cand_query<<<blocks_for(nA, 128), 128, 0, s->stream>>>(total, kind, nA, Tp, g, bb.a, 1, nullptr, cnt,
                                                                as<int>(out));
       LAUNCH_CHECK(s, "k_cand_query");
     }

@@ -95,7 +95,7 @@ struct yasps_system {
   gbuf scal;      // device scalars (PCG and reductions)
   gbuf red;       // reduction partials
   gbuf scan_tmp;  // scan block sums
-  gbuf ws[10];    // scratch (sort keys/values, grid, counts)
+  gbuf ws[12];    // scratch (sort keys/values, grid, counts)
   gbuf vec[10];   // PCG vectors
   gbuf stepv[6];  // step vectors
   cudaEvent_t ev[8] = {};

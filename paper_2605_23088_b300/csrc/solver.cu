@@ -192,6 +192,24 @@ __device__ double block_sum(double v) {
   __syncthreads();
   return r;
 }
+// block-wide sum in the vector precision (FP64 ALU is scarce on this part:
+// keep per-block reductions of FP32 PCG vectors in FP32)
+template <typename V>
+__device__ V block_sum_v(V v) {
+  __shared__ V shv[32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) shv[threadIdx.x >> 5] = v;
+  __syncthreads();
+  V r = 0;
+  if (threadIdx.x < 32) {
+    r = (threadIdx.x < (blockDim.x >> 5)) ? shv[threadIdx.x] : V(0);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
+  }
+  __syncthreads();
+  return r;
+}
 __device__ double sum_partials(const double* part, int n) {
   double v = 0.0;
   for (int i = threadIdx.x; i < n; i += blockDim.x) v += part[i];
@@ -200,29 +218,29 @@ __device__ double sum_partials(const double* part, int n) {
 
 // z = M^-1 r on free nodes (3x3) and bodies (12x12); v_i = z_i, returns r_i . z_i partial
 template <typename T, typename V>
-__device__ __forceinline__ double precond_row(int i, int nfree, const T* __restrict__ Mi, const V* __restrict__ r,
-                                              V* __restrict__ z) {
+__device__ __forceinline__ V precond_row(int i, int nfree, const T* __restrict__ Mi, const V* __restrict__ r,
+                                         V* __restrict__ z) {
   if (i < nfree) {
     const T* M = Mi + 9 * (size_t)i;
     const V r0 = r[3 * i], r1 = r[3 * i + 1], r2 = r[3 * i + 2];
-    double acc = 0.0;
+    V acc = 0;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
       const V za = (V)M[3 * a] * r0 + (V)M[3 * a + 1] * r1 + (V)M[3 * a + 2] * r2;
       z[3 * i + a] = za;
-      acc += (double)za * (double)r[3 * i + a];
+      acc += za * r[3 * i + a];
     }
     return acc;
   }
   const int b = i - nfree;
   const T* M = Mi + 9 * (size_t)nfree + 144 * (size_t)b;
   const size_t o = 3 * ((size_t)nfree + 4 * (size_t)b);
-  double acc = 0.0;
+  V acc = 0;
   for (int a = 0; a < 12; ++a) {
     V s = 0;
     for (int c = 0; c < 12; ++c) s += (V)M[12 * a + c] * r[o + c];
     z[o + a] = s;
-    acc += (double)s * (double)r[o + a];
+    acc += s * r[o + a];
   }
   return acc;
 }
@@ -234,7 +252,7 @@ __global__ void k_pcg_init(int nfree, int nb, const double* __restrict__ rhs, co
                            pcg_dev* sc) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int nu = nfree + nb;
-  double acc = 0.0;
+  V acc = 0;
   if (i < nu) {
     const int cnt = (i < nfree) ? 3 : 12;
     const size_t o = (i < nfree) ? 3 * (size_t)i : 3 * ((size_t)nfree + 4 * (size_t)(i - nfree));
@@ -246,8 +264,8 @@ __global__ void k_pcg_init(int nfree, int nb, const double* __restrict__ rhs, co
   }
   __syncthreads();
   if (i < nu) acc = precond_row<T, V>(i, nfree, Mi, r, z);
-  acc = block_sum(acc);
-  if (threadIdx.x == 0) part[blockIdx.x] = acc;
+  const double bs = (double)block_sum_v<V>(acc);
+  if (threadIdx.x == 0) part[blockIdx.x] = bs;
   if (last_block(&sc->counter_rz)) {
     const double rz = sum_partials(part, gridDim.x);
     if (threadIdx.x == 0) {
@@ -310,7 +328,7 @@ __global__ void k_pcg_update(int nfree, int nb, const T* __restrict__ Mi, V* __r
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int nu = nfree + nb;
   const V alpha = (V)sc->alpha;
-  double acc = 0.0;
+  V acc = 0;
   if (i < nu) {
     const int cnt = (i < nfree) ? 3 : 12;
     const size_t o = (i < nfree) ? 3 * (size_t)i : 3 * ((size_t)nfree + 4 * (size_t)(i - nfree));
@@ -320,8 +338,8 @@ __global__ void k_pcg_update(int nfree, int nb, const T* __restrict__ Mi, V* __r
     }
     acc = precond_row<T, V>(i, nfree, Mi, r, z);
   }
-  acc = block_sum(acc);
-  if (threadIdx.x == 0) part[blockIdx.x] = acc;
+  const double bs = (double)block_sum_v<V>(acc);
+  if (threadIdx.x == 0) part[blockIdx.x] = bs;
 }
 
 // ---------------------------------------------------------------- fused PCG iteration
@@ -348,7 +366,7 @@ __global__ void k_pcg_dir_dd(int nn, const T* __restrict__ D, const V* __restric
       accv += dv[a] * qa;
     }
   }
-  const double acc = block_sum((double)accv);
+  const double acc = (double)block_sum_v<V>(accv);
   if (threadIdx.x == 0) part[blockIdx.x] = acc;
 }
 
@@ -401,7 +419,7 @@ __global__ void __launch_bounds__(256) k_spmv_both(int n_s, const int* __restric
       atomicAdd(&y[3 * r + 2], a2);
     }
   }
-  const double acc = block_sum((double)accv);
+  const double acc = (double)block_sum_v<V>(accv);
   if (threadIdx.x == 0) part[n_dir_parts + blockIdx.x] = acc;
 }
 
