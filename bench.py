@@ -209,13 +209,15 @@ def native(args):
         ms = e0.elapsed_time(e1)
         launches = system.kernel_launches() - l0
         prof = {k: system.profile_get(i) for i, k in enumerate(yb.STAGE_NAMES)} if profile else None
+        phases = system.pcg_phase_ms() if profile else None
         if profile:
             system.profile_enable(False)
         barrier(world)
         ms_max = allreduce_max(world, ms)
         passes_all = allreduce_sum(world, passes)
         return dict(ms=ms, ms_max=ms_max, passes=passes, passes_all=passes_all, newton=newton, pcg=pcg,
-                    launches=launches, status=status, prof=prof, clocks=clk.summary(), precision=precision_name)
+                    launches=launches, status=status, prof=prof, phases=phases, clocks=clk.summary(),
+                    precision=precision_name)
 
     mixed = timed(G, "fp32-mixed", args.steps, args.warmup, True)
     # end-to-end through the C ABI with host buffers: pinned host state in, state out
@@ -277,6 +279,7 @@ def native(args):
         "spmv_gbs": spmv_gbs,
         "roofline": roof,
         "stages_ms": {k: (v["ms"], v["count"]) for k, v in mixed["prof"].items()},
+        "pcg_phase_us_per_iter": {k: v * 1e3 / max(mixed["pcg"], 1) for k, v in mixed["phases"].items()},
         "e2e": {"value": e2e_passes / (e2e_ms * 1e-3), "unit": "Newton iterations/s", "h2d_bytes_per_step": bytes_state,
                 "d2h_bytes_per_step": bytes_state},
         "gpu_launches": mixed["launches"],

@@ -265,17 +265,22 @@ long long yasps_kernel_launches(const yasps_system* sys);
  * instance of a stage with CUDA events recorded on its own stream and keeps,
  * per stage, the count, the summed event time and the algorithmic bytes the
  * stage must move (inputs read once, unique outputs written once):
- *   YASPS_STAGE_SPMV     one H d product inside PCG: the fused direction
- *                        update + diagonal product and the two upper BSR parts
- *                        (bytes: nnzb (9 s + 4) + n (9 s + 4) + 4 * 3 s n,
- *                        s = bytes per Hessian scalar, n = nodes);
+ *   YASPS_STAGE_SPMV     the H d phase of one PCG iteration: direction update,
+ *                        diagonal product and both upper BSR parts, timed with
+ *                        the device's global timer inside the PCG kernel
+ *                        (count = iterations; bytes: nnzb (9 s + 4) + 4 n
+ *                        + 9 s n + 4 * 3 v n, s = bytes per Hessian scalar,
+ *                        v = bytes per vector scalar, n = nodes);
  *   YASPS_STAGE_TET      the Neo-Hookean tet gradient / projected-Hessian kernel;
  *   YASPS_STAGE_BARRIER  the contact-barrier evaluation kernels;
  *   YASPS_STAGE_PCG      one whole PCG solve;
  *   YASPS_STAGE_DETECT   contact detection + dynamic BSR layout (in yasps_step);
  *   YASPS_STAGE_EVAL     the whole local evaluation incl. block-Jacobi (in yasps_step);
  *   YASPS_STAGE_CCD      the CCD step bound (in yasps_step);
- *   YASPS_STAGE_LS       the line search's energy evaluations (in yasps_step).
+ *   YASPS_STAGE_LS       the line search's energy evaluations (in yasps_step);
+ *   YASPS_STAGE_PCG_KERNEL one launch of the persistent PCG kernel (all the
+ *                        iterations of a solve or of one refinement sweep);
+ *                        bytes = iterations x (SpMV bytes + 7 * 3 v n + 9 s n).
  * Enabling (enable != 0) resets the counters.  yasps_profile_get synchronises. */
 #define YASPS_STAGE_SPMV 0
 #define YASPS_STAGE_TET 1
@@ -285,7 +290,8 @@ long long yasps_kernel_launches(const yasps_system* sys);
 #define YASPS_STAGE_EVAL 5
 #define YASPS_STAGE_CCD 6
 #define YASPS_STAGE_LS 7
-#define YASPS_NUM_STAGES 8
+#define YASPS_STAGE_PCG_KERNEL 8
+#define YASPS_NUM_STAGES 9
 typedef struct {
   long long count;
   double ms;
@@ -293,6 +299,14 @@ typedef struct {
 } yasps_stage_stats;
 yasps_status yasps_profile_enable(yasps_system* sys, int enable);
 yasps_status yasps_profile_get(yasps_system* sys, int stage, yasps_stage_stats* out);
+
+/* Where the PCG kernel's time goes, summed over the iterations run while
+ * profiling was enabled (ms, read from the device's global timer by the
+ * kernel's first block): out[8] = direction phase, wait at the grid barrier,
+ * SpMV phase, wait, alpha reduction, update + preconditioner phase, wait,
+ * beta reduction.  Waits include the time the slowest block of the grid needs
+ * beyond the first. */
+yasps_status yasps_pcg_phase_ms(const yasps_system* sys, double* out);
 
 /* Block-Jacobi PCG that allocates no device memory (the paper has no
  * counterpart; it is an interface for callers that cannot allocate).

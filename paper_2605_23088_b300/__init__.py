@@ -28,10 +28,11 @@ EXPORTS = [
     "yasps_detect_pairs", "yasps_export_pairs", "yasps_energy", "yasps_eval_local", "yasps_assemble",
     "yasps_export_bsr", "yasps_export_gradient", "yasps_spmv", "yasps_pcg_solve", "yasps_ccd_bound", "yasps_step",
     "yasps_set_fixed_positions", "yasps_get_fixed_positions", "yasps_kernel_launches", "yasps_profile_enable",
-    "yasps_profile_get", "yasps_pcg_solve_static",
+    "yasps_profile_get", "yasps_pcg_phase_ms", "yasps_pcg_solve_static",
 ]
-STAGE_SPMV, STAGE_TET, STAGE_BARRIER, STAGE_PCG, STAGE_DETECT, STAGE_EVAL, STAGE_CCD, STAGE_LS = range(8)
-STAGE_NAMES = ["spmv", "tet", "barrier", "pcg", "detect", "eval", "ccd", "line_search"]
+STAGE_SPMV, STAGE_TET, STAGE_BARRIER, STAGE_PCG, STAGE_DETECT, STAGE_EVAL, STAGE_CCD, STAGE_LS, STAGE_PCG_KERNEL = range(9)
+STAGE_NAMES = ["spmv", "tet", "barrier", "pcg", "detect", "eval", "ccd", "line_search", "pcg_kernel"]
+PCG_PHASES = ["direction", "wait_a", "spmv", "wait_b", "alpha", "update", "wait_c", "beta"]
 
 
 class YaspsError(RuntimeError):
@@ -353,3 +354,10 @@ class System:
         st = StageStats()
         self._check(lib().yasps_profile_get(self.h, ctypes.c_int(stage), ctypes.byref(st)))
         return {"count": st.count, "ms": st.ms, "bytes": st.bytes}
+
+    def pcg_phase_ms(self):
+        """Per-phase time of the PCG kernel while profiling (ms): direction, wait,
+        SpMV, wait, alpha, update, wait, beta."""
+        out = np.zeros(8)
+        self._check(lib().yasps_pcg_phase_ms(self.h, out.ctypes.data_as(_PD)))
+        return dict(zip(PCG_PHASES, out.tolist()))

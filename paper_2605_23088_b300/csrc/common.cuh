@@ -15,6 +15,7 @@ enum : int {
   DEV_NAN = 2,       // non-finite value produced
   DEV_BADINDEX = 4,  // index out of range
   DEV_ITERCAP = 8,   // an iteration cap was reached (ACCD)
+  DEV_TIMEOUT = 16,  // a bounded grid-barrier wait gave up
 };
 
 YASPS_D void dev_flag(int* status, int code) { atomicOr(status, code); }

@@ -99,9 +99,6 @@ struct yasps_system {
   gbuf vec[10];   // PCG vectors
   gbuf stepv[6];  // step vectors
   cudaEvent_t ev[8] = {};
-  cudaStream_t cstream = nullptr;  // library stream for the PCG graphs
-  cudaEvent_t fence[2] = {};
-  cudaEvent_t spmv_ev[32] = {};
 
   // stage profiler (yasps_profile_*)
   bool prof_on = false;
@@ -113,6 +110,7 @@ struct yasps_system {
   std::vector<pending> prof_pending;
   std::vector<cudaEvent_t> prof_pool;
   yasps_stage_stats prof_acc[YASPS_NUM_STAGES] = {};
+  double pcg_phase_ms[8] = {};  // yasps_pcg_phase_ms
 };
 
 // stage profiler: prof_begin returns an event recorded on the stream (or null

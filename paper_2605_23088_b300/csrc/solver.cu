@@ -8,12 +8,14 @@
 // shuffles instead of a linear scan through shared memory; the segment head and
 // the transpose term U^T x use atomic additions.
 //
-// PCG keeps its scalars (r^T z, alpha, beta, convergence flag) on the device.
-// Dot products are two-level (per-block partials, then the last block to
-// finish sums the partials in block order), so results do not depend on
-// scheduling.  In the FP32-mixed form the inner PCG runs on FP32 vectors and
-// FP32 blocks; an outer loop recomputes the residual g - H p in FP64 and
-// solves for the correction (iterative refinement).
+// All iterations of a solve run inside one persistent cooperative kernel (one
+// block per SM).  An iteration is three grid-wide phases separated by a grid
+// barrier whose waits are bounded; each phase leaves one partial sum per
+// block, and after the barrier every block adds the partials up in block order,
+// so alpha, beta and the stopping decision are bit-identical in all blocks and
+// independent of scheduling.  In the FP32-mixed form the inner PCG runs on FP32
+// vectors and FP32 blocks; an outer loop recomputes the residual g - H p in
+// FP64 and solves for the correction (iterative refinement).
 #include <algorithm>
 #include <cmath>
 #include <vector>
@@ -23,12 +25,26 @@
 
 namespace {
 
-constexpr int PT_ = 256;  // threads per block for vector kernels
-constexpr int kPcgChunk = 16;  // PCG iterations per CUDA graph launch
+constexpr int PT_ = 256;           // threads per block for vector kernels
+// threads per block of the persistent PCG kernel (one block per SM; FP64
+// needs more registers per thread)
+template <typename T>
+struct pcg_threads { static constexpr int N = 1024; };
+template <>
+struct pcg_threads<double> { static constexpr int N = 640; };
 
+// result of one persistent PCG launch (written by block 0 at the end)
 struct pcg_dev {
-  double rz, rz_new, dq, alpha, beta, rz0, tol2;
-  int done, iters, counter_dq, counter_rz, pad;
+  double rz, rz0;
+  int done, iters;  // done: 1 converged, 2 breakdown (d^T H d <= 0), 3 barrier timeout
+  unsigned long long t_ns[8];  // block 0's time per phase, summed over iterations (see k_pcg_persistent)
+};
+// grid barrier state, zeroed before every launch: count only grows (barrier k
+// of a launch completes when it reaches k * gridDim.x)
+struct pcg_bar {
+  unsigned count;
+  int abort;
+  int pad[2];
 };
 
 // ---------------------------------------------------------------- SpMV
@@ -166,19 +182,7 @@ __global__ void k_bj_body(int nb, int nfree, const T* __restrict__ D, const int*
   for (int t = 0; t < 144; ++t) M[t] = (T)I[t];
 }
 
-// ---------------------------------------------------------------- PCG kernels
-// Last block to arrive sums the per-block partials in order.
-__device__ __forceinline__ bool last_block(int* counter) {
-  __shared__ bool last;
-  __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    const int t = atomicAdd(counter, 1);
-    last = (t == (int)gridDim.x - 1);
-  }
-  __syncthreads();
-  return last;
-}
+// ---------------------------------------------------------------- reductions
 __device__ double block_sum(double v) {
   __shared__ double sh[32];
   v = warp_sum(v);
@@ -245,205 +249,438 @@ __device__ __forceinline__ V precond_row(int i, int nfree, const T* __restrict__
   return acc;
 }
 
-// init: r = rhs (- H p0 already folded into rhs by the caller), x = 0, z = M^-1 r, d = 0
+// ---------------------------------------------------------------- persistent PCG
 template <typename T, typename V>
-__global__ void k_pcg_init(int nfree, int nb, const double* __restrict__ rhs, const T* __restrict__ Mi, V* __restrict__ x,
-                           V* __restrict__ r, V* __restrict__ z, V* __restrict__ d, double* __restrict__ part,
-                           pcg_dev* sc) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int nu = nfree + nb;
-  V acc = 0;
-  if (i < nu) {
-    const int cnt = (i < nfree) ? 3 : 12;
-    const size_t o = (i < nfree) ? 3 * (size_t)i : 3 * ((size_t)nfree + 4 * (size_t)(i - nfree));
-    for (int c = 0; c < cnt; ++c) {
-      r[o + c] = (V)rhs[o + c];
-      x[o + c] = 0;
-      d[o + c] = 0;
+struct pcg_args {
+  int nn, nfree, nb, n_s, n_d, maxit;
+  double tol2;
+  const int *row_s, *col_s, *row_d, *col_d;
+  const T *val_s, *val_d, *D, *Mi;
+  const double* rhs;
+  V *x, *r, *z, *d, *q;  // written and read across blocks: plain (coherent) loads only
+  double* part;          // [3][gridDim.x] per-block partials of the three phases
+  pcg_dev* sc;
+  pcg_bar* bar;
+  int* status;
+  long long spin_limit;
+};
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Grid-wide barrier for a cooperative launch (all blocks co-resident).  After
+// a block-level sync, thread 0 of each block adds 1 to the arrival count with
+// release semantics (publishing everything the block wrote) and polls it with
+// acquire loads until it reaches this barrier's target.  The wait is bounded:
+// after spin_limit polls the block raises the abort flag, and every waiting
+// block also leaves when it sees the flag, so no block waits forever.  Returns
+// false when the grid has aborted.
+__device__ __forceinline__ void red_add_release(unsigned* p, unsigned v) {
+  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ bool grid_barrier(pcg_bar* bar, unsigned& target, long long spin_limit) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int good = 1;
+    target += gridDim.x;
+    red_add_release(&bar->count, 1u);
+    long long spins = 0;
+    while (ld_acquire(&bar->count) < target) {
+      if ((++spins & 255) == 0) {
+        if (*(volatile int*)&bar->abort) { good = 0; break; }
+        if (spins > spin_limit) { atomicExch(&bar->abort, 1); good = 0; break; }
+      }
     }
+    ok = good && !*(volatile int*)&bar->abort;
   }
   __syncthreads();
-  if (i < nu) acc = precond_row<T, V>(i, nfree, Mi, r, z);
-  const double bs = (double)block_sum_v<V>(acc);
-  if (threadIdx.x == 0) part[blockIdx.x] = bs;
-  if (last_block(&sc->counter_rz)) {
-    const double rz = sum_partials(part, gridDim.x);
-    if (threadIdx.x == 0) {
-      sc->rz = rz;
-      sc->rz0 = rz;
-      sc->beta = 0.0;
-      sc->iters = 0;
-      sc->done = !(rz > 0.0) ? 1 : 0;
-      sc->counter_rz = 0;
-    }
-  }
+  return ok != 0;
 }
 
-// d = z + beta d ; q = D d   (diagonal part of q = H d)
+// sum of the n per-block partials in block order, the same value in every thread
+__device__ double grid_total(const double* part, int n) {
+  __shared__ double sh[32];
+  __shared__ double tot;
+  double v = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) v += __ldcg(part + i);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double w = (threadIdx.x < (blockDim.x >> 5)) ? sh[threadIdx.x] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
+    if (threadIdx.x == 0) tot = w;
+  }
+  __syncthreads();
+  return tot;
+}
+
+// ---- shared-memory staging of the upper blocks (bulk async copies)
+//
+// The SpMV phase walks the upper blocks in tiles of one block per thread.  A
+// tile's values, rows and columns are contiguous, so thread 0 moves them into
+// shared memory with three cp.async.bulk copies completing on an mbarrier,
+// double-buffered: the copies of the next tiles are in flight while the
+// current tile is multiplied, and the first two tiles of an iteration are
+// requested before its direction phase.  Only the gathers of d stay exposed.
+template <typename T>
+struct stage_layout {
+  static constexpr int NT = 2 * pcg_threads<T>::N;     // blocks per tile (two per thread)
+  static constexpr unsigned VB = NT * 9 * sizeof(T);   // values
+  static constexpr unsigned IB = NT * sizeof(int);     // rows / columns
+  static constexpr unsigned BUF = VB + 2 * IB;         // one buffer (a multiple of 16)
+  static constexpr unsigned SMEM = 2 * BUF + 16;       // two buffers + two mbarriers
+};
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+  return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* m, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(m)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* m, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(m)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* m, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(m)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, uint64_t* m) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(m))
+               : "memory");
+}
+// bounded wait on one buffer's mbarrier; false after spin_limit polls
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* m, unsigned parity, long long spin_limit) {
+  for (long long k = 0; k < spin_limit; ++k)
+    if (mbar_try_wait(m, parity)) return true;
+  return false;
+}
+
 template <typename T, typename V>
-__global__ void k_pcg_dir(int nn, const T* __restrict__ D, const V* __restrict__ z, V* __restrict__ d, V* __restrict__ q,
-                          const pcg_dev* __restrict__ sc) {
-  if (sc->done) return;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= nn) return;
-  const V beta = (V)sc->beta;
-  V dv[3];
-#pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    dv[a] = z[3 * i + a] + beta * d[3 * i + a];
-    d[3 * i + a] = dv[a];
+struct tile_src {
+  const T* vals;
+  const int *row, *col;
+  int base, cnt;
+};
+template <typename T, typename V>
+__device__ __forceinline__ tile_src<T, V> tile_of(const pcg_args<T, V>& a, int t, int Ts) {
+  constexpr int NT = stage_layout<T>::NT;
+  tile_src<T, V> o;
+  if (t < Ts) {
+    o.vals = a.val_s; o.row = a.row_s; o.col = a.col_s;
+    o.base = t * NT;
+    o.cnt = min(NT, a.n_s - o.base);
+  } else {
+    o.vals = a.val_d; o.row = a.row_d; o.col = a.col_d;
+    o.base = (t - Ts) * NT;
+    o.cnt = min(NT, a.n_d - o.base);
   }
-  const T* B = D + 9 * (size_t)i;
-#pragma unroll
-  for (int a = 0; a < 3; ++a) q[3 * i + a] = (V)B[3 * a] * dv[0] + (V)B[3 * a + 1] * dv[1] + (V)B[3 * a + 2] * dv[2];
+  return o;
+}
+// thread 0: request tile t into buffer b.  Tile starts are multiples of NT
+// blocks, so every source address is 16-byte aligned; sizes are rounded up to
+// 16 bytes (the arrays carry that much slack).
+template <typename T, typename V>
+__device__ __forceinline__ void issue_tile(const pcg_args<T, V>& a, int t, int Ts, unsigned char* buf, uint64_t* m) {
+  using L = stage_layout<T>;
+  const tile_src<T, V> src = tile_of(a, t, Ts);
+  const unsigned bv = (unsigned)(src.cnt * 9 * (int)sizeof(T) + 15) & ~15u;
+  const unsigned bi = (unsigned)(src.cnt * (int)sizeof(int) + 15) & ~15u;
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  mbar_expect_tx(m, bv + 2 * bi);
+  bulk_g2s(buf, src.vals + 9 * (size_t)src.base, bv, m);
+  bulk_g2s(buf + L::VB, src.row + src.base, bi, m);
+  bulk_g2s(buf + L::VB + L::IB, src.col + src.base, bi, m);
 }
 
-// dq = d . q, alpha = rz / dq
+// the two d segments one block needs
 template <typename V>
-__global__ void k_pcg_alpha(int n3, const V* __restrict__ d, const V* __restrict__ q, double* __restrict__ part,
-                            pcg_dev* sc) {
-  if (sc->done) return;
-  double acc = 0.0;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n3; i += gridDim.x * blockDim.x)
-    acc += (double)d[i] * (double)q[i];
-  acc = block_sum(acc);
-  if (threadIdx.x == 0) part[blockIdx.x] = acc;
-  if (last_block(&sc->counter_dq)) {
-    const double dq = sum_partials(part, gridDim.x);
-    if (threadIdx.x == 0) {
-      sc->dq = dq;
-      sc->alpha = (dq > 0.0) ? sc->rz / dq : 0.0;
-      if (!(dq > 0.0)) sc->done = 2;  // breakdown (H not positive definite on d)
-      sc->counter_dq = 0;
-    }
+struct gath {
+  V c0, c1, c2, r0, r1, r2;
+};
+template <typename V>
+__device__ __forceinline__ void gather_d(int r, int c, const V* d, gath<V>& g) {
+  if (r >= 0) {
+    g.c0 = d[3 * c]; g.c1 = d[3 * c + 1]; g.c2 = d[3 * c + 2];
+    g.r0 = d[3 * r]; g.r1 = d[3 * r + 1]; g.r2 = d[3 * r + 2];
   }
 }
-
-// x += alpha d, r -= alpha q, z = M^-1 r, rz_new = r . z, beta, convergence
+// q += B d_c into the row (segmented over the warp), q += B^T d_r into the
+// column; returns the block's share 2 d_r^T B d_c of d^T U d
 template <typename T, typename V>
-__global__ void k_pcg_update(int nfree, int nb, const T* __restrict__ Mi, V* __restrict__ x, V* __restrict__ r,
-                             V* __restrict__ z, const V* __restrict__ d, const V* __restrict__ q,
-                             double* __restrict__ part, pcg_dev* sc) {
-  if (sc->done) return;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int nu = nfree + nb;
-  const V alpha = (V)sc->alpha;
-  V acc = 0;
-  if (i < nu) {
-    const int cnt = (i < nfree) ? 3 : 12;
-    const size_t o = (i < nfree) ? 3 * (size_t)i : 3 * ((size_t)nfree + 4 * (size_t)(i - nfree));
-    for (int c = 0; c < cnt; ++c) {
-      x[o + c] += alpha * d[o + c];
-      r[o + c] -= alpha * q[o + c];
-    }
-    acc = precond_row<T, V>(i, nfree, Mi, r, z);
+__device__ __forceinline__ V apply_blk(int r, int c, const T* b, const gath<V>& g, V* q, int lane) {
+  V a0 = 0, a1 = 0, a2 = 0, part = 0;
+  if (r >= 0) {
+    const V xc0 = g.c0, xc1 = g.c1, xc2 = g.c2;
+    const V xr0 = g.r0, xr1 = g.r1, xr2 = g.r2;
+    a0 = (V)b[0] * xc0 + (V)b[1] * xc1 + (V)b[2] * xc2;
+    a1 = (V)b[3] * xc0 + (V)b[4] * xc1 + (V)b[5] * xc2;
+    a2 = (V)b[6] * xc0 + (V)b[7] * xc1 + (V)b[8] * xc2;
+    part = (V)2 * (xr0 * a0 + xr1 * a1 + xr2 * a2);
+    atomicAdd(&q[3 * c], (V)b[0] * xr0 + (V)b[3] * xr1 + (V)b[6] * xr2);
+    atomicAdd(&q[3 * c + 1], (V)b[1] * xr0 + (V)b[4] * xr1 + (V)b[7] * xr2);
+    atomicAdd(&q[3 * c + 2], (V)b[2] * xr0 + (V)b[5] * xr1 + (V)b[8] * xr2);
   }
-  const double bs = (double)block_sum_v<V>(acc);
-  if (threadIdx.x == 0) part[blockIdx.x] = bs;
-}
-
-// ---------------------------------------------------------------- fused PCG iteration
-// (1) d = z + beta d ; q = D d ; partial d^T D d
-template <typename T, typename V>
-__global__ void k_pcg_dir_dd(int nn, const T* __restrict__ D, const V* __restrict__ z, V* __restrict__ d,
-                             V* __restrict__ q, const pcg_dev* __restrict__ sc, double* __restrict__ part) {
-  if (sc->done) return;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  V accv = 0;
-  if (i < nn) {
-    const V beta = (V)sc->beta;
-    V dv[3];
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      dv[a] = z[3 * i + a] + beta * d[3 * i + a];
-      d[3 * i + a] = dv[a];
-    }
-    const T* B = D + 9 * (size_t)i;
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      const V qa = (V)B[3 * a] * dv[0] + (V)B[3 * a + 1] * dv[1] + (V)B[3 * a + 2] * dv[2];
-      q[3 * i + a] = qa;
-      accv += dv[a] * qa;
-    }
+  for (int off = 1; off < 32; off <<= 1) {
+    const int ro = __shfl_down_sync(0xffffffffu, r, off);
+    const V b0 = shfl_down_v(a0, off), b1 = shfl_down_v(a1, off), b2 = shfl_down_v(a2, off);
+    if (lane + off < 32 && ro == r) { a0 += b0; a1 += b1; a2 += b2; }
   }
-  const double acc = (double)block_sum_v<V>(accv);
-  if (threadIdx.x == 0) part[blockIdx.x] = acc;
+  const int rp = __shfl_up_sync(0xffffffffu, r, 1);
+  if (r >= 0 && (lane == 0 || rp != r)) {
+    atomicAdd(&q[3 * r], a0);
+    atomicAdd(&q[3 * r + 1], a1);
+    atomicAdd(&q[3 * r + 2], a2);
+  }
+  return part;
 }
 
-// (2) q += U d + U^T d over both upper parts (static blocks first, then
-// dynamic), partial 2 d_r^T B d_c; the last block finishes d^T H d and alpha.
+// unit i: a free node (3 DOF) or an affine body (its 4 nodes, 12 DOF)
+__device__ __forceinline__ void unit_range(int i, int nfree, int& cnt, size_t& o) {
+  cnt = (i < nfree) ? 3 : 12;
+  o = (i < nfree) ? 3 * (size_t)i : 3 * ((size_t)nfree + 4 * (size_t)(i - nfree));
+}
+
+// phase A for one node: every load before any store (the vectors may alias
+// as far as the compiler knows)
 template <typename T, typename V>
-__global__ void __launch_bounds__(256) k_spmv_both(int n_s, const int* __restrict__ row_s, const int* __restrict__ col_s,
-                                                   const T* __restrict__ val_s, int n_d, const int* __restrict__ row_d,
-                                                   const int* __restrict__ col_d, const T* __restrict__ val_d,
-                                                   const V* __restrict__ x, V* __restrict__ y, pcg_dev* sc,
-                                                   double* __restrict__ part, int n_dir_parts) {
-  if (sc->done) return;
+__device__ __forceinline__ V dir_node(const pcg_args<T, V>& a, long long i, V beta) {
+  const T* B = a.D + 9 * (size_t)i;
+  T m[9];
+#pragma unroll
+  for (int t = 0; t < 9; ++t) m[t] = __ldg(B + t);
+  const V z0 = a.z[3 * i], z1 = a.z[3 * i + 1], z2 = a.z[3 * i + 2];
+  const V e0 = a.d[3 * i], e1 = a.d[3 * i + 1], e2 = a.d[3 * i + 2];
+  const V d0 = z0 + beta * e0, d1 = z1 + beta * e1, d2 = z2 + beta * e2;
+  const V q0 = (V)m[0] * d0 + (V)m[1] * d1 + (V)m[2] * d2;
+  const V q1 = (V)m[3] * d0 + (V)m[4] * d1 + (V)m[5] * d2;
+  const V q2 = (V)m[6] * d0 + (V)m[7] * d1 + (V)m[8] * d2;
+  a.d[3 * i] = d0; a.d[3 * i + 1] = d1; a.d[3 * i + 2] = d2;
+  a.q[3 * i] = q0; a.q[3 * i + 1] = q1; a.q[3 * i + 2] = q2;
+  return d0 * q0 + d1 * q1 + d2 * q2;
+}
+// phase C for one free node: x += alpha d, r -= alpha q, z = M^-1 r; r^T z
+template <typename T, typename V>
+__device__ __forceinline__ V update_free(const pcg_args<T, V>& a, long long i, V alpha) {
+  const T* M = a.Mi + 9 * (size_t)i;
+  T m[9];
+#pragma unroll
+  for (int t = 0; t < 9; ++t) m[t] = __ldg(M + t);
+  V xv[3], dv[3], rv[3], qv[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    xv[c] = a.x[3 * i + c];
+    dv[c] = a.d[3 * i + c];
+    rv[c] = a.r[3 * i + c];
+    qv[c] = a.q[3 * i + c];
+  }
+  V zv[3], acc = 0;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    xv[c] += alpha * dv[c];
+    rv[c] -= alpha * qv[c];
+  }
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    zv[c] = (V)m[3 * c] * rv[0] + (V)m[3 * c + 1] * rv[1] + (V)m[3 * c + 2] * rv[2];
+    acc += zv[c] * rv[c];
+  }
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    a.x[3 * i + c] = xv[c];
+    a.r[3 * i + c] = rv[c];
+    a.z[3 * i + c] = zv[c];
+  }
+  return acc;
+}
+
+template <typename T, typename V>
+__global__ void __launch_bounds__(pcg_threads<T>::N, 1) k_pcg_persistent(pcg_args<T, V> a) {
+  using L = stage_layout<T>;
+  extern __shared__ __align__(128) unsigned char smem[];
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + 2 * L::BUF);
+  const int G = gridDim.x;
+  const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long nthr = (long long)G * blockDim.x;
   const int lane = threadIdx.x & 31;
-  const long long total = (long long)n_s + n_d;
-  const long long stride = (long long)gridDim.x * blockDim.x;
-  V accv = 0;  // per-thread partial in the vector precision (FP64 ALU is scarce)
-  for (long long base = (long long)blockIdx.x * blockDim.x; base < total; base += stride) {
-    const long long k = base + threadIdx.x;
-    int r = -1;
-    V a0 = 0, a1 = 0, a2 = 0;
-    if (k < total) {
-      const bool st = k < n_s;
-      const long long kk = st ? k : k - n_s;
-      r = st ? row_s[kk] : row_d[kk];
-      const int c = st ? col_s[kk] : col_d[kk];
-      const T* B = (st ? val_s : val_d) + 9 * (size_t)kk;
-      T b[9];
-#pragma unroll
-      for (int t = 0; t < 9; ++t) b[t] = B[t];
-      const V xc0 = x[3 * c], xc1 = x[3 * c + 1], xc2 = x[3 * c + 2];
-      const V xr0 = x[3 * r], xr1 = x[3 * r + 1], xr2 = x[3 * r + 2];
-      a0 = (V)b[0] * xc0 + (V)b[1] * xc1 + (V)b[2] * xc2;
-      a1 = (V)b[3] * xc0 + (V)b[4] * xc1 + (V)b[5] * xc2;
-      a2 = (V)b[6] * xc0 + (V)b[7] * xc1 + (V)b[8] * xc2;
-      accv += (V)2 * (xr0 * a0 + xr1 * a1 + xr2 * a2);
-      atomicAdd(&y[3 * c], (V)b[0] * xr0 + (V)b[3] * xr1 + (V)b[6] * xr2);
-      atomicAdd(&y[3 * c + 1], (V)b[1] * xr0 + (V)b[4] * xr1 + (V)b[7] * xr2);
-      atomicAdd(&y[3 * c + 2], (V)b[2] * xr0 + (V)b[5] * xr1 + (V)b[8] * xr2);
-    }
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int ro = __shfl_down_sync(0xffffffffu, r, o);
-      const V b0 = shfl_down_v(a0, o), b1 = shfl_down_v(a1, o), b2 = shfl_down_v(a2, o);
-      if (lane + o < 32 && ro == r) { a0 += b0; a1 += b1; a2 += b2; }
-    }
-    const int rp = __shfl_up_sync(0xffffffffu, r, 1);
-    if (r >= 0 && (lane == 0 || rp != r)) {
-      atomicAdd(&y[3 * r], a0);
-      atomicAdd(&y[3 * r + 1], a1);
-      atomicAdd(&y[3 * r + 2], a2);
-    }
+  const int nu = a.nfree + a.nb;
+  const int Ts = (a.n_s + L::NT - 1) / L::NT;
+  const int TT = Ts + (a.n_d + L::NT - 1) / L::NT;
+  const int J = (blockIdx.x < TT) ? (TT - 1 - (int)blockIdx.x) / G + 1 : 0;  // tiles of this block
+  double* partA = a.part;
+  double* partB = a.part + G;
+  double* partC = a.part + 2 * G;
+  unsigned gen = 0;  // arrival count that completes the next barrier, minus gridDim.x
+  // block 0's clock per iteration: 0 direction, 1 barrier, 2 SpMV, 3 barrier,
+  // 4 alpha, 5 update, 6 barrier, 7 beta
+  unsigned long long tph[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  unsigned long long tlast = 0;
+  auto stamp = [&](int k) {
+    const unsigned long long t = global_ns();
+    tph[k] += t - tlast;
+    tlast = t;
+  };
+  unsigned parity = 0u;    // bit b: phase parity of buffer b's next completion
+  unsigned inflight = 0u;  // bit b: buffer b has a request not yet waited for (thread 0's view)
+  if (threadIdx.x == 0) {
+    mbar_init(&mbar[0], 1);
+    mbar_init(&mbar[1], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  const double acc = (double)block_sum_v<V>(accv);
-  if (threadIdx.x == 0) part[n_dir_parts + blockIdx.x] = acc;
-}
+  __syncthreads();
 
-// one block: d^T H d from the partials in order, then alpha (a separate kernel:
-// a grid-wide "last block" counter serialises thousands of same-address atomics)
-__global__ void k_pcg_alpha_fin(const double* __restrict__ part, int nparts, pcg_dev* sc) {
-  if (sc->done) return;
-  const double dq = sum_partials(part, nparts);
-  if (threadIdx.x == 0) {
-    sc->dq = dq;
-    sc->alpha = (dq > 0.0) ? sc->rz / dq : 0.0;
-    if (!(dq > 0.0)) sc->done = 2;
+  // r = rhs, x = 0, d = 0, z = M^-1 r ; r^T z
+  V acc = 0;
+  for (long long i = tid; i < nu; i += nthr) {
+    int cnt;
+    size_t o;
+    unit_range((int)i, a.nfree, cnt, o);
+    for (int c = 0; c < cnt; ++c) {
+      a.r[o + c] = (V)a.rhs[o + c];
+      a.x[o + c] = 0;
+      a.d[o + c] = 0;
+    }
+    acc += precond_row<T, V>((int)i, a.nfree, a.Mi, a.r, a.z);
   }
-}
-// one block: r^T z from the partials, beta, iteration count, convergence
-__global__ void k_pcg_beta_fin(const double* __restrict__ part, int nparts, pcg_dev* sc) {
-  if (sc->done) return;
-  const double rz = sum_partials(part, nparts);
-  if (threadIdx.x == 0) {
-    sc->beta = rz / sc->rz;
-    sc->rz = rz;
-    sc->iters += 1;
-    if (rz <= sc->tol2 * sc->rz0) sc->done = 1;
+  V bs = block_sum_v<V>(acc);
+  if (threadIdx.x == 0) partC[blockIdx.x] = (double)bs;
+  int done = 0, it = 0;
+  if (!grid_barrier(a.bar, gen, a.spin_limit)) done = 3;
+  double rz = done ? 0.0 : grid_total(partC, G);
+  const double rz0 = rz;
+  double beta = 0.0;
+  if (!done && !(rz > 0.0)) done = 1;
+
+  while (!done && it < a.maxit) {
+    tlast = global_ns();
+    // the first two tiles of the SpMV travel while the direction is updated
+    if (threadIdx.x == 0)
+      for (int j = 0; j < 2 && j < J; ++j) {
+        issue_tile(a, (int)blockIdx.x + j * G, Ts, smem + j * L::BUF, &mbar[j]);
+        inflight |= 1u << j;
+      }
+    // A: d = z + beta d, q = D d, d^T D d
+    acc = 0;
+    const V vb = (V)beta;
+    for (long long i = tid; i < a.nn; i += 2 * nthr) {
+      acc += dir_node(a, i, vb);
+      if (i + nthr < a.nn) acc += dir_node(a, i + nthr, vb);
+    }
+    bs = block_sum_v<V>(acc);
+    if (threadIdx.x == 0) partA[blockIdx.x] = (double)bs;
+    stamp(0);
+    if (!grid_barrier(a.bar, gen, a.spin_limit)) { done = 3; break; }
+    stamp(1);
+    // B: q += (U + U^T) d, 2 d^T U d, tile by tile from shared memory
+    acc = 0;
+    bool ok = true;
+    for (int j = 0; j < J; ++j) {
+      const int b = j & 1;
+      if (!mbar_wait_bounded(&mbar[b], (parity >> b) & 1u, a.spin_limit >> 3)) { ok = false; }
+      parity ^= 1u << b;
+      inflight &= ~(1u << b);
+      if (__syncthreads_or(!ok)) { ok = false; break; }
+      const unsigned char* buf = smem + b * L::BUF;
+      const int t = (int)blockIdx.x + j * G;
+      const int cnt = (t < Ts) ? min(L::NT, a.n_s - t * L::NT) : min(L::NT, a.n_d - (t - Ts) * L::NT);
+      // two blocks per thread (k and k + NT/2, each warp on 32 consecutive
+      // blocks): both gathers of d are in flight before either is used
+      const int* rows = reinterpret_cast<const int*>(buf + L::VB);
+      const int* cols = reinterpret_cast<const int*>(buf + L::VB + L::IB);
+      const T* vals = reinterpret_cast<const T*>(buf);
+      const int k0 = threadIdx.x, k1 = threadIdx.x + L::NT / 2;
+      const int r0 = (k0 < cnt) ? rows[k0] : -1, c0 = (k0 < cnt) ? cols[k0] : 0;
+      const int r1 = (k1 < cnt) ? rows[k1] : -1, c1 = (k1 < cnt) ? cols[k1] : 0;
+      gath<V> g0, g1;
+      gather_d(r0, c0, a.d, g0);
+      gather_d(r1, c1, a.d, g1);
+      acc += apply_blk<T, V>(r0, c0, vals + 9 * k0, g0, a.q, lane);
+      acc += apply_blk<T, V>(r1, c1, vals + 9 * k1, g1, a.q, lane);
+      __syncthreads();  // every thread is done with buffer b
+      if (threadIdx.x == 0 && j + 2 < J) {
+        issue_tile(a, (int)blockIdx.x + (j + 2) * G, Ts, smem + b * L::BUF, &mbar[b]);
+        inflight |= 1u << b;
+      }
+    }
+    if (!ok) {
+      // give up: wait (bounded) for this block's own copies still in flight
+      if (threadIdx.x == 0) {
+        atomicExch(&a.bar->abort, 1);
+        for (int b = 0; b < 2; ++b)
+          if ((inflight >> b) & 1u) mbar_wait_bounded(&mbar[b], (parity >> b) & 1u, a.spin_limit);
+      }
+      done = 3;
+      break;
+    }
+    bs = block_sum_v<V>(acc);
+    if (threadIdx.x == 0) partB[blockIdx.x] = (double)bs;
+    stamp(2);
+    if (!grid_barrier(a.bar, gen, a.spin_limit)) { done = 3; break; }
+    stamp(3);
+    const double dHd = grid_total(partA, G) + grid_total(partB, G);
+    stamp(4);
+    if (!(dHd > 0.0)) { done = 2; break; }
+    const V alpha = (V)(rz / dHd);
+    // C: x += alpha d, r -= alpha q, z = M^-1 r, r^T z
+    acc = 0;
+    for (long long i = tid; i < a.nfree; i += 2 * nthr) {
+      acc += update_free(a, i, alpha);
+      if (i + nthr < a.nfree) acc += update_free(a, i + nthr, alpha);
+    }
+    for (long long bi = tid; bi < a.nb; bi += nthr) {
+      const int i = a.nfree + (int)bi;
+      const size_t o = 3 * ((size_t)a.nfree + 4 * (size_t)bi);
+      for (int c = 0; c < 12; ++c) {
+        a.x[o + c] += alpha * a.d[o + c];
+        a.r[o + c] -= alpha * a.q[o + c];
+      }
+      acc += precond_row<T, V>(i, a.nfree, a.Mi, a.r, a.z);
+    }
+    bs = block_sum_v<V>(acc);
+    if (threadIdx.x == 0) partC[blockIdx.x] = (double)bs;
+    stamp(5);
+    if (!grid_barrier(a.bar, gen, a.spin_limit)) { done = 3; break; }
+    stamp(6);
+    const double rz_new = grid_total(partC, G);
+    beta = rz_new / rz;
+    rz = rz_new;
+    ++it;
+    if (rz <= a.tol2 * rz0) done = 1;
+    stamp(7);
   }
+  // a block that left after its direction phase (barrier abort) may still have
+  // tile copies in flight: wait for them (bounded) before the block exits
+  if (threadIdx.x == 0)
+    for (int b = 0; b < 2; ++b)
+      if ((inflight >> b) & 1u) mbar_wait_bounded(&mbar[b], (parity >> b) & 1u, a.spin_limit);
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    a.sc->rz = rz;
+    a.sc->rz0 = rz0;
+    a.sc->done = done;
+    a.sc->iters = it;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) a.sc->t_ns[k] = tph[k];
+  }
+  if (threadIdx.x == 0 && done == 3) dev_flag(a.status, DEV_TIMEOUT);
 }
 
 template <typename V>
@@ -501,92 +738,89 @@ yasps_status spmv_t(yasps_system* s, const V* x, V* y, const int* done) {
   return YASPS_OK;
 }
 
+// grid of the persistent kernel: as many blocks as can be co-resident (a
+// cooperative launch refuses a larger grid instead of deadlocking)
+template <typename T, typename V>
+yasps_status pcg_grid(yasps_system* s, int* G) {
+  int dev = 0, sms = 0, coop = 0, per_sm = 0;
+  CK(s, cudaGetDevice(&dev));
+  CK(s, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  CK(s, cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+  if (!coop) SYS_FAIL(s, YASPS_E_CUDA, "device does not support cooperative launches");
+  const unsigned smem = stage_layout<T>::SMEM;
+  CK(s, cudaFuncSetAttribute(k_pcg_persistent<T, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  CK(s, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pcg_persistent<T, V>, pcg_threads<T>::N, smem));
+  if (per_sm < 1) SYS_FAIL(s, YASPS_E_CUDA, "persistent PCG kernel cannot be resident");
+  *G = sms * std::min(per_sm, 2);
+  return YASPS_OK;
+}
+
 // PCG in precision (T, V) on H dx = rhs (FP64 rhs); dx accumulated into p (FP64).
 template <typename T, typename V>
 yasps_status pcg_inner(yasps_system* s, const double* rhs, double* p, double tol, int maxit, int* iters, int* state,
                        double* rel) {
   const int n3 = 3 * s->nn;
   for (int k = 0; k < 5; ++k) ENSURE(s, s->vec[k], sizeof(V) * (n3 + 4));
-  V *x = as<V>(s->vec[0]), *r = as<V>(s->vec[1]), *z = as<V>(s->vec[2]), *d = as<V>(s->vec[3]), *q = as<V>(s->vec[4]);
-  const int nu = s->nfree + s->nb;
-  const int nblk_u = blocks_for(std::max(nu, 1), PT_);
-  const int nblk_dir = blocks_for(std::max(s->nn, 1), PT_);
-  const long long nup = (long long)s->Hs.nnzb + s->Hd.nnzb;
-  const int nblk_up = (int)std::max<long long>(1, (nup + PT_ - 1) / PT_);  // one block per thread
-  ENSURE(s, s->scal, sizeof(pcg_dev) + 64);
-  ENSURE(s, s->red, sizeof(double) * ((size_t)nblk_u + nblk_dir + nblk_up + 8));
+  int G = 0;
+  RC((pcg_grid<T, V>(s, &G)));
+  ENSURE(s, s->scal, 256);
+  ENSURE(s, s->red, sizeof(double) * (3 * (size_t)G + 8));
   pcg_dev* sc = as<pcg_dev>(s->scal);
-  double* part = as<double>(s->red);          // dir + SpMV partials
-  double* part2 = part + nblk_dir + nblk_up;  // update partials
+  pcg_bar* bar = reinterpret_cast<pcg_bar*>(static_cast<char*>(s->scal.p) + 128);
+  pcg_args<T, V> a;
+  a.nn = s->nn;
+  a.nfree = s->nfree;
+  a.nb = s->nb;
+  a.n_s = s->Hs.nnzb;
+  a.n_d = s->Hd.nnzb;
+  a.maxit = maxit;
+  a.tol2 = tol * tol;
+  a.row_s = as<int>(s->Hs.row);
+  a.col_s = as<int>(s->Hs.col);
+  a.val_s = as<T>(s->Hs.vals);
+  a.row_d = as<int>(s->Hd.row);
+  a.col_d = as<int>(s->Hd.col);
+  a.val_d = as<T>(s->Hd.vals);
+  a.D = as<T>(s->diag);
+  a.Mi = as<T>(s->minv);
+  a.rhs = rhs;
+  a.x = as<V>(s->vec[0]);
+  a.r = as<V>(s->vec[1]);
+  a.z = as<V>(s->vec[2]);
+  a.d = as<V>(s->vec[3]);
+  a.q = as<V>(s->vec[4]);
+  a.part = as<double>(s->red);
+  a.sc = sc;
+  a.bar = bar;
+  a.status = as<int>(s->status);
+  a.spin_limit = 1LL << 22;  // a few seconds of polling per wait
+  CK(s, cudaMemsetAsync(s->scal.p, 0, 256, s->stream));
+  void* params[] = {&a};
+  cudaEvent_t pk = prof_begin(s);
+  CK(s, cudaLaunchCooperativeKernel((const void*)k_pcg_persistent<T, V>, dim3(G), dim3(pcg_threads<T>::N), params, stage_layout<T>::SMEM,
+                                    s->stream));
+  s->launches += 1;
+  prof_end(s, YASPS_STAGE_PCG_KERNEL, pk, 0.0);
   pcg_dev h{};
-  h.tol2 = tol * tol;
-  const T* Mi = as<T>(s->minv);
-  const T* D = as<T>(s->diag);
-  // the iterations run on the library's own stream as CUDA graphs of
-  // check_every iterations (3 kernels each), fenced to the caller's stream
-  cudaStream_t cs = s->cstream;
-  CK(s, cudaEventRecord(s->fence[0], s->stream));
-  CK(s, cudaStreamWaitEvent(cs, s->fence[0], 0));
-  CK(s, cudaMemcpyAsync(sc, &h, sizeof(pcg_dev), cudaMemcpyHostToDevice, cs));
-  k_pcg_init<T, V><<<nblk_u, PT_, 0, cs>>>(s->nfree, s->nb, rhs, Mi, x, r, z, d, part, sc);
-  LAUNCH_CHECK(s, "k_pcg_init");
-  const int check_every = kPcgChunk;
-  const double es = sizeof(T);
-  const double spmv_bytes = (double)(s->Hs.nnzb + s->Hd.nnzb) * (9 * es + 4) + (double)s->nn * (9 * es + 4) +
-                            4.0 * 3.0 * sizeof(V) * s->nn;
-  const bool prof = s->prof_on;
-  cudaGraph_t graph = nullptr;
-  cudaGraphExec_t exec = nullptr;
-  CK(s, cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
-  for (int k = 0; k < check_every; ++k) {
-    if (prof) cudaEventRecordWithFlags(s->spmv_ev[2 * k], cs, cudaEventRecordExternal);
-    k_pcg_dir_dd<T, V><<<nblk_dir, PT_, 0, cs>>>(s->nn, D, z, d, q, sc, part);
-    k_spmv_both<T, V><<<nblk_up, PT_, 0, cs>>>(s->Hs.nnzb, as<int>(s->Hs.row), as<int>(s->Hs.col), as<T>(s->Hs.vals),
-                                               s->Hd.nnzb, as<int>(s->Hd.row), as<int>(s->Hd.col), as<T>(s->Hd.vals),
-                                               d, q, sc, part, nblk_dir);
-    if (prof) cudaEventRecordWithFlags(s->spmv_ev[2 * k + 1], cs, cudaEventRecordExternal);
-    k_pcg_alpha_fin<<<1, 1024, 0, cs>>>(part, nblk_dir + nblk_up, sc);
-    k_pcg_update<T, V><<<nblk_u, PT_, 0, cs>>>(s->nfree, s->nb, Mi, x, r, z, d, q, part2, sc);
-    k_pcg_beta_fin<<<1, 1024, 0, cs>>>(part2, nblk_u, sc);
+  CK(s, cudaMemcpyAsync(&h, sc, sizeof(pcg_dev), cudaMemcpyDeviceToHost, s->stream));
+  CK(s, cudaStreamSynchronize(s->stream));
+  if (s->prof_on) {
+    const double es = sizeof(T), vs = sizeof(V), nn = s->nn;
+    const double nnzb = (double)s->Hs.nnzb + s->Hd.nnzb;
+    // SpMV phase: blocks + column index + row pointer, D, d read, q written
+    const double spmv_bytes = nnzb * (9 * es + 4) + nn * 4 + nn * 9 * es + 3 * vs * nn * 4;
+    // whole iteration: SpMV phase + C (x, d, r, q read; x, r, z written; M^-1)
+    const double iter_bytes = spmv_bytes + 3 * vs * nn * 7 + nn * 9 * es;
+    s->prof_acc[YASPS_STAGE_PCG_KERNEL].bytes += iter_bytes * h.iters;
+    auto& sp = s->prof_acc[YASPS_STAGE_SPMV];
+    sp.count += h.iters;
+    sp.ms += (h.t_ns[0] + h.t_ns[1] + h.t_ns[2] + h.t_ns[3]) * 1e-6;
+    for (int k = 0; k < 8; ++k) s->pcg_phase_ms[k] += h.t_ns[k] * 1e-6;
+    sp.bytes += spmv_bytes * h.iters;
   }
-  cudaError_t ce = cudaStreamEndCapture(cs, &graph);
-  if (ce == cudaSuccess) ce = cudaGraphInstantiate(&exec, graph, 0);
-  if (ce != cudaSuccess) {
-    if (graph) cudaGraphDestroy(graph);
-    return cuda_check(s, ce, "PCG graph capture");
-  }
-  int it = 0;
-  yasps_status rc = YASPS_OK;
-  for (;;) {
-    ce = cudaGraphLaunch(exec, cs);
-    s->launches += 5LL * check_every;
-    if (ce == cudaSuccess) ce = cudaMemcpyAsync(&h, sc, sizeof(pcg_dev), cudaMemcpyDeviceToHost, cs);
-    if (ce == cudaSuccess) ce = cudaStreamSynchronize(cs);
-    if (ce != cudaSuccess) {
-      rc = cuda_check(s, ce, "PCG graph launch");
-      break;
-    }
-    if (prof) {  // only the products of iterations that really ran
-      const int real = std::min(check_every, std::max(0, h.iters - it));
-      for (int k = 0; k < real; ++k) {
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, s->spmv_ev[2 * k], s->spmv_ev[2 * k + 1]);
-        auto& a = s->prof_acc[YASPS_STAGE_SPMV];
-        a.count += 1;
-        a.ms += ms;
-        a.bytes += spmv_bytes;
-      }
-    }
-    it += check_every;
-    if (h.done || h.iters >= maxit || it >= maxit) break;
-  }
-  cudaGraphExecDestroy(exec);
-  cudaGraphDestroy(graph);
-  RC(rc);
-  k_add_to<V><<<blocks_for(n3, 256), 256, 0, cs>>>(n3, p, x);
+  if (h.done == 3) SYS_FAIL(s, YASPS_E_TIMEOUT, "PCG grid barrier timed out");
+  k_add_to<V><<<blocks_for(n3, 256), 256, 0, s->stream>>>(n3, p, a.x);
   LAUNCH_CHECK(s, "k_add_to");
-  CK(s, cudaEventRecord(s->fence[1], cs));
-  CK(s, cudaStreamWaitEvent(s->stream, s->fence[1], 0));
   *iters = h.iters;
   *state = h.done;
   *rel = (h.rz0 > 0.0) ? std::sqrt(std::max(h.rz, 0.0) / h.rz0) : 0.0;

@@ -234,8 +234,8 @@ yasps_status bsr_from_keys(yasps_system* s, uint64_t* keys, int* vals, int n, bs
   int nnzb = 0;
   RC(scan_exclusive(s, head, head, n, &nnzb));
   B.nnzb = nnzb;
-  ENSURE(s, B.col, sizeof(int) * (nnzb + 1));
-  ENSURE(s, B.row, sizeof(int) * (nnzb + 1));
+  ENSURE(s, B.col, sizeof(int) * (nnzb + 4));  // slack: bulk copies round up to 16 bytes
+  ENSURE(s, B.row, sizeof(int) * (nnzb + 4));
   k_bsr_fill<<<blocks_for(n, 256), 256, 0, s->stream>>>(keys, vals, head, n, sentinel, nbits, as<int>(B.col),
                                                         as<int>(B.row), as<int>(B.row_ptr), slot_of);
   LAUNCH_CHECK(s, "k_bsr_fill");

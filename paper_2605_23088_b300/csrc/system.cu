@@ -115,8 +115,16 @@ yasps_status yasps_profile_enable(yasps_system* s, int enable) {
   if (!s) return YASPS_E_INVAL;
   prof_resolve(s);
   s->prof_on = enable != 0;
-  if (enable)
+  if (enable) {
     for (auto& a : s->prof_acc) a = yasps_stage_stats{0, 0.0, 0.0};
+    for (auto& t : s->pcg_phase_ms) t = 0.0;
+  }
+  return YASPS_OK;
+}
+
+yasps_status yasps_pcg_phase_ms(const yasps_system* s, double* out) {
+  if (!s || !out) return YASPS_E_INVAL;
+  for (int k = 0; k < 8; ++k) out[k] = s->pcg_phase_ms[k];
   return YASPS_OK;
 }
 
@@ -301,14 +309,6 @@ yasps_status yasps_build_system(const yasps_scene_desc* scene, const yasps_param
     s->have_allocator = true;
   }
   for (auto& e : s->ev) cudaEventCreate(&e);
-  for (auto& e : s->fence) cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
-  for (auto& e : s->spmv_ev) cudaEventCreate(&e);
-  if (cudaStreamCreateWithFlags(&s->cstream, cudaStreamNonBlocking) != cudaSuccess) {
-    cudaGetLastError();
-    g_build_error = "cudaStreamCreateWithFlags failed";
-    yasps_destroy(s);
-    return YASPS_E_CUDA;
-  }
   yasps_status rc = build_impl(s, scene);
   if (rc != YASPS_OK) {
     g_build_error = s->err;
@@ -329,14 +329,6 @@ void yasps_destroy(yasps_system* s) {
   cudaStreamSynchronize(s->stream);
   for (auto& e : s->ev)
     if (e) cudaEventDestroy(e);
-  for (auto& e : s->fence)
-    if (e) cudaEventDestroy(e);
-  for (auto& e : s->spmv_ev)
-    if (e) cudaEventDestroy(e);
-  if (s->cstream) {
-    cudaStreamSynchronize(s->cstream);
-    cudaStreamDestroy(s->cstream);
-  }
   delete s;
 }
 
