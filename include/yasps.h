@@ -265,12 +265,13 @@ long long yasps_kernel_launches(const yasps_system* sys);
  * instance of a stage with CUDA events recorded on its own stream and keeps,
  * per stage, the count, the summed event time and the algorithmic bytes the
  * stage must move (inputs read once, unique outputs written once):
- *   YASPS_STAGE_SPMV     the H d phase of one PCG iteration: direction update,
- *                        diagonal product and both upper BSR parts, timed with
- *                        the device's global timer inside the PCG kernel
- *                        (count = iterations; bytes: nnzb (9 s + 4) + 4 n
- *                        + 9 s n + 4 * 3 v n, s = bytes per Hessian scalar,
- *                        v = bytes per vector scalar, n = nodes);
+ *   YASPS_STAGE_SPMV     the H d phase of one PCG iteration (new direction,
+ *                        diagonal product, both upper BSR parts, and the
+ *                        grid-wide d^T H d), timed with the device's global
+ *                        timer inside the PCG kernel (count = iterations;
+ *                        bytes: nnzb (9 s + 4) + 4 n + 9 s n + 4 * 3 v n,
+ *                        s = bytes per Hessian scalar, v = bytes per vector
+ *                        scalar, n = nodes);
  *   YASPS_STAGE_TET      the Neo-Hookean tet gradient / projected-Hessian kernel;
  *   YASPS_STAGE_BARRIER  the contact-barrier evaluation kernels;
  *   YASPS_STAGE_PCG      one whole PCG solve;
@@ -280,7 +281,7 @@ long long yasps_kernel_launches(const yasps_system* sys);
  *   YASPS_STAGE_LS       the line search's energy evaluations (in yasps_step);
  *   YASPS_STAGE_PCG_KERNEL one launch of the persistent PCG kernel (all the
  *                        iterations of a solve or of one refinement sweep);
- *                        bytes = iterations x (SpMV bytes + 7 * 3 v n + 9 s n).
+ *                        bytes = iterations x (SpMV bytes + 8 * 3 v n + 9 s n).
  * Enabling (enable != 0) resets the counters.  yasps_profile_get synchronises. */
 #define YASPS_STAGE_SPMV 0
 #define YASPS_STAGE_TET 1
@@ -302,10 +303,11 @@ yasps_status yasps_profile_get(yasps_system* sys, int stage, yasps_stage_stats* 
 
 /* Where the PCG kernel's time goes, summed over the iterations run while
  * profiling was enabled (ms, read from the device's global timer by the
- * kernel's first block): out[8] = direction phase, wait at the grid barrier,
- * SpMV phase, wait, alpha reduction, update + preconditioner phase, wait,
- * beta reduction.  Waits include the time the slowest block of the grid needs
- * beyond the first. */
+ * kernel's first block): out[0] the block's own nodes (new direction and
+ * diagonal product), out[1] the upper BSR blocks, out[2] the wait for the
+ * grid's d^T H d, out[3] the update + preconditioner phase, out[4] the wait
+ * for the grid's r^T z; out[5..7] = 0.  Waits include the time the slowest
+ * block of the grid needs beyond the first. */
 yasps_status yasps_pcg_phase_ms(const yasps_system* sys, double* out);
 
 /* Block-Jacobi PCG that allocates no device memory (the paper has no

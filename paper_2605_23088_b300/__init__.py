@@ -32,7 +32,7 @@ EXPORTS = [
 ]
 STAGE_SPMV, STAGE_TET, STAGE_BARRIER, STAGE_PCG, STAGE_DETECT, STAGE_EVAL, STAGE_CCD, STAGE_LS, STAGE_PCG_KERNEL = range(9)
 STAGE_NAMES = ["spmv", "tet", "barrier", "pcg", "detect", "eval", "ccd", "line_search", "pcg_kernel"]
-PCG_PHASES = ["direction", "wait_a", "spmv", "wait_b", "alpha", "update", "wait_c", "beta"]
+PCG_PHASES = ["own_nodes", "upper_blocks", "wait_dHd", "update", "wait_rz", "unused5", "unused6", "unused7"]
 
 
 class YaspsError(RuntimeError):
@@ -356,8 +356,8 @@ class System:
         return {"count": st.count, "ms": st.ms, "bytes": st.bytes}
 
     def pcg_phase_ms(self):
-        """Per-phase time of the PCG kernel while profiling (ms): direction, wait,
-        SpMV, wait, alpha, update, wait, beta."""
+        """Per-phase time of the PCG kernel while profiling (ms): own nodes' direction
+        and diagonal product, upper blocks, wait + d^T H d, update, wait + r^T z."""
         out = np.zeros(8)
         self._check(lib().yasps_pcg_phase_ms(self.h, out.ctypes.data_as(_PD)))
         return dict(zip(PCG_PHASES, out.tolist()))

@@ -40,11 +40,13 @@ struct pcg_dev {
   unsigned long long t_ns[8];  // block 0's time per phase, summed over iterations (see k_pcg_persistent)
 };
 // grid barrier state, zeroed before every launch: count only grows (barrier k
-// of a launch completes when it reaches k * gridDim.x)
+// of a launch completes when it reaches (k + 1) * gridDim.x); sum[k % 4]
+// collects the per-block partials reduced at barrier k
 struct pcg_bar {
   unsigned count;
   int abort;
   int pad[2];
+  double sum[4];
 };
 
 // ---------------------------------------------------------------- SpMV
@@ -250,6 +252,14 @@ __device__ __forceinline__ V precond_row(int i, int nfree, const T* __restrict__
 }
 
 // ---------------------------------------------------------------- persistent PCG
+//
+// One cooperative launch (one block per SM) runs all iterations of a solve.
+// An iteration has two grid-wide phases, each closed by a reducing barrier:
+//   B  d' = z + beta d for the block's own nodes, q += D d', and the upper
+//      blocks' q += U d' + U^T d' (d' of other nodes is formed on the fly from
+//      z and d, which nobody writes during the phase); partial d'^T H d'
+//   C  x += alpha d', r -= alpha q, z = M^-1 r, q = 0; partial r^T z
+// d and d' swap roles every iteration.
 template <typename T, typename V>
 struct pcg_args {
   int nn, nfree, nb, n_s, n_d, maxit;
@@ -257,8 +267,8 @@ struct pcg_args {
   const int *row_s, *col_s, *row_d, *col_d;
   const T *val_s, *val_d, *D, *Mi;
   const double* rhs;
-  V *x, *r, *z, *d, *q;  // written and read across blocks: plain (coherent) loads only
-  double* part;          // [3][gridDim.x] per-block partials of the three phases
+  V *x, *r, *z, *q;  // written and read across blocks: plain (coherent) loads only
+  V *d0, *d1;        // the direction, ping-ponged between iterations
   pcg_dev* sc;
   pcg_bar* bar;
   int* status;
@@ -270,14 +280,6 @@ __device__ __forceinline__ unsigned long long global_ns() {
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
   return t;
 }
-
-// Grid-wide barrier for a cooperative launch (all blocks co-resident).  After
-// a block-level sync, thread 0 of each block adds 1 to the arrival count with
-// release semantics (publishing everything the block wrote) and polls it with
-// acquire loads until it reaches this barrier's target.  The wait is bounded:
-// after spin_limit polls the block raises the abort flag, and every waiting
-// block also leaves when it sees the flag, so no block waits forever.  Returns
-// false when the grid has aborted.
 __device__ __forceinline__ void red_add_release(unsigned* p, unsigned v) {
   asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
@@ -286,13 +288,28 @@ __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
   asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
   return v;
 }
-__device__ __forceinline__ bool grid_barrier(pcg_bar* bar, unsigned& target, long long spin_limit) {
+
+// Reducing grid barrier k for a cooperative launch (all blocks co-resident).
+// Thread 0 of each block adds the block's partial into sum[k % 4], then adds 1
+// to the arrival count with release semantics (publishing everything the block
+// wrote) and polls the count with acquire loads until all blocks arrived; it
+// then reads the total and hands it to the block.  Slot (k - 1) % 4 is dead
+// once barrier k completes (every block read it before arriving), so block 0
+// clears it for barrier k + 3.  The wait is bounded: after spin_limit polls
+// the block raises the abort flag, and every waiting block also leaves when it
+// sees the flag, so no block waits forever.  Returns false when the grid has
+// aborted.  Float addition order in the slot follows arrival order, so totals
+// can differ in the last bits from run to run (never between blocks).
+__device__ __forceinline__ bool grid_reduce(pcg_bar* bar, unsigned& k, double partial, double& total,
+                                            long long spin_limit) {
   __shared__ int ok;
+  __shared__ double tot;
   __syncthreads();
   if (threadIdx.x == 0) {
     int good = 1;
-    target += gridDim.x;
+    atomicAdd(&bar->sum[k & 3], partial);
     red_add_release(&bar->count, 1u);
+    const unsigned target = (k + 1) * gridDim.x;
     long long spins = 0;
     while (ld_acquire(&bar->count) < target) {
       if ((++spins & 255) == 0) {
@@ -300,40 +317,25 @@ __device__ __forceinline__ bool grid_barrier(pcg_bar* bar, unsigned& target, lon
         if (spins > spin_limit) { atomicExch(&bar->abort, 1); good = 0; break; }
       }
     }
+    tot = *(volatile double*)&bar->sum[k & 3];
+    if (blockIdx.x == 0 && k > 0) bar->sum[(k - 1) & 3] = 0.0;
     ok = good && !*(volatile int*)&bar->abort;
   }
   __syncthreads();
+  k += 1;
+  total = tot;
   return ok != 0;
-}
-
-// sum of the n per-block partials in block order, the same value in every thread
-__device__ double grid_total(const double* part, int n) {
-  __shared__ double sh[32];
-  __shared__ double tot;
-  double v = 0.0;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) v += __ldcg(part + i);
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    double w = (threadIdx.x < (blockDim.x >> 5)) ? sh[threadIdx.x] : 0.0;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
-    if (threadIdx.x == 0) tot = w;
-  }
-  __syncthreads();
-  return tot;
 }
 
 // ---- shared-memory staging of the upper blocks (bulk async copies)
 //
-// The SpMV phase walks the upper blocks in tiles of one block per thread.  A
+// Each block owns an even, 4-aligned share of the static upper blocks and a
+// chunk of the dynamic ones, walked in tiles of two blocks per thread.  A
 // tile's values, rows and columns are contiguous, so thread 0 moves them into
 // shared memory with three cp.async.bulk copies completing on an mbarrier,
-// double-buffered: the copies of the next tiles are in flight while the
-// current tile is multiplied, and the first two tiles of an iteration are
-// requested before its direction phase.  Only the gathers of d stay exposed.
+// double-buffered: the next tile travels while the current one is multiplied,
+// and the first two travel while the block does its own nodes' diagonal part.
+// Only the gathers of z and d stay exposed.
 template <typename T>
 struct stage_layout {
   static constexpr int NT = 2 * pcg_threads<T>::N;     // blocks per tile (two per thread)
@@ -374,6 +376,27 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* m, unsigned parity, 
   return false;
 }
 
+// this block's share of the upper blocks: static [s0, s1), dynamic [e0, e1)
+struct spmv_share {
+  int s0, s1, e0, e1, ts, tt;  // ts static tiles, tt tiles in all
+};
+template <typename T, typename V>
+__device__ __forceinline__ spmv_share share_of(const pcg_args<T, V>& a) {
+  constexpr int NT = stage_layout<T>::NT;
+  const long long G = gridDim.x, b = blockIdx.x;
+  spmv_share o;
+  o.s0 = (int)((b * a.n_s / G) & ~3LL);
+  o.s1 = (b + 1 == G) ? a.n_s : (int)(((b + 1) * a.n_s / G) & ~3LL);
+  // dynamic blocks in 4-aligned chunks of at least 512, from the last block down
+  long long dc = (a.n_d + G - 1) / G;
+  dc = dc < 512 ? 512 : ((dc + 3) & ~3LL);
+  const long long c = G - 1 - b;
+  o.e0 = (int)(c * dc < a.n_d ? c * dc : a.n_d);
+  o.e1 = (int)((c + 1) * dc < a.n_d ? (c + 1) * dc : a.n_d);
+  o.ts = (o.s1 - o.s0 + NT - 1) / NT;
+  o.tt = o.ts + (o.e1 - o.e0 + NT - 1) / NT;
+  return o;
+}
 template <typename T, typename V>
 struct tile_src {
   const T* vals;
@@ -381,27 +404,26 @@ struct tile_src {
   int base, cnt;
 };
 template <typename T, typename V>
-__device__ __forceinline__ tile_src<T, V> tile_of(const pcg_args<T, V>& a, int t, int Ts) {
+__device__ __forceinline__ tile_src<T, V> tile_of(const pcg_args<T, V>& a, const spmv_share& sh, int j) {
   constexpr int NT = stage_layout<T>::NT;
   tile_src<T, V> o;
-  if (t < Ts) {
+  if (j < sh.ts) {
     o.vals = a.val_s; o.row = a.row_s; o.col = a.col_s;
-    o.base = t * NT;
-    o.cnt = min(NT, a.n_s - o.base);
+    o.base = sh.s0 + j * NT;
+    o.cnt = min(NT, sh.s1 - o.base);
   } else {
     o.vals = a.val_d; o.row = a.row_d; o.col = a.col_d;
-    o.base = (t - Ts) * NT;
-    o.cnt = min(NT, a.n_d - o.base);
+    o.base = sh.e0 + (j - sh.ts) * NT;
+    o.cnt = min(NT, sh.e1 - o.base);
   }
   return o;
 }
-// thread 0: request tile t into buffer b.  Tile starts are multiples of NT
+// thread 0: request tile j into buffer buf.  Tile starts are multiples of 4
 // blocks, so every source address is 16-byte aligned; sizes are rounded up to
 // 16 bytes (the arrays carry that much slack).
 template <typename T, typename V>
-__device__ __forceinline__ void issue_tile(const pcg_args<T, V>& a, int t, int Ts, unsigned char* buf, uint64_t* m) {
+__device__ __forceinline__ void issue_tile(const tile_src<T, V>& src, unsigned char* buf, uint64_t* m) {
   using L = stage_layout<T>;
-  const tile_src<T, V> src = tile_of(a, t, Ts);
   const unsigned bv = (unsigned)(src.cnt * 9 * (int)sizeof(T) + 15) & ~15u;
   const unsigned bi = (unsigned)(src.cnt * (int)sizeof(int) + 15) & ~15u;
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -411,20 +433,29 @@ __device__ __forceinline__ void issue_tile(const pcg_args<T, V>& a, int t, int T
   bulk_g2s(buf + L::VB + L::IB, src.col + src.base, bi, m);
 }
 
-// the two d segments one block needs
+// the new direction z + beta d, one rounding per component (the same
+// expression wherever it is formed, so every thread sees the same d')
+YASPS_D float dnew(float z, float beta, float d) { return __fmaf_rn(beta, d, z); }
+YASPS_D double dnew(double z, double beta, double d) { return __fma_rn(beta, d, z); }
+
+// the two d' segments one block needs
 template <typename V>
 struct gath {
   V c0, c1, c2, r0, r1, r2;
 };
 template <typename V>
-__device__ __forceinline__ void gather_d(int r, int c, const V* d, gath<V>& g) {
+__device__ __forceinline__ void gather_d(int r, int c, const V* z, const V* d, V beta, gath<V>& g) {
   if (r >= 0) {
-    g.c0 = d[3 * c]; g.c1 = d[3 * c + 1]; g.c2 = d[3 * c + 2];
-    g.r0 = d[3 * r]; g.r1 = d[3 * r + 1]; g.r2 = d[3 * r + 2];
+    const V zc0 = z[3 * c], zc1 = z[3 * c + 1], zc2 = z[3 * c + 2];
+    const V zr0 = z[3 * r], zr1 = z[3 * r + 1], zr2 = z[3 * r + 2];
+    const V dc0 = d[3 * c], dc1 = d[3 * c + 1], dc2 = d[3 * c + 2];
+    const V dr0 = d[3 * r], dr1 = d[3 * r + 1], dr2 = d[3 * r + 2];
+    g.c0 = dnew(zc0, beta, dc0); g.c1 = dnew(zc1, beta, dc1); g.c2 = dnew(zc2, beta, dc2);
+    g.r0 = dnew(zr0, beta, dr0); g.r1 = dnew(zr1, beta, dr1); g.r2 = dnew(zr2, beta, dr2);
   }
 }
-// q += B d_c into the row (segmented over the warp), q += B^T d_r into the
-// column; returns the block's share 2 d_r^T B d_c of d^T U d
+// q += B d'_c into the row (segmented over the warp), q += B^T d'_r into the
+// column; returns the block's share 2 d'_r^T B d'_c of d'^T U d'
 template <typename T, typename V>
 __device__ __forceinline__ V apply_blk(int r, int c, const T* b, const gath<V>& g, V* q, int lane) {
   V a0 = 0, a1 = 0, a2 = 0, part = 0;
@@ -460,27 +491,28 @@ __device__ __forceinline__ void unit_range(int i, int nfree, int& cnt, size_t& o
   o = (i < nfree) ? 3 * (size_t)i : 3 * ((size_t)nfree + 4 * (size_t)(i - nfree));
 }
 
-// phase A for one node: every load before any store (the vectors may alias
-// as far as the compiler knows)
+// own node i in phase B: d'_i = z_i + beta d_i, q_i += D_i d'_i; d'_i^T D_i d'_i
 template <typename T, typename V>
-__device__ __forceinline__ V dir_node(const pcg_args<T, V>& a, long long i, V beta) {
+__device__ __forceinline__ V diag_node(const pcg_args<T, V>& a, long long i, V beta, const V* d, V* dn) {
   const T* B = a.D + 9 * (size_t)i;
   T m[9];
 #pragma unroll
   for (int t = 0; t < 9; ++t) m[t] = __ldg(B + t);
   const V z0 = a.z[3 * i], z1 = a.z[3 * i + 1], z2 = a.z[3 * i + 2];
-  const V e0 = a.d[3 * i], e1 = a.d[3 * i + 1], e2 = a.d[3 * i + 2];
-  const V d0 = z0 + beta * e0, d1 = z1 + beta * e1, d2 = z2 + beta * e2;
+  const V e0 = d[3 * i], e1 = d[3 * i + 1], e2 = d[3 * i + 2];
+  const V d0 = dnew(z0, beta, e0), d1 = dnew(z1, beta, e1), d2 = dnew(z2, beta, e2);
   const V q0 = (V)m[0] * d0 + (V)m[1] * d1 + (V)m[2] * d2;
   const V q1 = (V)m[3] * d0 + (V)m[4] * d1 + (V)m[5] * d2;
   const V q2 = (V)m[6] * d0 + (V)m[7] * d1 + (V)m[8] * d2;
-  a.d[3 * i] = d0; a.d[3 * i + 1] = d1; a.d[3 * i + 2] = d2;
-  a.q[3 * i] = q0; a.q[3 * i + 1] = q1; a.q[3 * i + 2] = q2;
+  dn[3 * i] = d0; dn[3 * i + 1] = d1; dn[3 * i + 2] = d2;
+  atomicAdd(&a.q[3 * i], q0);
+  atomicAdd(&a.q[3 * i + 1], q1);
+  atomicAdd(&a.q[3 * i + 2], q2);
   return d0 * q0 + d1 * q1 + d2 * q2;
 }
-// phase C for one free node: x += alpha d, r -= alpha q, z = M^-1 r; r^T z
+// phase C for one free node: x += alpha d', r -= alpha q, z = M^-1 r, q = 0; r^T z
 template <typename T, typename V>
-__device__ __forceinline__ V update_free(const pcg_args<T, V>& a, long long i, V alpha) {
+__device__ __forceinline__ V update_free(const pcg_args<T, V>& a, long long i, V alpha, const V* dn) {
   const T* M = a.Mi + 9 * (size_t)i;
   T m[9];
 #pragma unroll
@@ -489,7 +521,7 @@ __device__ __forceinline__ V update_free(const pcg_args<T, V>& a, long long i, V
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
     xv[c] = a.x[3 * i + c];
-    dv[c] = a.d[3 * i + c];
+    dv[c] = dn[3 * i + c];
     rv[c] = a.r[3 * i + c];
     qv[c] = a.q[3 * i + c];
   }
@@ -509,6 +541,7 @@ __device__ __forceinline__ V update_free(const pcg_args<T, V>& a, long long i, V
     a.x[3 * i + c] = xv[c];
     a.r[3 * i + c] = rv[c];
     a.z[3 * i + c] = zv[c];
+    a.q[3 * i + c] = 0;
   }
   return acc;
 }
@@ -523,22 +556,15 @@ __global__ void __launch_bounds__(pcg_threads<T>::N, 1) k_pcg_persistent(pcg_arg
   const long long nthr = (long long)G * blockDim.x;
   const int lane = threadIdx.x & 31;
   const int nu = a.nfree + a.nb;
-  const int Ts = (a.n_s + L::NT - 1) / L::NT;
-  const int TT = Ts + (a.n_d + L::NT - 1) / L::NT;
-  const int J = (blockIdx.x < TT) ? (TT - 1 - (int)blockIdx.x) / G + 1 : 0;  // tiles of this block
-  double* partA = a.part;
-  double* partB = a.part + G;
-  double* partC = a.part + 2 * G;
-  unsigned gen = 0;  // arrival count that completes the next barrier, minus gridDim.x
-  // block 0's clock per iteration: 0 direction, 1 barrier, 2 SpMV, 3 barrier,
-  // 4 alpha, 5 update, 6 barrier, 7 beta
-  unsigned long long tph[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  const spmv_share sh = share_of(a);
+  const long long n0 = (long long)blockIdx.x * a.nn / G, n1 = (long long)(blockIdx.x + 1) * a.nn / G;
+  unsigned kbar = 0;  // reducing barriers passed in this launch
+  const bool clock0 = blockIdx.x == 0 && threadIdx.x == 0;
+  // block 0's clock per iteration: 0 own nodes (d', D d'), 1 upper blocks,
+  // 2 wait + d^T H d, 3 update, 4 wait + r^T z
+  __shared__ unsigned long long tph[5];
   unsigned long long tlast = 0;
-  auto stamp = [&](int k) {
-    const unsigned long long t = global_ns();
-    tph[k] += t - tlast;
-    tlast = t;
-  };
+  if (threadIdx.x < 5) tph[threadIdx.x] = 0;
   unsigned parity = 0u;    // bit b: phase parity of buffer b's next completion
   unsigned inflight = 0u;  // bit b: buffer b has a request not yet waited for (thread 0's view)
   if (threadIdx.x == 0) {
@@ -548,7 +574,7 @@ __global__ void __launch_bounds__(pcg_threads<T>::N, 1) k_pcg_persistent(pcg_arg
   }
   __syncthreads();
 
-  // r = rhs, x = 0, d = 0, z = M^-1 r ; r^T z
+  // r = rhs, x = 0, d = 0, q = 0, z = M^-1 r ; r^T z
   V acc = 0;
   for (long long i = tid; i < nu; i += nthr) {
     int cnt;
@@ -557,53 +583,45 @@ __global__ void __launch_bounds__(pcg_threads<T>::N, 1) k_pcg_persistent(pcg_arg
     for (int c = 0; c < cnt; ++c) {
       a.r[o + c] = (V)a.rhs[o + c];
       a.x[o + c] = 0;
-      a.d[o + c] = 0;
+      a.d0[o + c] = 0;
+      a.q[o + c] = 0;
     }
     acc += precond_row<T, V>((int)i, a.nfree, a.Mi, a.r, a.z);
   }
   V bs = block_sum_v<V>(acc);
-  if (threadIdx.x == 0) partC[blockIdx.x] = (double)bs;
   int done = 0, it = 0;
-  if (!grid_barrier(a.bar, gen, a.spin_limit)) done = 3;
-  double rz = done ? 0.0 : grid_total(partC, G);
+  double rz = 0.0;
+  if (!grid_reduce(a.bar, kbar, (double)bs, rz, a.spin_limit)) done = 3;
   const double rz0 = rz;
   double beta = 0.0;
   if (!done && !(rz > 0.0)) done = 1;
 
   while (!done && it < a.maxit) {
-    tlast = global_ns();
-    // the first two tiles of the SpMV travel while the direction is updated
+    V* d = (it & 1) ? a.d1 : a.d0;   // previous direction
+    V* dn = (it & 1) ? a.d0 : a.d1;  // this iteration's direction
+    const V vb = (V)beta;
+    if (clock0) tlast = global_ns();
+    // the first two tiles travel while the block does its own nodes
     if (threadIdx.x == 0)
-      for (int j = 0; j < 2 && j < J; ++j) {
-        issue_tile(a, (int)blockIdx.x + j * G, Ts, smem + j * L::BUF, &mbar[j]);
+      for (int j = 0; j < 2 && j < sh.tt; ++j) {
+        issue_tile(tile_of(a, sh, j), smem + j * L::BUF, &mbar[j]);
         inflight |= 1u << j;
       }
-    // A: d = z + beta d, q = D d, d^T D d
     acc = 0;
-    const V vb = (V)beta;
-    for (long long i = tid; i < a.nn; i += 2 * nthr) {
-      acc += dir_node(a, i, vb);
-      if (i + nthr < a.nn) acc += dir_node(a, i + nthr, vb);
-    }
-    bs = block_sum_v<V>(acc);
-    if (threadIdx.x == 0) partA[blockIdx.x] = (double)bs;
-    stamp(0);
-    if (!grid_barrier(a.bar, gen, a.spin_limit)) { done = 3; break; }
-    stamp(1);
-    // B: q += (U + U^T) d, 2 d^T U d, tile by tile from shared memory
-    acc = 0;
+    for (long long i = n0 + threadIdx.x; i < n1; i += blockDim.x) acc += diag_node(a, i, vb, d, dn);
+    if (clock0) { const unsigned long long t = global_ns(); tph[0] += t - tlast; tlast = t; }
+    // upper blocks, tile by tile from shared memory
     bool ok = true;
-    for (int j = 0; j < J; ++j) {
+    for (int j = 0; j < sh.tt; ++j) {
       const int b = j & 1;
-      if (!mbar_wait_bounded(&mbar[b], (parity >> b) & 1u, a.spin_limit >> 3)) { ok = false; }
+      if (!mbar_wait_bounded(&mbar[b], (parity >> b) & 1u, a.spin_limit >> 3)) ok = false;
       parity ^= 1u << b;
       inflight &= ~(1u << b);
       if (__syncthreads_or(!ok)) { ok = false; break; }
       const unsigned char* buf = smem + b * L::BUF;
-      const int t = (int)blockIdx.x + j * G;
-      const int cnt = (t < Ts) ? min(L::NT, a.n_s - t * L::NT) : min(L::NT, a.n_d - (t - Ts) * L::NT);
+      const int cnt = tile_of(a, sh, j).cnt;
       // two blocks per thread (k and k + NT/2, each warp on 32 consecutive
-      // blocks): both gathers of d are in flight before either is used
+      // blocks): both gathers are in flight before either is used
       const int* rows = reinterpret_cast<const int*>(buf + L::VB);
       const int* cols = reinterpret_cast<const int*>(buf + L::VB + L::IB);
       const T* vals = reinterpret_cast<const T*>(buf);
@@ -611,64 +629,56 @@ __global__ void __launch_bounds__(pcg_threads<T>::N, 1) k_pcg_persistent(pcg_arg
       const int r0 = (k0 < cnt) ? rows[k0] : -1, c0 = (k0 < cnt) ? cols[k0] : 0;
       const int r1 = (k1 < cnt) ? rows[k1] : -1, c1 = (k1 < cnt) ? cols[k1] : 0;
       gath<V> g0, g1;
-      gather_d(r0, c0, a.d, g0);
-      gather_d(r1, c1, a.d, g1);
+      gather_d(r0, c0, a.z, d, vb, g0);
+      gather_d(r1, c1, a.z, d, vb, g1);
       acc += apply_blk<T, V>(r0, c0, vals + 9 * k0, g0, a.q, lane);
       acc += apply_blk<T, V>(r1, c1, vals + 9 * k1, g1, a.q, lane);
       __syncthreads();  // every thread is done with buffer b
-      if (threadIdx.x == 0 && j + 2 < J) {
-        issue_tile(a, (int)blockIdx.x + (j + 2) * G, Ts, smem + b * L::BUF, &mbar[b]);
+      if (threadIdx.x == 0 && j + 2 < sh.tt) {
+        issue_tile(tile_of(a, sh, j + 2), smem + b * L::BUF, &mbar[b]);
         inflight |= 1u << b;
       }
     }
     if (!ok) {
-      // give up: wait (bounded) for this block's own copies still in flight
-      if (threadIdx.x == 0) {
-        atomicExch(&a.bar->abort, 1);
-        for (int b = 0; b < 2; ++b)
-          if ((inflight >> b) & 1u) mbar_wait_bounded(&mbar[b], (parity >> b) & 1u, a.spin_limit);
-      }
+      if (threadIdx.x == 0) atomicExch(&a.bar->abort, 1);
       done = 3;
       break;
     }
     bs = block_sum_v<V>(acc);
-    if (threadIdx.x == 0) partB[blockIdx.x] = (double)bs;
-    stamp(2);
-    if (!grid_barrier(a.bar, gen, a.spin_limit)) { done = 3; break; }
-    stamp(3);
-    const double dHd = grid_total(partA, G) + grid_total(partB, G);
-    stamp(4);
+    if (clock0) { const unsigned long long t = global_ns(); tph[1] += t - tlast; tlast = t; }
+    double dHd = 0.0;
+    if (!grid_reduce(a.bar, kbar, (double)bs, dHd, a.spin_limit)) { done = 3; break; }
+    if (clock0) { const unsigned long long t = global_ns(); tph[2] += t - tlast; tlast = t; }
     if (!(dHd > 0.0)) { done = 2; break; }
     const V alpha = (V)(rz / dHd);
-    // C: x += alpha d, r -= alpha q, z = M^-1 r, r^T z
+    // C: x += alpha d', r -= alpha q, z = M^-1 r, q = 0 ; r^T z
     acc = 0;
     for (long long i = tid; i < a.nfree; i += 2 * nthr) {
-      acc += update_free(a, i, alpha);
-      if (i + nthr < a.nfree) acc += update_free(a, i + nthr, alpha);
+      acc += update_free(a, i, alpha, dn);
+      if (i + nthr < a.nfree) acc += update_free(a, i + nthr, alpha, dn);
     }
     for (long long bi = tid; bi < a.nb; bi += nthr) {
       const int i = a.nfree + (int)bi;
       const size_t o = 3 * ((size_t)a.nfree + 4 * (size_t)bi);
       for (int c = 0; c < 12; ++c) {
-        a.x[o + c] += alpha * a.d[o + c];
+        a.x[o + c] += alpha * dn[o + c];
         a.r[o + c] -= alpha * a.q[o + c];
+        a.q[o + c] = 0;
       }
       acc += precond_row<T, V>(i, a.nfree, a.Mi, a.r, a.z);
     }
     bs = block_sum_v<V>(acc);
-    if (threadIdx.x == 0) partC[blockIdx.x] = (double)bs;
-    stamp(5);
-    if (!grid_barrier(a.bar, gen, a.spin_limit)) { done = 3; break; }
-    stamp(6);
-    const double rz_new = grid_total(partC, G);
+    if (clock0) { const unsigned long long t = global_ns(); tph[3] += t - tlast; tlast = t; }
+    double rz_new = 0.0;
+    if (!grid_reduce(a.bar, kbar, (double)bs, rz_new, a.spin_limit)) { done = 3; break; }
+    if (clock0) { const unsigned long long t = global_ns(); tph[4] += t - tlast; tlast = t; }
     beta = rz_new / rz;
     rz = rz_new;
     ++it;
     if (rz <= a.tol2 * rz0) done = 1;
-    stamp(7);
   }
-  // a block that left after its direction phase (barrier abort) may still have
-  // tile copies in flight: wait for them (bounded) before the block exits
+  // a block that gave up may still have tile copies in flight: wait for them
+  // (bounded) before the block exits
   if (threadIdx.x == 0)
     for (int b = 0; b < 2; ++b)
       if ((inflight >> b) & 1u) mbar_wait_bounded(&mbar[b], (parity >> b) & 1u, a.spin_limit);
@@ -678,7 +688,7 @@ __global__ void __launch_bounds__(pcg_threads<T>::N, 1) k_pcg_persistent(pcg_arg
     a.sc->done = done;
     a.sc->iters = it;
 #pragma unroll
-    for (int k = 0; k < 8; ++k) a.sc->t_ns[k] = tph[k];
+    for (int k = 0; k < 8; ++k) a.sc->t_ns[k] = k < 5 ? tph[k] : 0ull;
   }
   if (threadIdx.x == 0 && done == 3) dev_flag(a.status, DEV_TIMEOUT);
 }
@@ -761,10 +771,10 @@ yasps_status pcg_inner(yasps_system* s, const double* rhs, double* p, double tol
                        double* rel) {
   const int n3 = 3 * s->nn;
   for (int k = 0; k < 5; ++k) ENSURE(s, s->vec[k], sizeof(V) * (n3 + 4));
+  ENSURE(s, s->vec[8], sizeof(V) * (n3 + 4));
   int G = 0;
   RC((pcg_grid<T, V>(s, &G)));
   ENSURE(s, s->scal, 256);
-  ENSURE(s, s->red, sizeof(double) * (3 * (size_t)G + 8));
   pcg_dev* sc = as<pcg_dev>(s->scal);
   pcg_bar* bar = reinterpret_cast<pcg_bar*>(static_cast<char*>(s->scal.p) + 128);
   pcg_args<T, V> a;
@@ -787,9 +797,9 @@ yasps_status pcg_inner(yasps_system* s, const double* rhs, double* p, double tol
   a.x = as<V>(s->vec[0]);
   a.r = as<V>(s->vec[1]);
   a.z = as<V>(s->vec[2]);
-  a.d = as<V>(s->vec[3]);
   a.q = as<V>(s->vec[4]);
-  a.part = as<double>(s->red);
+  a.d0 = as<V>(s->vec[3]);
+  a.d1 = as<V>(s->vec[8]);
   a.sc = sc;
   a.bar = bar;
   a.status = as<int>(s->status);
@@ -807,14 +817,14 @@ yasps_status pcg_inner(yasps_system* s, const double* rhs, double* p, double tol
   if (s->prof_on) {
     const double es = sizeof(T), vs = sizeof(V), nn = s->nn;
     const double nnzb = (double)s->Hs.nnzb + s->Hd.nnzb;
-    // SpMV phase: blocks + column index + row pointer, D, d read, q written
+    // H d phase: blocks + column index + row pointer, D, z and d read, d' and q written
     const double spmv_bytes = nnzb * (9 * es + 4) + nn * 4 + nn * 9 * es + 3 * vs * nn * 4;
-    // whole iteration: SpMV phase + C (x, d, r, q read; x, r, z written; M^-1)
-    const double iter_bytes = spmv_bytes + 3 * vs * nn * 7 + nn * 9 * es;
+    // whole iteration: H d phase + update (x, d', r, q read; x, r, z, q written; M^-1)
+    const double iter_bytes = spmv_bytes + 3 * vs * nn * 8 + nn * 9 * es;
     s->prof_acc[YASPS_STAGE_PCG_KERNEL].bytes += iter_bytes * h.iters;
     auto& sp = s->prof_acc[YASPS_STAGE_SPMV];
     sp.count += h.iters;
-    sp.ms += (h.t_ns[0] + h.t_ns[1] + h.t_ns[2] + h.t_ns[3]) * 1e-6;
+    sp.ms += (h.t_ns[0] + h.t_ns[1] + h.t_ns[2]) * 1e-6;
     for (int k = 0; k < 8; ++k) s->pcg_phase_ms[k] += h.t_ns[k] * 1e-6;
     sp.bytes += spmv_bytes * h.iters;
   }
