@@ -55,15 +55,17 @@ def source_sha(*files):
     return h.hexdigest()[:16]
 
 
-def traffic_record(kernel_files):
-    """dram bytes per launch from a committed ncu summary, if it matches the current source."""
-    p = os.path.join(ROOT, "profiles", "spmv_traffic.json")
+def traffic_rate(kernel_files):
+    """DRAM bytes per second of the PCG kernel from a committed ncu capture
+    (dram__bytes_read.sum + dram__bytes_write.sum over gpu__time_duration.sum of
+    one launch), if it was taken on the current source; else None."""
+    p = os.path.join(ROOT, "profiles", "pcg_kernel_traffic.json")
     if not os.path.exists(p):
         return None
     d = json.load(open(p))
     if d.get("source_sha") != source_sha(*kernel_files):
         return None
-    return d.get("traffic_bytes_per_launch")
+    return d.get("dram_bytes") / d.get("duration_s")
 
 
 class ClockSampler:
@@ -171,11 +173,21 @@ def native(args):
     ntol = NEWTON_VEL_TOL * scene["dt"]
     G = yb.System(scene, precision=1, pcg_rel_tol=PCG_TOL, newton_tol=ntol)
     x, v = G.initial_state()
-    # untimed pre-roll: let the pile fall until tori touch the ground and each other
-    for _ in range(args.preroll):
-        G.step(x, v, raise_on_error=False)
+    preroll = args.preroll
+    if args.load_state:
+        # the state a pre-roll left (written by --save-state): skips the untimed pre-roll
+        st = np.load(args.load_state)
+        x.copy_(torch.as_tensor(st["x"], device=dev))
+        v.copy_(torch.as_tensor(st["v"], device=dev))
+        preroll = int(st["preroll"])
+    else:
+        # untimed pre-roll: let the pile fall until tori touch the ground and each other
+        for _ in range(args.preroll):
+            G.step(x, v, raise_on_error=False)
     torch.cuda.synchronize()
     x0, v0 = x.clone(), v.clone()
+    if args.save_state and rank == 0:
+        np.savez(args.save_state, x=x0.cpu().numpy(), v=v0.cpu().numpy(), preroll=preroll)
     npt, nee, npg = G.detect_pairs(x0)
 
     def timed(system, precision_name, steps, warmup, profile):
@@ -256,13 +268,18 @@ def native(args):
     peak, peak_kind = load_peaks()
     sp = mixed["prof"]["spmv"]
     spmv_gbs = sp["bytes"] / (sp["ms"] * 1e-3) / 1e9 if sp["count"] and sp["ms"] > 0 else None
-    tr = traffic_record(["paper_2605_23088_b300/csrc/solver.cu"])
-    roof = {"bound": "hbm", "kernel": "PCG SpMV (k_pcg_dir + k_spmv_upper x2), FP32",
-            "achieved": spmv_gbs, "peak": peak, "unit": "GB/s",
-            "frac": (spmv_gbs / peak) if spmv_gbs else None,
-            "traffic": tr, "peak_kind": peak_kind,
-            "bytes_per_launch": sp["bytes"] / max(sp["count"], 1),
-            "launch_us": sp["ms"] * 1e3 / max(sp["count"], 1), "launches": sp["count"]}
+    # dominant kernel: the persistent PCG kernel (one launch per solve / refinement sweep)
+    pk = mixed["prof"]["pcg_kernel"]
+    pk_gbs = pk["bytes"] / (pk["ms"] * 1e-3) / 1e9 if pk["count"] and pk["ms"] > 0 else None
+    launch_s = pk["ms"] * 1e-3 / max(pk["count"], 1)
+    rate = traffic_rate(["paper_2605_23088_b300/csrc/solver.cu"])
+    roof = {"bound": "hbm", "kernel": "k_pcg_persistent<float,float> (block-Jacobi PCG, FP32 inner solve)",
+            "achieved": pk_gbs, "peak": peak, "unit": "GB/s",
+            "frac": (pk_gbs / peak) if pk_gbs else None,
+            "traffic": rate * launch_s if rate else None, "peak_kind": peak_kind,
+            "bytes_per_launch": pk["bytes"] / max(pk["count"], 1), "launch_us": launch_s * 1e6,
+            "launches": pk["count"], "iterations_per_launch": mixed["pcg"] / max(pk["count"], 1),
+            "spmv_phase_gbs": spmv_gbs}
 
     value = mixed["passes_all"] / (mixed["ms_max"] * 1e-3)
     line = {
@@ -270,7 +287,7 @@ def native(args):
         "warmup": args.warmup, "ms_per_step": mixed["ms_max"] / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32-mixed (f64 positions/gradients/energies)",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n_tets": n_tets, "n_nodes": G.n_nodes, "preroll_steps": args.preroll,
+        "config": {"workload": WORKLOAD, "n_tets": n_tets, "n_nodes": G.n_nodes, "preroll_steps": preroll,
                    "newton_tol": "||dx||_inf/dt < 1e-2 m/s", "pcg_rel_tol": PCG_TOL,
                    "pairs_at_start": {"pt": npt, "ee": nee, "pg": npg}, "newton_iters": mixed["newton"],
                    "pcg_iters": mixed["pcg"], "statuses": sorted(set(mixed["status"])),
@@ -291,6 +308,8 @@ def native(args):
             "value": fp64["passes_all"] / (fp64["ms_max"] * 1e-3), "unit": "Newton iterations/s",
             "ms_per_step": fp64["ms_max"] / args.steps, "newton_iters": fp64["newton"], "pcg_iters": fp64["pcg"],
             "spmv_gbs": sp64["bytes"] / (sp64["ms"] * 1e-3) / 1e9 if sp64["count"] and sp64["ms"] > 0 else None,
+            "pcg_kernel_gbs": (fp64["prof"]["pcg_kernel"]["bytes"] / (fp64["prof"]["pcg_kernel"]["ms"] * 1e-3) / 1e9
+                               if fp64["prof"]["pcg_kernel"]["ms"] > 0 else None),
             "stages_ms": {k: (v["ms"], v["count"]) for k, v in fp64["prof"].items()},
             "gpu_launches": fp64["launches"], "clocks": fp64["clocks"]}
     if rank == 0 and world == 1 and not args.skip_cpu:
@@ -354,6 +373,8 @@ def main():
     ap.add_argument("--preroll", type=int, default=14)
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--save-state", default=None, help="write the post-pre-roll state (.npz) for --load-state")
+    ap.add_argument("--load-state", default=None, help="start from a state written by --save-state")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
