@@ -338,6 +338,45 @@ class OracleSystem:
         lib().or_spmv(self.h, _dp(_f64(x)), _dp(y))
         return y
 
+    def set_tet_young(self, E):
+        """Per-tet Young's moduli (Poisson ratios kept)."""
+        lib().or_set_tet_young(self.h, _dp(_f64(E)))
+
+    def adjoint_step(self, xt, vt, xnext, xbar, vbar, tol=1e-12, maxit=100000):
+        """One reverse step of the implicit-function adjoint (form 2).  Returns
+        (dL/dx_t, dL/dv_t, dL/dE increment per tet, PCG iterations, status)."""
+        xp = np.zeros((self.nn, 3))
+        vp = np.zeros((self.nn, 3))
+        Eb = np.zeros(len(self.scene["tets"]))
+        it = ctypes.c_int()
+        rc = lib().or_adjoint_step(self.h, _dp(_f64(xt)), _dp(_f64(vt)), _dp(_f64(xnext)), _dp(_f64(xbar)),
+                                   _dp(_f64(vbar)), ctypes.c_double(tol), ctypes.c_int(maxit), _dp(xp), _dp(vp),
+                                   _dp(Eb), ctypes.byref(it))
+        return xp, vp, Eb, it.value, rc
+
+    def rollout(self, x0, v0, n_steps, brute=False):
+        """Forward rollout; returns the list of (x_t, v_t) for t = 0..n_steps and the statuses."""
+        x, v = _f64(x0).copy(), _f64(v0).copy()
+        states = [(x.copy(), v.copy())]
+        rcs = []
+        for _ in range(n_steps):
+            x, v, rc, _st = self.step(x, v, brute=brute)
+            states.append((x.copy(), v.copy()))
+            rcs.append(rc)
+        return states, rcs
+
+    def rollout_adjoint(self, states, xbar_T, vbar_T, tol=1e-12):
+        """Reverse pass over a rollout: dL/dx_0, dL/dv_0, dL/dE per tet."""
+        xbar, vbar = _f64(xbar_T).copy(), _f64(vbar_T).copy()
+        Ebar = np.zeros(len(self.scene["tets"]))
+        for t in range(len(states) - 2, -1, -1):
+            xt, vt = states[t]
+            xbar, vbar, Eb, _it, rc = self.adjoint_step(xt, vt, states[t + 1][0], xbar, vbar, tol=tol)
+            if rc != 0:
+                raise RuntimeError(f"adjoint PCG did not converge at step {t}")
+            Ebar += Eb
+        return xbar, vbar, Ebar
+
     def pcg(self, rhs, tol=1e-4, maxit=100000):
         x = np.zeros((self.nn, 3))
         it = ctypes.c_int()

@@ -1671,7 +1671,9 @@ OR_EXPORT int or_step(void* p, double* x, double* v, int brute, double* stats) {
     for (ls = 0; ls < S->ls_max; ++ls) {
       for (int i = 0; i < n; ++i) xtrial[i] = x[i] - alpha * dir[i];
       double E1 = or_energy(S, xtrial, xtil, brute, NULL);
-      if (E1 <= E0) break;
+      /* a decrease, up to the rounding of the energy sums (reading c15):
+       * differences below 1e-12 |E0| are not resolved by FP64 element energies */
+      if (E1 <= E0 + 1e-12 * fabs(E0)) break;
       alpha *= 0.5;
     }
     if (ls == S->ls_max) { ls_fail++; rc = -6; break; }
@@ -1685,6 +1687,88 @@ OR_EXPORT int or_step(void* p, double* x, double* v, int brute, double* stats) {
     stats[7] = ls_fail;
   }
   free(xt); free(xtil); free(g); free(dir); free(xtrial);
+  return rc;
+}
+
+/* ------------------------------------------------------------------------ */
+/* adjoint of one implicit step (form 2 of the hot path; the paper lists     */
+/* differentiable simulation as future work, Sec. "Conclusion and Future     */
+/* Work", so this follows the implicit-function theorem on the step's        */
+/* optimality condition grad E(x_{t+1}; x_t, v_t, E) = 0)                    */
+/* ------------------------------------------------------------------------ */
+/* per-tet Young's moduli (Poisson ratios kept): mu, lam follow (reading c2) */
+OR_EXPORT void or_set_tet_young(void* p, const double* E) {
+  osys* S = p;
+  for (int e = 0; e < S->nt; ++e) {
+    S->tE[e] = E[e];
+    or_lame(E[e], S->tnu[e], &S->tmu[e], &S->tlam[e]);
+  }
+}
+
+/* y = M x with the lumped node masses (free: m I3; body: 4x4 (x) I3) */
+static void mass_apply(const osys* S, const double* x, double* y) {
+  for (int i = 0; i < S->nfree; ++i)
+    for (int c = 0; c < 3; ++c) y[3 * i + c] = S->nodemass[i] * x[3 * i + c];
+  for (int b = 0; b < S->nb; ++b) {
+    const double* M = S->nodemass + S->nfree + 16 * b;
+    int b0 = S->nfree + 4 * b;
+    for (int a = 0; a < 4; ++a)
+      for (int c = 0; c < 3; ++c) {
+        double s = 0.0;
+        for (int k = 0; k < 4; ++k) s += M[4 * a + k] * x[3 * (b0 + k) + c];
+        y[3 * (b0 + a) + c] = s;
+      }
+  }
+}
+
+/* One reverse step.  With v_{t+1} = (x_{t+1} - x_t)/h and the optimality
+ * condition, given xbar = dL/dx_{t+1} and vbar = dL/dv_{t+1} (total
+ * derivatives of everything downstream):
+ *   H lambda = xbar + vbar / h          (H: the EXACT Hessian at x_{t+1})
+ *   dL/dx_t  = M lambda - vbar / h      (x_tilde = x_t + h v_t + h^2 g)
+ *   dL/dv_t  = h M lambda
+ *   dL/dE_e -= h^2 lambda^T d(grad V Psi_e)/dE_e = h^2 lambda_e^T grad(V Psi_e) / E_e
+ * because Psi_SNH is linear in E at a fixed Poisson ratio (mu, lam are both
+ * proportional to E and alpha = 1 + 3 mu / (4 lam) does not change).  Ebar
+ * is accumulated (not overwritten).  Returns the PCG status. */
+OR_EXPORT int or_adjoint_step(void* p, const double* xt, const double* vt, const double* xnext, const double* xbar,
+                              const double* vbar, double tol, int maxit, double* xbar_prev, double* vbar_prev,
+                              double* Ebar, int* iters) {
+  osys* S = p;
+  int n = 3 * S->nn;
+  double h = S->dt, h2 = h * h;
+  double *xtil = malloc(sizeof(double) * (n + 1)), *rhs = malloc(sizeof(double) * (n + 1)),
+         *lam = malloc(sizeof(double) * (n + 1)), *Ml = malloc(sizeof(double) * (n + 1));
+  or_xtilde(S, xt, vt, xtil);
+  or_assemble(S, xnext, xtil, 0, 0);
+  for (int i = 0; i < n; ++i) rhs[i] = xbar[i] + vbar[i] / h;
+  int rc = or_pcg(S, rhs, lam, tol, maxit, iters);
+  mass_apply(S, lam, Ml);
+  for (int i = 0; i < n; ++i) {
+    xbar_prev[i] = Ml[i] - vbar[i] / h;
+    vbar_prev[i] = h * Ml[i];
+  }
+  double* P = malloc(sizeof(double) * 3 * (S->nv + 1));
+  or_vertex_positions(S, xnext, P);
+  for (int e = 0; e < S->nt; ++e) {
+    double xl[12], Xl[12], gl[12], Hl[144];
+    gather_pos(S, P, S->tets + 4 * e, 4, xl);
+    gather_pos(S, S->rest, S->tets + 4 * e, 4, Xl);
+    or_snh_local(xl, Xl, S->tmu[e], S->tlam[e], 0, NULL, gl, Hl);
+    double acc = 0.0;
+    for (int a = 0; a < 4; ++a) {
+      int nodes[4];
+      double w[4];
+      int m = vmap(S, S->tets[4 * e + a], nodes, w);
+      for (int c = 0; c < 3; ++c) {
+        double lv = 0.0;
+        for (int k = 0; k < m; ++k) lv += w[k] * lam[3 * nodes[k] + c];
+        acc += lv * gl[3 * a + c];
+      }
+    }
+    Ebar[e] -= h2 * acc / S->tE[e];
+  }
+  free(P); free(xtil); free(rhs); free(lam); free(Ml);
   return rc;
 }
 

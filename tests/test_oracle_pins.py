@@ -466,3 +466,75 @@ def test_pp_barrier_dof_sizes():
     assert st == 0
     support = np.nonzero(np.abs(H).sum(0) > 0)[0]
     assert len(support) == g["projected"] and set(support) == set(range(6))
+
+
+# ----------------------------------------------------------------- adjoint (differentiation form)
+def _beam_rollout_setup(lift, T):
+    s = scenes.beam_scene(nx=4, ny=1, nz=1, length=0.2, width=0.05, lift=lift, n_steps=T)
+    O = oracle.OracleSystem(s, newton_tol=1e-10, pcg_tol=1e-12)
+    x0, v0 = O.initial_state()
+    return s, O, x0, v0
+
+
+@pytest.mark.parametrize("lift", [0.0015, 0.05])  # with point-ground contact / free flight
+def test_adjoint_matches_directional_fd(lift):
+    """dL/dE and dL/dv0 of a 3-step rollout against central differences of the
+    rollout itself (Richardson-extrapolated), along random directions: this pins
+    the implicit-function adjoint to the forward steps it differentiates."""
+    T = 3
+    s, O, x0, v0 = _beam_rollout_setup(lift, T)
+    E0 = np.array(s["tet_E"], float)
+    r = np.random.default_rng(7)
+
+    def run(E, v):
+        # a step may stop on a line search that can no longer resolve the
+        # energy decrease; accept that only once the Newton step is below 1e-9 m
+        O.set_tet_young(E)
+        states = [(x0, v)]
+        for _ in range(T):
+            x, vv, rc, st = O.step(*states[-1])
+            assert rc == 0 or (rc == -6 and st["p_inf"] < 1e-9)
+            states.append((x, vv))
+        return states
+
+    states = run(E0, v0)
+    target = states[-1][0] + r.normal(0, 1e-2, size=x0.shape)
+    loss = lambda st: 0.5 * np.sum((st[-1][0] - target) ** 2)
+    _, vb, Eb = O.rollout_adjoint(states, states[-1][0] - target, np.zeros_like(v0))
+    if lift < 0.01:
+        assert len(O.pairs(states[-1][0])[2]) > 0  # the ground barrier is active
+    for _ in range(2):
+        d = r.normal(size=len(E0))
+        dv = r.normal(size=v0.shape)
+
+        def DE(eps):
+            return (loss(run(E0 * (1 + eps * d), v0)) - loss(run(E0 * (1 - eps * d), v0))) / (2 * eps)
+
+        def Dv(eps):
+            return (loss(run(E0, v0 + eps * dv)) - loss(run(E0, v0 - eps * dv))) / (2 * eps)
+
+        # relative steps in E are larger: the trajectory is far less sensitive
+        # to E than to v0, and each forward step is exact only to ~1e-9 m
+        fdE = (4 * DE(5e-3) - DE(1e-2)) / 3
+        fdv = (4 * Dv(5e-4) - Dv(1e-3)) / 3
+        assert abs(np.sum(Eb * E0 * d) - fdE) <= 2e-5 * abs(fdE)
+        assert abs(np.sum(vb * dv) - fdv) <= 2e-5 * abs(fdv)
+
+
+def test_adjoint_single_step_closed_form_free_fall():
+    """No elastic or contact term active: a lone free vertex in free fall has
+    x1 = x0 + h v0 + h^2 g, so dL/dv0 = h dL/dx1 and dL/dx0 = dL/dx1 exactly."""
+    s = scenes.cubes_scene(n=1)
+    s = dict(s)
+    O = oracle.OracleSystem(s, newton_tol=1e-12, pcg_tol=1e-14)
+    x0, v0 = O.initial_state()
+    # make every tet modulus tiny so the elastic force vanishes to rounding
+    O.set_tet_young(np.full(len(s["tets"]), 1e-12))
+    x1, v1, rc, _ = O.step(x0, v0)
+    assert rc == 0
+    w = np.random.default_rng(3).normal(size=x0.shape)
+    xp, vp, Eb, it, rc = O.adjoint_step(x0, v0, x1, w, np.zeros_like(w))
+    assert rc == 0
+    h = s["dt"]
+    assert rel(vp, h * w) < 1e-9
+    assert rel(xp, w) < 1e-9
