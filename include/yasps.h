@@ -257,6 +257,36 @@ yasps_status yasps_step(yasps_system* sys, double* x_dev, double* v_dev, yasps_s
 yasps_status yasps_set_fixed_positions(yasps_system* sys, const double* P_host);
 yasps_status yasps_get_fixed_positions(yasps_system* sys, double* P_host);
 
+/* ---- adjoint of the implicit step (differentiation form) ----------------
+ * The paper names differentiable simulation as future work (Sec. "Conclusion
+ * and Future Work"); the adjoint here follows the implicit-function theorem on
+ * the step's optimality condition grad E(x_{t+1}; x_t, v_t, E) = 0 of the
+ * incremental potential, with v_{t+1} = (x_{t+1} - x_t) / h.
+ *
+ * yasps_set_tet_young: per-tet Young's moduli E_dev (device, [n_tets]),
+ * Poisson ratios kept; mu and lam are recomputed (standard Lame).  Returns
+ * YASPS_E_INVAL for a non-positive or non-finite modulus.
+ *
+ * yasps_adjoint_step: one reverse step.  Inputs (device, [n_nodes][3] FP64
+ * unless noted): the step's start state x_t, v_t, its solution x_next (as
+ * yasps_step returned it), and the adjoints xbar = dL/dx_{t+1}, vbar =
+ * dL/dv_{t+1}.  It detects the pairs at x_next, assembles the EXACT
+ * (unprojected) Hessian H there, solves H lambda = xbar + vbar / h with the
+ * same block-Jacobi PCG (relative tolerance pcg_rel_tol; the system's
+ * precision), and writes
+ *   xbar_prev = dL/dx_t = M lambda - vbar / h,   vbar_prev = dL/dv_t = h M lambda,
+ * and ADDS to Ebar (device, [n_tets]) the per-tet dL/dE_e = -h^2 lambda_e .
+ * grad(V Psi_e) / E_e (Psi_SNH is linear in E at a fixed Poisson ratio).
+ * Fixed vertices must sit where they were at the end of the forward step
+ * (yasps_set_fixed_positions).  Errors: YASPS_E_NAN if the exact Hessian has a
+ * non-positive diagonal block (the step solution is not a strict minimum),
+ * YASPS_E_NOCONV if the PCG hits its cap, YASPS_E_INVAL for null pointers.
+ * Output buffers must not alias the inputs.  Synchronises. */
+yasps_status yasps_set_tet_young(yasps_system* sys, const double* E_dev);
+yasps_status yasps_adjoint_step(yasps_system* sys, const double* x_t, const double* v_t, const double* x_next,
+                                const double* xbar, const double* vbar, double* xbar_prev, double* vbar_prev,
+                                double* Ebar, double pcg_rel_tol, int* pcg_iters, double* rel_res);
+
 /* Number of kernels this system has launched since it was built (a host
  * counter incremented at every launch). */
 long long yasps_kernel_launches(const yasps_system* sys);

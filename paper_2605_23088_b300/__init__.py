@@ -27,7 +27,7 @@ EXPORTS = [
     "yasps_set_params", "yasps_get_sizes", "yasps_initial_state", "yasps_vertex_positions", "yasps_xtilde",
     "yasps_detect_pairs", "yasps_export_pairs", "yasps_energy", "yasps_eval_local", "yasps_assemble",
     "yasps_export_bsr", "yasps_export_gradient", "yasps_spmv", "yasps_pcg_solve", "yasps_ccd_bound", "yasps_step",
-    "yasps_set_fixed_positions", "yasps_get_fixed_positions", "yasps_kernel_launches", "yasps_profile_enable",
+    "yasps_set_fixed_positions", "yasps_get_fixed_positions", "yasps_set_tet_young", "yasps_adjoint_step", "yasps_kernel_launches", "yasps_profile_enable",
     "yasps_profile_get", "yasps_pcg_phase_ms", "yasps_pcg_solve_static",
 ]
 STAGE_SPMV, STAGE_TET, STAGE_BARRIER, STAGE_PCG, STAGE_DETECT, STAGE_EVAL, STAGE_CCD, STAGE_LS, STAGE_PCG_KERNEL = range(9)
@@ -343,6 +343,22 @@ class System:
         P = np.zeros((self.n_verts, 3))
         self._check(lib().yasps_get_fixed_positions(self.h, P.ctypes.data_as(_PD)))
         return P
+
+    def set_tet_young(self, E):
+        """Per-tet Young's moduli (CUDA float64 tensor [n_tets]); Poisson ratios kept."""
+        E = E.detach().to(device=self.device, dtype=self.torch.float64).contiguous()
+        self._check(lib().yasps_set_tet_young(self.h, _ptr(E)))
+
+    def adjoint_step(self, x_t, v_t, x_next, xbar, vbar, Ebar, tol=1e-10):
+        """One reverse step (yasps_adjoint_step): returns (dL/dx_t, dL/dv_t, PCG iterations,
+        relative residual) and adds this step's dL/dE into Ebar in place."""
+        xp = self.zeros(self.n_nodes, 3)
+        vp = self.zeros(self.n_nodes, 3)
+        it, rel = ctypes.c_int(), ctypes.c_double()
+        self._check(lib().yasps_adjoint_step(self.h, _ptr(x_t), _ptr(v_t), _ptr(x_next), _ptr(xbar), _ptr(vbar),
+                                             _ptr(xp), _ptr(vp), _ptr(Ebar), ctypes.c_double(tol),
+                                             ctypes.byref(it), ctypes.byref(rel)))
+        return xp, vp, it.value, rel.value
 
     def kernel_launches(self):
         return lib().yasps_kernel_launches(self.h)

@@ -490,6 +490,78 @@ __global__ void __launch_bounds__(128) k_snh(int nt, const int* __restrict__ tv,
   scatter_fspace<T, 4, 3>(Hf, w, sc, nodes, slots, diag, vals);
 }
 
+// ---------------------------------------------------------------- adjoint (form 2)
+// Parameter derivative of the tet term for the implicit-step adjoint.  At a
+// fixed Poisson ratio mu and lam are both proportional to E and alpha = 1 +
+// 3 mu / (4 lam) does not change, so Psi_SNH (Eq. snh) is linear in E and
+// d(h^2 grad V Psi_e)/dE_e = h^2 grad(V Psi_e) / E_e.  Each tet adds
+// -lambda_e . that to Ebar_e (lambda_e: the adjoint at its 4 nodes, 0 on fixed
+// vertices); the gradient is formed exactly as in k_snh.
+__global__ void __launch_bounds__(128) k_snh_young_adj(int nt, const int* __restrict__ tv, const int* __restrict__ tn,
+                                                       const double* __restrict__ trest, const double* __restrict__ tE,
+                                                       const double* __restrict__ P, const double* __restrict__ lamv,
+                                                       double h2, double* __restrict__ Ebar) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= nt) return;
+  const int4 v = reinterpret_cast<const int4*>(tv)[e];
+  const int4 n4 = reinterpret_cast<const int4*>(tn)[e];
+  const int nodes[4] = {n4.x, n4.y, n4.z, n4.w};
+  const double* R = trest + 12 * (size_t)e;
+  double Dmi[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) Dmi[k] = R[k];
+  const double vol = R[9], mu = R[10], lam = R[11];
+  const v3<double> x0 = ld3(P, v.x);
+  const v3<double> d1 = ld3(P, v.y) - x0, d2 = ld3(P, v.z) - x0, d3_ = ld3(P, v.w) - x0;
+  const double Ds[9] = {d1.x, d2.x, d3_.x, d1.y, d2.y, d3_.y, d1.z, d2.z, d3_.z};
+  double F[9];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) F[3 * i + j] = Ds[3 * i] * Dmi[j] + Ds[3 * i + 1] * Dmi[3 + j] + Ds[3 * i + 2] * Dmi[6 + j];
+  double Ic = 0.0;
+#pragma unroll
+  for (int k = 0; k < 9; ++k) Ic += F[k] * F[k];
+  double C[9];
+  C[0] = F[4] * F[8] - F[5] * F[7]; C[1] = F[5] * F[6] - F[3] * F[8]; C[2] = F[3] * F[7] - F[4] * F[6];
+  C[3] = F[2] * F[7] - F[1] * F[8]; C[4] = F[0] * F[8] - F[2] * F[6]; C[5] = F[1] * F[6] - F[0] * F[7];
+  C[6] = F[1] * F[5] - F[2] * F[4]; C[7] = F[2] * F[3] - F[0] * F[5]; C[8] = F[0] * F[4] - F[1] * F[3];
+  const double J = F[0] * C[0] + F[1] * C[1] + F[2] * C[2];
+  const double alpha = 1.0 + 0.75 * mu / lam;
+  const double c1 = mu * (1.0 - 1.0 / (Ic + 1.0));
+  const double c4 = lam * (J - alpha);
+  double Pk[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) Pk[k] = c1 * F[k] + c4 * C[k];
+  double w[4][3];
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    w[1][j] = Dmi[j]; w[2][j] = Dmi[3 + j]; w[3][j] = Dmi[6 + j];
+    w[0][j] = -(Dmi[j] + Dmi[3 + j] + Dmi[6 + j]);
+  }
+  double acc = 0.0;
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    if (nodes[a] < 0) continue;
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+      acc += lamv[3 * nodes[a] + i] * vol * (Pk[3 * i] * w[a][0] + Pk[3 * i + 1] * w[a][1] + Pk[3 * i + 2] * w[a][2]);
+  }
+  Ebar[e] -= h2 * acc / tE[e];
+}
+
+// per-tet Young's moduli at fixed Poisson ratios: mu, lam as in k_rest_tet
+__global__ void k_set_young(int nt, const double* __restrict__ E, const double* __restrict__ nu,
+                            double* __restrict__ tE, double* __restrict__ trest, int* status) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= nt) return;
+  const double Ee = E[e];
+  if (!(Ee > 0.0) || !isfinite(Ee)) dev_flag(status, DEV_NAN);
+  tE[e] = Ee;
+  trest[12 * (size_t)e + 10] = Ee / (2.0 * (1.0 + nu[e]));
+  trest[12 * (size_t)e + 11] = Ee * nu[e] / ((1.0 + nu[e]) * (1.0 - 2.0 * nu[e]));
+}
+
 // ---------------------------------------------------------------- StVK membrane
 template <typename T>
 __global__ void __launch_bounds__(128) k_membrane(int nc, const int* __restrict__ cv, const int* __restrict__ cn,
@@ -787,6 +859,23 @@ yasps_status setup_rest(yasps_system* s, const double* tE, const double* tnu, co
                                                                   as<double>(s->vmass), as<double>(s->nodemass));
     LAUNCH_CHECK(s, "k_free_nodemass");
   }
+  return YASPS_OK;
+}
+
+yasps_status launch_snh_young_adj(yasps_system* s, const double* P, const double* lam, double h2, double* Ebar) {
+  if (s->nt == 0) return YASPS_OK;
+  k_snh_young_adj<<<blocks_for(s->nt, 128), 128, 0, s->stream>>>(s->nt, as<int>(s->tet_v), as<int>(s->tet_n),
+                                                                 as<double>(s->tet_rest), as<double>(s->tet_E), P, lam,
+                                                                 h2, Ebar);
+  LAUNCH_CHECK(s, "k_snh_young_adj");
+  return YASPS_OK;
+}
+
+yasps_status launch_set_young(yasps_system* s, const double* E) {
+  if (s->nt == 0) return YASPS_OK;
+  k_set_young<<<blocks_for(s->nt, 256), 256, 0, s->stream>>>(s->nt, E, as<double>(s->tet_nu), as<double>(s->tet_E),
+                                                             as<double>(s->tet_rest), as<int>(s->status));
+  LAUNCH_CHECK(s, "k_set_young");
   return YASPS_OK;
 }
 

@@ -57,6 +57,8 @@ struct yasps_system {
   gbuf tet_v;     // int [nt][4] vertex ids
   gbuf tet_n;     // int [nt][4] node ids (-1 fixed)
   gbuf tet_rest;  // double [nt][12]: Dm^-1 (9, row-major), vol, mu, lam
+  gbuf tet_E;     // double [nt] current Young's moduli
+  gbuf tet_nu;    // double [nt] Poisson ratios
   gbuf tet_slot;  // int [nt][6] static BSR slot of local pairs (01,02,03,12,13,23), -1 none
   gbuf tri_v, tri_n;  // int [nc][3]
   gbuf tri_rest;      // double [nc][8]: Dm^-1 (4), area*thick, mu, lam, 0
@@ -172,6 +174,8 @@ yasps_status launch_xtilde(yasps_system* s, const double* xt, const double* vt, 
 yasps_status launch_eval_static(yasps_system* s, const double* x, const double* xtil, int mask, int project);
 // bend.cu: discrete-shell hinges (gradient + projected Hessian), precision by s->hess_precision
 yasps_status launch_bend(yasps_system* s, int project);
+yasps_status launch_snh_young_adj(yasps_system* s, const double* P, const double* lam, double h2, double* Ebar);
+yasps_status launch_set_young(yasps_system* s, const double* E);
 // five static terms (inertia, tet, membrane, bend, ABD) into out5 (host); synchronises
 yasps_status energy_static(yasps_system* s, const double* x, const double* xtil, double* out5);
 

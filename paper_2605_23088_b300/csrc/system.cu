@@ -60,7 +60,7 @@ static yasps_status upload(yasps_system* s, gbuf& b, const T* host, size_t count
 
 static void all_bufs(yasps_system* s, std::vector<gbuf*>& v) {
   gbuf* one[] = {&s->vnode, &s->vbody, &s->vr, &s->vmass, &s->rest, &s->xfix, &s->fixed, &s->fixvel, &s->nodemass,
-                 &s->tet_v, &s->tet_n, &s->tet_rest, &s->tet_slot, &s->tri_v, &s->tri_n, &s->tri_rest, &s->tri_slot,
+                 &s->tet_v, &s->tet_n, &s->tet_rest, &s->tet_E, &s->tet_nu, &s->tet_slot, &s->tri_v, &s->tri_n, &s->tri_rest, &s->tri_slot,
                  &s->hinge_v, &s->hinge_n, &s->hinge_rest, &s->hinge_slot, &s->body_kv, &s->body_slot, &s->stri,
                  &s->sedge, &s->svert, &s->planes, &s->Hs.row_ptr, &s->Hs.col, &s->Hs.row, &s->Hs.vals,
                  &s->Hd.row_ptr, &s->Hd.col, &s->Hd.row, &s->Hd.vals, &s->diag, &s->grad, &s->minv, &s->P, &s->pt,
@@ -277,6 +277,8 @@ static yasps_status build_impl(yasps_system* s, const yasps_scene_desc* d) {
                                                   {d->tri_rho, (size_t)s->nc},   {d->hinge_kb, (size_t)s->nh}};
   yasps_status rc = YASPS_OK;
   for (int k = 0; k < 8 && rc == YASPS_OK; ++k) rc = upload(s, tmp[k], mats[k].p, mats[k].n);
+  if (rc == YASPS_OK) rc = upload(s, s->tet_E, d->tet_E, (size_t)s->nt);
+  if (rc == YASPS_OK) rc = upload(s, s->tet_nu, d->tet_nu, (size_t)s->nt);
   if (rc == YASPS_OK)
     rc = setup_rest(s, as<double>(tmp[0]), as<double>(tmp[1]), as<double>(tmp[2]), as<double>(tmp[3]),
                     as<double>(tmp[4]), as<double>(tmp[5]), as<double>(tmp[6]), as<double>(tmp[7]));
@@ -647,7 +649,9 @@ extern "C" yasps_status yasps_step(yasps_system* s, double* x, double* v, yasps_
       k_axpy_out<<<blocks_for(n3, 256), 256, 0, s->stream>>>(n3, x, alpha, p, xtrial);
       LAUNCH_CHECK(s, "k_axpy_out");
       RC(energy_impl(s, xtrial, xtil, &E1, nullptr, true));
-      if (E1 <= E0) break;
+      // a decrease, up to the rounding of the energy sums: FP64 element
+      // energies do not resolve differences below 1e-12 |E0|
+      if (E1 <= E0 + 1e-12 * std::fabs(E0)) break;
       alpha *= 0.5;
     }
     prof_end(s, YASPS_STAGE_LS, pl, 0.0);
@@ -675,4 +679,92 @@ extern "C" yasps_status yasps_step(yasps_system* s, double* x, double* v, yasps_
   st.status = rc;
   if (stats) *stats = st;
   return rc;
+}
+
+// ---------------------------------------------------------------- adjoint (form 2)
+namespace {
+__global__ void k_adj_rhs(int n, const double* __restrict__ xbar, const double* __restrict__ vbar, double inv_h,
+                          double* __restrict__ rhs) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) rhs[i] = xbar[i] + vbar[i] * inv_h;
+}
+// y = M x: free nodes m I3, bodies their 4x4 mass matrix (x) I3
+__global__ void k_mass_apply(int nfree, int nb, const double* __restrict__ nodemass, const double* __restrict__ x,
+                             double* __restrict__ y) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < nfree) {
+    const double m = nodemass[i];
+    for (int c = 0; c < 3; ++c) y[3 * (size_t)i + c] = m * x[3 * (size_t)i + c];
+  } else if (i < nfree + nb) {
+    const int b = i - nfree;
+    const double* M = nodemass + nfree + 16 * (size_t)b;
+    const size_t o = 3 * ((size_t)nfree + 4 * (size_t)b);
+    for (int a = 0; a < 4; ++a)
+      for (int c = 0; c < 3; ++c) {
+        double acc = 0.0;
+        for (int k = 0; k < 4; ++k) acc += M[4 * a + k] * x[o + 3 * k + c];
+        y[o + 3 * a + c] = acc;
+      }
+  }
+}
+__global__ void k_adj_out(int n, const double* __restrict__ Ml, const double* __restrict__ vbar, double h,
+                          double* __restrict__ xbar_prev, double* __restrict__ vbar_prev) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) {
+    const double m = Ml[i];
+    xbar_prev[i] = m - vbar[i] / h;
+    vbar_prev[i] = h * m;
+  }
+}
+}  // namespace
+
+extern "C" yasps_status yasps_set_tet_young(yasps_system* s, const double* E_dev) {
+  if (!s || (!E_dev && s->nt > 0)) return YASPS_E_INVAL;
+  RC(launch_set_young(s, E_dev));
+  int bits = 0;
+  RC(read_status(s, &bits));
+  if (bits & DEV_NAN) SYS_FAIL(s, YASPS_E_INVAL, "Young's moduli must be positive and finite");
+  return YASPS_OK;
+}
+
+extern "C" yasps_status yasps_adjoint_step(yasps_system* s, const double* x_t, const double* v_t, const double* x_next,
+                                           const double* xbar, const double* vbar, double* xbar_prev,
+                                           double* vbar_prev, double* Ebar, double pcg_rel_tol, int* pcg_iters,
+                                           double* rel_res) {
+  if (!s || !x_t || !v_t || !x_next || !xbar || !vbar || !xbar_prev || !vbar_prev || (!Ebar && s->nt > 0))
+    return YASPS_E_INVAL;
+  const int n3 = 3 * s->nn;
+  const double h = s->prm.dt;
+  ENSURE(s, s->stepv[1], sizeof(double) * (n3 + 4));
+  ENSURE(s, s->stepv[2], sizeof(double) * (n3 + 4));
+  ENSURE(s, s->stepv[4], sizeof(double) * (n3 + 4));
+  ENSURE(s, s->stepv[5], sizeof(double) * (n3 + 4));
+  double* xtil = as<double>(s->stepv[1]);
+  double* Ml = as<double>(s->stepv[2]);
+  double* rhs = as<double>(s->stepv[4]);
+  double* lam = as<double>(s->stepv[5]);
+  RC(launch_xtilde(s, x_t, v_t, xtil));
+  // pairs and the EXACT (unprojected) Hessian at the step's solution
+  RC(launch_positions(s, x_next, as<double>(s->P)));
+  RC(detect_pairs(s, as<double>(s->P)));
+  RC(eval_impl(s, x_next, xtil, YASPS_TERM_ALL, 0));
+  int bits = 0;
+  RC(read_status(s, &bits));
+  if (bits & (DEV_NAN | DEV_BADINDEX))
+    SYS_FAIL(s, YASPS_E_NAN, "exact Hessian at the step solution has a non-positive diagonal block");
+  k_adj_rhs<<<blocks_for(n3, 256), 256, 0, s->stream>>>(n3, xbar, vbar, 1.0 / h, rhs);
+  LAUNCH_CHECK(s, "k_adj_rhs");
+  int it = 0;
+  double rel = 0.0;
+  RC(pcg_solve(s, rhs, lam, pcg_rel_tol, s->prm.pcg_max_iter, &it, &rel));
+  if (pcg_iters) *pcg_iters = it;
+  if (rel_res) *rel_res = rel;
+  k_mass_apply<<<blocks_for(std::max(s->nfree + s->nb, 1), 256), 256, 0, s->stream>>>(
+      s->nfree, s->nb, as<double>(s->nodemass), lam, Ml);
+  LAUNCH_CHECK(s, "k_mass_apply");
+  k_adj_out<<<blocks_for(n3, 256), 256, 0, s->stream>>>(n3, Ml, vbar, h, xbar_prev, vbar_prev);
+  LAUNCH_CHECK(s, "k_adj_out");
+  RC(launch_snh_young_adj(s, as<double>(s->P), lam, h * h, Ebar));
+  CK(s, cudaStreamSynchronize(s->stream));
+  return YASPS_OK;
 }
