@@ -117,6 +117,15 @@ typedef struct {
   const int* surf_verts;    /* [n_surf_verts] collision vertices, strictly increasing */
   int n_planes;
   const double* planes;     /* [n_planes][4] (n, c): the half-space n.x >= c is free space */
+  /* Batching: n_scenes independent scenes in one system (0 or 1 = one scene).
+   * vert_scene[v] in [0, n_scenes), non-decreasing in v; every element, body
+   * and fixed vertex lies in one scene.  Pairs between scenes are never formed
+   * (scenes may overlap in space; planes are shared), and yasps_step runs
+   * Newton, the CCD bound, the line search and PCG's alpha / beta / stopping
+   * test per scene, so each scene evolves exactly as it would alone.  At most
+   * 1024 scenes (YASPS_E_CAPACITY beyond). */
+  int n_scenes;
+  const int* vert_scene;    /* [n_verts] or NULL when n_scenes <= 1 */
 } yasps_scene_desc;
 
 /* Per-call statistics of yasps_step (the paper's counters, Sec. "Simulation
@@ -256,6 +265,13 @@ yasps_status yasps_step(yasps_system* sys, double* x_dev, double* v_dev, yasps_s
  * are read / written). */
 yasps_status yasps_set_fixed_positions(yasps_system* sys, const double* P_host);
 yasps_status yasps_get_fixed_positions(yasps_system* sys, double* P_host);
+
+/* Per-scene results of the last yasps_step on a batch (host arrays of
+ * n_scenes, each nullable): Newton iterations, PCG iterations summed over the
+ * step, and status (YASPS_OK, YASPS_E_NOCONV or YASPS_E_LINESEARCH; a scene
+ * whose line search fails stops where it is while the others go on, and
+ * yasps_step then returns that status). */
+yasps_status yasps_scene_stats(const yasps_system* sys, int* newton_iters, int* pcg_iters, int* status);
 
 /* ---- adjoint of the implicit step (differentiation form) ----------------
  * The paper names differentiable simulation as future work (Sec. "Conclusion

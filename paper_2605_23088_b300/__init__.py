@@ -27,7 +27,7 @@ EXPORTS = [
     "yasps_set_params", "yasps_get_sizes", "yasps_initial_state", "yasps_vertex_positions", "yasps_xtilde",
     "yasps_detect_pairs", "yasps_export_pairs", "yasps_energy", "yasps_eval_local", "yasps_assemble",
     "yasps_export_bsr", "yasps_export_gradient", "yasps_spmv", "yasps_pcg_solve", "yasps_ccd_bound", "yasps_step",
-    "yasps_set_fixed_positions", "yasps_get_fixed_positions", "yasps_set_tet_young", "yasps_adjoint_step", "yasps_kernel_launches", "yasps_profile_enable",
+    "yasps_set_fixed_positions", "yasps_get_fixed_positions", "yasps_set_tet_young", "yasps_adjoint_step", "yasps_scene_stats", "yasps_kernel_launches", "yasps_profile_enable",
     "yasps_profile_get", "yasps_pcg_phase_ms", "yasps_pcg_solve_static",
 ]
 STAGE_SPMV, STAGE_TET, STAGE_BARRIER, STAGE_PCG, STAGE_DETECT, STAGE_EVAL, STAGE_CCD, STAGE_LS, STAGE_PCG_KERNEL = range(9)
@@ -63,7 +63,7 @@ class SceneDesc(ctypes.Structure):
                 ("n_bodies", ctypes.c_int), ("body_mass", _PD), ("body_vol", _PD), ("body_kappa", _PD),
                 ("n_surf_tris", ctypes.c_int), ("surf_tri2v", _PI), ("n_surf_edges", ctypes.c_int),
                 ("surf_edge2v", _PI), ("n_surf_verts", ctypes.c_int), ("surf_verts", _PI),
-                ("n_planes", ctypes.c_int), ("planes", _PD)]
+                ("n_planes", ctypes.c_int), ("planes", _PD), ("n_scenes", ctypes.c_int), ("vert_scene", _PI)]
 
 
 class StepStats(ctypes.Structure):
@@ -192,6 +192,9 @@ class System:
         d.n_surf_edges = len(s["surf_edges"]); d.surf_edge2v = arr(s["surf_edges"], np.int32)
         d.n_surf_verts = len(s["surf_verts"]); d.surf_verts = arr(s["surf_verts"], np.int32)
         d.n_planes = len(s["planes"]); d.planes = arr(s["planes"], np.float64)
+        if s.get("vert_scene") is not None and int(s.get("n_scenes", 1)) > 1:
+            d.n_scenes = int(s["n_scenes"]); d.vert_scene = arr(s["vert_scene"], np.int32)
+        self.n_scenes = max(1, int(d.n_scenes))
         self.scene = scene
         self._alloc = None
         if use_torch_allocator:
@@ -343,6 +346,13 @@ class System:
         P = np.zeros((self.n_verts, 3))
         self._check(lib().yasps_get_fixed_positions(self.h, P.ctypes.data_as(_PD)))
         return P
+
+    def scene_stats(self):
+        """Per-scene (Newton iterations, PCG iterations, status) of the last step (batches)."""
+        n = self.n_scenes
+        a, b, c = (np.zeros(n, np.int32) for _ in range(3))
+        self._check(lib().yasps_scene_stats(self.h, a.ctypes.data_as(_PI), b.ctypes.data_as(_PI), c.ctypes.data_as(_PI)))
+        return a, b, c
 
     def set_tet_young(self, E):
         """Per-tet Young's moduli (CUDA float64 tensor [n_tets]); Poisson ratios kept."""

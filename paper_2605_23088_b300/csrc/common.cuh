@@ -99,6 +99,22 @@ YASPS_D ksum warp_ksum(ksum k) {
 }
 // Block-wide compensated reduction; result valid in thread 0.  blockDim.x must
 // be a multiple of 32 and at most 1024.
+// Batches: warp-segmented FP64 sum over runs of equal keys (the runs must be
+// contiguous across the lanes, as sorted keys are); the head lane of each run
+// adds the run's sum into acc[key]; key < 0 adds nothing.  All 32 lanes of the
+// warp must call.
+YASPS_D void seg_add_global(double* acc, int key, double v) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const int ko = __shfl_down_sync(0xffffffffu, key, off);
+    const double vo = __shfl_down_sync(0xffffffffu, v, off);
+    if (lane + off < 32 && ko == key) v += vo;
+  }
+  const int kp = __shfl_up_sync(0xffffffffu, key, 1);
+  if (key >= 0 && (lane == 0 || kp != key)) atomicAdd(&acc[key], v);
+}
+
 YASPS_D ksum block_ksum(ksum k) {
   __shared__ double sh_s[32], sh_c[32];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;

@@ -199,9 +199,11 @@ __device__ __forceinline__ void grid_visit(const grid_dev& g, const boxes& A, in
 struct topo {
   const int *vnode, *vbody, *stri, *sedge, *svert;
   int* status;
+  const int* vscene;  // scene of each vertex in a batch, else null: pairs never cross scenes
 };
 __device__ __forceinline__ bool pt_excluded(const topo& T, int v, int t0, int t1, int t2) {
   if (v == t0 || v == t1 || v == t2) return true;
+  if (T.vscene && T.vscene[v] != T.vscene[t0]) return true;
   const int bv = T.vbody[v];
   if (bv >= 0 && bv == T.vbody[t0]) return true;
   if (T.vnode[v] < 0 && T.vnode[t0] < 0 && T.vnode[t1] < 0 && T.vnode[t2] < 0) return true;
@@ -209,6 +211,7 @@ __device__ __forceinline__ bool pt_excluded(const topo& T, int v, int t0, int t1
 }
 __device__ __forceinline__ bool ee_excluded(const topo& T, int e0, int e1, int f0, int f1) {
   if (e0 == f0 || e0 == f1 || e1 == f0 || e1 == f1) return true;
+  if (T.vscene && T.vscene[e0] != T.vscene[f0]) return true;
   const int be = T.vbody[e0];
   if (be >= 0 && be == T.vbody[f0]) return true;
   if (T.vnode[e0] < 0 && T.vnode[e1] < 0 && T.vnode[f0] < 0 && T.vnode[f1] < 0) return true;
@@ -332,9 +335,12 @@ __global__ void k_ee_query(int total, int nse, topo T, const double* __restrict_
 // point-plane pairs: d = n.p - c, active when d > 0 and d^2 < dhat^2
 __global__ void k_pg_query(int total, int nsv, int npl, topo T, const double* __restrict__ P, const double* __restrict__ planes,
                            double sh, int mode, int* __restrict__ cnt, const int* __restrict__ off,
-                           int* __restrict__ out, double kappa, int form, ksum* __restrict__ part) {
+                           int* __restrict__ out, double kappa, int form, ksum* __restrict__ part,
+                           double* __restrict__ sacc = nullptr) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   ksum acc{0.0, 0.0};
+  int key = -1;
+  if (i < nsv && sacc) key = T.vscene[T.svert[i]];
   if (i < nsv) {
     const int v = T.svert[i];
     int c = 0;
@@ -359,8 +365,12 @@ __global__ void k_pg_query(int total, int nsv, int npl, topo T, const double* __
     if (mode == 0) cnt[i] = c;
   }
   if (mode == 2) {
-    acc = block_ksum(acc);
-    if (threadIdx.x == 0) part[blockIdx.x] = acc;
+    if (sacc) {  // batches: per scene (surface vertices are sorted, so are their scenes)
+      seg_add_global(sacc, key, acc.s + acc.c);
+    } else {
+      acc = block_ksum(acc);
+      if (threadIdx.x == 0) part[blockIdx.x] = acc;
+    }
   }
 }
 
@@ -659,7 +669,7 @@ __global__ void k_ccd_pg(int nsv, int npl, topo T, const double* __restrict__ P0
     const double t = dv(mul(sub(1.0, gap), d0), -vel);
     best = fmin(best, t);
   }
-  if (best < 1.0) atomic_min_pos(tmin, best);
+  if (best < 1.0) atomic_min_pos(tmin + (T.vscene ? T.vscene[v] : 0), best);
 }
 
 __global__ void k_sub(int n, const double* __restrict__ a, const double* __restrict__ b, double* __restrict__ out) {
@@ -724,6 +734,11 @@ __device__ __forceinline__ void cand_vertices(int kind, const int* cand, size_t 
   }
 }
 
+__device__ __forceinline__ int cand_first_vertex(int kind, const int* cand, size_t k, const topo& T) {
+  const int a = cand[2 * k];
+  return kind == 0 ? a : T.sedge[2 * a];
+}
+
 // additive CCD over the candidate list; one atomic min per block
 __global__ void k_ccd_cand(int kind, int n, const int* __restrict__ cand, topo T, const double* __restrict__ P0,
                            const double* __restrict__ D, double gap, int max_iter, double* __restrict__ tmin, int* status) {
@@ -738,6 +753,10 @@ __global__ void k_ccd_cand(int kind, int n, const int* __restrict__ cand, topo T
     best = accd(kind, x, dx, gap, 1.0, max_iter, &capped);
   }
   if (capped) dev_flag(status, DEV_ITERCAP);
+  if (T.vscene) {  // batches: one bound per scene
+    if (best < 1.0) atomic_min_pos(tmin + T.vscene[cand_first_vertex(kind, cand, (size_t)k, T)], best);
+    return;
+  }
   for (int o = 16; o > 0; o >>= 1) best = fmin(best, __shfl_xor_sync(0xffffffffu, best, o));
   __shared__ double sh[32];
   if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = best;
@@ -751,18 +770,32 @@ __global__ void k_ccd_cand(int kind, int n, const int* __restrict__ cand, topo T
 
 // barrier energy over the candidate list at positions P (fixed grid: deterministic)
 __global__ void k_energy_cand(int kind, int n, const int* __restrict__ cand, topo T, const double* __restrict__ P,
-                              double sh, double kappa, int form, ksum* __restrict__ part) {
+                              double sh, double kappa, int form, ksum* __restrict__ part,
+                              double* __restrict__ sacc = nullptr) {
   ksum acc{0.0, 0.0};
-  for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
-    int ids[4];
-    cand_vertices(kind, cand, (size_t)k, T, ids);
-    double s;
-    if (kind == 0) dist::pt_classify(ld3(P, ids[0]), ld3(P, ids[1]), ld3(P, ids[2]), ld3(P, ids[3]), &s);
-    else dist::ee_classify(ld3(P, ids[0]), ld3(P, ids[1]), ld3(P, ids[2]), ld3(P, ids[3]), &s);
-    if (s < sh) kadd(acc, kappa * barrier_fn(s, sh, form).b);
+  const int lane = threadIdx.x & 31;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long base = ((long long)blockIdx.x * blockDim.x + threadIdx.x) & ~31LL; base < n; base += stride) {
+    const long long k = base + lane;
+    double e = 0.0;
+    int key = -1;
+    if (k < n) {
+      int ids[4];
+      cand_vertices(kind, cand, (size_t)k, T, ids);
+      double s;
+      if (kind == 0) dist::pt_classify(ld3(P, ids[0]), ld3(P, ids[1]), ld3(P, ids[2]), ld3(P, ids[3]), &s);
+      else dist::ee_classify(ld3(P, ids[0]), ld3(P, ids[1]), ld3(P, ids[2]), ld3(P, ids[3]), &s);
+      if (s < sh) e = kappa * barrier_fn(s, sh, form).b;
+      if (sacc) key = T.vscene[ids[0]];
+    }
+    // batches: candidates are sorted by their first primitive, so by scene
+    if (sacc) seg_add_global(sacc, key, e);
+    else kadd(acc, e);
   }
-  acc = block_ksum(acc);
-  if (threadIdx.x == 0) part[blockIdx.x] = acc;
+  if (!sacc) {
+    acc = block_ksum(acc);
+    if (threadIdx.x == 0) part[blockIdx.x] = acc;
+  }
 }
 
 // active pairs among the candidates at positions P: flag + subtype
@@ -794,7 +827,7 @@ __global__ void k_compact_cand(int n, const int* __restrict__ cand, const int* _
 // ======================================================================== host
 topo make_topo(yasps_system* s) {
   return topo{as<int>(s->vnode), as<int>(s->vbody), as<int>(s->stri), as<int>(s->sedge), as<int>(s->svert),
-              as<int>(s->status)};
+              as<int>(s->status), s->nscene > 1 ? as<int>(s->vscene) : nullptr};
 }
 
 // Build a grid on boxes (blo, bhi) of n primitives.  Buffers: ws[3] start,
@@ -1124,9 +1157,11 @@ yasps_status ccd_candidates(yasps_system* s, double* alpha_host) {
   const size_t nv3 = 3 * (size_t)s->nv;
   double* P0 = as<double>(s->P);
   double* D = as<double>(s->stepv[4]) + nv3;
-  double* tmin = D + nv3;
-  const double one = 1.0;
-  CK(s, cudaMemcpyAsync(tmin, &one, sizeof(double), cudaMemcpyHostToDevice, s->stream));
+  // one bound per scene (batches) or one in all
+  const int nb_t = s->nscene;
+  double* tmin = (nb_t > 1) ? as<double>(s->scene_buf) + 3 * (size_t)nb_t : D + nv3;
+  const std::vector<double> ones(nb_t, 1.0);
+  CK(s, cudaMemcpyAsync(tmin, ones.data(), sizeof(double) * nb_t, cudaMemcpyHostToDevice, s->stream));
   int* st = as<int>(s->status);
   if (s->nsv > 0 && s->npl > 0) {
     k_ccd_pg<<<blocks_for(s->nsv, 128), 128, 0, s->stream>>>(s->nsv, s->npl, Tp, P0, D, as<double>(s->planes),
@@ -1140,12 +1175,12 @@ yasps_status ccd_candidates(yasps_system* s, double* alpha_host) {
                                                          s->prm.ccd_gap, s->prm.ccd_max_iter, tmin, st);
     LAUNCH_CHECK(s, "k_ccd_cand");
   }
-  CK(s, cudaMemcpyAsync(alpha_host, tmin, sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+  CK(s, cudaMemcpyAsync(alpha_host, tmin, sizeof(double) * nb_t, cudaMemcpyDeviceToHost, s->stream));
   CK(s, cudaStreamSynchronize(s->stream));
   return YASPS_OK;
 }
 
-yasps_status barrier_energy_candidates(yasps_system* s, const double* P, double* E_host) {
+yasps_status barrier_energy_candidates(yasps_system* s, const double* P, double* E_host, double* sacc) {
   const topo Tp = make_topo(s);
   const double sh = s->prm.dhat * s->prm.dhat;
   const int nblk_v = blocks_for(std::max(s->nsv, 1), 128);
@@ -1157,16 +1192,17 @@ yasps_status barrier_energy_candidates(yasps_system* s, const double* P, double*
   CK(s, cudaMemsetAsync(part, 0, sizeof(ksum) * (npart + 4), s->stream));
   if (s->nsv > 0 && s->npl > 0) {
     k_pg_query<<<nblk_v, 128, 0, s->stream>>>(0, s->nsv, s->npl, Tp, P, as<double>(s->planes), sh, 2, nullptr, nullptr,
-                                              nullptr, s->prm.kappa, s->prm.barrier_form, part);
+                                              nullptr, s->prm.kappa, s->prm.barrier_form, part, sacc);
     LAUNCH_CHECK(s, "k_pg_query(E)");
   }
   for (int kind = 0; kind < 2; ++kind) {
     const int n = kind == 0 ? s->ncpt : s->ncee;
     if (n == 0) continue;
     k_energy_cand<<<nblk_c, 128, 0, s->stream>>>(kind, n, as<int>(kind == 0 ? s->cpt : s->cee), Tp, P, sh, s->prm.kappa,
-                                                 s->prm.barrier_form, part + nblk_v + kind * nblk_c);
+                                                 s->prm.barrier_form, part + nblk_v + kind * nblk_c, sacc);
     LAUNCH_CHECK(s, "k_energy_cand");
   }
+  if (sacc) return YASPS_OK;  // batches: the per-scene sums are the result
   double* out = reinterpret_cast<double*>(part + npart + 2);
   k_reduce_ksum<<<1, 256, 0, s->stream>>>(part, npart, out);
   LAUNCH_CHECK(s, "k_reduce_ksum");

@@ -675,97 +675,165 @@ __global__ void k_abd(int nb, int nfree, const double* __restrict__ kv, const in
 // ---------------------------------------------------------------- energies (FP64, compensated)
 constexpr int EN_T = 256, EN_MAXB = 148 * 4;
 
+// Every energy kernel walks its items in warp-uniform strides.  With sacc set
+// (batches) each item's energy goes to its scene's accumulator (warp-segmented
+// by scene; items are sorted by scene); otherwise into the compensated block
+// partials.
+struct scene_acc {
+  const int* vscene;      // [nv] vertex -> scene
+  const int* node_scene;  // [nn] node -> scene
+  double* acc;            // [nscene] or null
+};
+__device__ __forceinline__ void add_energy(const scene_acc& sa, ksum& k, int key, double v) {
+  if (sa.acc) seg_add_global(sa.acc, key, v);
+  else kadd(k, v);
+}
+
 __global__ void k_energy_inertia(int nfree, int nb, const double* __restrict__ m, const double* __restrict__ x,
-                                 const double* __restrict__ xtil, ksum* __restrict__ part) {
+                                 const double* __restrict__ xtil, ksum* __restrict__ part, scene_acc sa) {
   ksum k{0.0, 0.0};
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nfree; i += gridDim.x * blockDim.x) {
-    double s = 0.0;
-    for (int c = 0; c < 3; ++c) {
-      const double d = x[3 * i + c] - xtil[3 * i + c];
-      s += d * d;
-    }
-    kadd(k, 0.5 * m[i] * s);
-  }
-  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nb; b += gridDim.x * blockDim.x) {
-    const double* M = m + nfree + 16 * b;
-    const int b0 = nfree + 4 * b;
+  const int lane = threadIdx.x & 31;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  const long long first = ((long long)blockIdx.x * blockDim.x + threadIdx.x) & ~31LL;
+  for (long long base = first; base < nfree; base += stride) {
+    const long long i = base + lane;
     double e = 0.0;
-    for (int a = 0; a < 4; ++a)
-      for (int q = 0; q < 4; ++q)
-        for (int c = 0; c < 3; ++c)
-          e += M[4 * a + q] * (x[3 * (b0 + a) + c] - xtil[3 * (b0 + a) + c]) * (x[3 * (b0 + q) + c] - xtil[3 * (b0 + q) + c]);
-    kadd(k, 0.5 * e);
+    int key = -1;
+    if (i < nfree) {
+      double s = 0.0;
+      for (int c = 0; c < 3; ++c) {
+        const double d = x[3 * i + c] - xtil[3 * i + c];
+        s += d * d;
+      }
+      e = 0.5 * m[i] * s;
+      key = sa.acc ? sa.node_scene[i] : 0;
+    }
+    add_energy(sa, k, key, e);
+  }
+  for (long long base = first; base < nb; base += stride) {
+    const long long b = base + lane;
+    double e = 0.0;
+    int key = -1;
+    if (b < nb) {
+      const double* M = m + nfree + 16 * b;
+      const long long b0 = nfree + 4 * b;
+      for (int a = 0; a < 4; ++a)
+        for (int q = 0; q < 4; ++q)
+          for (int c = 0; c < 3; ++c)
+            e += M[4 * a + q] * (x[3 * (b0 + a) + c] - xtil[3 * (b0 + a) + c]) *
+                 (x[3 * (b0 + q) + c] - xtil[3 * (b0 + q) + c]);
+      e *= 0.5;
+      key = sa.acc ? sa.node_scene[b0] : 0;
+    }
+    add_energy(sa, k, key, e);
   }
   k = block_ksum(k);
   if (threadIdx.x == 0) part[blockIdx.x] = k;
 }
 
 __global__ void k_energy_snh(int nt, const int* __restrict__ tv, const double* __restrict__ trest,
-                             const double* __restrict__ P, double h2, ksum* __restrict__ part) {
+                             const double* __restrict__ P, double h2, ksum* __restrict__ part, scene_acc sa) {
   ksum k{0.0, 0.0};
-  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nt; e += gridDim.x * blockDim.x) {
-    const int4 v = reinterpret_cast<const int4*>(tv)[e];
-    const double* R = trest + 12 * (size_t)e;
-    const v3<double> x0 = ld3(P, v.x);
-    const v3<double> d1 = ld3(P, v.y) - x0, d2 = ld3(P, v.z) - x0, d3_ = ld3(P, v.w) - x0;
-    const double Ds[9] = {d1.x, d2.x, d3_.x, d1.y, d2.y, d3_.y, d1.z, d2.z, d3_.z};
-    double F[9];
-    for (int i = 0; i < 3; ++i)
-      for (int j = 0; j < 3; ++j) F[3 * i + j] = Ds[3 * i] * R[j] + Ds[3 * i + 1] * R[3 + j] + Ds[3 * i + 2] * R[6 + j];
-    double Ic = 0.0;
-    for (int q = 0; q < 9; ++q) Ic += F[q] * F[q];
-    const double J = F[0] * (F[4] * F[8] - F[5] * F[7]) - F[1] * (F[3] * F[8] - F[5] * F[6]) +
-                     F[2] * (F[3] * F[7] - F[4] * F[6]);
-    const double mu = R[10], lam = R[11];
-    const double alpha = 1.0 + 0.75 * mu / lam;
-    const double psi = 0.5 * mu * (Ic - 3.0) - 0.5 * mu * log(Ic + 1.0) + 0.5 * lam * (J - alpha) * (J - alpha);
-    kadd(k, h2 * R[9] * psi);
+  const int lane = threadIdx.x & 31;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long base = ((long long)blockIdx.x * blockDim.x + threadIdx.x) & ~31LL; base < nt; base += stride) {
+    const long long e = base + lane;
+    double val = 0.0;
+    int key = -1;
+    if (e < nt) {
+      const int4 v = reinterpret_cast<const int4*>(tv)[e];
+      const double* R = trest + 12 * (size_t)e;
+      const v3<double> x0 = ld3(P, v.x);
+      const v3<double> d1 = ld3(P, v.y) - x0, d2 = ld3(P, v.z) - x0, d3_ = ld3(P, v.w) - x0;
+      const double Ds[9] = {d1.x, d2.x, d3_.x, d1.y, d2.y, d3_.y, d1.z, d2.z, d3_.z};
+      double F[9];
+      for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) F[3 * i + j] = Ds[3 * i] * R[j] + Ds[3 * i + 1] * R[3 + j] + Ds[3 * i + 2] * R[6 + j];
+      double Ic = 0.0;
+      for (int q = 0; q < 9; ++q) Ic += F[q] * F[q];
+      const double J = F[0] * (F[4] * F[8] - F[5] * F[7]) - F[1] * (F[3] * F[8] - F[5] * F[6]) +
+                       F[2] * (F[3] * F[7] - F[4] * F[6]);
+      const double mu = R[10], lam = R[11];
+      const double alpha = 1.0 + 0.75 * mu / lam;
+      const double psi = 0.5 * mu * (Ic - 3.0) - 0.5 * mu * log(Ic + 1.0) + 0.5 * lam * (J - alpha) * (J - alpha);
+      val = h2 * R[9] * psi;
+      key = sa.acc ? sa.vscene[v.x] : 0;
+    }
+    add_energy(sa, k, key, val);
   }
   k = block_ksum(k);
   if (threadIdx.x == 0) part[blockIdx.x] = k;
 }
 
 __global__ void k_energy_membrane(int nc, const int* __restrict__ cv, const double* __restrict__ crest,
-                                  const double* __restrict__ P, double h2, ksum* __restrict__ part) {
+                                  const double* __restrict__ P, double h2, ksum* __restrict__ part, scene_acc sa) {
   ksum k{0.0, 0.0};
-  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nc; e += gridDim.x * blockDim.x) {
-    const double* R = crest + 8 * (size_t)e;
-    const v3<double> x0 = ld3(P, cv[3 * e]);
-    const v3<double> a1 = ld3(P, cv[3 * e + 1]) - x0, a2 = ld3(P, cv[3 * e + 2]) - x0;
-    const v3<double> f0 = R[0] * a1 + R[2] * a2, f1 = R[1] * a1 + R[3] * a2;  // columns of F
-    const double E00 = 0.5 * (dot(f0, f0) - 1.0), E11 = 0.5 * (dot(f1, f1) - 1.0), E01 = 0.5 * dot(f0, f1);
-    const double tr = E00 + E11;
-    const double psi = R[5] * (E00 * E00 + E11 * E11 + 2.0 * E01 * E01) + 0.5 * R[6] * tr * tr;
-    kadd(k, h2 * R[4] * psi);
+  const int lane = threadIdx.x & 31;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long base = ((long long)blockIdx.x * blockDim.x + threadIdx.x) & ~31LL; base < nc; base += stride) {
+    const long long e = base + lane;
+    double val = 0.0;
+    int key = -1;
+    if (e < nc) {
+      const double* R = crest + 8 * (size_t)e;
+      const v3<double> x0 = ld3(P, cv[3 * e]);
+      const v3<double> a1 = ld3(P, cv[3 * e + 1]) - x0, a2 = ld3(P, cv[3 * e + 2]) - x0;
+      const v3<double> f0 = R[0] * a1 + R[2] * a2, f1 = R[1] * a1 + R[3] * a2;  // columns of F
+      const double E00 = 0.5 * (dot(f0, f0) - 1.0), E11 = 0.5 * (dot(f1, f1) - 1.0), E01 = 0.5 * dot(f0, f1);
+      const double tr = E00 + E11;
+      const double psi = R[5] * (E00 * E00 + E11 * E11 + 2.0 * E01 * E01) + 0.5 * R[6] * tr * tr;
+      val = h2 * R[4] * psi;
+      key = sa.acc ? sa.vscene[cv[3 * e]] : 0;
+    }
+    add_energy(sa, k, key, val);
   }
   k = block_ksum(k);
   if (threadIdx.x == 0) part[blockIdx.x] = k;
 }
 
 __global__ void k_energy_bend(int nh, const int* __restrict__ hv, const double* __restrict__ hrest,
-                              const double* __restrict__ P, double h2, ksum* __restrict__ part) {
+                              const double* __restrict__ P, double h2, ksum* __restrict__ part, scene_acc sa) {
   ksum k{0.0, 0.0};
-  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nh; e += gridDim.x * blockDim.x) {
-    const double th = hinge_theta(ld3(P, hv[4 * e]), ld3(P, hv[4 * e + 1]), ld3(P, hv[4 * e + 2]), ld3(P, hv[4 * e + 3]));
-    const double d = th - hrest[2 * e];
-    kadd(k, h2 * hrest[2 * e + 1] * d * d);
+  const int lane = threadIdx.x & 31;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long base = ((long long)blockIdx.x * blockDim.x + threadIdx.x) & ~31LL; base < nh; base += stride) {
+    const long long e = base + lane;
+    double val = 0.0;
+    int key = -1;
+    if (e < nh) {
+      const double th =
+          hinge_theta(ld3(P, hv[4 * e]), ld3(P, hv[4 * e + 1]), ld3(P, hv[4 * e + 2]), ld3(P, hv[4 * e + 3]));
+      const double d = th - hrest[2 * e];
+      val = h2 * hrest[2 * e + 1] * d * d;
+      key = sa.acc ? sa.vscene[hv[4 * e]] : 0;
+    }
+    add_energy(sa, k, key, val);
   }
   k = block_ksum(k);
   if (threadIdx.x == 0) part[blockIdx.x] = k;
 }
 
 __global__ void k_energy_abd(int nb, int nfree, const double* __restrict__ kv, const double* __restrict__ x, double h2,
-                             ksum* __restrict__ part) {
+                             ksum* __restrict__ part, scene_acc sa) {
   ksum k{0.0, 0.0};
-  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nb; b += gridDim.x * blockDim.x) {
-    const int a0 = nfree + 4 * b + 1;
-    double s = 0.0;
-    for (int i = 0; i < 3; ++i)
-      for (int j = 0; j < 3; ++j) {
-        const double d = dot(ld3(x, a0 + i), ld3(x, a0 + j)) - (i == j ? 1.0 : 0.0);
-        s += d * d;
-      }
-    kadd(k, h2 * 0.5 * kv[b] * s);
+  const int lane = threadIdx.x & 31;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long base = ((long long)blockIdx.x * blockDim.x + threadIdx.x) & ~31LL; base < nb; base += stride) {
+    const long long b = base + lane;
+    double val = 0.0;
+    int key = -1;
+    if (b < nb) {
+      const long long a0 = nfree + 4 * b + 1;
+      double s = 0.0;
+      for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+          const double d = dot(ld3(x, (int)(a0 + i)), ld3(x, (int)(a0 + j))) - (i == j ? 1.0 : 0.0);
+          s += d * d;
+        }
+      val = h2 * 0.5 * kv[b] * s;
+      key = sa.acc ? sa.node_scene[a0 - 1] : 0;
+    }
+    add_energy(sa, k, key, val);
   }
   k = block_ksum(k);
   if (threadIdx.x == 0) part[blockIdx.x] = k;
@@ -942,7 +1010,8 @@ yasps_status launch_eval_static(yasps_system* s, const double* x, const double* 
   return eval_static_t<double>(s, x, xtil, mask, project);
 }
 
-yasps_status energy_static(yasps_system* s, const double* x, const double* xtil, double* out5) {
+yasps_status energy_static(yasps_system* s, const double* x, const double* xtil, double* out5, double* sacc) {
+  const scene_acc sa{sacc ? as<int>(s->vscene) : nullptr, sacc ? as<int>(s->node_scene) : nullptr, sacc};
   const double h2 = s->prm.dt * s->prm.dt;
   const int stride = EN_MAXB;
   ENSURE(s, s->red, sizeof(ksum) * 5 * stride + 64);
@@ -951,26 +1020,29 @@ yasps_status energy_static(yasps_system* s, const double* x, const double* xtil,
   const double* P = as<double>(s->P);
   auto nblk = [](long long n) { return (int)std::min<long long>(EN_MAXB, std::max<long long>(1, (n + EN_T - 1) / EN_T)); };
   k_energy_inertia<<<nblk(std::max(s->nfree, s->nb)), EN_T, 0, s->stream>>>(s->nfree, s->nb, as<double>(s->nodemass), x,
-                                                                            xtil, part);
+                                                                            xtil, part, sa);
   LAUNCH_CHECK(s, "k_energy_inertia");
   if (s->nt) {
-    k_energy_snh<<<nblk(s->nt), EN_T, 0, s->stream>>>(s->nt, as<int>(s->tet_v), as<double>(s->tet_rest), P, h2, part + stride);
+    k_energy_snh<<<nblk(s->nt), EN_T, 0, s->stream>>>(s->nt, as<int>(s->tet_v), as<double>(s->tet_rest), P, h2,
+                                                      part + stride, sa);
     LAUNCH_CHECK(s, "k_energy_snh");
   }
   if (s->nc) {
     k_energy_membrane<<<nblk(s->nc), EN_T, 0, s->stream>>>(s->nc, as<int>(s->tri_v), as<double>(s->tri_rest), P, h2,
-                                                          part + 2 * stride);
+                                                          part + 2 * stride, sa);
     LAUNCH_CHECK(s, "k_energy_membrane");
   }
   if (s->nh) {
     k_energy_bend<<<nblk(s->nh), EN_T, 0, s->stream>>>(s->nh, as<int>(s->hinge_v), as<double>(s->hinge_rest), P, h2,
-                                                      part + 3 * stride);
+                                                      part + 3 * stride, sa);
     LAUNCH_CHECK(s, "k_energy_bend");
   }
   if (s->nb) {
-    k_energy_abd<<<nblk(s->nb), EN_T, 0, s->stream>>>(s->nb, s->nfree, as<double>(s->body_kv), x, h2, part + 4 * stride);
+    k_energy_abd<<<nblk(s->nb), EN_T, 0, s->stream>>>(s->nb, s->nfree, as<double>(s->body_kv), x, h2, part + 4 * stride,
+                                                      sa);
     LAUNCH_CHECK(s, "k_energy_abd");
   }
+  if (sacc) return YASPS_OK;  // batches: the per-scene sums are the result
   double* out_dev = reinterpret_cast<double*>(part + 5 * stride);
   k_reduce_parts<<<5, 256, 0, s->stream>>>(part, stride, stride, out_dev);
   LAUNCH_CHECK(s, "k_reduce_parts");

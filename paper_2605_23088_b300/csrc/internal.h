@@ -10,6 +10,7 @@
 #include "yasps.h"
 
 struct yasps_system;
+constexpr int kMaxScenes = 1024;  // scenes per batch (per-block scene sums in shared memory)
 
 // a growable device buffer owned by the system (contents are not kept on growth)
 struct gbuf {
@@ -43,6 +44,12 @@ struct yasps_system {
   int nv = 0, nn = 0, nfree = 0, nb = 0, nt = 0, nc = 0, nh = 0, nst = 0, nse = 0, nsv = 0, npl = 0, nfix = 0;
   double bbox_diag = 1.0;
   int nbits = 1;  // bits of a node id in packed (row, col) keys; node 2^nbits - 1 is the sentinel
+  int nscene = 1;  // independent scenes in this system (batching)
+  gbuf vscene;     // int [nv] scene of each vertex (batches only)
+  gbuf node_scene; // int [nn] scene of each node (batches only)
+  // per-scene results of the last yasps_step (batches)
+  std::vector<int> scene_newton, scene_status, scene_pcg;
+  gbuf scene_buf;  // per-scene device scratch (sums, tolerances, step bounds)
 
   // scene, device
   gbuf vnode;     // int [nv] free: node; body: first node of its body; fixed: -1
@@ -177,7 +184,9 @@ yasps_status launch_bend(yasps_system* s, int project);
 yasps_status launch_snh_young_adj(yasps_system* s, const double* P, const double* lam, double h2, double* Ebar);
 yasps_status launch_set_young(yasps_system* s, const double* E);
 // five static terms (inertia, tet, membrane, bend, ABD) into out5 (host); synchronises
-yasps_status energy_static(yasps_system* s, const double* x, const double* xtil, double* out5);
+// out5: the five static terms (single scene); with sacc (device [nscene],
+// batches) every item's energy is added to its scene's entry instead
+yasps_status energy_static(yasps_system* s, const double* x, const double* xtil, double* out5, double* sacc = nullptr);
 
 // ---------------------------------------------------------------- contact.cu
 yasps_status detect_pairs(yasps_system* s, const double* P);
@@ -188,8 +197,10 @@ yasps_status ccd_bound(yasps_system* s, const double* x, const double* p, double
 // candidates of the segment [x, x - p] (positions at x left in s->P, P(x - p) and
 // the displacement in s->stepv[4]); CCD, barrier energy and detection on them
 yasps_status swept_candidates(yasps_system* s, const double* x, const double* p);
+// alpha_host: one bound, or one per scene for batches ([nscene])
 yasps_status ccd_candidates(yasps_system* s, double* alpha_host);
-yasps_status barrier_energy_candidates(yasps_system* s, const double* P, double* E_host);
+// sacc (device [nscene], batches): per-scene sums added there, E_host untouched
+yasps_status barrier_energy_candidates(yasps_system* s, const double* P, double* E_host, double* sacc = nullptr);
 yasps_status detect_from_candidates(yasps_system* s, const double* P);
 
 // ---------------------------------------------------------------- solver.cu

@@ -273,6 +273,14 @@ struct pcg_args {
   pcg_bar* bar;
   int* status;
   long long spin_limit;
+  // batches (nscene > 1): per-scene alpha, beta and stopping test
+  int nscene;
+  const int* node_scene;  // [nn]
+  double* ring;           // [8][nscene]: per-scene sums of reducing barrier k in row k % 8
+  double* srz0;           // [nscene] r0^T z0 per scene
+  const double* stol2;    // [nscene] squared relative tolerance per scene, or null (tol2)
+  int* siters;            // [nscene] iterations each scene ran
+  int* sflag;             // [nscene] 2 = breakdown (d^T H d <= 0) in that scene
 };
 
 __device__ __forceinline__ unsigned long long global_ns() {
@@ -546,11 +554,51 @@ __device__ __forceinline__ V update_free(const pcg_args<T, V>& a, long long i, V
   return acc;
 }
 
+// ---- batches: per-scene sums
+// Warp-segmented sum over runs of equal keys (runs must be contiguous across
+// the lanes, as sorted keys are); the head lane of each run adds the run's sum
+// into shs[key].  key < 0 contributes nothing.  All 32 lanes must call.
+template <typename V>
+__device__ __forceinline__ void seg_add_shared(double* shs, int key, V v, int lane) {
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const int ko = __shfl_down_sync(0xffffffffu, key, off);
+    const V vo = shfl_down_v(v, off);
+    if (lane + off < 32 && ko == key) v += vo;
+  }
+  const int kp = __shfl_up_sync(0xffffffffu, key, 1);
+  if (key >= 0 && (lane == 0 || kp != key)) atomicAdd(&shs[key], (double)v);
+}
+// the block's per-scene partials into row `row` of the ring; shs is cleared
+__device__ __forceinline__ void flush_scene_sums(double* shs, double* ring, int row, int nscene) {
+  __syncthreads();
+  for (int t = threadIdx.x; t < nscene; t += blockDim.x) {
+    const double v = shs[t];
+    if (v != 0.0) {
+      atomicAdd(&ring[(size_t)row * nscene + t], v);
+      shs[t] = 0.0;
+    }
+  }
+}
+// per-scene scalars after the barriers of an iteration
 template <typename T, typename V>
+struct scene_view {
+  const pcg_args<T, V>* a;
+  int cp, cpp, kb;  // ring rows: last r^T z, the one before, this iteration's d^T H d
+  __device__ double rz(int sc) const { return __ldcg(a->ring + (size_t)cp * a->nscene + sc); }
+  __device__ double rz_old(int sc) const { return __ldcg(a->ring + (size_t)cpp * a->nscene + sc); }
+  __device__ double tol2(int sc, double t) const { return a->stol2 ? a->stol2[sc] : t; }
+  __device__ bool finished(int sc, double t) const {
+    return __ldcg(a->sflag + sc) != 0 || !(rz(sc) > tol2(sc, t) * __ldcg(a->srz0 + sc));
+  }
+};
+
+template <typename T, typename V, bool BATCH>
 __global__ void __launch_bounds__(pcg_threads<T>::N, 1) k_pcg_persistent(pcg_args<T, V> a) {
   using L = stage_layout<T>;
   extern __shared__ __align__(128) unsigned char smem[];
   uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + 2 * L::BUF);
+  double* shs = reinterpret_cast<double*>(smem + 2 * L::BUF + 16);  // batches: per-scene partials
   const int G = gridDim.x;
   const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const long long nthr = (long long)G * blockDim.x;
@@ -563,8 +611,11 @@ __global__ void __launch_bounds__(pcg_threads<T>::N, 1) k_pcg_persistent(pcg_arg
   // block 0's clock per iteration: 0 own nodes (d', D d'), 1 upper blocks,
   // 2 wait + d^T H d, 3 update, 4 wait + r^T z
   __shared__ unsigned long long tph[5];
+  __shared__ int sh_active;
   unsigned long long tlast = 0;
   if (threadIdx.x < 5) tph[threadIdx.x] = 0;
+  if constexpr (BATCH)
+    for (int t = threadIdx.x; t < a.nscene; t += blockDim.x) shs[t] = 0.0;
   unsigned parity = 0u;    // bit b: phase parity of buffer b's next completion
   unsigned inflight = 0u;  // bit b: buffer b has a request not yet waited for (thread 0's view)
   if (threadIdx.x == 0) {
@@ -573,20 +624,65 @@ __global__ void __launch_bounds__(pcg_threads<T>::N, 1) k_pcg_persistent(pcg_arg
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
+  // batches: per-scene sums live in ring rows; block 0 clears the row of
+  // barrier k - 3 once barrier k has completed (nobody reads it any more)
+  auto after_barrier = [&](unsigned kdone) {
+    if constexpr (BATCH) {
+      if (blockIdx.x == 0 && kdone >= 3) {
+        double* row = a.ring + (size_t)((kdone - 3) & 7) * a.nscene;
+        for (int t = threadIdx.x; t < a.nscene; t += blockDim.x) row[t] = 0.0;
+      }
+    }
+  };
+  // batches: number of scenes still iterating (the same value in every block)
+  auto count_active = [&](const scene_view<T, V>& sv) -> int {
+    int c = 0;
+    for (int t = threadIdx.x; t < a.nscene; t += blockDim.x) c += sv.finished(t, a.tol2) ? 0 : 1;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if (threadIdx.x == 0) sh_active = 0;
+    __syncthreads();
+    if (lane == 0) atomicAdd(&sh_active, c);
+    __syncthreads();
+    return sh_active;
+  };
 
   // r = rhs, x = 0, d = 0, q = 0, z = M^-1 r ; r^T z
   V acc = 0;
-  for (long long i = tid; i < nu; i += nthr) {
-    int cnt;
-    size_t o;
-    unit_range((int)i, a.nfree, cnt, o);
-    for (int c = 0; c < cnt; ++c) {
-      a.r[o + c] = (V)a.rhs[o + c];
-      a.x[o + c] = 0;
-      a.d0[o + c] = 0;
-      a.q[o + c] = 0;
+  if constexpr (!BATCH) {
+    for (long long i = tid; i < nu; i += nthr) {
+      int cnt;
+      size_t o;
+      unit_range((int)i, a.nfree, cnt, o);
+      for (int c = 0; c < cnt; ++c) {
+        a.r[o + c] = (V)a.rhs[o + c];
+        a.x[o + c] = 0;
+        a.d0[o + c] = 0;
+        a.q[o + c] = 0;
+      }
+      acc += precond_row<T, V>((int)i, a.nfree, a.Mi, a.r, a.z);
     }
-    acc += precond_row<T, V>((int)i, a.nfree, a.Mi, a.r, a.z);
+  } else {
+    for (long long base = tid & ~31LL; base < nu; base += nthr) {
+      const long long i = base + lane;
+      int key = -1;
+      V v = 0;
+      if (i < nu) {
+        int cnt;
+        size_t o;
+        unit_range((int)i, a.nfree, cnt, o);
+        for (int c = 0; c < cnt; ++c) {
+          a.r[o + c] = (V)a.rhs[o + c];
+          a.x[o + c] = 0;
+          a.d0[o + c] = 0;
+          a.q[o + c] = 0;
+        }
+        v = precond_row<T, V>((int)i, a.nfree, a.Mi, a.r, a.z);
+        key = a.node_scene[i < a.nfree ? i : a.nfree + 4 * (i - a.nfree)];
+      }
+      seg_add_shared(shs, key, v, lane);
+    }
+    flush_scene_sums(shs, a.ring, 0, a.nscene);
   }
   V bs = block_sum_v<V>(acc);
   int done = 0, it = 0;
@@ -594,12 +690,38 @@ __global__ void __launch_bounds__(pcg_threads<T>::N, 1) k_pcg_persistent(pcg_arg
   if (!grid_reduce(a.bar, kbar, (double)bs, rz, a.spin_limit)) done = 3;
   const double rz0 = rz;
   double beta = 0.0;
-  if (!done && !(rz > 0.0)) done = 1;
+  int cp = 0, cpp = 0;  // batches: ring rows of the last and the previous r^T z
+  if constexpr (BATCH) {
+    if (!done) {
+      if (blockIdx.x == 0)
+        for (int t = threadIdx.x; t < a.nscene; t += blockDim.x) a.srz0[t] = __ldcg(a.ring + t);
+      // the first stopping test uses the sums themselves (srz0 is visible only
+      // after the next barrier): a scene with r0^T z0 = 0 is finished
+      int c = 0;
+      for (int t = threadIdx.x; t < a.nscene; t += blockDim.x) c += (__ldcg(a.ring + t) > 0.0) ? 1 : 0;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+      if (threadIdx.x == 0) sh_active = 0;
+      __syncthreads();
+      if (lane == 0) atomicAdd(&sh_active, c);
+      __syncthreads();
+      if (sh_active == 0) done = 1;
+    }
+  } else {
+    if (!done && !(rz > 0.0)) done = 1;
+  }
 
   while (!done && it < a.maxit) {
     V* d = (it & 1) ? a.d1 : a.d0;   // previous direction
     V* dn = (it & 1) ? a.d0 : a.d1;  // this iteration's direction
     const V vb = (V)beta;
+    const scene_view<T, V> sv{&a, cp, cpp, (int)(kbar & 7)};
+    // batches: beta of scene sc (0 in the first iteration and once finished)
+    auto beta_of = [&](int sc) -> V {
+      if (it == 0 || sc < 0) return V(0);
+      if (sv.finished(sc, a.tol2)) return V(0);
+      return (V)(sv.rz(sc) / sv.rz_old(sc));
+    };
     if (clock0) tlast = global_ns();
     // the first two tiles travel while the block does its own nodes
     if (threadIdx.x == 0)
@@ -608,7 +730,20 @@ __global__ void __launch_bounds__(pcg_threads<T>::N, 1) k_pcg_persistent(pcg_arg
         inflight |= 1u << j;
       }
     acc = 0;
-    for (long long i = n0 + threadIdx.x; i < n1; i += blockDim.x) acc += diag_node(a, i, vb, d, dn);
+    if constexpr (!BATCH) {
+      for (long long i = n0 + threadIdx.x; i < n1; i += blockDim.x) acc += diag_node(a, i, vb, d, dn);
+    } else {
+      for (long long base = n0 + (threadIdx.x & ~31); base < n1; base += blockDim.x) {
+        const long long i = base + lane;
+        int key = -1;
+        V v = 0;
+        if (i < n1) {
+          key = a.node_scene[i];
+          v = diag_node(a, i, beta_of(key), d, dn);
+        }
+        seg_add_shared(shs, key, v, lane);
+      }
+    }
     if (clock0) { const unsigned long long t = global_ns(); tph[0] += t - tlast; tlast = t; }
     // upper blocks, tile by tile from shared memory
     bool ok = true;
@@ -629,10 +764,21 @@ __global__ void __launch_bounds__(pcg_threads<T>::N, 1) k_pcg_persistent(pcg_arg
       const int r0 = (k0 < cnt) ? rows[k0] : -1, c0 = (k0 < cnt) ? cols[k0] : 0;
       const int r1 = (k1 < cnt) ? rows[k1] : -1, c1 = (k1 < cnt) ? cols[k1] : 0;
       gath<V> g0, g1;
-      gather_d(r0, c0, a.z, d, vb, g0);
-      gather_d(r1, c1, a.z, d, vb, g1);
-      acc += apply_blk<T, V>(r0, c0, vals + 9 * k0, g0, a.q, lane);
-      acc += apply_blk<T, V>(r1, c1, vals + 9 * k1, g1, a.q, lane);
+      if constexpr (!BATCH) {
+        gather_d(r0, c0, a.z, d, vb, g0);
+        gather_d(r1, c1, a.z, d, vb, g1);
+        acc += apply_blk<T, V>(r0, c0, vals + 9 * k0, g0, a.q, lane);
+        acc += apply_blk<T, V>(r1, c1, vals + 9 * k1, g1, a.q, lane);
+      } else {
+        // a block couples two nodes of one scene: the row's scene gives beta
+        const int s0 = r0 >= 0 ? a.node_scene[r0] : -1, s1 = r1 >= 0 ? a.node_scene[r1] : -1;
+        gather_d(r0, c0, a.z, d, beta_of(s0), g0);
+        gather_d(r1, c1, a.z, d, beta_of(s1), g1);
+        const V p0 = apply_blk<T, V>(r0, c0, vals + 9 * k0, g0, a.q, lane);
+        const V p1 = apply_blk<T, V>(r1, c1, vals + 9 * k1, g1, a.q, lane);
+        seg_add_shared(shs, s0, p0, lane);
+        seg_add_shared(shs, s1, p1, lane);
+      }
       __syncthreads();  // every thread is done with buffer b
       if (threadIdx.x == 0 && j + 2 < sh.tt) {
         issue_tile(tile_of(a, sh, j + 2), smem + b * L::BUF, &mbar[b]);
@@ -644,38 +790,85 @@ __global__ void __launch_bounds__(pcg_threads<T>::N, 1) k_pcg_persistent(pcg_arg
       done = 3;
       break;
     }
+    if constexpr (BATCH) flush_scene_sums(shs, a.ring, (int)(kbar & 7), a.nscene);
     bs = block_sum_v<V>(acc);
     if (clock0) { const unsigned long long t = global_ns(); tph[1] += t - tlast; tlast = t; }
     double dHd = 0.0;
+    const int kb = (int)(kbar & 7);
     if (!grid_reduce(a.bar, kbar, (double)bs, dHd, a.spin_limit)) { done = 3; break; }
+    after_barrier(kbar - 1);
     if (clock0) { const unsigned long long t = global_ns(); tph[2] += t - tlast; tlast = t; }
-    if (!(dHd > 0.0)) { done = 2; break; }
-    const V alpha = (V)(rz / dHd);
+    V alpha = 0;
+    if constexpr (!BATCH) {
+      if (!(dHd > 0.0)) { done = 2; break; }
+      alpha = (V)(rz / dHd);
+    }
+    // batches: alpha of scene sc (0 once finished; a breakdown finishes it)
+    auto alpha_of = [&](int sc) -> V {
+      if (sv.finished(sc, a.tol2)) return V(0);
+      const double q = __ldcg(a.ring + (size_t)kb * a.nscene + sc);
+      if (!(q > 0.0)) {
+        if (blockIdx.x == 0) a.sflag[sc] = 2;
+        return V(0);
+      }
+      return (V)(sv.rz(sc) / q);
+    };
     // C: x += alpha d', r -= alpha q, z = M^-1 r, q = 0 ; r^T z
     acc = 0;
-    for (long long i = tid; i < a.nfree; i += 2 * nthr) {
-      acc += update_free(a, i, alpha, dn);
-      if (i + nthr < a.nfree) acc += update_free(a, i + nthr, alpha, dn);
+    if constexpr (!BATCH) {
+      for (long long i = tid; i < a.nfree; i += 2 * nthr) {
+        acc += update_free(a, i, alpha, dn);
+        if (i + nthr < a.nfree) acc += update_free(a, i + nthr, alpha, dn);
+      }
+    } else {
+      for (long long base = tid & ~31LL; base < a.nfree; base += nthr) {
+        const long long i = base + lane;
+        int key = -1;
+        V v = 0;
+        if (i < a.nfree) {
+          key = a.node_scene[i];
+          v = update_free(a, i, alpha_of(key), dn);
+        }
+        seg_add_shared(shs, key, v, lane);
+      }
     }
     for (long long bi = tid; bi < a.nb; bi += nthr) {
       const int i = a.nfree + (int)bi;
       const size_t o = 3 * ((size_t)a.nfree + 4 * (size_t)bi);
+      V al = alpha;
+      if constexpr (BATCH) al = alpha_of(a.node_scene[a.nfree + 4 * bi]);
       for (int c = 0; c < 12; ++c) {
-        a.x[o + c] += alpha * dn[o + c];
-        a.r[o + c] -= alpha * a.q[o + c];
+        a.x[o + c] += al * dn[o + c];
+        a.r[o + c] -= al * a.q[o + c];
         a.q[o + c] = 0;
       }
-      acc += precond_row<T, V>(i, a.nfree, a.Mi, a.r, a.z);
+      const V v = precond_row<T, V>(i, a.nfree, a.Mi, a.r, a.z);
+      if constexpr (BATCH) atomicAdd(&shs[a.node_scene[a.nfree + 4 * bi]], (double)v);
+      else acc += v;
     }
+    if constexpr (BATCH) flush_scene_sums(shs, a.ring, (int)(kbar & 7), a.nscene);
     bs = block_sum_v<V>(acc);
     if (clock0) { const unsigned long long t = global_ns(); tph[3] += t - tlast; tlast = t; }
     double rz_new = 0.0;
+    const int kc = (int)(kbar & 7);
     if (!grid_reduce(a.bar, kbar, (double)bs, rz_new, a.spin_limit)) { done = 3; break; }
+    after_barrier(kbar - 1);
     if (clock0) { const unsigned long long t = global_ns(); tph[4] += t - tlast; tlast = t; }
-    beta = rz_new / rz;
-    rz = rz_new;
     ++it;
-    if (rz <= a.tol2 * rz0) done = 1;
+    if constexpr (!BATCH) {
+      beta = rz_new / rz;
+      rz = rz_new;
+      if (rz <= a.tol2 * rz0) done = 1;
+    } else {
+      // iterations per scene: scenes that were still running this iteration
+      if (blockIdx.x == 0)
+        for (int t = threadIdx.x; t < a.nscene; t += blockDim.x)
+          if (!sv.finished(t, a.tol2)) a.siters[t] += 1;
+      cpp = cp;
+      cp = kc;
+      const scene_view<T, V> nv{&a, cp, cpp, kc};
+      if (count_active(nv) == 0) done = 1;
+    }
   }
   // a block that gave up may still have tile copies in flight: wait for them
   // (bounded) before the block exits
@@ -750,33 +943,48 @@ yasps_status spmv_t(yasps_system* s, const V* x, V* y, const int* done) {
 
 // grid of the persistent kernel: as many blocks as can be co-resident (a
 // cooperative launch refuses a larger grid instead of deadlocking)
-template <typename T, typename V>
+template <typename T, typename V, bool BATCH>
+constexpr unsigned pcg_smem() {
+  return stage_layout<T>::SMEM + (BATCH ? 8u * kMaxScenes : 0u);
+}
+template <typename T, typename V, bool BATCH>
 yasps_status pcg_grid(yasps_system* s, int* G) {
   int dev = 0, sms = 0, coop = 0, per_sm = 0;
   CK(s, cudaGetDevice(&dev));
   CK(s, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   CK(s, cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
   if (!coop) SYS_FAIL(s, YASPS_E_CUDA, "device does not support cooperative launches");
-  const unsigned smem = stage_layout<T>::SMEM;
-  CK(s, cudaFuncSetAttribute(k_pcg_persistent<T, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  CK(s, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pcg_persistent<T, V>, pcg_threads<T>::N, smem));
+  const unsigned smem = pcg_smem<T, V, BATCH>();
+  CK(s, cudaFuncSetAttribute(k_pcg_persistent<T, V, BATCH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  CK(s, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pcg_persistent<T, V, BATCH>, pcg_threads<T>::N,
+                                                      smem));
   if (per_sm < 1) SYS_FAIL(s, YASPS_E_CUDA, "persistent PCG kernel cannot be resident");
   *G = sms * std::min(per_sm, 2);
   return YASPS_OK;
 }
 
+// per-scene outputs of one batched launch
+struct scene_out {
+  std::vector<int> iters, flag;
+};
+
 // PCG in precision (T, V) on H dx = rhs (FP64 rhs); dx accumulated into p (FP64).
-template <typename T, typename V>
-yasps_status pcg_inner(yasps_system* s, const double* rhs, double* p, double tol, int maxit, int* iters, int* state,
-                       double* rel) {
+// Batches: stol2 (device, per scene) or null, per-scene iterations / flags out.
+template <typename T, typename V, bool BATCH>
+yasps_status pcg_launch(yasps_system* s, const double* rhs, double* p, double tol, int maxit, const double* stol2,
+                        int* iters, int* state, double* rel, scene_out* so) {
   const int n3 = 3 * s->nn;
   for (int k = 0; k < 5; ++k) ENSURE(s, s->vec[k], sizeof(V) * (n3 + 4));
   ENSURE(s, s->vec[8], sizeof(V) * (n3 + 4));
   int G = 0;
-  RC((pcg_grid<T, V>(s, &G)));
-  ENSURE(s, s->scal, 256);
-  pcg_dev* sc = as<pcg_dev>(s->scal);
-  pcg_bar* bar = reinterpret_cast<pcg_bar*>(static_cast<char*>(s->scal.p) + 128);
+  RC((pcg_grid<T, V, BATCH>(s, &G)));
+  const int ns = s->nscene;
+  // scalars, barrier, and for batches: ring [8][ns], srz0, siters, sflag
+  const size_t scal_bytes = 256 + (BATCH ? (size_t)ns * (8 * 8 + 8 + 4 + 4) + 64 : 0);
+  ENSURE(s, s->scal, scal_bytes);
+  char* base = static_cast<char*>(s->scal.p);
+  pcg_dev* sc = reinterpret_cast<pcg_dev*>(base);
+  pcg_bar* bar = reinterpret_cast<pcg_bar*>(base + 128);
   pcg_args<T, V> a;
   a.nn = s->nn;
   a.nfree = s->nfree;
@@ -804,15 +1012,28 @@ yasps_status pcg_inner(yasps_system* s, const double* rhs, double* p, double tol
   a.bar = bar;
   a.status = as<int>(s->status);
   a.spin_limit = 1LL << 22;  // a few seconds of polling per wait
-  CK(s, cudaMemsetAsync(s->scal.p, 0, 256, s->stream));
+  a.nscene = ns;
+  a.node_scene = BATCH ? as<int>(s->node_scene) : nullptr;
+  a.ring = BATCH ? reinterpret_cast<double*>(base + 256) : nullptr;
+  a.srz0 = BATCH ? a.ring + 8 * (size_t)ns : nullptr;
+  a.siters = BATCH ? reinterpret_cast<int*>(a.srz0 + ns) : nullptr;
+  a.sflag = BATCH ? a.siters + ns : nullptr;
+  a.stol2 = stol2;
+  CK(s, cudaMemsetAsync(s->scal.p, 0, scal_bytes, s->stream));
   void* params[] = {&a};
   cudaEvent_t pk = prof_begin(s);
-  CK(s, cudaLaunchCooperativeKernel((const void*)k_pcg_persistent<T, V>, dim3(G), dim3(pcg_threads<T>::N), params, stage_layout<T>::SMEM,
-                                    s->stream));
+  CK(s, cudaLaunchCooperativeKernel((const void*)k_pcg_persistent<T, V, BATCH>, dim3(G), dim3(pcg_threads<T>::N),
+                                    params, pcg_smem<T, V, BATCH>(), s->stream));
   s->launches += 1;
   prof_end(s, YASPS_STAGE_PCG_KERNEL, pk, 0.0);
   pcg_dev h{};
   CK(s, cudaMemcpyAsync(&h, sc, sizeof(pcg_dev), cudaMemcpyDeviceToHost, s->stream));
+  if (BATCH && so) {
+    so->iters.assign(ns, 0);
+    so->flag.assign(ns, 0);
+    CK(s, cudaMemcpyAsync(so->iters.data(), a.siters, sizeof(int) * ns, cudaMemcpyDeviceToHost, s->stream));
+    CK(s, cudaMemcpyAsync(so->flag.data(), a.sflag, sizeof(int) * ns, cudaMemcpyDeviceToHost, s->stream));
+  }
   CK(s, cudaStreamSynchronize(s->stream));
   if (s->prof_on) {
     const double es = sizeof(T), vs = sizeof(V), nn = s->nn;
@@ -837,6 +1058,36 @@ yasps_status pcg_inner(yasps_system* s, const double* rhs, double* p, double tol
   return YASPS_OK;
 }
 
+template <typename T, typename V>
+yasps_status pcg_inner(yasps_system* s, const double* rhs, double* p, double tol, int maxit, int* iters, int* state,
+                       double* rel) {
+  return pcg_launch<T, V, false>(s, rhs, p, tol, maxit, nullptr, iters, state, rel, nullptr);
+}
+
+// r^T M^-1 r per scene in FP64 (the refinement check of a batch): warp-segmented
+// by scene, run heads add into out[scene]
+template <typename T>
+__global__ void k_rz64_scene(int nfree, int nb, const T* __restrict__ Mi, const double* __restrict__ r,
+                             double* __restrict__ z, const int* __restrict__ node_scene, double* __restrict__ out) {
+  const long long base = ((long long)blockIdx.x * blockDim.x + threadIdx.x) & ~31LL;
+  const int lane = threadIdx.x & 31;
+  const long long i = base + lane;
+  const int nu = nfree + nb;
+  double v = 0.0;
+  int key = -1;
+  if (i < nu) {
+    v = precond_row<T, double>((int)i, nfree, Mi, r, z);
+    key = node_scene[i < nfree ? i : nfree + 4 * (i - nfree)];
+  }
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const int ko = __shfl_down_sync(0xffffffffu, key, off);
+    const double vo = __shfl_down_sync(0xffffffffu, v, off);
+    if (lane + off < 32 && ko == key) v += vo;
+  }
+  const int kp = __shfl_up_sync(0xffffffffu, key, 1);
+  if (key >= 0 && (lane == 0 || kp != key)) atomicAdd(&out[key], v);
+}
 
 template <typename T>
 yasps_status rz64(yasps_system* s, const double* r, double* out) {
@@ -914,11 +1165,97 @@ yasps_status pcg_solve(yasps_system* s, const double* rhs, double* p, double tol
   return rc;
 }
 
+// r^T M^-1 r per scene (FP64) into out[nscene]
+template <typename T>
+static yasps_status rz64_scene(yasps_system* s, const double* r, std::vector<double>& out) {
+  const int nu = s->nfree + s->nb, ns = s->nscene;
+  ENSURE(s, s->vec[5], sizeof(double) * (3 * (size_t)s->nn + 4));
+  ENSURE(s, s->scene_buf, sizeof(double) * (2 * (size_t)ns + 4));
+  double* acc = as<double>(s->scene_buf);
+  CK(s, cudaMemsetAsync(acc, 0, sizeof(double) * ns, s->stream));
+  k_rz64_scene<T><<<blocks_for(std::max(nu, 1), 256), 256, 0, s->stream>>>(s->nfree, s->nb, as<T>(s->minv), r,
+                                                                          as<double>(s->vec[5]), as<int>(s->node_scene),
+                                                                          acc);
+  LAUNCH_CHECK(s, "k_rz64_scene");
+  out.assign(ns, 0.0);
+  CK(s, cudaMemcpyAsync(out.data(), acc, sizeof(double) * ns, cudaMemcpyDeviceToHost, s->stream));
+  CK(s, cudaStreamSynchronize(s->stream));
+  return YASPS_OK;
+}
+
+// Batches: one PCG per scene, all in the same launches (per-scene alpha, beta
+// and stopping test).  FP32-mixed: FP32 inner PCG, FP64 residual per scene,
+// refinement sweeps until every scene meets the tolerance; a finished scene
+// gets an inner tolerance of 1, so later sweeps leave it alone.
+static yasps_status pcg_solve_batch(yasps_system* s, const double* rhs, double* p, double tol, int maxit, int* iters,
+                                    double* rel_res) {
+  const int n3 = 3 * s->nn, ns = s->nscene;
+  scene_out so;
+  int it = 0, state = 0;
+  double rel = 0.0;
+  s->scene_pcg.assign(ns, 0);
+  auto take = [&](const scene_out& o) -> bool {  // true if some scene broke down
+    bool broke = false;
+    for (int k = 0; k < ns; ++k) {
+      s->scene_pcg[k] += o.iters[k];
+      broke |= o.flag[k] == 2;
+    }
+    return broke;
+  };
+  if (s->hess_precision != 1) {
+    RC((pcg_launch<double, double, true>(s, rhs, p, tol, maxit, nullptr, &it, &state, &rel, &so)));
+    if (iters) *iters = it;
+    if (rel_res) *rel_res = state == 1 ? 0.0 : 1.0;
+    if (take(so)) SYS_FAIL(s, YASPS_E_NAN, "PCG breakdown in a scene: d^T H d <= 0");
+    if (state != 1) SYS_FAIL(s, YASPS_E_NOCONV, "PCG hit its iteration cap");
+    return YASPS_OK;
+  }
+  ENSURE(s, s->vec[6], sizeof(double) * (n3 + 4));
+  double* res = as<double>(s->vec[6]);
+  std::vector<double> rz0, rz;
+  RC(rz64_scene<float>(s, rhs, rz0));
+  rz = rz0;
+  std::vector<double> stol2(ns);
+  int total = 0;
+  bool all = false, broke = false;
+  const int sweeps = std::max(1, s->prm.refine_sweeps);
+  for (int sw = 0; sw < sweeps && !all; ++sw) {
+    for (int k = 0; k < ns; ++k) {
+      const bool fin = !(rz[k] > tol * tol * rz0[k]);
+      const double inner = fin ? 1.0 : std::max(tol * std::sqrt(rz0[k] / rz[k]), 5e-6);
+      stol2[k] = inner * inner;
+    }
+    ENSURE(s, s->scene_buf, sizeof(double) * (2 * (size_t)ns + 4));
+    double* st_dev = as<double>(s->scene_buf) + ns;
+    CK(s, cudaMemcpyAsync(st_dev, stol2.data(), sizeof(double) * ns, cudaMemcpyHostToDevice, s->stream));
+    RC((pcg_launch<float, float, true>(s, sw == 0 ? rhs : res, p, tol, maxit - total, st_dev, &it, &state, &rel,
+                                       &so)));
+    total += it;
+    broke |= take(so);
+    RC(spmv64(s, p, res));
+    k_sub_from<<<blocks_for(n3, 256), 256, 0, s->stream>>>(n3, rhs, res);
+    LAUNCH_CHECK(s, "k_sub_from");
+    RC(rz64_scene<float>(s, res, rz));
+    all = true;
+    for (int k = 0; k < ns; ++k) all &= !(rz[k] > tol * tol * rz0[k]);
+    if (total >= maxit || broke) break;
+  }
+  if (iters) *iters = total;
+  double worst = 0.0;
+  for (int k = 0; k < ns; ++k)
+    if (rz0[k] > 0.0) worst = std::max(worst, std::sqrt(std::max(rz[k], 0.0) / rz0[k]));
+  if (rel_res) *rel_res = worst;
+  if (broke) SYS_FAIL(s, YASPS_E_NAN, "PCG breakdown in a scene: d^T H d <= 0");
+  if (!all && total >= maxit) SYS_FAIL(s, YASPS_E_NOCONV, "PCG hit its iteration cap");
+  return YASPS_OK;
+}
+
 yasps_status pcg_solve_impl(yasps_system* s, const double* rhs, double* p, double tol, int maxit, int* iters,
                             double* rel_res) {
   const int n3 = 3 * s->nn;
   if (maxit <= 0) maxit = 10 * n3;
   CK(s, cudaMemsetAsync(p, 0, sizeof(double) * n3, s->stream));
+  if (s->nscene > 1) return pcg_solve_batch(s, rhs, p, tol, maxit, iters, rel_res);
   int it = 0, state = 0;
   double rel = 0.0;
   if (s->hess_precision != 1) {

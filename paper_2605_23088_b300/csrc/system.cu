@@ -60,7 +60,7 @@ static yasps_status upload(yasps_system* s, gbuf& b, const T* host, size_t count
 
 static void all_bufs(yasps_system* s, std::vector<gbuf*>& v) {
   gbuf* one[] = {&s->vnode, &s->vbody, &s->vr, &s->vmass, &s->rest, &s->xfix, &s->fixed, &s->fixvel, &s->nodemass,
-                 &s->tet_v, &s->tet_n, &s->tet_rest, &s->tet_E, &s->tet_nu, &s->tet_slot, &s->tri_v, &s->tri_n, &s->tri_rest, &s->tri_slot,
+                 &s->tet_v, &s->tet_n, &s->tet_rest, &s->tet_E, &s->tet_nu, &s->vscene, &s->node_scene, &s->scene_buf, &s->tet_slot, &s->tri_v, &s->tri_n, &s->tri_rest, &s->tri_slot,
                  &s->hinge_v, &s->hinge_n, &s->hinge_rest, &s->hinge_slot, &s->body_kv, &s->body_slot, &s->stri,
                  &s->sedge, &s->svert, &s->planes, &s->Hs.row_ptr, &s->Hs.col, &s->Hs.row, &s->Hs.vals,
                  &s->Hd.row_ptr, &s->Hd.col, &s->Hd.row, &s->Hd.vals, &s->diag, &s->grad, &s->minv, &s->P, &s->pt,
@@ -178,6 +178,32 @@ static yasps_status build_impl(yasps_system* s, const yasps_scene_desc* d) {
   for (int v = 0; v < nv; ++v)
     if (d->vert_body[v] < -1 || d->vert_body[v] >= d->n_bodies) SYS_FAIL(s, YASPS_E_INVAL, "vert_body out of range");
 
+  // batching: scenes contiguous in vertex order, every element inside one scene
+  const int ns = (d->n_scenes > 1) ? d->n_scenes : 1;
+  if (ns > 1) {
+    if (ns > kMaxScenes) SYS_FAIL(s, YASPS_E_CAPACITY, "more scenes than a batch may hold");
+    if (!d->vert_scene) SYS_FAIL(s, YASPS_E_INVAL, "vert_scene missing for a batch");
+    for (int v = 0; v < nv; ++v)
+      if (d->vert_scene[v] < 0 || d->vert_scene[v] >= ns || (v > 0 && d->vert_scene[v] < d->vert_scene[v - 1]))
+        SYS_FAIL(s, YASPS_E_INVAL, "vert_scene must be non-decreasing and in [0, n_scenes)");
+    auto mixed = [&](const int* a, int k, long long n) {
+      for (long long e = 0; e < n; ++e)
+        for (int q = 1; q < k; ++q)
+          if (d->vert_scene[a[k * e + q]] != d->vert_scene[a[k * e]]) return true;
+      return false;
+    };
+    if (mixed(d->tet2v, 4, d->n_tets) || mixed(d->tri2v, 3, d->n_tris) || mixed(d->hinge2v, 4, d->n_hinges) ||
+        mixed(d->surf_tri2v, 3, d->n_surf_tris) || mixed(d->surf_edge2v, 2, d->n_surf_edges))
+      SYS_FAIL(s, YASPS_E_INVAL, "an element spans two scenes");
+    std::vector<int> bscene(d->n_bodies, -1);
+    for (int v = 0; v < nv; ++v) {
+      const int b = d->vert_body[v];
+      if (b < 0) continue;
+      if (bscene[b] >= 0 && bscene[b] != d->vert_scene[v]) SYS_FAIL(s, YASPS_E_INVAL, "an affine body spans two scenes");
+      bscene[b] = d->vert_scene[v];
+    }
+  }
+  s->nscene = ns;
   s->nv = nv; s->nt = d->n_tets; s->nc = d->n_tris; s->nh = d->n_hinges; s->nb = d->n_bodies;
   s->nst = d->n_surf_tris; s->nse = d->n_surf_edges; s->nsv = d->n_surf_verts; s->npl = d->n_planes;
   s->nfix = d->n_fixed;
@@ -198,6 +224,18 @@ static yasps_status build_impl(yasps_system* s, const yasps_scene_desc* d) {
   while (((1LL << nbits) - 1) < (long long)s->nn + 1) ++nbits;
   if (nbits > 31) SYS_FAIL(s, YASPS_E_INVAL, "too many nodes");
   s->nbits = nbits;
+  if (ns > 1) {
+    std::vector<int> nscene(s->nn, 0);
+    for (int v = 0; v < nv; ++v) {
+      if (isfixed[v]) continue;
+      if (d->vert_body[v] < 0) nscene[vnode[v]] = d->vert_scene[v];
+      else
+        for (int k = 0; k < 4; ++k) nscene[vnode[v] + k] = d->vert_scene[v];
+    }
+    RC(upload(s, s->vscene, d->vert_scene, (size_t)nv));
+    RC(upload(s, s->node_scene, nscene.data(), (size_t)s->nn));
+    ENSURE(s, s->scene_buf, sizeof(double) * 8 * (size_t)ns);
+  }
 
   // affine bodies: body-centred rest coordinates r, uniformly lumped masses,
   // node mass matrix M_ab = sum_v m_v w_a w_b with w = (1, r1, r2, r3)
@@ -574,8 +612,11 @@ static float elapsed(cudaEvent_t a, cudaEvent_t b) {
   return ms;
 }
 
+static yasps_status step_batched(yasps_system* s, double* x, double* v, yasps_step_stats* stats);
+
 extern "C" yasps_status yasps_step(yasps_system* s, double* x, double* v, yasps_step_stats* stats) {
   if (!s || !x || !v) return YASPS_E_INVAL;
+  if (s->nscene > 1) return step_batched(s, x, v, stats);
   const int n3 = 3 * s->nn;
   const double h = s->prm.dt;
   yasps_step_stats st{};
@@ -766,5 +807,211 @@ extern "C" yasps_status yasps_adjoint_step(yasps_system* s, const double* x_t, c
   LAUNCH_CHECK(s, "k_adj_out");
   RC(launch_snh_young_adj(s, as<double>(s->P), lam, h * h, Ebar));
   CK(s, cudaStreamSynchronize(s->stream));
+  return YASPS_OK;
+}
+
+// ---------------------------------------------------------------- batches
+namespace {
+// per-scene max |p| over the scene's nodes (bit patterns of non-negative doubles order like the values)
+__global__ void k_absmax_scene(int nn, const double* __restrict__ p, const int* __restrict__ node_scene,
+                               unsigned long long* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nn) return;
+  const double m = fmax(fabs(p[3 * (size_t)i]), fmax(fabs(p[3 * (size_t)i + 1]), fabs(p[3 * (size_t)i + 2])));
+  atomicMax(&out[node_scene[i]], (unsigned long long)__double_as_longlong(m));
+}
+// zero the gradient of the scenes whose Newton iteration has finished: their
+// PCG then starts converged (r0 = 0) and their step stays 0
+__global__ void k_zero_done(int nn, double* __restrict__ g, const int* __restrict__ node_scene,
+                            const int* __restrict__ done) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nn || !done[node_scene[i]]) return;
+  g[3 * (size_t)i] = 0.0;
+  g[3 * (size_t)i + 1] = 0.0;
+  g[3 * (size_t)i + 2] = 0.0;
+}
+// out = x - alpha[scene] p
+__global__ void k_axpy_scene(int nn, const double* __restrict__ x, const double* __restrict__ alpha,
+                             const int* __restrict__ node_scene, const double* __restrict__ p, double* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nn) return;
+  const double a = alpha[node_scene[i]];
+  for (int c = 0; c < 3; ++c) out[3 * (size_t)i + c] = x[3 * (size_t)i + c] - a * p[3 * (size_t)i + c];
+}
+}  // namespace
+
+// incremental potential per scene at x (swept candidates for the barrier)
+static yasps_status energy_scenes(yasps_system* s, const double* x, const double* xtil, std::vector<double>& E) {
+  const int ns = s->nscene;
+  double* acc = as<double>(s->scene_buf) + 2 * (size_t)ns;
+  CK(s, cudaMemsetAsync(acc, 0, sizeof(double) * ns, s->stream));
+  RC(launch_positions(s, x, as<double>(s->P)));
+  RC(energy_static(s, x, xtil, nullptr, acc));
+  RC(barrier_energy_candidates(s, as<double>(s->P), nullptr, acc));
+  E.assign(ns, 0.0);
+  CK(s, cudaMemcpyAsync(E.data(), acc, sizeof(double) * ns, cudaMemcpyDeviceToHost, s->stream));
+  CK(s, cudaStreamSynchronize(s->stream));
+  return YASPS_OK;
+}
+
+// One implicit step of every scene of a batch.  The scenes share the launches
+// (detection, evaluation, assembly, one PCG with per-scene alpha / beta /
+// stopping test, CCD, energies) but every decision is per scene: a scene whose
+// Newton step is below newton_tol stops moving (its step length is 0), each
+// scene has its own CCD bound and its own backtracking, so each scene follows
+// the trajectory it would follow alone.
+static yasps_status step_batched(yasps_system* s, double* x, double* v, yasps_step_stats* stats) {
+  const int n3 = 3 * s->nn, ns = s->nscene;
+  const double h = s->prm.dt;
+  yasps_step_stats st{};
+  for (int k = 0; k < 4; ++k) ENSURE(s, s->stepv[k], sizeof(double) * (n3 + 4));
+  double* xt = as<double>(s->stepv[0]);
+  double* xtil = as<double>(s->stepv[1]);
+  double* p = as<double>(s->stepv[2]);
+  gbuf& trial = s->vec[7];
+  ENSURE(s, trial, sizeof(double) * (n3 + 4));
+  double* xtrial = as<double>(trial);
+  double* sb = as<double>(s->scene_buf);
+  double* alpha_dev = sb + 5 * (size_t)ns;
+  unsigned long long* pmax_dev = reinterpret_cast<unsigned long long*>(sb + 4 * (size_t)ns);
+  if (s->nfix) {
+    k_fixed_advance<<<blocks_for(s->nfix, 128), 128, 0, s->stream>>>(s->nfix, as<int>(s->fixed), as<double>(s->fixvel),
+                                                                    h, as<double>(s->xfix));
+    LAUNCH_CHECK(s, "k_fixed_advance");
+  }
+  CK(s, cudaMemcpyAsync(xt, x, sizeof(double) * n3, cudaMemcpyDeviceToDevice, s->stream));
+  RC(launch_xtilde(s, x, v, xtil));
+  s->cand_valid = false;
+  s->scene_newton.assign(ns, 0);
+  s->scene_status.assign(ns, YASPS_OK);
+  std::vector<int> pcg_tot(ns, 0);
+  std::vector<char> done(ns, 0);
+  std::vector<double> pinf(ns), alpha(ns), E0, E1;
+  std::vector<unsigned long long> pbits(ns);
+  yasps_status rc = YASPS_OK;
+  int it = 0;
+  for (it = 0; it < s->prm.newton_max_iter; ++it) {
+    RC(launch_positions(s, x, as<double>(s->P)));
+    if (it > 0 && s->cand_valid) RC(detect_from_candidates(s, as<double>(s->P)));
+    else RC(detect_pairs(s, as<double>(s->P)));
+    RC(eval_impl(s, x, xtil, YASPS_TERM_ALL, 1));
+    if (it > 0) {
+      std::vector<int> dm(done.begin(), done.end());
+      int* done_dev = reinterpret_cast<int*>(sb + 6 * (size_t)ns);
+      CK(s, cudaMemcpyAsync(done_dev, dm.data(), sizeof(int) * ns, cudaMemcpyHostToDevice, s->stream));
+      k_zero_done<<<blocks_for(s->nn, 256), 256, 0, s->stream>>>(s->nn, as<double>(s->grad), as<int>(s->node_scene),
+                                                                done_dev);
+      LAUNCH_CHECK(s, "k_zero_done");
+    }
+    int pit = 0;
+    double rel = 0.0;
+    rc = pcg_solve(s, as<double>(s->grad), p, s->prm.pcg_rel_tol, s->prm.pcg_max_iter, &pit, &rel);
+    st.pcg_iters_total += pit;
+    for (int k = 0; k < ns; ++k)
+      if (!done[k] && (int)s->scene_pcg.size() == ns) pcg_tot[k] += s->scene_pcg[k];
+    if (rc == YASPS_E_NOCONV) rc = YASPS_OK;  // inexact Newton: keep the last iterate
+    if (rc != YASPS_OK) break;
+    int bits = 0;
+    RC(read_status(s, &bits));
+    if (bits & (DEV_NAN | DEV_BADINDEX)) {
+      s->err = "device error during evaluation";
+      rc = YASPS_E_NAN;
+      break;
+    }
+    // per-scene Newton convergence
+    CK(s, cudaMemsetAsync(pmax_dev, 0, sizeof(double) * ns, s->stream));
+    k_absmax_scene<<<blocks_for(s->nn, 256), 256, 0, s->stream>>>(s->nn, p, as<int>(s->node_scene), pmax_dev);
+    LAUNCH_CHECK(s, "k_absmax_scene");
+    CK(s, cudaMemcpyAsync(pbits.data(), pmax_dev, sizeof(double) * ns, cudaMemcpyDeviceToHost, s->stream));
+    CK(s, cudaStreamSynchronize(s->stream));
+    bool any = false;
+    for (int k = 0; k < ns; ++k) {
+      std::memcpy(&pinf[k], &pbits[k], sizeof(double));
+      if (!std::isfinite(pinf[k])) {
+        s->err = "non-finite Newton direction";
+        return YASPS_E_NAN;
+      }
+      if (!done[k] && pinf[k] <= s->prm.newton_tol) {
+        done[k] = 1;
+        s->scene_newton[k] = it;
+      }
+      any |= !done[k];
+    }
+    st.p_inf = *std::max_element(pinf.begin(), pinf.end());
+    st.n_pt = s->npt; st.n_ee = s->nee; st.n_pg = s->npg;
+    if (!any) break;
+    // per-scene CCD bound, then per-scene backtracking from it
+    RC(swept_candidates(s, x, p));
+    RC(ccd_candidates(s, alpha.data()));
+    for (int k = 0; k < ns; ++k)
+      if (done[k]) alpha[k] = 0.0;
+    RC(energy_scenes(s, x, xtil, E0));
+    std::vector<char> acc(ns, 0);
+    for (int k = 0; k < ns; ++k) acc[k] = done[k];
+    int ls = 0;
+    for (ls = 0; ls < s->prm.ls_max_iter; ++ls) {
+      CK(s, cudaMemcpyAsync(alpha_dev, alpha.data(), sizeof(double) * ns, cudaMemcpyHostToDevice, s->stream));
+      k_axpy_scene<<<blocks_for(s->nn, 256), 256, 0, s->stream>>>(s->nn, x, alpha_dev, as<int>(s->node_scene), p,
+                                                                 xtrial);
+      LAUNCH_CHECK(s, "k_axpy_scene");
+      RC(energy_scenes(s, xtrial, xtil, E1));
+      bool all = true;
+      for (int k = 0; k < ns; ++k) {
+        if (acc[k]) continue;
+        // a decrease, up to the rounding of the energy sums
+        if (E1[k] <= E0[k] + 1e-12 * std::fabs(E0[k])) acc[k] = 1;
+        else alpha[k] *= 0.5;
+        all &= acc[k] != 0;
+      }
+      if (all) break;
+    }
+    if (ls == s->prm.ls_max_iter) {
+      // scenes whose line search found no decreasing step stop where they are
+      for (int k = 0; k < ns; ++k)
+        if (!acc[k]) {
+          alpha[k] = 0.0;
+          done[k] = 1;
+          s->scene_newton[k] = it;
+          s->scene_status[k] = YASPS_E_LINESEARCH;
+        }
+      CK(s, cudaMemcpyAsync(alpha_dev, alpha.data(), sizeof(double) * ns, cudaMemcpyHostToDevice, s->stream));
+      k_axpy_scene<<<blocks_for(s->nn, 256), 256, 0, s->stream>>>(s->nn, x, alpha_dev, as<int>(s->node_scene), p,
+                                                                 xtrial);
+      LAUNCH_CHECK(s, "k_axpy_scene");
+    }
+    CK(s, cudaMemcpyAsync(x, xtrial, sizeof(double) * n3, cudaMemcpyDeviceToDevice, s->stream));
+    st.alpha_last = *std::max_element(alpha.begin(), alpha.end());
+  }
+  for (int k = 0; k < ns; ++k)
+    if (!done[k]) {
+      s->scene_newton[k] = it;
+      if (rc == YASPS_OK) s->scene_status[k] = YASPS_E_NOCONV;
+    }
+  s->scene_pcg = pcg_tot;
+  if (rc == YASPS_OK)
+    for (int k = 0; k < ns; ++k)
+      if (s->scene_status[k] != YASPS_OK) {
+        rc = s->scene_status[k];
+        s->err = rc == YASPS_E_LINESEARCH ? "line search found no decreasing step in a scene"
+                                          : "Newton hit its iteration cap in a scene";
+        break;
+      }
+  k_velocity<<<blocks_for(n3, 256), 256, 0, s->stream>>>(n3, x, xt, 1.0 / h, v);
+  LAUNCH_CHECK(s, "k_velocity");
+  CK(s, cudaStreamSynchronize(s->stream));
+  st.newton_iters = it;
+  st.status = rc;
+  if (stats) *stats = st;
+  return rc;
+}
+
+extern "C" yasps_status yasps_scene_stats(const yasps_system* s, int* newton_iters, int* pcg_iters, int* status) {
+  if (!s) return YASPS_E_INVAL;
+  for (int k = 0; k < s->nscene; ++k) {
+    const bool have = (int)s->scene_newton.size() == s->nscene;
+    if (newton_iters) newton_iters[k] = have ? s->scene_newton[k] : 0;
+    if (pcg_iters) pcg_iters[k] = (int)s->scene_pcg.size() == s->nscene ? s->scene_pcg[k] : 0;
+    if (status) status[k] = (int)s->scene_status.size() == s->nscene ? s->scene_status[k] : 0;
+  }
   return YASPS_OK;
 }

@@ -436,10 +436,10 @@ def gripper_scene(n_tets_target, rng, dt=0.01, dhat=1e-3, kappa=1e4, n_steps=100
     nxf = max(2, int(round((nh * fl * fl / (fw * fw)) ** (1 / 3))))
     nyf = max(1, int(round(nxf * fw / fl)))
     xmin, xmax = ov[:, 0].min(), ov[:, 0].max()
-    ymid = (ov[:, 1].min() + ov[:, 1].max()) / 2
     for side in (-1, 1):
         fv = hex_grid(nyf, nxf, nyf, 1.0) * np.array([fw / nyf, fl / nxf, fw / nyf])
-        fv = fv + np.array([0.0, ymid - fl / 2 + 0.0, -fw / 2])
+        # fingers stand 2 mm above the ground and reach above the object
+        fv = fv + np.array([0.0, 2e-3, -fw / 2])
         if side < 0:
             fv[:, 0] += xmin - 5e-3 - fw
         else:
@@ -458,6 +458,47 @@ def gripper_batch(n_scenes=256, lo=1000, hi=20000, seed=0):
     rng = np.random.default_rng(seed)
     sizes = np.exp(rng.uniform(np.log(lo), np.log(hi), n_scenes)).astype(int)
     return [gripper_scene(int(s), rng) for s in sizes]
+
+
+def concat_scenes(scenes, newton_tol=None):
+    """One batch of independent scenes: arrays concatenated with vertex and body
+    offsets, ``vert_scene`` the scene of every vertex.  The scenes must share
+    dt, dhat, kappa, gravity and planes; the batch's Newton tolerance is the
+    smallest of theirs unless given."""
+    first = scenes[0]
+    for sc in scenes[1:]:
+        for k in ("dt", "dhat", "kappa"):
+            if sc[k] != first[k]:
+                raise ValueError(f"scenes of a batch must share {k}")
+        if not (np.array_equal(sc["gravity"], first["gravity"]) and np.array_equal(sc["planes"], first["planes"])):
+            raise ValueError("scenes of a batch must share gravity and planes")
+    out = {"name": "batch", "planes": first["planes"].copy(), "dt": first["dt"], "dhat": first["dhat"],
+           "kappa": first["kappa"], "gravity": first["gravity"].copy(), "n_steps": first["n_steps"]}
+    voff, boff = 0, 0
+    acc = {k: [] for k in ("rest_pos", "vel0", "vert_body", "fixed", "fixed_vel", "tets", "tet_E", "tet_nu", "tet_rho",
+                           "tris", "tri_E", "tri_nu", "tri_thick", "tri_rho", "hinges", "hinge_kb", "body_mass",
+                           "body_vol", "body_kappa", "surf_tris", "surf_edges", "surf_verts", "vert_scene")}
+    for k, sc in enumerate(scenes):
+        nv = len(sc["rest_pos"])
+        for key in ("rest_pos", "vel0", "fixed_vel", "tet_E", "tet_nu", "tet_rho", "tri_E", "tri_nu", "tri_thick",
+                    "tri_rho", "hinge_kb", "body_mass", "body_vol", "body_kappa"):
+            acc[key].append(np.asarray(sc[key]))
+        vb = np.asarray(sc["vert_body"]).copy()
+        vb[vb >= 0] += boff
+        acc["vert_body"].append(vb)
+        for key in ("fixed", "tets", "tris", "hinges", "surf_tris", "surf_edges", "surf_verts"):
+            acc[key].append(np.asarray(sc[key]) + voff)
+        acc["vert_scene"].append(np.full(nv, k, np.int32))
+        voff += nv
+        boff += len(sc["body_mass"])
+    ints = ("vert_body", "fixed", "tets", "tris", "hinges", "surf_tris", "surf_edges", "surf_verts", "vert_scene")
+    for key, lst in acc.items():
+        out[key] = np.ascontiguousarray(np.concatenate(lst, axis=0).astype(np.int32 if key in ints else np.float64))
+    out["n_scenes"] = len(scenes)
+    out["scene_vert_offsets"] = np.cumsum([0] + [len(sc["rest_pos"]) for sc in scenes])
+    out["bbox_diag"] = max(sc["bbox_diag"] for sc in scenes)
+    out["newton_tol"] = float(newton_tol if newton_tol is not None else min(sc["newton_tol"] for sc in scenes))
+    return out
 
 
 def scene_by_name(name, **kw):
