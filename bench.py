@@ -312,11 +312,74 @@ def native(args):
                                if fp64["prof"]["pcg_kernel"]["ms"] > 0 else None),
             "stages_ms": {k: (v["ms"], v["count"]) for k, v in fp64["prof"].items()},
             "gpu_launches": fp64["launches"], "clocks": fp64["clocks"]}
+    if not args.skip_batch:
+        line["batch"] = batch_bench(args, dev)
     if rank == 0 and world == 1 and not args.skip_cpu:
         line["cpu_baseline"] = cpu_baseline(args)
     if rank == 0:
         print(json.dumps(line), flush=True)
     G.close()
+
+
+# ---------------------------------------------------------------------------
+BATCH_SCENES = 256
+
+
+def batch_bench(args, dev):
+    """The batching form on its own workload: 256 independent two-finger soft
+    grippers closing on deformable objects (sizes log-uniform in 1k-20k tets),
+    all in one system, one implicit step of every scene per call.  Reported
+    per precision: scene-steps/s and Newton iterations/s summed over scenes;
+    and, against it, the first 16 scenes stepped one system at a time."""
+    import torch
+
+    import paper_2605_23088_b300 as yb
+    import scenes
+
+    parts = scenes.gripper_batch(BATCH_SCENES)
+    b = scenes.concat_scenes(parts)
+    ntol = NEWTON_VEL_TOL * b["dt"]
+    out = {"workload": f"{BATCH_SCENES} soft grippers on deformable objects (1k-20k tets each, log-uniform)",
+           "n_scenes": BATCH_SCENES, "n_tets": int(len(b["tets"])), "steps": args.batch_steps,
+           "newton_tol": "||dx||_inf/dt < 1e-2 m/s", "pcg_rel_tol": PCG_TOL}
+    stream = torch.cuda.current_stream()
+    for prec, name in ((1, "fp32_mixed"), (0, "fp64")):
+        G = yb.System(b, precision=prec, pcg_rel_tol=PCG_TOL, newton_tol=ntol)
+        x, v = G.initial_state()
+        G.step(x, v, raise_on_error=False)  # warm-up
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        newton = 0
+        rcs = []
+        e0.record(stream)
+        for _ in range(args.batch_steps):
+            st = G.step(x, v, raise_on_error=False)
+            rcs.append(st["rc"])
+            newton += int(G.scene_stats()[0].sum())
+        e1.record(stream)
+        torch.cuda.synchronize()
+        sec = e0.elapsed_time(e1) * 1e-3
+        out[name] = {"scene_steps_per_s": BATCH_SCENES * args.batch_steps / sec, "newton_iters_per_s": newton / sec,
+                     "ms_per_step": sec * 1e3 / args.batch_steps, "statuses": sorted(set(rcs))}
+        G.close()
+    # the same kind of work without batching: 16 scenes, one system each
+    seq = 0.0
+    nseq = 16
+    for sc in parts[:nseq]:
+        G = yb.System(sc, precision=1, pcg_rel_tol=PCG_TOL, newton_tol=ntol)
+        x, v = G.initial_state()
+        G.step(x, v, raise_on_error=False)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.batch_steps):
+            G.step(x, v, raise_on_error=False)
+        torch.cuda.synchronize()
+        seq += time.perf_counter() - t0
+        G.close()
+    seq_rate = nseq * args.batch_steps / seq
+    out["sequential_fp32_mixed"] = {"scenes": nseq, "scene_steps_per_s": seq_rate}
+    out["batched_vs_sequential"] = out["fp32_mixed"]["scene_steps_per_s"] / seq_rate
+    return out
 
 
 # ---------------------------------------------------------------------------
@@ -373,6 +436,8 @@ def main():
     ap.add_argument("--preroll", type=int, default=14)
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--skip-batch", action="store_true", help="leave out the batching-form measurement")
+    ap.add_argument("--batch-steps", type=int, default=2)
     ap.add_argument("--save-state", default=None, help="write the post-pre-roll state (.npz) for --load-state")
     ap.add_argument("--load-state", default=None, help="start from a state written by --save-state")
     args = ap.parse_args()

@@ -54,8 +54,18 @@ struct boxes {  // n boxes, 3 per corner, FP64 exact + FP32 outward-rounded copi
 struct boxw {
   double *lo, *hi;
   float *lof, *hif;
+  // batches: every scene's boxes are moved to its own cell of a lattice with
+  // this spacing, so the grid does not stack the (overlapping) scenes; pairs
+  // across scenes are excluded anyway, so this only saves work
+  const int* vscene;
+  double spacing;
   operator boxes() const { return boxes{lo, hi, lof, hif}; }
 };
+__device__ __forceinline__ void scene_offset(int sc, double spacing, double* off) {
+  off[0] = (double)(sc & 7) * spacing;
+  off[1] = (double)((sc >> 3) & 7) * spacing;
+  off[2] = (double)(sc >> 6) * spacing;
+}
 
 // boxes of k-vertex primitives at positions P0 (and P1 when swept), grown by infl
 __global__ void k_boxes(int n, int k, const int* __restrict__ idx, const double* __restrict__ P0,
@@ -80,8 +90,10 @@ __global__ void k_boxes(int n, int k, const int* __restrict__ idx, const double*
     }
     for (int c = 0; c < 3; ++c) { l[c] = fmin(l[c], l1[c]); h[c] = fmax(h[c], h1[c]); }
   }
+  double off[3] = {0.0, 0.0, 0.0};
+  if (out.vscene) scene_offset(out.vscene[v0], out.spacing, off);
   for (int c = 0; c < 3; ++c) {
-    const double lc = l[c] - infl, hc = h[c] + infl;
+    const double lc = l[c] - infl + off[c], hc = h[c] + infl + off[c];
     lo[3 * e + c] = lc;
     hi[3 * e + c] = hc;
     out.lof[3 * e + c] = __double2float_rd(lc);
@@ -905,6 +917,8 @@ yasps_status alloc_boxes(yasps_system* s, boxbufs* bb) {
     w.hi = d + 3 * nmax;
     w.lof = reinterpret_cast<float*>(d + 6 * nmax);
     w.hif = w.lof + 3 * nmax;
+    w.vscene = s->nscene > 1 ? as<int>(s->vscene) : nullptr;
+    w.spacing = s->scene_spacing;
   }
   return YASPS_OK;
 }

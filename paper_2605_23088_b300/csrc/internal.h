@@ -47,6 +47,7 @@ struct yasps_system {
   int nscene = 1;  // independent scenes in this system (batching)
   gbuf vscene;     // int [nv] scene of each vertex (batches only)
   gbuf node_scene; // int [nn] scene of each node (batches only)
+  double scene_spacing = 0.0;  // lattice spacing of the scenes' broadphase boxes (batches)
   // per-scene results of the last yasps_step (batches)
   std::vector<int> scene_newton, scene_status, scene_pcg;
   gbuf scene_buf;  // per-scene device scratch (sums, tolerances, step bounds)

@@ -569,6 +569,39 @@ __device__ __forceinline__ void seg_add_shared(double* shs, int key, V v, int la
   const int kp = __shfl_up_sync(0xffffffffu, key, 1);
   if (key >= 0 && (lane == 0 || kp != key)) atomicAdd(&shs[key], (double)v);
 }
+// Per-warp running sum for the scene the warp is on (held by lane 0): a warp
+// whose 32 items belong to one scene adds into it without touching shared
+// memory; the sum goes to shs when the warp moves to another scene or at
+// wacc_flush.  Mixed warps fall back to seg_add_shared.  All lanes call.
+struct wacc {
+  int key = -1;
+  double v = 0.0;
+};
+template <typename V>
+__device__ __forceinline__ void wacc_add(wacc& w, double* shs, int key, V val, int lane) {
+  const int k0 = __shfl_sync(0xffffffffu, key, 0);
+  if (__all_sync(0xffffffffu, key == k0)) {
+    if (k0 < 0) return;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) val += shfl_down_v(val, o);
+    if (lane == 0) {
+      if (k0 != w.key) {
+        if (w.key >= 0) atomicAdd(&shs[w.key], w.v);
+        w.key = k0;
+        w.v = 0.0;
+      }
+      w.v += (double)val;
+    }
+  } else {
+    seg_add_shared(shs, key, val, lane);
+  }
+}
+__device__ __forceinline__ void wacc_flush(wacc& w, double* shs, int lane) {
+  if (lane == 0 && w.key >= 0) atomicAdd(&shs[w.key], w.v);
+  w.key = -1;
+  w.v = 0.0;
+}
+
 // the block's per-scene partials into row `row` of the ring; shs is cleared
 __device__ __forceinline__ void flush_scene_sums(double* shs, double* ring, int row, int nscene) {
   __syncthreads();
@@ -599,6 +632,7 @@ __global__ void __launch_bounds__(pcg_threads<T>::N, 1) k_pcg_persistent(pcg_arg
   extern __shared__ __align__(128) unsigned char smem[];
   uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + 2 * L::BUF);
   double* shs = reinterpret_cast<double*>(smem + 2 * L::BUF + 16);  // batches: per-scene partials
+  V* tab = reinterpret_cast<V*>(shs + kMaxScenes);                   // batches: per-scene beta, then alpha
   const int G = gridDim.x;
   const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const long long nthr = (long long)G * blockDim.x;
@@ -730,18 +764,21 @@ __global__ void __launch_bounds__(pcg_threads<T>::N, 1) k_pcg_persistent(pcg_arg
         inflight |= 1u << j;
       }
     acc = 0;
+    wacc wa;
     if constexpr (!BATCH) {
       for (long long i = n0 + threadIdx.x; i < n1; i += blockDim.x) acc += diag_node(a, i, vb, d, dn);
     } else {
+      for (int t = threadIdx.x; t < a.nscene; t += blockDim.x) tab[t] = beta_of(t);
+      __syncthreads();
       for (long long base = n0 + (threadIdx.x & ~31); base < n1; base += blockDim.x) {
         const long long i = base + lane;
         int key = -1;
         V v = 0;
         if (i < n1) {
           key = a.node_scene[i];
-          v = diag_node(a, i, beta_of(key), d, dn);
+          v = diag_node(a, i, tab[key], d, dn);
         }
-        seg_add_shared(shs, key, v, lane);
+        wacc_add(wa, shs, key, v, lane);
       }
     }
     if (clock0) { const unsigned long long t = global_ns(); tph[0] += t - tlast; tlast = t; }
@@ -772,12 +809,12 @@ __global__ void __launch_bounds__(pcg_threads<T>::N, 1) k_pcg_persistent(pcg_arg
       } else {
         // a block couples two nodes of one scene: the row's scene gives beta
         const int s0 = r0 >= 0 ? a.node_scene[r0] : -1, s1 = r1 >= 0 ? a.node_scene[r1] : -1;
-        gather_d(r0, c0, a.z, d, beta_of(s0), g0);
-        gather_d(r1, c1, a.z, d, beta_of(s1), g1);
+        gather_d(r0, c0, a.z, d, s0 >= 0 ? tab[s0] : V(0), g0);
+        gather_d(r1, c1, a.z, d, s1 >= 0 ? tab[s1] : V(0), g1);
         const V p0 = apply_blk<T, V>(r0, c0, vals + 9 * k0, g0, a.q, lane);
         const V p1 = apply_blk<T, V>(r1, c1, vals + 9 * k1, g1, a.q, lane);
-        seg_add_shared(shs, s0, p0, lane);
-        seg_add_shared(shs, s1, p1, lane);
+        wacc_add(wa, shs, s0, p0, lane);
+        wacc_add(wa, shs, s1, p1, lane);
       }
       __syncthreads();  // every thread is done with buffer b
       if (threadIdx.x == 0 && j + 2 < sh.tt) {
@@ -790,7 +827,10 @@ __global__ void __launch_bounds__(pcg_threads<T>::N, 1) k_pcg_persistent(pcg_arg
       done = 3;
       break;
     }
-    if constexpr (BATCH) flush_scene_sums(shs, a.ring, (int)(kbar & 7), a.nscene);
+    if constexpr (BATCH) {
+      wacc_flush(wa, shs, lane);
+      flush_scene_sums(shs, a.ring, (int)(kbar & 7), a.nscene);
+    }
     bs = block_sum_v<V>(acc);
     if (clock0) { const unsigned long long t = global_ns(); tph[1] += t - tlast; tlast = t; }
     double dHd = 0.0;
@@ -821,22 +861,26 @@ __global__ void __launch_bounds__(pcg_threads<T>::N, 1) k_pcg_persistent(pcg_arg
         if (i + nthr < a.nfree) acc += update_free(a, i + nthr, alpha, dn);
       }
     } else {
+      __syncthreads();  // everyone is done with the beta table
+      for (int t = threadIdx.x; t < a.nscene; t += blockDim.x) tab[t] = alpha_of(t);
+      __syncthreads();
       for (long long base = tid & ~31LL; base < a.nfree; base += nthr) {
         const long long i = base + lane;
         int key = -1;
         V v = 0;
         if (i < a.nfree) {
           key = a.node_scene[i];
-          v = update_free(a, i, alpha_of(key), dn);
+          v = update_free(a, i, tab[key], dn);
         }
-        seg_add_shared(shs, key, v, lane);
+        wacc_add(wa, shs, key, v, lane);
       }
+      wacc_flush(wa, shs, lane);
     }
     for (long long bi = tid; bi < a.nb; bi += nthr) {
       const int i = a.nfree + (int)bi;
       const size_t o = 3 * ((size_t)a.nfree + 4 * (size_t)bi);
       V al = alpha;
-      if constexpr (BATCH) al = alpha_of(a.node_scene[a.nfree + 4 * bi]);
+      if constexpr (BATCH) al = tab[a.node_scene[a.nfree + 4 * bi]];
       for (int c = 0; c < 12; ++c) {
         a.x[o + c] += al * dn[o + c];
         a.r[o + c] -= al * a.q[o + c];
@@ -945,7 +989,7 @@ yasps_status spmv_t(yasps_system* s, const V* x, V* y, const int* done) {
 // cooperative launch refuses a larger grid instead of deadlocking)
 template <typename T, typename V, bool BATCH>
 constexpr unsigned pcg_smem() {
-  return stage_layout<T>::SMEM + (BATCH ? 8u * kMaxScenes : 0u);
+  return stage_layout<T>::SMEM + (BATCH ? 16u * kMaxScenes : 0u);
 }
 template <typename T, typename V, bool BATCH>
 yasps_status pcg_grid(yasps_system* s, int* G) {

@@ -232,6 +232,19 @@ static yasps_status build_impl(yasps_system* s, const yasps_scene_desc* d) {
       else
         for (int k = 0; k < 4; ++k) nscene[vnode[v] + k] = d->vert_scene[v];
     }
+    // broadphase lattice: 1.5 x the largest scene extent plus 0.1 m between scene origins
+    std::vector<double> lo(3 * (size_t)ns, 1e300), hi(3 * (size_t)ns, -1e300);
+    for (int v = 0; v < nv; ++v)
+      for (int c = 0; c < 3; ++c) {
+        const int k = d->vert_scene[v];
+        lo[3 * k + c] = std::min(lo[3 * k + c], d->rest_pos[3 * v + c]);
+        hi[3 * k + c] = std::max(hi[3 * k + c], d->rest_pos[3 * v + c]);
+      }
+    double ext = 0.0;
+    for (int k = 0; k < ns; ++k)
+      for (int c = 0; c < 3; ++c)
+        if (hi[3 * k + c] >= lo[3 * k + c]) ext = std::max(ext, hi[3 * k + c] - lo[3 * k + c]);
+    s->scene_spacing = 1.5 * ext + 0.1;
     RC(upload(s, s->vscene, d->vert_scene, (size_t)nv));
     RC(upload(s, s->node_scene, nscene.data(), (size_t)s->nn));
     ENSURE(s, s->scene_buf, sizeof(double) * 8 * (size_t)ns);
@@ -891,10 +904,14 @@ static yasps_status step_batched(yasps_system* s, double* x, double* v, yasps_st
   yasps_status rc = YASPS_OK;
   int it = 0;
   for (it = 0; it < s->prm.newton_max_iter; ++it) {
+    cudaEvent_t pd = prof_begin(s);
     RC(launch_positions(s, x, as<double>(s->P)));
     if (it > 0 && s->cand_valid) RC(detect_from_candidates(s, as<double>(s->P)));
     else RC(detect_pairs(s, as<double>(s->P)));
+    prof_end(s, YASPS_STAGE_DETECT, pd, 0.0);
+    cudaEvent_t pe = prof_begin(s);
     RC(eval_impl(s, x, xtil, YASPS_TERM_ALL, 1));
+    prof_end(s, YASPS_STAGE_EVAL, pe, 0.0);
     if (it > 0) {
       std::vector<int> dm(done.begin(), done.end());
       int* done_dev = reinterpret_cast<int*>(sb + 6 * (size_t)ns);
@@ -941,10 +958,13 @@ static yasps_status step_batched(yasps_system* s, double* x, double* v, yasps_st
     st.n_pt = s->npt; st.n_ee = s->nee; st.n_pg = s->npg;
     if (!any) break;
     // per-scene CCD bound, then per-scene backtracking from it
+    cudaEvent_t pc = prof_begin(s);
     RC(swept_candidates(s, x, p));
     RC(ccd_candidates(s, alpha.data()));
+    prof_end(s, YASPS_STAGE_CCD, pc, 0.0);
     for (int k = 0; k < ns; ++k)
       if (done[k]) alpha[k] = 0.0;
+    cudaEvent_t pl = prof_begin(s);
     RC(energy_scenes(s, x, xtil, E0));
     std::vector<char> acc(ns, 0);
     for (int k = 0; k < ns; ++k) acc[k] = done[k];
@@ -979,6 +999,9 @@ static yasps_status step_batched(yasps_system* s, double* x, double* v, yasps_st
                                                                  xtrial);
       LAUNCH_CHECK(s, "k_axpy_scene");
     }
+    prof_end(s, YASPS_STAGE_LS, pl, 0.0);
+    st.n_cand_pt = s->ncpt;
+    st.n_cand_ee = s->ncee;
     CK(s, cudaMemcpyAsync(x, xtrial, sizeof(double) * n3, cudaMemcpyDeviceToDevice, s->stream));
     st.alpha_last = *std::max_element(alpha.begin(), alpha.end());
   }
