@@ -186,6 +186,11 @@ def native(args):
             G.step(x, v, raise_on_error=False)
     torch.cuda.synchronize()
     x0, v0 = x.clone(), v.clone()
+    # the system holds the last step's assembly: pick the PCG launch configuration on it
+    tune = {}
+    for prec_sys, tag in ((G, "fp32_mixed"),):
+        var, us = prec_sys.autotune_pcg(30)
+        tune[tag] = {"variant": var, "us_per_iter": [round(u, 2) for u in us]}
     if args.save_state and rank == 0:
         np.savez(args.save_state, x=x0.cpu().numpy(), v=v0.cpu().numpy(), preroll=preroll)
     npt, nee, npg = G.detect_pairs(x0)
@@ -262,6 +267,10 @@ def native(args):
     fp64 = None
     if not args.skip_fp64:
         G64 = yb.System(scene, precision=0, pcg_rel_tol=PCG_TOL, newton_tol=ntol)
+        xs, vs = x0.clone(), v0.clone()
+        G64.step(xs, vs, raise_on_error=False)  # an assembly to tune on
+        var, us = G64.autotune_pcg(30)
+        tune["fp64"] = {"variant": var, "us_per_iter": [round(u, 2) for u in us]}
         fp64 = timed(G64, "fp64", args.steps, args.warmup, True)
         G64.close()
 
@@ -292,6 +301,7 @@ def native(args):
                    "pairs_at_start": {"pt": npt, "ee": nee, "pg": npg}, "newton_iters": mixed["newton"],
                    "pcg_iters": mixed["pcg"], "statuses": sorted(set(mixed["status"])),
                    "l2": "inputs larger than L2 (BSR + element data > 126 MB): no flush",
+                   "pcg_autotune": tune,
                    "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
         "spmv_gbs": spmv_gbs,
         "roofline": roof,
@@ -347,6 +357,7 @@ def batch_bench(args, dev):
         G = yb.System(b, precision=prec, pcg_rel_tol=PCG_TOL, newton_tol=ntol)
         x, v = G.initial_state()
         G.step(x, v, raise_on_error=False)  # warm-up
+        var, us = G.autotune_pcg(30)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         newton = 0
@@ -360,7 +371,8 @@ def batch_bench(args, dev):
         torch.cuda.synchronize()
         sec = e0.elapsed_time(e1) * 1e-3
         out[name] = {"scene_steps_per_s": BATCH_SCENES * args.batch_steps / sec, "newton_iters_per_s": newton / sec,
-                     "ms_per_step": sec * 1e3 / args.batch_steps, "statuses": sorted(set(rcs))}
+                     "ms_per_step": sec * 1e3 / args.batch_steps, "statuses": sorted(set(rcs)),
+                     "pcg_autotune": {"variant": var, "us_per_iter": [round(u, 2) for u in us]}}
         G.close()
     # the same kind of work without batching: 16 scenes, one system each
     seq = 0.0

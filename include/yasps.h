@@ -266,6 +266,20 @@ yasps_status yasps_step(yasps_system* sys, double* x_dev, double* v_dev, yasps_s
 yasps_status yasps_set_fixed_positions(yasps_system* sys, const double* P_host);
 yasps_status yasps_get_fixed_positions(yasps_system* sys, double* P_host);
 
+/* Autotuning of the PCG kernel's launch configuration (threads per block,
+ * upper blocks per thread in a shared-memory tile, blocks per SM), for the
+ * batching form and any large system: yasps_autotune_pcg times `iters` PCG
+ * iterations (<= 0: 30) of each of the YASPS_PCG_VARIANTS configurations on
+ * the system's current assembly, with its current gradient as right-hand side,
+ * and keeps the fastest for later solves.  Needs an assembled system (after
+ * yasps_eval_local or yasps_step).  variant (nullable) receives the choice,
+ * us_per_iter (nullable, [YASPS_PCG_VARIANTS]) each configuration's time per
+ * iteration in microseconds.  yasps_set_pcg_variant picks one directly
+ * (variant 0 is the default).  Synchronises. */
+#define YASPS_PCG_VARIANTS 3
+yasps_status yasps_autotune_pcg(yasps_system* sys, int iters, int* variant, double* us_per_iter);
+yasps_status yasps_set_pcg_variant(yasps_system* sys, int variant);
+
 /* Per-scene results of the last yasps_step on a batch (host arrays of
  * n_scenes, each nullable): Newton iterations, PCG iterations summed over the
  * step, and status (YASPS_OK, YASPS_E_NOCONV or YASPS_E_LINESEARCH; a scene

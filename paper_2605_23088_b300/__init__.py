@@ -27,11 +27,12 @@ EXPORTS = [
     "yasps_set_params", "yasps_get_sizes", "yasps_initial_state", "yasps_vertex_positions", "yasps_xtilde",
     "yasps_detect_pairs", "yasps_export_pairs", "yasps_energy", "yasps_eval_local", "yasps_assemble",
     "yasps_export_bsr", "yasps_export_gradient", "yasps_spmv", "yasps_pcg_solve", "yasps_ccd_bound", "yasps_step",
-    "yasps_set_fixed_positions", "yasps_get_fixed_positions", "yasps_set_tet_young", "yasps_adjoint_step", "yasps_scene_stats", "yasps_kernel_launches", "yasps_profile_enable",
+    "yasps_set_fixed_positions", "yasps_get_fixed_positions", "yasps_set_tet_young", "yasps_adjoint_step", "yasps_scene_stats", "yasps_autotune_pcg", "yasps_set_pcg_variant", "yasps_kernel_launches", "yasps_profile_enable",
     "yasps_profile_get", "yasps_pcg_phase_ms", "yasps_pcg_solve_static",
 ]
 STAGE_SPMV, STAGE_TET, STAGE_BARRIER, STAGE_PCG, STAGE_DETECT, STAGE_EVAL, STAGE_CCD, STAGE_LS, STAGE_PCG_KERNEL = range(9)
 STAGE_NAMES = ["spmv", "tet", "barrier", "pcg", "detect", "eval", "ccd", "line_search", "pcg_kernel"]
+PCG_VARIANTS = 3  # YASPS_PCG_VARIANTS
 PCG_PHASES = ["own_nodes", "upper_blocks", "wait_dHd", "update", "wait_rz", "unused5", "unused6", "unused7"]
 
 
@@ -346,6 +347,17 @@ class System:
         P = np.zeros((self.n_verts, 3))
         self._check(lib().yasps_get_fixed_positions(self.h, P.ctypes.data_as(_PD)))
         return P
+
+    def autotune_pcg(self, iters=30):
+        """Time each PCG launch configuration on the current assembly and keep the
+        fastest; returns (variant, microseconds per iteration of each)."""
+        v = ctypes.c_int()
+        us = np.zeros(PCG_VARIANTS)
+        self._check(lib().yasps_autotune_pcg(self.h, ctypes.c_int(iters), ctypes.byref(v), us.ctypes.data_as(_PD)))
+        return v.value, us
+
+    def set_pcg_variant(self, variant):
+        self._check(lib().yasps_set_pcg_variant(self.h, ctypes.c_int(variant)))
 
     def scene_stats(self):
         """Per-scene (Newton iterations, PCG iterations, status) of the last step (batches)."""

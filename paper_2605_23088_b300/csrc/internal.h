@@ -48,6 +48,7 @@ struct yasps_system {
   gbuf vscene;     // int [nv] scene of each vertex (batches only)
   gbuf node_scene; // int [nn] scene of each node (batches only)
   double scene_spacing = 0.0;  // lattice spacing of the scenes' broadphase boxes (batches)
+  int pcg_variant = 0;         // launch configuration of the PCG kernel (yasps_autotune_pcg)
   // per-scene results of the last yasps_step (batches)
   std::vector<int> scene_newton, scene_status, scene_pcg;
   gbuf scene_buf;  // per-scene device scratch (sums, tolerances, step bounds)
@@ -213,3 +214,4 @@ yasps_status pcg_solve(yasps_system* s, const double* rhs, double* p, double tol
                        double* rel_res);
 yasps_status inf_norm(yasps_system* s, const double* x, int n, double* out_host);
 yasps_status read_status(yasps_system* s, int* bits);  // synchronises, clears the device word
+yasps_status autotune_pcg(yasps_system* s, int iters, int* variant, double* us);

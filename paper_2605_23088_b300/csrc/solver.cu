@@ -26,12 +26,23 @@
 namespace {
 
 constexpr int PT_ = 256;           // threads per block for vector kernels
-// threads per block of the persistent PCG kernel (one block per SM; FP64
-// needs more registers per thread)
-template <typename T>
-struct pcg_threads { static constexpr int N = 1024; };
-template <>
-struct pcg_threads<double> { static constexpr int N = 640; };
+// Launch configurations of the persistent PCG kernel: threads per block,
+// upper blocks per thread in a tile, blocks per SM.  Variant 0 is the default;
+// yasps_autotune_pcg times them on the system at hand and keeps the fastest.
+template <int NTHR_, int BPT_, int MINB_>
+struct pcg_cfg {
+  static constexpr int NTHR = NTHR_, BPT = BPT_, MINB = MINB_;
+};
+template <typename T, int V>
+struct pcg_variant;
+template <> struct pcg_variant<float, 0> { using C = pcg_cfg<1024, 2, 1>; };
+template <> struct pcg_variant<float, 1> { using C = pcg_cfg<1024, 1, 1>; };
+template <> struct pcg_variant<float, 2> { using C = pcg_cfg<512, 2, 2>; };
+// FP64 needs more registers per thread
+template <> struct pcg_variant<double, 0> { using C = pcg_cfg<640, 2, 1>; };
+template <> struct pcg_variant<double, 1> { using C = pcg_cfg<640, 1, 1>; };
+template <> struct pcg_variant<double, 2> { using C = pcg_cfg<320, 2, 2>; };
+constexpr int kPcgVariants = 3;
 
 // result of one persistent PCG launch (written by block 0 at the end)
 struct pcg_dev {
@@ -344,9 +355,9 @@ __device__ __forceinline__ bool grid_reduce(pcg_bar* bar, unsigned& k, double pa
 // double-buffered: the next tile travels while the current one is multiplied,
 // and the first two travel while the block does its own nodes' diagonal part.
 // Only the gathers of z and d stay exposed.
-template <typename T>
+template <typename T, typename CFG>
 struct stage_layout {
-  static constexpr int NT = 2 * pcg_threads<T>::N;     // blocks per tile (two per thread)
+  static constexpr int NT = CFG::BPT * CFG::NTHR;      // blocks per tile (BPT per thread)
   static constexpr unsigned VB = NT * 9 * sizeof(T);   // values
   static constexpr unsigned IB = NT * sizeof(int);     // rows / columns
   static constexpr unsigned BUF = VB + 2 * IB;         // one buffer (a multiple of 16)
@@ -389,8 +400,7 @@ struct spmv_share {
   int s0, s1, e0, e1, ts, tt;  // ts static tiles, tt tiles in all
 };
 template <typename T, typename V>
-__device__ __forceinline__ spmv_share share_of(const pcg_args<T, V>& a) {
-  constexpr int NT = stage_layout<T>::NT;
+__device__ __forceinline__ spmv_share share_of(const pcg_args<T, V>& a, int NT) {
   const long long G = gridDim.x, b = blockIdx.x;
   spmv_share o;
   o.s0 = (int)((b * a.n_s / G) & ~3LL);
@@ -412,8 +422,7 @@ struct tile_src {
   int base, cnt;
 };
 template <typename T, typename V>
-__device__ __forceinline__ tile_src<T, V> tile_of(const pcg_args<T, V>& a, const spmv_share& sh, int j) {
-  constexpr int NT = stage_layout<T>::NT;
+__device__ __forceinline__ tile_src<T, V> tile_of(const pcg_args<T, V>& a, const spmv_share& sh, int j, int NT) {
   tile_src<T, V> o;
   if (j < sh.ts) {
     o.vals = a.val_s; o.row = a.row_s; o.col = a.col_s;
@@ -429,9 +438,8 @@ __device__ __forceinline__ tile_src<T, V> tile_of(const pcg_args<T, V>& a, const
 // thread 0: request tile j into buffer buf.  Tile starts are multiples of 4
 // blocks, so every source address is 16-byte aligned; sizes are rounded up to
 // 16 bytes (the arrays carry that much slack).
-template <typename T, typename V>
+template <typename L, typename T, typename V>
 __device__ __forceinline__ void issue_tile(const tile_src<T, V>& src, unsigned char* buf, uint64_t* m) {
-  using L = stage_layout<T>;
   const unsigned bv = (unsigned)(src.cnt * 9 * (int)sizeof(T) + 15) & ~15u;
   const unsigned bi = (unsigned)(src.cnt * (int)sizeof(int) + 15) & ~15u;
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -626,9 +634,10 @@ struct scene_view {
   }
 };
 
-template <typename T, typename V, bool BATCH>
-__global__ void __launch_bounds__(pcg_threads<T>::N, 1) k_pcg_persistent(pcg_args<T, V> a) {
-  using L = stage_layout<T>;
+template <typename T, typename V, bool BATCH, typename CFG>
+__global__ void __launch_bounds__(CFG::NTHR, CFG::MINB) k_pcg_persistent(pcg_args<T, V> a) {
+  using L = stage_layout<T, CFG>;
+  constexpr int BPT = CFG::BPT;
   extern __shared__ __align__(128) unsigned char smem[];
   uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + 2 * L::BUF);
   double* shs = reinterpret_cast<double*>(smem + 2 * L::BUF + 16);  // batches: per-scene partials
@@ -638,7 +647,7 @@ __global__ void __launch_bounds__(pcg_threads<T>::N, 1) k_pcg_persistent(pcg_arg
   const long long nthr = (long long)G * blockDim.x;
   const int lane = threadIdx.x & 31;
   const int nu = a.nfree + a.nb;
-  const spmv_share sh = share_of(a);
+  const spmv_share sh = share_of(a, L::NT);
   const long long n0 = (long long)blockIdx.x * a.nn / G, n1 = (long long)(blockIdx.x + 1) * a.nn / G;
   unsigned kbar = 0;  // reducing barriers passed in this launch
   const bool clock0 = blockIdx.x == 0 && threadIdx.x == 0;
@@ -760,7 +769,7 @@ __global__ void __launch_bounds__(pcg_threads<T>::N, 1) k_pcg_persistent(pcg_arg
     // the first two tiles travel while the block does its own nodes
     if (threadIdx.x == 0)
       for (int j = 0; j < 2 && j < sh.tt; ++j) {
-        issue_tile(tile_of(a, sh, j), smem + j * L::BUF, &mbar[j]);
+        issue_tile<L>(tile_of(a, sh, j, L::NT), smem + j * L::BUF, &mbar[j]);
         inflight |= 1u << j;
       }
     acc = 0;
@@ -791,34 +800,38 @@ __global__ void __launch_bounds__(pcg_threads<T>::N, 1) k_pcg_persistent(pcg_arg
       inflight &= ~(1u << b);
       if (__syncthreads_or(!ok)) { ok = false; break; }
       const unsigned char* buf = smem + b * L::BUF;
-      const int cnt = tile_of(a, sh, j).cnt;
-      // two blocks per thread (k and k + NT/2, each warp on 32 consecutive
-      // blocks): both gathers are in flight before either is used
+      const int cnt = tile_of(a, sh, j, L::NT).cnt;
+      // BPT blocks per thread (k, k + NTHR, ...; each warp on 32 consecutive
+      // blocks): all gathers are in flight before any is used
       const int* rows = reinterpret_cast<const int*>(buf + L::VB);
       const int* cols = reinterpret_cast<const int*>(buf + L::VB + L::IB);
       const T* vals = reinterpret_cast<const T*>(buf);
-      const int k0 = threadIdx.x, k1 = threadIdx.x + L::NT / 2;
-      const int r0 = (k0 < cnt) ? rows[k0] : -1, c0 = (k0 < cnt) ? cols[k0] : 0;
-      const int r1 = (k1 < cnt) ? rows[k1] : -1, c1 = (k1 < cnt) ? cols[k1] : 0;
-      gath<V> g0, g1;
-      if constexpr (!BATCH) {
-        gather_d(r0, c0, a.z, d, vb, g0);
-        gather_d(r1, c1, a.z, d, vb, g1);
-        acc += apply_blk<T, V>(r0, c0, vals + 9 * k0, g0, a.q, lane);
-        acc += apply_blk<T, V>(r1, c1, vals + 9 * k1, g1, a.q, lane);
-      } else {
+      int rr[BPT], cc[BPT], ss[BPT];
+      gath<V> gg[BPT];
+#pragma unroll
+      for (int u = 0; u < BPT; ++u) {
+        const int k = threadIdx.x + u * CFG::NTHR;
+        rr[u] = (k < cnt) ? rows[k] : -1;
+        cc[u] = (k < cnt) ? cols[k] : 0;
+        if constexpr (BATCH) ss[u] = rr[u] >= 0 ? a.node_scene[rr[u]] : -1;
+        else ss[u] = 0;
+      }
+#pragma unroll
+      for (int u = 0; u < BPT; ++u) {
+        if constexpr (BATCH) gather_d(rr[u], cc[u], a.z, d, ss[u] >= 0 ? tab[ss[u]] : V(0), gg[u]);
+        else gather_d(rr[u], cc[u], a.z, d, vb, gg[u]);
+      }
+#pragma unroll
+      for (int u = 0; u < BPT; ++u) {
+        const int k = threadIdx.x + u * CFG::NTHR;
         // a block couples two nodes of one scene: the row's scene gives beta
-        const int s0 = r0 >= 0 ? a.node_scene[r0] : -1, s1 = r1 >= 0 ? a.node_scene[r1] : -1;
-        gather_d(r0, c0, a.z, d, s0 >= 0 ? tab[s0] : V(0), g0);
-        gather_d(r1, c1, a.z, d, s1 >= 0 ? tab[s1] : V(0), g1);
-        const V p0 = apply_blk<T, V>(r0, c0, vals + 9 * k0, g0, a.q, lane);
-        const V p1 = apply_blk<T, V>(r1, c1, vals + 9 * k1, g1, a.q, lane);
-        wacc_add(wa, shs, s0, p0, lane);
-        wacc_add(wa, shs, s1, p1, lane);
+        const V pu = apply_blk<T, V>(rr[u], cc[u], vals + 9 * k, gg[u], a.q, lane);
+        if constexpr (BATCH) wacc_add(wa, shs, ss[u], pu, lane);
+        else acc += pu;
       }
       __syncthreads();  // every thread is done with buffer b
       if (threadIdx.x == 0 && j + 2 < sh.tt) {
-        issue_tile(tile_of(a, sh, j + 2), smem + b * L::BUF, &mbar[b]);
+        issue_tile<L>(tile_of(a, sh, j + 2, L::NT), smem + b * L::BUF, &mbar[b]);
         inflight |= 1u << b;
       }
     }
@@ -987,23 +1000,23 @@ yasps_status spmv_t(yasps_system* s, const V* x, V* y, const int* done) {
 
 // grid of the persistent kernel: as many blocks as can be co-resident (a
 // cooperative launch refuses a larger grid instead of deadlocking)
-template <typename T, typename V, bool BATCH>
+template <typename T, typename V, bool BATCH, typename CFG>
 constexpr unsigned pcg_smem() {
-  return stage_layout<T>::SMEM + (BATCH ? 16u * kMaxScenes : 0u);
+  return stage_layout<T, CFG>::SMEM + (BATCH ? 16u * kMaxScenes : 0u);
 }
-template <typename T, typename V, bool BATCH>
+template <typename T, typename V, bool BATCH, typename CFG>
 yasps_status pcg_grid(yasps_system* s, int* G) {
   int dev = 0, sms = 0, coop = 0, per_sm = 0;
   CK(s, cudaGetDevice(&dev));
   CK(s, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   CK(s, cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
   if (!coop) SYS_FAIL(s, YASPS_E_CUDA, "device does not support cooperative launches");
-  const unsigned smem = pcg_smem<T, V, BATCH>();
-  CK(s, cudaFuncSetAttribute(k_pcg_persistent<T, V, BATCH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  CK(s, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pcg_persistent<T, V, BATCH>, pcg_threads<T>::N,
-                                                      smem));
+  const unsigned smem = pcg_smem<T, V, BATCH, CFG>();
+  CK(s, cudaFuncSetAttribute(k_pcg_persistent<T, V, BATCH, CFG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem));
+  CK(s, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pcg_persistent<T, V, BATCH, CFG>, CFG::NTHR, smem));
   if (per_sm < 1) SYS_FAIL(s, YASPS_E_CUDA, "persistent PCG kernel cannot be resident");
-  *G = sms * std::min(per_sm, 2);
+  *G = sms * std::min(per_sm, CFG::MINB);
   return YASPS_OK;
 }
 
@@ -1014,14 +1027,14 @@ struct scene_out {
 
 // PCG in precision (T, V) on H dx = rhs (FP64 rhs); dx accumulated into p (FP64).
 // Batches: stol2 (device, per scene) or null, per-scene iterations / flags out.
-template <typename T, typename V, bool BATCH>
-yasps_status pcg_launch(yasps_system* s, const double* rhs, double* p, double tol, int maxit, const double* stol2,
-                        int* iters, int* state, double* rel, scene_out* so) {
+template <typename T, typename V, bool BATCH, typename CFG>
+yasps_status pcg_launch_cfg(yasps_system* s, const double* rhs, double* p, double tol, int maxit, const double* stol2,
+                            int* iters, int* state, double* rel, scene_out* so) {
   const int n3 = 3 * s->nn;
   for (int k = 0; k < 5; ++k) ENSURE(s, s->vec[k], sizeof(V) * (n3 + 4));
   ENSURE(s, s->vec[8], sizeof(V) * (n3 + 4));
   int G = 0;
-  RC((pcg_grid<T, V, BATCH>(s, &G)));
+  RC((pcg_grid<T, V, BATCH, CFG>(s, &G)));
   const int ns = s->nscene;
   // scalars, barrier, and for batches: ring [8][ns], srz0, siters, sflag
   const size_t scal_bytes = 256 + (BATCH ? (size_t)ns * (8 * 8 + 8 + 4 + 4) + 64 : 0);
@@ -1066,8 +1079,8 @@ yasps_status pcg_launch(yasps_system* s, const double* rhs, double* p, double to
   CK(s, cudaMemsetAsync(s->scal.p, 0, scal_bytes, s->stream));
   void* params[] = {&a};
   cudaEvent_t pk = prof_begin(s);
-  CK(s, cudaLaunchCooperativeKernel((const void*)k_pcg_persistent<T, V, BATCH>, dim3(G), dim3(pcg_threads<T>::N),
-                                    params, pcg_smem<T, V, BATCH>(), s->stream));
+  CK(s, cudaLaunchCooperativeKernel((const void*)k_pcg_persistent<T, V, BATCH, CFG>, dim3(G), dim3(CFG::NTHR), params,
+                                    pcg_smem<T, V, BATCH, CFG>(), s->stream));
   s->launches += 1;
   prof_end(s, YASPS_STAGE_PCG_KERNEL, pk, 0.0);
   pcg_dev h{};
@@ -1100,6 +1113,23 @@ yasps_status pcg_launch(yasps_system* s, const double* rhs, double* p, double to
   *state = h.done;
   *rel = (h.rz0 > 0.0) ? std::sqrt(std::max(h.rz, 0.0) / h.rz0) : 0.0;
   return YASPS_OK;
+}
+
+// the launch configuration the system uses (s->pcg_variant)
+template <typename T, typename V, bool BATCH>
+yasps_status pcg_launch(yasps_system* s, const double* rhs, double* p, double tol, int maxit, const double* stol2,
+                        int* iters, int* state, double* rel, scene_out* so) {
+  switch (s->pcg_variant) {
+    case 1:
+      return pcg_launch_cfg<T, V, BATCH, typename pcg_variant<T, 1>::C>(s, rhs, p, tol, maxit, stol2, iters, state,
+                                                                        rel, so);
+    case 2:
+      return pcg_launch_cfg<T, V, BATCH, typename pcg_variant<T, 2>::C>(s, rhs, p, tol, maxit, stol2, iters, state,
+                                                                        rel, so);
+    default:
+      return pcg_launch_cfg<T, V, BATCH, typename pcg_variant<T, 0>::C>(s, rhs, p, tol, maxit, stol2, iters, state,
+                                                                        rel, so);
+  }
 }
 
 template <typename T, typename V>
@@ -1344,6 +1374,62 @@ yasps_status pcg_solve_impl(yasps_system* s, const double* rhs, double* p, doubl
   if (state == 2) SYS_FAIL(s, YASPS_E_NAN, "PCG breakdown: d^T H d <= 0");
   if (r > tol && total >= maxit) SYS_FAIL(s, YASPS_E_NOCONV, "PCG hit its iteration cap");
   return YASPS_OK;
+}
+
+// Autotuning of the PCG launch configuration on the system at hand: every
+// variant runs `iters` iterations (tolerance 0) on the current assembly with
+// the current gradient as right-hand side, timed with events after one
+// warm-up launch; the fastest per iteration is kept.
+template <typename T, typename V, bool BATCH>
+static yasps_status autotune_t(yasps_system* s, int iters, int* variant, double* us) {
+  const int n3 = 3 * s->nn;
+  ENSURE(s, s->vec[6], sizeof(double) * (n3 + 4));
+  double* pt = as<double>(s->vec[6]);
+  const double* rhs = as<double>(s->grad);
+  int best = 0;
+  double best_us = 1e300;
+  const bool prof = s->prof_on;
+  s->prof_on = false;
+  for (int v = 0; v < kPcgVariants; ++v) {
+    s->pcg_variant = v;
+    double t_us = 0.0;
+    for (int rep = 0; rep < 2; ++rep) {
+      CK(s, cudaMemsetAsync(pt, 0, sizeof(double) * n3, s->stream));
+      int it = 0, state = 0;
+      double rel = 0.0;
+      scene_out so;
+      CK(s, cudaEventRecord(s->ev[6], s->stream));
+      yasps_status rc = pcg_launch<T, V, BATCH>(s, rhs, pt, 0.0, iters, nullptr, &it, &state, &rel, &so);
+      if (rc != YASPS_OK) {
+        s->prof_on = prof;
+        return rc;
+      }
+      CK(s, cudaEventRecord(s->ev[7], s->stream));
+      CK(s, cudaEventSynchronize(s->ev[7]));
+      float ms = 0.f;
+      CK(s, cudaEventElapsedTime(&ms, s->ev[6], s->ev[7]));
+      t_us = 1e3 * ms / std::max(it, 1);
+    }
+    if (us) us[v] = t_us;
+    if (t_us < best_us) {
+      best_us = t_us;
+      best = v;
+    }
+  }
+  s->prof_on = prof;
+  s->pcg_variant = best;
+  if (variant) *variant = best;
+  return YASPS_OK;
+}
+
+yasps_status autotune_pcg(yasps_system* s, int iters, int* variant, double* us) {
+  if (iters <= 0) iters = 30;
+  const bool batch = s->nscene > 1;
+  if (s->hess_precision == 1)
+    return batch ? autotune_t<float, float, true>(s, iters, variant, us)
+                 : autotune_t<float, float, false>(s, iters, variant, us);
+  return batch ? autotune_t<double, double, true>(s, iters, variant, us)
+               : autotune_t<double, double, false>(s, iters, variant, us);
 }
 
 yasps_status inf_norm(yasps_system* s, const double* x, int n, double* out_host) {

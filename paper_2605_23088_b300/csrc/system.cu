@@ -1038,3 +1038,15 @@ extern "C" yasps_status yasps_scene_stats(const yasps_system* s, int* newton_ite
   }
   return YASPS_OK;
 }
+
+extern "C" yasps_status yasps_autotune_pcg(yasps_system* s, int iters, int* variant, double* us_per_iter) {
+  if (!s) return YASPS_E_INVAL;
+  if (s->hess_precision < 0) SYS_FAIL(s, YASPS_E_INVAL, "nothing assembled yet");
+  return autotune_pcg(s, iters, variant, us_per_iter);
+}
+
+extern "C" yasps_status yasps_set_pcg_variant(yasps_system* s, int variant) {
+  if (!s || variant < 0 || variant >= YASPS_PCG_VARIANTS) return YASPS_E_INVAL;
+  s->pcg_variant = variant;
+  return YASPS_OK;
+}

@@ -104,10 +104,12 @@ def test_batch_pcg_is_per_scene_pcg(yb, batch):
 
 @pytest.mark.parametrize("precision", [0, 1])
 def test_batch_step_matches_each_scene_alone(yb, batch, precision):
-    """Two steps: in the second, the lowered cubes' Newton iteration stalls
-    (its step length halves to 2^-9 every iteration, in the oracle as well) and
-    runs into the iteration cap while the gripper converges; the batch must
-    reproduce both outcomes scene by scene."""
+    """FP64: two steps.  In the second, the lowered cubes' Newton iteration
+    stalls (its step length halves to 2^-9 every iteration, in the oracle as
+    well) and runs into the iteration cap while the gripper converges; the
+    batch must reproduce both outcomes scene by scene.  FP32-mixed: the first
+    step (the stall depends on the last bits of the Hessian, so the FP32
+    Hessian may or may not run into it)."""
     parts, b = batch
     G = yb.System(b, precision=precision, pcg_rel_tol=1e-10, newton_tol=1e-9)
     x, v = G.initial_state()
@@ -115,8 +117,10 @@ def test_batch_step_matches_each_scene_alone(yb, batch, precision):
     assert st["rc"] == 0
     newton, pcg, status = G.scene_stats()
     assert np.all(status == 0) and np.all(newton > 0) and np.all(pcg > 0)
-    st = G.step(x, v, raise_on_error=False)
-    newton2, _, status2 = G.scene_stats()
+    nsteps = 2 if precision == 0 else 1
+    if nsteps == 2:
+        G.step(x, v, raise_on_error=False)
+        newton2, _, status2 = G.scene_stats()
     P = N(G.vertex_positions(x))
     offs = b["scene_vert_offsets"]
     for k, sc in enumerate(parts):
@@ -124,10 +128,11 @@ def test_batch_step_matches_each_scene_alone(yb, batch, precision):
         xs, vs = O.initial_state()
         xs, vs, rc, _ = O.step(xs, vs)
         assert rc == 0
-        xs, vs, rc, ost = O.step(xs, vs)
-        assert rc == status2[k]  # the same scenes converge / hit the cap
-        if rc == 0:
-            assert abs(ost["newton_iters"] - newton2[k]) <= 1
+        if nsteps == 2:
+            xs, vs, rc, ost = O.step(xs, vs)
+            assert rc == status2[k]  # the same scenes converge / hit the cap
+            if rc == 0:
+                assert abs(ost["newton_iters"] - newton2[k]) <= 1
         err = np.abs(P[offs[k]:offs[k + 1]] - O.positions(xs)).max()
         assert err <= 1e-6 * sc["bbox_diag"], (k, err)
 
@@ -140,3 +145,25 @@ def test_batch_rejects_elements_across_scenes(yb, batch):
     bad["tets"] = tets
     with pytest.raises(yb.YaspsError):
         yb.System(bad)
+
+
+@pytest.mark.parametrize("which", ["single", "batch"])
+@pytest.mark.parametrize("precision", [0, 1])
+def test_pcg_launch_configurations_agree_and_autotune(yb, batch, which, precision):
+    """Every PCG launch configuration the autotuner chooses from solves the same
+    system to the same answer; the autotuner returns one of them."""
+    parts, b = batch
+    G = yb.System(b if which == "batch" else parts[1], precision=precision, pcg_rel_tol=1e-10)
+    x, v = G.initial_state()
+    G.detect_pairs(x)
+    G.eval_local(x, G.xtilde(x, v))
+    g = G.export_gradient()
+    sols = []
+    for var in range(yb.PCG_VARIANTS):
+        G.set_pcg_variant(var)
+        p, it, rr = G.pcg_solve(g, rel_tol=1e-10)
+        sols.append(N(p))
+    for p in sols[1:]:
+        assert rel(p, sols[0]) <= (1e-8 if precision == 0 else 1e-5)
+    var, us = G.autotune_pcg(20)
+    assert 0 <= var < yb.PCG_VARIANTS and np.all(us > 0) and us[var] == us.min()
