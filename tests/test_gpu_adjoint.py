@@ -161,3 +161,23 @@ def test_full_beam_mixed_precision_gradient(yb, full_beam):
     _beam_loss(yb, Gm, s, Em, x0, v0, target).backward()
     g32 = N(Em.grad)
     assert np.linalg.norm(g32 - g64) <= 1e-4 * np.linalg.norm(g64)
+
+
+def test_checkpointing_recomputes_the_same_gradient(yb):
+    """Keeping every 3rd state and recomputing the others in the backward pass
+    gives the gradient of keeping them all."""
+    from paper_2605_23088_b300.adjoint import rollout
+    s = small_beam(steps=5)
+    G = yb.System(s, precision=0, pcg_rel_tol=1e-12, newton_tol=1e-10)
+    x0, v0 = G.initial_state()
+    E0 = T(s["tet_E"])
+    target = T(np.random.default_rng(9).normal(0, 1e-2, size=tuple(x0.shape))) + x0
+    grads = []
+    for every in (1, 3):
+        E = E0.clone().requires_grad_(True)
+        v = v0.clone().requires_grad_(True)
+        xT, vT = rollout(G, E, x0, v, 5, checkpoint_every=every, tol=1e-12)
+        (0.5 * ((xT - target) ** 2).sum() + 0.1 * (vT ** 2).sum()).backward()
+        grads.append((N(E.grad), N(v.grad)))
+    assert rel(grads[1][0], grads[0][0]) <= 1e-9
+    assert rel(grads[1][1], grads[0][1]) <= 1e-9
