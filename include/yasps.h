@@ -79,6 +79,10 @@ typedef struct {
   double ccd_gap;     /* additive CCD keeps at least ccd_gap times the starting distance */
   int ccd_max_iter;   /* cap on additive-CCD advancement steps per pair */
   int refine_sweeps;  /* FP32-mixed only: maximum FP64 residual-refinement sweeps */
+  int pcg_warm_start; /* yasps_step: start each Newton iteration's PCG from the part of the
+                         previous direction the line search did not take, (1 - alpha) p;
+                         PCG then stops when r^T z <= tol^2 g^T M^-1 g (the same accuracy
+                         relative to the right-hand side g as a cold start) */
 } yasps_params;
 
 /* Scene, host pointers, copied at build.  Index arrays are int32, 0-based.
@@ -143,7 +147,7 @@ typedef struct {
 
 /* Fill *p with defaults (FP64, dt 0.01, dhat 1e-3, kappa 1e4, g = (0,-9.81,0),
  * newton_tol 1e-6, pcg_rel_tol 1e-4, newton_max_iter 100, ls_max_iter 30,
- * barrier_form 0, ccd_gap 0.1, ccd_max_iter 100000, refine_sweeps 4). */
+ * barrier_form 0, ccd_gap 0.1, ccd_max_iter 100000, refine_sweeps 4, pcg_warm_start 1). */
 void yasps_default_params(yasps_params* p);
 
 /* Build a system: uploads the scene, computes rest-shape quantities
@@ -276,7 +280,7 @@ yasps_status yasps_get_fixed_positions(yasps_system* sys, double* P_host);
  * us_per_iter (nullable, [YASPS_PCG_VARIANTS]) each configuration's time per
  * iteration in microseconds.  yasps_set_pcg_variant picks one directly
  * (variant 0 is the default).  Synchronises. */
-#define YASPS_PCG_VARIANTS 3
+#define YASPS_PCG_VARIANTS 5
 yasps_status yasps_autotune_pcg(yasps_system* sys, int iters, int* variant, double* us_per_iter);
 yasps_status yasps_set_pcg_variant(yasps_system* sys, int variant);
 

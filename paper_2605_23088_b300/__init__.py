@@ -32,7 +32,7 @@ EXPORTS = [
 ]
 STAGE_SPMV, STAGE_TET, STAGE_BARRIER, STAGE_PCG, STAGE_DETECT, STAGE_EVAL, STAGE_CCD, STAGE_LS, STAGE_PCG_KERNEL = range(9)
 STAGE_NAMES = ["spmv", "tet", "barrier", "pcg", "detect", "eval", "ccd", "line_search", "pcg_kernel"]
-PCG_VARIANTS = 3  # YASPS_PCG_VARIANTS
+PCG_VARIANTS = 5  # YASPS_PCG_VARIANTS
 PCG_PHASES = ["own_nodes", "upper_blocks", "wait_dHd", "update", "wait_rz", "unused5", "unused6", "unused7"]
 
 
@@ -47,7 +47,7 @@ class Params(ctypes.Structure):
                 ("kappa", ctypes.c_double), ("gravity", ctypes.c_double * 3), ("newton_tol", ctypes.c_double),
                 ("pcg_rel_tol", ctypes.c_double), ("pcg_max_iter", ctypes.c_int), ("newton_max_iter", ctypes.c_int),
                 ("ls_max_iter", ctypes.c_int), ("barrier_form", ctypes.c_int), ("ccd_gap", ctypes.c_double),
-                ("ccd_max_iter", ctypes.c_int), ("refine_sweeps", ctypes.c_int)]
+                ("ccd_max_iter", ctypes.c_int), ("refine_sweeps", ctypes.c_int), ("pcg_warm_start", ctypes.c_int)]
 
 
 _PD = ctypes.POINTER(ctypes.c_double)

@@ -210,8 +210,9 @@ yasps_status alloc_hessian(yasps_system* s);
 yasps_status zero_system(yasps_system* s);
 yasps_status launch_bjacobi(yasps_system* s);
 yasps_status spmv64(yasps_system* s, const double* x, double* y);
+// x0 (nullable): initial guess; the stopping test is relative to rhs either way
 yasps_status pcg_solve(yasps_system* s, const double* rhs, double* p, double tol, int maxit, int* iters,
-                       double* rel_res);
+                       double* rel_res, const double* x0 = nullptr);
 yasps_status inf_norm(yasps_system* s, const double* x, int n, double* out_host);
 yasps_status read_status(yasps_system* s, int* bits);  // synchronises, clears the device word
 yasps_status autotune_pcg(yasps_system* s, int iters, int* variant, double* us);

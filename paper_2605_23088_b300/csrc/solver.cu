@@ -38,11 +38,15 @@ struct pcg_variant;
 template <> struct pcg_variant<float, 0> { using C = pcg_cfg<1024, 2, 1>; };
 template <> struct pcg_variant<float, 1> { using C = pcg_cfg<1024, 1, 1>; };
 template <> struct pcg_variant<float, 2> { using C = pcg_cfg<512, 2, 2>; };
+template <> struct pcg_variant<float, 3> { using C = pcg_cfg<256, 2, 4>; };
+template <> struct pcg_variant<float, 4> { using C = pcg_cfg<512, 4, 2>; };
 // FP64 needs more registers per thread
 template <> struct pcg_variant<double, 0> { using C = pcg_cfg<640, 2, 1>; };
 template <> struct pcg_variant<double, 1> { using C = pcg_cfg<640, 1, 1>; };
 template <> struct pcg_variant<double, 2> { using C = pcg_cfg<320, 2, 2>; };
-constexpr int kPcgVariants = 3;
+template <> struct pcg_variant<double, 3> { using C = pcg_cfg<320, 1, 2>; };
+template <> struct pcg_variant<double, 4> { using C = pcg_cfg<160, 2, 4>; };
+constexpr int kPcgVariants = 5;
 
 // result of one persistent PCG launch (written by block 0 at the end)
 struct pcg_dev {
@@ -1126,6 +1130,12 @@ yasps_status pcg_launch(yasps_system* s, const double* rhs, double* p, double to
     case 2:
       return pcg_launch_cfg<T, V, BATCH, typename pcg_variant<T, 2>::C>(s, rhs, p, tol, maxit, stol2, iters, state,
                                                                         rel, so);
+    case 3:
+      return pcg_launch_cfg<T, V, BATCH, typename pcg_variant<T, 3>::C>(s, rhs, p, tol, maxit, stol2, iters, state,
+                                                                        rel, so);
+    case 4:
+      return pcg_launch_cfg<T, V, BATCH, typename pcg_variant<T, 4>::C>(s, rhs, p, tol, maxit, stol2, iters, state,
+                                                                        rel, so);
     default:
       return pcg_launch_cfg<T, V, BATCH, typename pcg_variant<T, 0>::C>(s, rhs, p, tol, maxit, stol2, iters, state,
                                                                         rel, so);
@@ -1184,7 +1194,7 @@ yasps_status rz64(yasps_system* s, const double* r, double* out) {
 
 // ======================================================================== API
 yasps_status pcg_solve_impl(yasps_system* s, const double* rhs, double* p, double tol, int maxit, int* iters,
-                            double* rel_res);
+                            double* rel_res, const double* x0);
 
 yasps_status alloc_hessian(yasps_system* s) {
   const size_t es = (s->prm.precision == 1) ? sizeof(float) : sizeof(double);
@@ -1232,9 +1242,9 @@ yasps_status spmv64(yasps_system* s, const double* x, double* y) {
 }
 
 yasps_status pcg_solve(yasps_system* s, const double* rhs, double* p, double tol, int maxit, int* iters,
-                       double* rel_res) {
+                       double* rel_res, const double* x0) {
   cudaEvent_t pa = prof_begin(s);
-  yasps_status rc = pcg_solve_impl(s, rhs, p, tol, maxit, iters, rel_res);
+  yasps_status rc = pcg_solve_impl(s, rhs, p, tol, maxit, iters, rel_res, x0);
   prof_end(s, YASPS_STAGE_PCG, pa, 0.0);
   return rc;
 }
@@ -1325,15 +1335,44 @@ static yasps_status pcg_solve_batch(yasps_system* s, const double* rhs, double* 
 }
 
 yasps_status pcg_solve_impl(yasps_system* s, const double* rhs, double* p, double tol, int maxit, int* iters,
-                            double* rel_res) {
+                            double* rel_res, const double* x0) {
   const int n3 = 3 * s->nn;
   if (maxit <= 0) maxit = 10 * n3;
-  CK(s, cudaMemsetAsync(p, 0, sizeof(double) * n3, s->stream));
+  if (s->nscene > 1) x0 = nullptr;  // batches start cold
+  if (x0) CK(s, cudaMemcpyAsync(p, x0, sizeof(double) * n3, cudaMemcpyDeviceToDevice, s->stream));
+  else CK(s, cudaMemsetAsync(p, 0, sizeof(double) * n3, s->stream));
   if (s->nscene > 1) return pcg_solve_batch(s, rhs, p, tol, maxit, iters, rel_res);
   int it = 0, state = 0;
   double rel = 0.0;
-  if (s->hess_precision != 1) {
-    RC((pcg_inner<double, double>(s, rhs, p, tol, maxit, &it, &state, &rel)));
+  ENSURE(s, s->vec[6], sizeof(double) * (n3 + 4));
+  double* res = as<double>(s->vec[6]);
+  const bool mixed = s->hess_precision == 1;
+  // the stopping test is relative to the right-hand side: r^T z <= tol^2 g^T M^-1 g
+  double rz0 = 0.0, rz = 0.0;
+  RC(mixed ? rz64<float>(s, rhs, &rz0) : rz64<double>(s, rhs, &rz0));
+  if (!(rz0 > 0.0)) {
+    CK(s, cudaMemsetAsync(p, 0, sizeof(double) * n3, s->stream));
+    if (iters) *iters = 0;
+    if (rel_res) *rel_res = 0.0;
+    return YASPS_OK;
+  }
+  const double* r_cur = rhs;
+  rz = rz0;
+  if (x0) {  // warm start: solve for the correction of x0
+    RC(spmv64(s, p, res));
+    k_sub_from<<<blocks_for(n3, 256), 256, 0, s->stream>>>(n3, rhs, res);
+    LAUNCH_CHECK(s, "k_sub_from");
+    RC(mixed ? rz64<float>(s, res, &rz) : rz64<double>(s, res, &rz));
+    r_cur = res;
+  }
+  if (!mixed) {
+    if (rz > tol * tol * rz0) {
+      RC((pcg_inner<double, double>(s, r_cur, p, tol * std::sqrt(rz0 / rz), maxit, &it, &state, &rel)));
+      rel *= std::sqrt(rz / rz0);
+    } else {
+      state = 1;
+      rel = std::sqrt(rz / rz0);
+    }
     if (iters) *iters = it;
     if (rel_res) *rel_res = rel;
     if (state == 2) SYS_FAIL(s, YASPS_E_NAN, "PCG breakdown: d^T H d <= 0");
@@ -1341,32 +1380,19 @@ yasps_status pcg_solve_impl(yasps_system* s, const double* rhs, double* p, doubl
     return YASPS_OK;
   }
   // FP32-mixed: FP32 inner PCG, FP64 residual refinement
-  ENSURE(s, s->vec[6], sizeof(double) * (n3 + 4));
-  double* res = as<double>(s->vec[6]);
-  double rz0 = 0.0, rz = 0.0;
-  RC(rz64<float>(s, rhs, &rz0));
-  if (!(rz0 > 0.0)) {
-    if (iters) *iters = 0;
-    if (rel_res) *rel_res = 0.0;
-    return YASPS_OK;
-  }
-  rz = rz0;
   int total = 0;
   const int sweeps = std::max(1, s->prm.refine_sweeps);
-  for (int sw = 0; sw < sweeps; ++sw) {
+  for (int sw = 0; sw < sweeps && rz > tol * tol * rz0; ++sw) {
     const double inner_tol = std::max(tol * std::sqrt(rz0 / rz), 5e-6);
-    if (sw == 0) {
-      RC((pcg_inner<float, float>(s, rhs, p, inner_tol, maxit - total, &it, &state, &rel)));
-    } else {
-      RC((pcg_inner<float, float>(s, res, p, inner_tol, maxit - total, &it, &state, &rel)));
-    }
+    RC((pcg_inner<float, float>(s, r_cur, p, inner_tol, maxit - total, &it, &state, &rel)));
     total += it;
     // FP64 residual res = rhs - H p
     RC(spmv64(s, p, res));
     k_sub_from<<<blocks_for(n3, 256), 256, 0, s->stream>>>(n3, rhs, res);
     LAUNCH_CHECK(s, "k_sub_from");
     RC(rz64<float>(s, res, &rz));
-    if (rz <= tol * tol * rz0 || total >= maxit || state == 2) break;
+    r_cur = res;
+    if (total >= maxit || state == 2) break;
   }
   if (iters) *iters = total;
   const double r = std::sqrt(std::max(rz, 0.0) / rz0);

@@ -151,6 +151,7 @@ void yasps_default_params(yasps_params* p) {
   p->ccd_gap = 0.1;
   p->ccd_max_iter = 100000;
   p->refine_sweeps = 4;
+  p->pcg_warm_start = 1;
 }
 
 const char* yasps_build_error(void) { return g_build_error.c_str(); }
@@ -612,6 +613,10 @@ __global__ void k_axpy_out(int n, const double* __restrict__ x, double a, const 
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) out[i] = x[i] - a * p[i];
 }
+__global__ void k_scale_out(int n, double c, const double* __restrict__ p, double* __restrict__ out) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = c * p[i];
+}
 __global__ void k_velocity(int n, const double* __restrict__ x, const double* __restrict__ xt, double inv_h,
                            double* __restrict__ v) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -640,6 +645,8 @@ extern "C" yasps_status yasps_step(yasps_system* s, double* x, double* v, yasps_
   gbuf& trial = s->vec[7];
   ENSURE(s, trial, sizeof(double) * (n3 + 4));
   double* xtrial = as<double>(trial);
+  ENSURE(s, s->vec[9], sizeof(double) * (n3 + 4));
+  double* p0 = as<double>(s->vec[9]);
   if (s->nfix) {
     k_fixed_advance<<<blocks_for(s->nfix, 128), 128, 0, s->stream>>>(s->nfix, as<int>(s->fixed), as<double>(s->fixvel),
                                                                     h, as<double>(s->xfix));
@@ -650,7 +657,7 @@ extern "C" yasps_status yasps_step(yasps_system* s, double* x, double* v, yasps_
   s->cand_valid = false;
   yasps_status rc = YASPS_OK;
   int it = 0;
-  double pinf = 0.0, alpha = 0.0;
+  double pinf = 0.0, alpha = 1.0;
   for (it = 0; it < s->prm.newton_max_iter; ++it) {
     cudaEventRecord(s->ev[0], s->stream);
     cudaEvent_t pd = prof_begin(s);
@@ -666,7 +673,14 @@ extern "C" yasps_status yasps_step(yasps_system* s, double* x, double* v, yasps_
     cudaEventRecord(s->ev[1], s->stream);
     int pit = 0;
     double rel = 0.0;
-    rc = pcg_solve(s, as<double>(s->grad), p, s->prm.pcg_rel_tol, s->prm.pcg_max_iter, &pit, &rel);
+    // warm start from the part of the last direction the line search left
+    const double* x0 = nullptr;
+    if (s->prm.pcg_warm_start && it > 0 && alpha < 1.0) {
+      k_scale_out<<<blocks_for(n3, 256), 256, 0, s->stream>>>(n3, 1.0 - alpha, p, p0);
+      LAUNCH_CHECK(s, "k_scale_out");
+      x0 = p0;
+    }
+    rc = pcg_solve(s, as<double>(s->grad), p, s->prm.pcg_rel_tol, s->prm.pcg_max_iter, &pit, &rel, x0);
     st.pcg_iters_total += pit;
     if (rc == YASPS_E_NOCONV) rc = YASPS_OK;  // inexact Newton: keep the last iterate
     if (rc != YASPS_OK) break;
