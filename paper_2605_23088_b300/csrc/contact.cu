@@ -489,92 +489,229 @@ __device__ __forceinline__ void project_n(T* H) {
   project_psd<N, T>(H);
 }
 
-// kind 0 = PT, 1 = EE; one thread per pair
+// PT / EE barrier pairs (kind 0 = PT, 1 = EE), one warp per pair.  Lane 0 classifies
+// the pair and forms the distance derivatives; the warp then builds the
+// position-space Hessian, projects it with a parallel-ordering Jacobi EVD in
+// shared memory (n/2 disjoint rotations per step, round-robin over the n - 1
+// steps of a sweep; the same rotation formula and stopping rule as
+// project_psd, so Project(H), which is unique, agrees to rounding), and
+// scatters through the merged UNION Jacobians.  Pair counts are often small
+// (hundreds to thousands): a thread per pair would leave the GPU idle while
+// each thread runs a 12x12 EVD out of local memory.
 template <typename T>
-__global__ void __launch_bounds__(128) k_barrier(int kind, int npairs, int pair_base, const int* __restrict__ pairs,
-                                                 topo Tp, const double* __restrict__ vr, const double* __restrict__ P,
-                                                 double sh, double kappa, int form, int project,
-                                                 const int* __restrict__ koff, const int* __restrict__ dslot,
-                                                 double* __restrict__ g, T* __restrict__ diag, T* __restrict__ vals,
-                                                 int* status) {
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= npairs) return;
-  int ids[4], k;
-  pair_vertices(kind, p, pairs, Tp, ids, &k);
-  d3 y[4];
-  for (int a = 0; a < 4; ++a) y[a] = ld3(P, ids[a]);
-  double s;
-  dist::dclass dc;
-  if (kind == 0) dc = dist::pt_dclass(dist::pt_classify(y[0], y[1], y[2], y[3], &s));
-  else dc = dist::ee_dclass(dist::ee_classify(y[0], y[1], y[2], y[3], &s));
-  if (!(s < sh) || !(s > 0.0)) return;
-  const bder bd = barrier_fn(s, sh, form);
-  d3 yl[4];
-  for (int q = 0; q < dc.n; ++q) yl[q] = y[dc.loc[q]];
-  double gs[12], Hs[144];
-  switch (dc.dtype) {
-    case dist::PP: dist::ds_pp(yl, gs, Hs); break;
-    case dist::PE: dist::ds_pe(yl, gs, Hs); break;
-    case dist::PT: dist::ds_pt(yl, gs, Hs); break;
-    default: dist::ds_ee(yl, gs, Hs); break;
-  }
-  const int n3 = 3 * dc.n;
-  T H[144];
-  for (int r = 0; r < n3; ++r)
-    for (int c = 0; c < n3; ++c) H[r * n3 + c] = (T)(kappa * (bd.d2b * gs[r] * gs[c] + bd.db * Hs[r * n3 + c]));
-  if (project) {
-    if (dc.n == 2) project_n<6, T>(H);
-    else if (dc.n == 3) project_n<9, T>(H);
-    else project_n<12, T>(H);
-  }
-  // UNION Jacobians of the classified vertices, merged over the pair's node set
-  const nodeset S = pair_nodes(ids, k, Tp.vnode, Tp.vbody, vr);
+struct bar_ws {
+  double gs[12];
+  double Hs[144];
+  T A[144];
+  T V[144];
+  T cs[6], sn[6];
   double W[4][16];
-  for (int q = 0; q < dc.n; ++q) {
-    for (int u = 0; u < S.m; ++u) W[q][u] = 0.0;
-    const vmapd vm = vertex_map(ids[dc.loc[q]], Tp.vnode, Tp.vbody, vr);
-    for (int a = 0; a < vm.n; ++a) {
-      int u = 0;
-      while (S.node[u] != vm.node[a]) ++u;
-      W[q][u] += vm.w[a];
-    }
-  }
-  for (int u = 0; u < S.m; ++u) {
-    double gu[3] = {0, 0, 0};
-    bool any = false;
-    for (int q = 0; q < dc.n; ++q)
-      if (W[q][u] != 0.0) {
-        any = true;
-        for (int i = 0; i < 3; ++i) gu[i] += W[q][u] * kappa * bd.db * gs[3 * q + i];
-      }
-    if (any)
-      for (int i = 0; i < 3; ++i) atomicAdd(&g[3 * S.node[u] + i], gu[i]);
-  }
-  const int kbase = koff[pair_base + p];
-  for (int u = 0; u < S.m; ++u)
-    for (int w = u; w < S.m; ++w) {
-      T B[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
-      bool any = false;
+  double db, d2b;
+  int ids[4], loc[4];
+  int n, active, m, node[16];
+};
+
+template <typename T>
+__global__ void __launch_bounds__(128) k_barrier_w(int kind, int npairs, int pair_base, const int* __restrict__ pairs,
+                                                   topo Tp, const double* __restrict__ vr, const double* __restrict__ P,
+                                                   double sh, double kappa, int form, int project,
+                                                   const int* __restrict__ koff, const int* __restrict__ dslot,
+                                                   double* __restrict__ g, T* __restrict__ diag, T* __restrict__ vals,
+                                                   int* status) {
+  __shared__ bar_ws<T> wsa[4];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int p = blockIdx.x * 4 + wid;
+  if (p >= npairs) return;  // warp-uniform
+  bar_ws<T>& w = wsa[wid];
+  if (lane == 0) {
+    int k;
+    pair_vertices(kind, p, pairs, Tp, w.ids, &k);
+    d3 y[4];
+    for (int a = 0; a < 4; ++a) y[a] = ld3(P, w.ids[a]);
+    double sd;
+    dist::dclass dc;
+    if (kind == 0) dc = dist::pt_dclass(dist::pt_classify(y[0], y[1], y[2], y[3], &sd));
+    else dc = dist::ee_dclass(dist::ee_classify(y[0], y[1], y[2], y[3], &sd));
+    w.active = (sd < sh) && (sd > 0.0);
+    if (w.active) {
+      const bder bd = barrier_fn(sd, sh, form);
+      w.db = bd.db;
+      w.d2b = bd.d2b;
+      w.n = dc.n;
+      d3 yl[4];
       for (int q = 0; q < dc.n; ++q) {
-        if (W[q][u] == 0.0) continue;
-        for (int r = 0; r < dc.n; ++r) {
-          const double f = W[q][u] * W[r][w];
-          if (f == 0.0) continue;
-          any = true;
-          for (int i = 0; i < 3; ++i)
-            for (int j = 0; j < 3; ++j) B[3 * i + j] += (T)f * H[(3 * q + i) * n3 + 3 * r + j];
+        yl[q] = y[dc.loc[q]];
+        w.loc[q] = dc.loc[q];
+      }
+      switch (dc.dtype) {
+        case dist::PP: dist::ds_pp(yl, w.gs, w.Hs); break;
+        case dist::PE: dist::ds_pe(yl, w.gs, w.Hs); break;
+        case dist::PT: dist::ds_pt(yl, w.gs, w.Hs); break;
+        default: dist::ds_ee(yl, w.gs, w.Hs); break;
+      }
+      // merged node set and the UNION weights of the classified vertices
+      const nodeset S = pair_nodes(w.ids, k, Tp.vnode, Tp.vbody, vr);
+      w.m = S.m;
+      for (int u = 0; u < S.m; ++u) w.node[u] = S.node[u];
+      for (int q = 0; q < dc.n; ++q) {
+        for (int u = 0; u < S.m; ++u) w.W[q][u] = 0.0;
+        const vmapd vm = vertex_map(w.ids[dc.loc[q]], Tp.vnode, Tp.vbody, vr);
+        for (int a = 0; a < vm.n; ++a) {
+          int u = 0;
+          while (S.node[u] != vm.node[a]) ++u;
+          w.W[q][u] += vm.w[a];
         }
       }
-      if (!any) continue;
-      T* d;
-      if (u == w) d = diag + 9 * (size_t)S.node[u];
-      else {
-        const int sl = dslot[kbase + pair_rank(u, w, S.m)];
-        if (sl < 0) { dev_flag(status, DEV_BADINDEX); continue; }
-        d = vals + 9 * (size_t)sl;
-      }
-      for (int t = 0; t < 9; ++t) atomicAdd(d + t, B[t]);
     }
+  }
+  __syncwarp();
+  if (!w.active) return;  // warp-uniform
+  const int n3 = 3 * w.n;
+  const double db = w.db, d2b = w.d2b;
+  for (int e = lane; e < n3 * n3; e += 32) {
+    const int r = e / n3, c = e % n3;
+    w.A[e] = (T)(kappa * (d2b * w.gs[r] * w.gs[c] + db * w.Hs[e]));
+    w.V[e] = (r == c) ? T(1) : T(0);
+  }
+  __syncwarp();
+  if (project) {
+    const int np = n3 + (n3 & 1);  // even count for the round-robin (index n3 is a dummy when n3 is odd)
+    const int m = np / 2;
+    for (int sweep = 0; sweep < eig_traits<T>::max_sweeps; ++sweep) {
+      T off = 0, tot = 0;
+      for (int e = lane; e < n3 * n3; e += 32) {
+        const int r = e / n3, c = e % n3;
+        const T a = w.A[e];
+        if (r == c) tot += a * a;
+        else if (r < c) off += a * a;
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        off += __shfl_xor_sync(0xffffffffu, off, o);
+        tot += __shfl_xor_sync(0xffffffffu, tot, o);
+      }
+      tot += T(2) * off;
+      if (!(off > eig_traits<T>::rel_eps2 * tot)) break;
+      for (int step = 0; step < np - 1; ++step) {
+        // rotation i of this step: indices (a_i, b_i), disjoint over i
+        if (lane < m) {
+          int a = (lane == 0) ? 0 : 1 + (step + lane) % (np - 1);
+          int b = (lane == 0) ? 1 + step : 1 + (step - lane + np - 1) % (np - 1);
+          const int pp = min(a, b), qq = max(a, b);
+          T c = 1, sn = 0;
+          if (qq < n3) {
+            const T apq = w.A[pp * n3 + qq];
+            if (apq != T(0)) {
+              const T theta = (w.A[qq * n3 + qq] - w.A[pp * n3 + pp]) / (T(2) * apq);
+              const T t = (theta >= T(0) ? T(1) : T(-1)) / (fabs(theta) + sqrt(theta * theta + T(1)));
+              c = jacobi_c(t);
+              sn = t * c;
+            }
+          }
+          w.cs[lane] = c;
+          w.sn[lane] = sn;
+        }
+        __syncwarp();
+        // columns of A and V: A <- A J, V <- V J
+        for (int e = lane; e < m * n3; e += 32) {
+          const int i = e / n3, k = e % n3;
+          const int a = (i == 0) ? 0 : 1 + (step + i) % (np - 1);
+          const int b = (i == 0) ? 1 + step : 1 + (step - i + np - 1) % (np - 1);
+          const int pp = min(a, b), qq = max(a, b);
+          if (qq >= n3) continue;
+          const T c = w.cs[i], sn = w.sn[i];
+          if (sn == T(0)) continue;
+          const T akp = w.A[k * n3 + pp], akq = w.A[k * n3 + qq];
+          w.A[k * n3 + pp] = c * akp - sn * akq;
+          w.A[k * n3 + qq] = sn * akp + c * akq;
+          const T vkp = w.V[k * n3 + pp], vkq = w.V[k * n3 + qq];
+          w.V[k * n3 + pp] = c * vkp - sn * vkq;
+          w.V[k * n3 + qq] = sn * vkp + c * vkq;
+        }
+        __syncwarp();
+        // rows of A: A <- J^T A
+        for (int e = lane; e < m * n3; e += 32) {
+          const int i = e / n3, k = e % n3;
+          const int a = (i == 0) ? 0 : 1 + (step + i) % (np - 1);
+          const int b = (i == 0) ? 1 + step : 1 + (step - i + np - 1) % (np - 1);
+          const int pp = min(a, b), qq = max(a, b);
+          if (qq >= n3) continue;
+          const T c = w.cs[i], sn = w.sn[i];
+          if (sn == T(0)) continue;
+          const T apk = w.A[pp * n3 + k], aqk = w.A[qq * n3 + k];
+          w.A[pp * n3 + k] = c * apk - sn * aqk;
+          w.A[qq * n3 + k] = sn * apk + c * aqk;
+        }
+        __syncwarp();
+      }
+    }
+    // Project(H) = V max(Lambda, 0) V^T, written back over A (upper, then mirrored)
+    T lam[12];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) lam[k] = (k < n3 && w.A[k * n3 + k] > T(0)) ? w.A[k * n3 + k] : T(0);
+    __syncwarp();
+    T outv[5];
+    int outi[5];
+    int no = 0;
+    for (int e = lane; e < n3 * n3; e += 32) {
+      const int r = e / n3, c = e % n3;
+      if (r > c) continue;
+      T acc = 0;
+      for (int k = 0; k < n3; ++k) acc += w.V[r * n3 + k] * lam[k] * w.V[c * n3 + k];
+      outv[no] = acc;
+      outi[no] = e;
+      ++no;
+    }
+    __syncwarp();
+    for (int q = 0; q < no; ++q) {
+      const int e = outi[q], r = e / n3, c = e % n3;
+      w.A[r * n3 + c] = outv[q];
+      w.A[c * n3 + r] = outv[q];
+    }
+    __syncwarp();
+  }
+  // gradient rows of the merged nodes
+  const int M = w.m;
+  if (lane < M) {
+    double gu[3] = {0, 0, 0};
+    bool any = false;
+    for (int q = 0; q < w.n; ++q)
+      if (w.W[q][lane] != 0.0) {
+        any = true;
+        for (int i = 0; i < 3; ++i) gu[i] += w.W[q][lane] * kappa * db * w.gs[3 * q + i];
+      }
+    if (any)
+      for (int i = 0; i < 3; ++i) atomicAdd(&g[3 * w.node[lane] + i], gu[i]);
+  }
+  // Hessian blocks (u <= w) of the merged nodes, one per lane at a time
+  const int kbase = koff[pair_base + p];
+  const int nb = M * (M + 1) / 2;
+  for (int e = lane; e < nb; e += 32) {
+    int u = 0, rem = e;
+    while (rem >= M - u) { rem -= M - u; ++u; }
+    const int v2 = u + rem;
+    T B[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    bool any = false;
+    for (int q = 0; q < w.n; ++q) {
+      if (w.W[q][u] == 0.0) continue;
+      for (int r = 0; r < w.n; ++r) {
+        const double f = w.W[q][u] * w.W[r][v2];
+        if (f == 0.0) continue;
+        any = true;
+        for (int i = 0; i < 3; ++i)
+          for (int j = 0; j < 3; ++j) B[3 * i + j] += (T)f * w.A[(3 * q + i) * n3 + 3 * r + j];
+      }
+    }
+    if (!any) continue;
+    T* d;
+    if (u == v2) d = diag + 9 * (size_t)w.node[u];
+    else {
+      const int sl = dslot[kbase + pair_rank(u, v2, M)];
+      if (sl < 0) { dev_flag(status, DEV_BADINDEX); continue; }
+      d = vals + 9 * (size_t)sl;
+    }
+    for (int t = 0; t < 9; ++t) atomicAdd(d + t, B[t]);
+  }
 }
 
 // point-plane pairs: s = d^2, grad s = 2 d n, hess s = 2 n n^T; the position-
@@ -948,18 +1085,19 @@ yasps_status eval_barrier_t(yasps_system* s, int project) {
   const double* P = as<double>(s->P);
   const int* koff = as<int>(s->pair_key_off);
   const int* dslot = as<int>(s->dyn_slot);
+  // one warp per pair (4 pairs per block of 128)
   if (s->npt) {
-    k_barrier<T><<<blocks_for(s->npt, 128), 128, 0, s->stream>>>(0, s->npt, 0, as<int>(s->pt), Tp, as<double>(s->vr), P,
+    k_barrier_w<T><<<blocks_for(s->npt, 4), 128, 0, s->stream>>>(0, s->npt, 0, as<int>(s->pt), Tp, as<double>(s->vr), P,
                                                                 sh, s->prm.kappa, s->prm.barrier_form, project, koff,
                                                                 dslot, g, diag, vals, st);
-    LAUNCH_CHECK(s, "k_barrier(PT)");
+    LAUNCH_CHECK(s, "k_barrier_w(PT)");
   }
   if (s->nee) {
-    k_barrier<T><<<blocks_for(s->nee, 128), 128, 0, s->stream>>>(1, s->nee, s->npt, as<int>(s->ee), Tp,
+    k_barrier_w<T><<<blocks_for(s->nee, 4), 128, 0, s->stream>>>(1, s->nee, s->npt, as<int>(s->ee), Tp,
                                                                 as<double>(s->vr), P, sh, s->prm.kappa,
                                                                 s->prm.barrier_form, project, koff, dslot, g, diag,
                                                                 vals, st);
-    LAUNCH_CHECK(s, "k_barrier(EE)");
+    LAUNCH_CHECK(s, "k_barrier_w(EE)");
   }
   if (s->npg) {
     k_barrier_pg<T><<<blocks_for(s->npg, 128), 128, 0, s->stream>>>(s->npg, s->npt + s->nee, as<int>(s->pg), Tp,
