@@ -151,24 +151,33 @@ __global__ void k_grid_count(int n, const float* __restrict__ lo, const float* _
     for (int y = c0[1]; y <= c1[1]; ++y)
       for (int x = c0[0]; x <= c1[0]; ++x) atomicAdd(&cnt[((long long)z * G.dim[1] + y) * G.dim[0] + x], 1);
 }
+// Each cell's entries are stored as packed records (FP32 box + primitive id,
+// 32 bytes), so a query walks a cell as one contiguous stream instead of
+// gathering every box by primitive id.
 __global__ void k_grid_fill(int n, const float* __restrict__ lo, const float* __restrict__ hi, gridp G,
-                            const int* __restrict__ start, int* __restrict__ fill, int* __restrict__ items) {
+                            const int* __restrict__ start, int* __restrict__ fill, float4* __restrict__ pk) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= n) return;
   int c0[3], c1[3];
-  cell_range(G, lo + 3 * e, hi + 3 * e, c0, c1);
+  const float* l = lo + 3 * e;
+  const float* h = hi + 3 * e;
+  cell_range(G, l, h, c0, c1);
+  const float4 r0 = make_float4(l[0], l[1], l[2], __int_as_float(e));
+  const float4 r1 = make_float4(h[0], h[1], h[2], 0.0f);
   for (int z = c0[2]; z <= c1[2]; ++z)
     for (int y = c0[1]; y <= c1[1]; ++y)
       for (int x = c0[0]; x <= c1[0]; ++x) {
         const long long id = ((long long)z * G.dim[1] + y) * G.dim[0] + x;
-        items[start[id] + atomicAdd(&fill[id], 1)] = e;
+        const int q = start[id] + atomicAdd(&fill[id], 1);
+        pk[2 * (size_t)q] = r0;
+        pk[2 * (size_t)q + 1] = r1;
       }
 }
 
 struct grid_dev {
   gridp G;
   const int* start;
-  const int* items;
+  const float4* pk;  // [entries][2]: (lo, id), (hi, 0)
   boxes B;
 };
 
@@ -186,10 +195,12 @@ __device__ __forceinline__ void grid_visit(const grid_dev& g, const boxes& A, in
     for (int y = c0[1]; y <= c1[1]; ++y)
       for (int x = c0[0]; x <= c1[0]; ++x) {
         const long long id = ((long long)z * g.G.dim[1] + y) * g.G.dim[0] + x;
-        for (int q = g.start[id]; q < g.start[id + 1]; ++q) {
-          const int j = g.items[q];
-          const float* blf = g.B.lof + 3 * j;
-          const float* bhf = g.B.hif + 3 * j;
+        const int qe = g.start[id + 1];
+        for (int q = g.start[id]; q < qe; ++q) {
+          const float4 r0 = g.pk[2 * (size_t)q], r1 = g.pk[2 * (size_t)q + 1];
+          const int j = __float_as_int(r0.w);
+          const float blf[3] = {r0.x, r0.y, r0.z};
+          const float bhf[3] = {r1.x, r1.y, r1.z};
           if (ahf[0] < blf[0] || bhf[0] < alf[0] || ahf[1] < blf[1] || bhf[1] < alf[1] || ahf[2] < blf[2] ||
               bhf[2] < alf[2])
             continue;
@@ -1027,13 +1038,13 @@ yasps_status build_grid(yasps_system* s, int n, boxes B, grid_dev* out) {
   LAUNCH_CHECK(s, "k_grid_count");
   int total = 0;
   RC(scan_exclusive(s, start, start, (int)(ncell + 1), &total));
-  ENSURE(s, s->ws[5], sizeof(int) * (total + 1));
+  ENSURE(s, s->ws[5], sizeof(float4) * 2 * ((size_t)total + 1));
   CK(s, cudaMemsetAsync(fill, 0, sizeof(int) * (ncell + 1), s->stream));
-  k_grid_fill<<<blocks_for(n, 256), 256, 0, s->stream>>>(n, B.lof, B.hif, G, start, fill, as<int>(s->ws[5]));
+  k_grid_fill<<<blocks_for(n, 256), 256, 0, s->stream>>>(n, B.lof, B.hif, G, start, fill, as<float4>(s->ws[5]));
   LAUNCH_CHECK(s, "k_grid_fill");
   out->G = G;
   out->start = start;
-  out->items = as<int>(s->ws[5]);
+  out->pk = as<float4>(s->ws[5]);
   out->B = B;
   return YASPS_OK;
 }

@@ -474,6 +474,39 @@ __device__ __forceinline__ void gather_d(int r, int c, const V* z, const V* d, V
     g.r0 = dnew(zr0, beta, dr0); g.r1 = dnew(zr1, beta, dr1); g.r2 = dnew(zr2, beta, dr2);
   }
 }
+// Layout of the product q = H d inside the PCG kernel: FP32 uses 16 bytes
+// per node, so a node's three contributions go in one vector atomic
+// (red.global.add.v4.f32); FP64 keeps 3 scalars per node.
+template <typename V>
+struct qlay { static constexpr int S = 3; };
+template <>
+struct qlay<float> { static constexpr int S = 4; };
+// index in q of entry o3 of a 3-per-node vector
+template <typename V>
+__device__ __forceinline__ size_t q_idx(size_t o3) {
+  return (o3 / 3) * qlay<V>::S + o3 % 3;
+}
+__device__ __forceinline__ void q_add3(float* q, int node, float a, float b, float c) {
+  atomicAdd(reinterpret_cast<float4*>(q) + node, make_float4(a, b, c, 0.0f));
+}
+__device__ __forceinline__ void q_add3(double* q, int node, double a, double b, double c) {
+  atomicAdd(&q[3 * (size_t)node], a);
+  atomicAdd(&q[3 * (size_t)node + 1], b);
+  atomicAdd(&q[3 * (size_t)node + 2], c);
+}
+__device__ __forceinline__ void q_take3(float* q, long long node, float* out) {  // read and clear
+  float4* p = reinterpret_cast<float4*>(q) + node;
+  const float4 v = *p;
+  out[0] = v.x; out[1] = v.y; out[2] = v.z;
+  *p = make_float4(0.f, 0.f, 0.f, 0.f);
+}
+__device__ __forceinline__ void q_take3(double* q, long long node, double* out) {
+  for (int c = 0; c < 3; ++c) {
+    out[c] = q[3 * node + c];
+    q[3 * node + c] = 0.0;
+  }
+}
+
 // q += B d'_c into the row (segmented over the warp), q += B^T d'_r into the
 // column; returns the block's share 2 d'_r^T B d'_c of d'^T U d'
 template <typename T, typename V>
@@ -486,9 +519,8 @@ __device__ __forceinline__ V apply_blk(int r, int c, const T* b, const gath<V>& 
     a1 = (V)b[3] * xc0 + (V)b[4] * xc1 + (V)b[5] * xc2;
     a2 = (V)b[6] * xc0 + (V)b[7] * xc1 + (V)b[8] * xc2;
     part = (V)2 * (xr0 * a0 + xr1 * a1 + xr2 * a2);
-    atomicAdd(&q[3 * c], (V)b[0] * xr0 + (V)b[3] * xr1 + (V)b[6] * xr2);
-    atomicAdd(&q[3 * c + 1], (V)b[1] * xr0 + (V)b[4] * xr1 + (V)b[7] * xr2);
-    atomicAdd(&q[3 * c + 2], (V)b[2] * xr0 + (V)b[5] * xr1 + (V)b[8] * xr2);
+    q_add3(q, c, (V)b[0] * xr0 + (V)b[3] * xr1 + (V)b[6] * xr2, (V)b[1] * xr0 + (V)b[4] * xr1 + (V)b[7] * xr2,
+           (V)b[2] * xr0 + (V)b[5] * xr1 + (V)b[8] * xr2);
   }
 #pragma unroll
   for (int off = 1; off < 32; off <<= 1) {
@@ -497,11 +529,7 @@ __device__ __forceinline__ V apply_blk(int r, int c, const T* b, const gath<V>& 
     if (lane + off < 32 && ro == r) { a0 += b0; a1 += b1; a2 += b2; }
   }
   const int rp = __shfl_up_sync(0xffffffffu, r, 1);
-  if (r >= 0 && (lane == 0 || rp != r)) {
-    atomicAdd(&q[3 * r], a0);
-    atomicAdd(&q[3 * r + 1], a1);
-    atomicAdd(&q[3 * r + 2], a2);
-  }
+  if (r >= 0 && (lane == 0 || rp != r)) q_add3(q, r, a0, a1, a2);
   return part;
 }
 
@@ -525,9 +553,7 @@ __device__ __forceinline__ V diag_node(const pcg_args<T, V>& a, long long i, V b
   const V q1 = (V)m[3] * d0 + (V)m[4] * d1 + (V)m[5] * d2;
   const V q2 = (V)m[6] * d0 + (V)m[7] * d1 + (V)m[8] * d2;
   dn[3 * i] = d0; dn[3 * i + 1] = d1; dn[3 * i + 2] = d2;
-  atomicAdd(&a.q[3 * i], q0);
-  atomicAdd(&a.q[3 * i + 1], q1);
-  atomicAdd(&a.q[3 * i + 2], q2);
+  q_add3(a.q, (int)i, q0, q1, q2);
   return d0 * q0 + d1 * q1 + d2 * q2;
 }
 // phase C for one free node: x += alpha d', r -= alpha q, z = M^-1 r, q = 0; r^T z
@@ -543,8 +569,8 @@ __device__ __forceinline__ V update_free(const pcg_args<T, V>& a, long long i, V
     xv[c] = a.x[3 * i + c];
     dv[c] = dn[3 * i + c];
     rv[c] = a.r[3 * i + c];
-    qv[c] = a.q[3 * i + c];
   }
+  q_take3(a.q, i, qv);
   V zv[3], acc = 0;
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
@@ -561,7 +587,6 @@ __device__ __forceinline__ V update_free(const pcg_args<T, V>& a, long long i, V
     a.x[3 * i + c] = xv[c];
     a.r[3 * i + c] = rv[c];
     a.z[3 * i + c] = zv[c];
-    a.q[3 * i + c] = 0;
   }
   return acc;
 }
@@ -705,7 +730,7 @@ __global__ void __launch_bounds__(CFG::NTHR, CFG::MINB) k_pcg_persistent(pcg_arg
         a.r[o + c] = (V)a.rhs[o + c];
         a.x[o + c] = 0;
         a.d0[o + c] = 0;
-        a.q[o + c] = 0;
+        a.q[q_idx<V>(o + c)] = 0;
       }
       acc += precond_row<T, V>((int)i, a.nfree, a.Mi, a.r, a.z);
     }
@@ -722,7 +747,7 @@ __global__ void __launch_bounds__(CFG::NTHR, CFG::MINB) k_pcg_persistent(pcg_arg
           a.r[o + c] = (V)a.rhs[o + c];
           a.x[o + c] = 0;
           a.d0[o + c] = 0;
-          a.q[o + c] = 0;
+          a.q[q_idx<V>(o + c)] = 0;
         }
         v = precond_row<T, V>((int)i, a.nfree, a.Mi, a.r, a.z);
         key = a.node_scene[i < a.nfree ? i : a.nfree + 4 * (i - a.nfree)];
@@ -900,8 +925,8 @@ __global__ void __launch_bounds__(CFG::NTHR, CFG::MINB) k_pcg_persistent(pcg_arg
       if constexpr (BATCH) al = tab[a.node_scene[a.nfree + 4 * bi]];
       for (int c = 0; c < 12; ++c) {
         a.x[o + c] += al * dn[o + c];
-        a.r[o + c] -= al * a.q[o + c];
-        a.q[o + c] = 0;
+        a.r[o + c] -= al * a.q[q_idx<V>(o + c)];
+        a.q[q_idx<V>(o + c)] = 0;
       }
       const V v = precond_row<T, V>(i, a.nfree, a.Mi, a.r, a.z);
       if constexpr (BATCH) atomicAdd(&shs[a.node_scene[a.nfree + 4 * bi]], (double)v);
@@ -1036,6 +1061,7 @@ yasps_status pcg_launch_cfg(yasps_system* s, const double* rhs, double* p, doubl
                             int* iters, int* state, double* rel, scene_out* so) {
   const int n3 = 3 * s->nn;
   for (int k = 0; k < 5; ++k) ENSURE(s, s->vec[k], sizeof(V) * (n3 + 4));
+  ENSURE(s, s->vec[4], sizeof(V) * 4 * ((size_t)s->nn + 1));  // q: qlay<V>::S per node
   ENSURE(s, s->vec[8], sizeof(V) * (n3 + 4));
   int G = 0;
   RC((pcg_grid<T, V, BATCH, CFG>(s, &G)));
