@@ -241,6 +241,34 @@ __device__ __forceinline__ bool ee_excluded(const topo& T, int e0, int e1, int f
   return false;
 }
 
+// A lower bound of the squared distance between the primitives of a pair
+// (point vs triangle: kind 0, y0 | y1 y2 y3; segment vs segment: kind 1,
+// y0 y1 | y2 y3): the squared distance between their axis-aligned boxes.  A
+// few FP64 operations instead of the exact classification, which is skipped
+// whenever the bound already exceeds what matters (dhat^2, or the CCD step);
+// the comparisons keep a 1e-9 relative margin, so every skipped pair is one the
+// exact test would also have rejected.
+__device__ __forceinline__ double pair_lb2(int kind, d3 y0, d3 y1, d3 y2, d3 y3) {
+  const double alo[3] = {kind == 0 ? y0.x : fmin(y0.x, y1.x), kind == 0 ? y0.y : fmin(y0.y, y1.y),
+                         kind == 0 ? y0.z : fmin(y0.z, y1.z)};
+  const double ahi[3] = {kind == 0 ? y0.x : fmax(y0.x, y1.x), kind == 0 ? y0.y : fmax(y0.y, y1.y),
+                         kind == 0 ? y0.z : fmax(y0.z, y1.z)};
+  double blo[3] = {fmin(y2.x, y3.x), fmin(y2.y, y3.y), fmin(y2.z, y3.z)};
+  double bhi[3] = {fmax(y2.x, y3.x), fmax(y2.y, y3.y), fmax(y2.z, y3.z)};
+  if (kind == 0) {
+    blo[0] = fmin(blo[0], y1.x); blo[1] = fmin(blo[1], y1.y); blo[2] = fmin(blo[2], y1.z);
+    bhi[0] = fmax(bhi[0], y1.x); bhi[1] = fmax(bhi[1], y1.y); bhi[2] = fmax(bhi[2], y1.z);
+  }
+  double s = 0.0;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const double g = fmax(fmax(alo[c] - bhi[c], blo[c] - ahi[c]), 0.0);
+    s += g * g;
+  }
+  return s;
+}
+__device__ __forceinline__ bool surely_apart(double lb2, double sh) { return lb2 > sh * (1.0 + 1e-9); }
+
 // ---------------------------------------------------------------- barrier scalar
 struct bder {
   double b, db, d2b;
@@ -270,8 +298,10 @@ __global__ void k_pt_query(int total, int nsv, topo T, const double* __restrict_
     grid_visit(g, A, i, [&](int t) {
       const int t0 = T.stri[3 * t], t1 = T.stri[3 * t + 1], t2 = T.stri[3 * t + 2];
       if (pt_excluded(T, v, t0, t1, t2)) return;
+      const d3 q0 = ld3(P, t0), q1 = ld3(P, t1), q2 = ld3(P, t2);
+      if (surely_apart(pair_lb2(0, p, q0, q1, q2), sh)) return;
       double s;
-      const int st = dist::pt_classify(p, ld3(P, t0), ld3(P, t1), ld3(P, t2), &s);
+      const int st = dist::pt_classify(p, q0, q1, q2, &s);
       if (!(s < sh)) return;
       if (mode == 1) {
         if (base + c >= lim) { dev_flag(T.status, DEV_CAPACITY); return; }
@@ -320,8 +350,10 @@ __global__ void k_ee_query(int total, int nse, topo T, const double* __restrict_
       if (j <= i) return;
       const int f0 = T.sedge[2 * j], f1 = T.sedge[2 * j + 1];
       if (ee_excluded(T, e0, e1, f0, f1)) return;
+      const d3 b0 = ld3(P, f0), b1 = ld3(P, f1);
+      if (surely_apart(pair_lb2(1, a0, a1, b0, b1), sh)) return;
       double s;
-      const int st = dist::ee_classify(a0, a1, ld3(P, f0), ld3(P, f1), &s);
+      const int st = dist::ee_classify(a0, a1, b0, b1, &s);
       if (!(s < sh)) return;
       if (mode == 1) {
         if (base + c >= lim) { dev_flag(T.status, DEV_CAPACITY); return; }
@@ -775,6 +807,23 @@ __device__ double pair_dist2(int kind, const d3* x) {
 // additive CCD along x + t dx, t in [0, tmax]: advance by (1 - gap) d / l_p,
 // where l_p bounds the relative motion; stop before the distance falls below
 // gap * (starting distance).  Explicitly rounded like the reference arithmetic.
+// lp of ACCD (the bound on the pair's relative motion over the step), as accd forms it
+__device__ __forceinline__ double accd_motion_bound(int kind, const d3* dx0) {
+  using namespace dist;
+  double m[3] = {0.0, 0.0, 0.0};
+  for (int i = 0; i < 4; ++i) {
+    m[0] = add(m[0], mul(0.25, dx0[i].x));
+    m[1] = add(m[1], mul(0.25, dx0[i].y));
+    m[2] = add(m[2], mul(0.25, dx0[i].z));
+  }
+  double nrm[4];
+  for (int i = 0; i < 4; ++i) {
+    const d3 c = d3{sub(dx0[i].x, m[0]), sub(dx0[i].y, m[1]), sub(dx0[i].z, m[2])};
+    nrm[i] = sqrt(vdot(c, c));
+  }
+  return (kind == 0) ? add(nrm[0], fmax(nrm[1], fmax(nrm[2], nrm[3]))) : add(fmax(nrm[0], nrm[1]), fmax(nrm[2], nrm[3]));
+}
+
 __device__ double accd(int kind, d3* x, d3* dx, double gap, double tmax, int max_iter, bool* capped) {
   using namespace dist;
   double m[3] = {0.0, 0.0, 0.0};
@@ -910,7 +959,13 @@ __global__ void k_ccd_cand(int kind, int n, const int* __restrict__ cand, topo T
     cand_vertices(kind, cand, (size_t)k, T, ids);
     d3 x[4], dx[4];
     for (int q = 0; q < 4; ++q) { x[q] = ld3(P0, ids[q]); dx[q] = ld3(D, ids[q]); }
-    best = accd(kind, x, dx, gap, 1.0, max_iter, &capped);
+    // ACCD's first advance is (1 - gap) d0 / lp with lp its bound on the
+    // relative motion: when that already exceeds the whole step the answer is
+    // the full step, so skip the exact distances
+    const double lp = accd_motion_bound(kind, dx);
+    const double lb2 = pair_lb2(kind, x[0], x[1], x[2], x[3]);
+    if (!(lp == 0.0) && !((1.0 - gap) * (1.0 - gap) * lb2 > lp * lp * (1.0 + 1e-9)))
+      best = accd(kind, x, dx, gap, 1.0, max_iter, &capped);
   }
   if (capped) dev_flag(status, DEV_ITERCAP);
   if (T.vscene) {  // batches: one bound per scene
@@ -942,10 +997,13 @@ __global__ void k_energy_cand(int kind, int n, const int* __restrict__ cand, top
     if (k < n) {
       int ids[4];
       cand_vertices(kind, cand, (size_t)k, T, ids);
-      double s;
-      if (kind == 0) dist::pt_classify(ld3(P, ids[0]), ld3(P, ids[1]), ld3(P, ids[2]), ld3(P, ids[3]), &s);
-      else dist::ee_classify(ld3(P, ids[0]), ld3(P, ids[1]), ld3(P, ids[2]), ld3(P, ids[3]), &s);
-      if (s < sh) e = kappa * barrier_fn(s, sh, form).b;
+      const d3 y0 = ld3(P, ids[0]), y1 = ld3(P, ids[1]), y2 = ld3(P, ids[2]), y3 = ld3(P, ids[3]);
+      if (!surely_apart(pair_lb2(kind, y0, y1, y2, y3), sh)) {
+        double s;
+        if (kind == 0) dist::pt_classify(y0, y1, y2, y3, &s);
+        else dist::ee_classify(y0, y1, y2, y3, &s);
+        if (s < sh) e = kappa * barrier_fn(s, sh, form).b;
+      }
       if (sacc) key = T.vscene[ids[0]];
     }
     // batches: candidates are sorted by their first primitive, so by scene
@@ -965,10 +1023,16 @@ __global__ void k_filter_cand(int kind, int n, const int* __restrict__ cand, top
   if (k >= n) return;
   int ids[4];
   cand_vertices(kind, cand, (size_t)k, T, ids);
+  const d3 y0 = ld3(P, ids[0]), y1 = ld3(P, ids[1]), y2 = ld3(P, ids[2]), y3 = ld3(P, ids[3]);
+  if (surely_apart(pair_lb2(kind, y0, y1, y2, y3), sh)) {
+    flag[k] = 0;
+    sub[k] = 0;
+    return;
+  }
   double s;
   int st;
-  if (kind == 0) st = dist::pt_classify(ld3(P, ids[0]), ld3(P, ids[1]), ld3(P, ids[2]), ld3(P, ids[3]), &s);
-  else st = dist::ee_classify(ld3(P, ids[0]), ld3(P, ids[1]), ld3(P, ids[2]), ld3(P, ids[3]), &s);
+  if (kind == 0) st = dist::pt_classify(y0, y1, y2, y3, &s);
+  else st = dist::ee_classify(y0, y1, y2, y3, &s);
   flag[k] = (s < sh) ? 1 : 0;
   sub[k] = st;
 }

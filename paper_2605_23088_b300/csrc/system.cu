@@ -658,6 +658,8 @@ extern "C" yasps_status yasps_step(yasps_system* s, double* x, double* v, yasps_
   yasps_status rc = YASPS_OK;
   int it = 0;
   double pinf = 0.0, alpha = 1.0;
+  double E_acc = 0.0;  // energy at x after the last accepted line search
+  bool have_E = false;
   for (it = 0; it < s->prm.newton_max_iter; ++it) {
     cudaEventRecord(s->ev[0], s->stream);
     cudaEvent_t pd = prof_begin(s);
@@ -710,8 +712,11 @@ extern "C" yasps_status yasps_step(yasps_system* s, double* x, double* v, yasps_
     st.n_cand_ee = s->ncee;
     cudaEventRecord(s->ev[4], s->stream);
     cudaEvent_t pl = prof_begin(s);
-    double E0 = 0.0, E1 = 0.0;
-    RC(energy_impl(s, x, xtil, &E0, nullptr, true));
+    // E(x) is the energy the previous line search accepted (the same sum over
+    // the same active pairs, since both candidate sets hold every pair within
+    // dhat of x); only the first iteration evaluates it
+    double E0 = E_acc, E1 = 0.0;
+    if (!have_E) RC(energy_impl(s, x, xtil, &E0, nullptr, true));
     int ls = 0;
     for (ls = 0; ls < s->prm.ls_max_iter; ++ls) {
       k_axpy_out<<<blocks_for(n3, 256), 256, 0, s->stream>>>(n3, x, alpha, p, xtrial);
@@ -734,6 +739,8 @@ extern "C" yasps_status yasps_step(yasps_system* s, double* x, double* v, yasps_
     }
     CK(s, cudaMemcpyAsync(x, xtrial, sizeof(double) * n3, cudaMemcpyDeviceToDevice, s->stream));
     st.alpha_last = alpha;
+    E_acc = E1;
+    have_E = true;
   }
   if (rc == YASPS_OK && it == s->prm.newton_max_iter) {
     s->err = "Newton hit its iteration cap";
@@ -979,7 +986,7 @@ static yasps_status step_batched(yasps_system* s, double* x, double* v, yasps_st
     for (int k = 0; k < ns; ++k)
       if (done[k]) alpha[k] = 0.0;
     cudaEvent_t pl = prof_begin(s);
-    RC(energy_scenes(s, x, xtil, E0));
+    if (it == 0) RC(energy_scenes(s, x, xtil, E0));  // later: the energies the last line search accepted
     std::vector<char> acc(ns, 0);
     for (int k = 0; k < ns; ++k) acc[k] = done[k];
     int ls = 0;
@@ -1016,6 +1023,9 @@ static yasps_status step_batched(yasps_system* s, double* x, double* v, yasps_st
     prof_end(s, YASPS_STAGE_LS, pl, 0.0);
     st.n_cand_pt = s->ncpt;
     st.n_cand_ee = s->ncee;
+    // energies at the new x: accepted trials; scenes that did not move keep E0
+    for (int k = 0; k < ns; ++k)
+      if (alpha[k] != 0.0) E0[k] = E1[k];
     CK(s, cudaMemcpyAsync(x, xtrial, sizeof(double) * n3, cudaMemcpyDeviceToDevice, s->stream));
     st.alpha_last = *std::max_element(alpha.begin(), alpha.end());
   }
