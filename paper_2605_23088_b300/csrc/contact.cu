@@ -899,10 +899,15 @@ __global__ void k_reduce_ksum(const ksum* __restrict__ part, int n, double* __re
 // pair that comes within dhat anywhere on the segment, and every pair the CCD
 // must examine, is in the list.  mode 0: count per query primitive, mode 1:
 // write (a, b) sorted by b.
+// mode 3: one traversal that counts every candidate of query i into cnt[i]
+// and keeps the first kCandSlots partners in tmp[i][.]; k_cand_gather then
+// writes the queries that fit, and only overflowing queries run mode 1.
+constexpr int kCandSlots = 16;
 __global__ void k_cand_query(int total, int kind, int nA, topo T, grid_dev g, boxes A, int mode, int* __restrict__ cnt,
-                             const int* __restrict__ off, int* __restrict__ out) {
+                             const int* __restrict__ off, int* __restrict__ out, int* __restrict__ tmp = nullptr) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nA) return;
+  if (mode == 1 && tmp && off[i + 1] - off[i] <= kCandSlots) return;  // written by k_cand_gather
   int c = 0;
   const int base = (mode == 1) ? off[i] : 0;
   const int lim = (mode == 1) ? ((i + 1 < nA) ? off[i + 1] : total) : 0;
@@ -918,10 +923,12 @@ __global__ void k_cand_query(int total, int kind, int nA, topo T, grid_dev g, bo
       if (base + c >= lim) { dev_flag(T.status, DEV_CAPACITY); return; }
       out[2 * (size_t)(base + c)] = a;
       out[2 * (size_t)(base + c) + 1] = j;
+    } else if (mode == 3 && c < kCandSlots) {
+      tmp[(size_t)i * kCandSlots + c] = j;
     }
     ++c;
   });
-  if (mode == 0) cnt[i] = c;
+  if (mode == 0 || mode == 3) cnt[i] = c;
   if (mode == 1) {
     c = min(c, lim - base);
     int* o = out + 2 * (size_t)base;
@@ -931,6 +938,27 @@ __global__ void k_cand_query(int total, int kind, int nA, topo T, grid_dev g, bo
       while (r >= 0 && o[2 * r + 1] > kb) { o[2 * (r + 1) + 1] = o[2 * r + 1]; --r; }
       o[2 * (r + 1) + 1] = kb;
     }
+  }
+}
+
+// queries whose partners all fit in tmp: sorted by partner id into place
+__global__ void k_cand_gather(int kind, int nA, topo T, const int* __restrict__ cnt_off, const int* __restrict__ tmp,
+                              int* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nA) return;
+  const int base = cnt_off[i], c = cnt_off[i + 1] - base;
+  if (c == 0 || c > kCandSlots) return;
+  int b[kCandSlots];
+  for (int q = 0; q < c; ++q) {
+    const int kb = tmp[(size_t)i * kCandSlots + q];
+    int r = q - 1;
+    while (r >= 0 && b[r] > kb) { b[r + 1] = b[r]; --r; }
+    b[r + 1] = kb;
+  }
+  const int a = (kind == 0) ? T.svert[i] : i;
+  for (int q = 0; q < c; ++q) {
+    out[2 * (size_t)(base + q)] = a;
+    out[2 * (size_t)(base + q) + 1] = b[q];
   }
 }
 
@@ -1360,17 +1388,24 @@ yasps_status swept_candidates(yasps_system* s, const double* x, const double* p)
     }
     grid_dev g;
     RC(build_grid(s, nB, bb.b, &g));
-    ENSURE(s, s->ws[2], sizeof(int) * (nA + 1));
+    ENSURE(s, s->ws[2], sizeof(int) * (nA + 2));
+    ENSURE(s, s->ws[10], sizeof(int) * ((size_t)nA * kCandSlots + 1));
     int* cnt = as<int>(s->ws[2]);
-    k_cand_query<<<blocks_for(nA, 128), 128, 0, s->stream>>>(0, kind, nA, Tp, g, bb.a, 0, cnt, nullptr, nullptr);
+    int* tmp = as<int>(s->ws[10]);
+    // one traversal: exact counts, the first kCandSlots partners kept
+    k_cand_query<<<blocks_for(nA, 128), 128, 0, s->stream>>>(0, kind, nA, Tp, g, bb.a, 3, cnt, nullptr, nullptr, tmp);
     LAUNCH_CHECK(s, "k_cand_query");
     int total = 0;
     RC(scan_exclusive(s, cnt, cnt, nA, &total));
+    CK(s, cudaMemcpyAsync(cnt + nA, &total, sizeof(int), cudaMemcpyHostToDevice, s->stream));
     gbuf& out = kind == 0 ? s->cpt : s->cee;
     ENSURE(s, out, sizeof(int) * 2 * ((size_t)total + 1));
     if (total > 0) {
+      k_cand_gather<<<blocks_for(nA, 256), 256, 0, s->stream>>>(kind, nA, Tp, cnt, tmp, as<int>(out));
+      LAUNCH_CHECK(s, "k_cand_gather");
+      // queries with more partners than slots traverse again and write in place
       k_cand_query<<<blocks_for(nA, 128), 128, 0, s->stream>>>(total, kind, nA, Tp, g, bb.a, 1, nullptr, cnt,
-                                                               as<int>(out));
+                                                               as<int>(out), tmp);
       LAUNCH_CHECK(s, "k_cand_query");
     }
     (kind == 0 ? s->ncpt : s->ncee) = total;
