@@ -539,15 +539,28 @@ __device__ __forceinline__ void unit_range(int i, int nfree, int& cnt, size_t& o
   o = (i < nfree) ? 3 * (size_t)i : 3 * ((size_t)nfree + 4 * (size_t)(i - nfree));
 }
 
-// own node i in phase B: d'_i = z_i + beta d_i, q_i += D_i d'_i; d'_i^T D_i d'_i
-template <typename T, typename V>
-__device__ __forceinline__ V diag_node(const pcg_args<T, V>& a, long long i, V beta, const V* d, V* dn) {
+// own node i in phase B: d'_i = z_i + beta d_i, q_i += D_i d'_i; d'_i^T D_i d'_i.
+// DEFER: the previous iteration's x_i += alpha d_i happens here, where d_i is
+// read anyway (the owning thread is the one that wrote d_i), instead of in
+// phase C; the last one is applied after the loop.
+template <typename T, typename V, bool DEFER>
+__device__ __forceinline__ V diag_node(const pcg_args<T, V>& a, long long i, V beta, V alpha_prev, const V* d,
+                                       V* dn) {
   const T* B = a.D + 9 * (size_t)i;
   T m[9];
 #pragma unroll
   for (int t = 0; t < 9; ++t) m[t] = __ldg(B + t);
   const V z0 = a.z[3 * i], z1 = a.z[3 * i + 1], z2 = a.z[3 * i + 2];
   const V e0 = d[3 * i], e1 = d[3 * i + 1], e2 = d[3 * i + 2];
+  if constexpr (DEFER) {
+    if (alpha_prev != V(0)) {
+      V* x = a.x + 3 * i;
+      const V x0 = x[0], x1 = x[1], x2 = x[2];
+      x[0] = x0 + alpha_prev * e0;
+      x[1] = x1 + alpha_prev * e1;
+      x[2] = x2 + alpha_prev * e2;
+    }
+  }
   const V d0 = dnew(z0, beta, e0), d1 = dnew(z1, beta, e1), d2 = dnew(z2, beta, e2);
   const V q0 = (V)m[0] * d0 + (V)m[1] * d1 + (V)m[2] * d2;
   const V q1 = (V)m[3] * d0 + (V)m[4] * d1 + (V)m[5] * d2;
@@ -556,8 +569,9 @@ __device__ __forceinline__ V diag_node(const pcg_args<T, V>& a, long long i, V b
   q_add3(a.q, (int)i, q0, q1, q2);
   return d0 * q0 + d1 * q1 + d2 * q2;
 }
-// phase C for one free node: x += alpha d', r -= alpha q, z = M^-1 r, q = 0; r^T z
-template <typename T, typename V>
+// phase C for one free node: x += alpha d' (unless DEFER), r -= alpha q,
+// z = M^-1 r, q = 0; r^T z
+template <typename T, typename V, bool DEFER>
 __device__ __forceinline__ V update_free(const pcg_args<T, V>& a, long long i, V alpha, const V* dn) {
   const T* M = a.Mi + 9 * (size_t)i;
   T m[9];
@@ -566,15 +580,17 @@ __device__ __forceinline__ V update_free(const pcg_args<T, V>& a, long long i, V
   V xv[3], dv[3], rv[3], qv[3];
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
-    xv[c] = a.x[3 * i + c];
-    dv[c] = dn[3 * i + c];
+    if constexpr (!DEFER) {
+      xv[c] = a.x[3 * i + c];
+      dv[c] = dn[3 * i + c];
+    }
     rv[c] = a.r[3 * i + c];
   }
   q_take3(a.q, i, qv);
   V zv[3], acc = 0;
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
-    xv[c] += alpha * dv[c];
+    if constexpr (!DEFER) xv[c] += alpha * dv[c];
     rv[c] -= alpha * qv[c];
   }
 #pragma unroll
@@ -584,7 +600,7 @@ __device__ __forceinline__ V update_free(const pcg_args<T, V>& a, long long i, V
   }
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
-    a.x[3 * i + c] = xv[c];
+    if constexpr (!DEFER) a.x[3 * i + c] = xv[c];
     a.r[3 * i + c] = rv[c];
     a.z[3 * i + c] = zv[c];
   }
@@ -783,6 +799,8 @@ __global__ void __launch_bounds__(CFG::NTHR, CFG::MINB) k_pcg_persistent(pcg_arg
     if (!done && !(rz > 0.0)) done = 1;
   }
 
+  V apend = 0;            // single system: x += apend * dpend still to do on own nodes
+  const V* dpend = a.d0;
   while (!done && it < a.maxit) {
     V* d = (it & 1) ? a.d1 : a.d0;   // previous direction
     V* dn = (it & 1) ? a.d0 : a.d1;  // this iteration's direction
@@ -804,7 +822,9 @@ __global__ void __launch_bounds__(CFG::NTHR, CFG::MINB) k_pcg_persistent(pcg_arg
     acc = 0;
     wacc wa;
     if constexpr (!BATCH) {
-      for (long long i = n0 + threadIdx.x; i < n1; i += blockDim.x) acc += diag_node(a, i, vb, d, dn);
+      for (long long i = n0 + threadIdx.x; i < n1; i += blockDim.x)
+        acc += diag_node<T, V, true>(a, i, vb, apend, d, dn);
+      apend = 0;
     } else {
       for (int t = threadIdx.x; t < a.nscene; t += blockDim.x) tab[t] = beta_of(t);
       __syncthreads();
@@ -814,7 +834,7 @@ __global__ void __launch_bounds__(CFG::NTHR, CFG::MINB) k_pcg_persistent(pcg_arg
         V v = 0;
         if (i < n1) {
           key = a.node_scene[i];
-          v = diag_node(a, i, tab[key], d, dn);
+          v = diag_node<T, V, false>(a, i, tab[key], V(0), d, dn);
         }
         wacc_add(wa, shs, key, v, lane);
       }
@@ -899,9 +919,11 @@ __global__ void __launch_bounds__(CFG::NTHR, CFG::MINB) k_pcg_persistent(pcg_arg
     acc = 0;
     if constexpr (!BATCH) {
       for (long long i = tid; i < a.nfree; i += 2 * nthr) {
-        acc += update_free(a, i, alpha, dn);
-        if (i + nthr < a.nfree) acc += update_free(a, i + nthr, alpha, dn);
+        acc += update_free<T, V, true>(a, i, alpha, dn);
+        if (i + nthr < a.nfree) acc += update_free<T, V, true>(a, i + nthr, alpha, dn);
       }
+      apend = alpha;  // x += alpha d' in the next own-node pass (or after the loop)
+      dpend = dn;
     } else {
       __syncthreads();  // everyone is done with the beta table
       for (int t = threadIdx.x; t < a.nscene; t += blockDim.x) tab[t] = alpha_of(t);
@@ -912,7 +934,7 @@ __global__ void __launch_bounds__(CFG::NTHR, CFG::MINB) k_pcg_persistent(pcg_arg
         V v = 0;
         if (i < a.nfree) {
           key = a.node_scene[i];
-          v = update_free(a, i, tab[key], dn);
+          v = update_free<T, V, false>(a, i, tab[key], dn);
         }
         wacc_add(wa, shs, key, v, lane);
       }
@@ -924,7 +946,7 @@ __global__ void __launch_bounds__(CFG::NTHR, CFG::MINB) k_pcg_persistent(pcg_arg
       V al = alpha;
       if constexpr (BATCH) al = tab[a.node_scene[a.nfree + 4 * bi]];
       for (int c = 0; c < 12; ++c) {
-        a.x[o + c] += al * dn[o + c];
+        if constexpr (BATCH) a.x[o + c] += al * dn[o + c];
         a.r[o + c] -= al * a.q[q_idx<V>(o + c)];
         a.q[q_idx<V>(o + c)] = 0;
       }
@@ -955,6 +977,13 @@ __global__ void __launch_bounds__(CFG::NTHR, CFG::MINB) k_pcg_persistent(pcg_arg
       const scene_view<T, V> nv{&a, cp, cpp, kc};
       if (count_active(nv) == 0) done = 1;
     }
+  }
+  if constexpr (!BATCH) {
+    // the last iteration's x update, on the nodes this thread owns (it wrote
+    // their d' itself)
+    if (apend != V(0))
+      for (long long i = n0 + threadIdx.x; i < n1; i += blockDim.x)
+        for (int c = 0; c < 3; ++c) a.x[3 * i + c] += apend * dpend[3 * i + c];
   }
   // a block that gave up may still have tile copies in flight: wait for them
   // (bounded) before the block exits
