@@ -323,14 +323,22 @@ __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
 // sees the flag, so no block waits forever.  Returns false when the grid has
 // aborted.  Float addition order in the slot follows arrival order, so totals
 // can differ in the last bits from run to run (never between blocks).
-__device__ __forceinline__ bool grid_reduce(pcg_bar* bar, unsigned& k, double partial, double& total,
-                                            long long spin_limit) {
+struct no_epilogue {
+  __device__ void operator()(double) const {}
+};
+// The block's partial (thread 0's value) joins the grid-wide sum; every block
+// gets the total.  epi(total) runs on thread 0 alone before the block is
+// released: scalar work on the total (divisions, tests) belongs there, since
+// FP64 arithmetic repeated by every thread of the grid is slow on this part.
+template <typename P, typename F = no_epilogue>
+__device__ __forceinline__ bool grid_reduce(pcg_bar* bar, unsigned& k, P partial, double& total,
+                                            long long spin_limit, F epi = F{}) {
   __shared__ int ok;
   __shared__ double tot;
   __syncthreads();
   if (threadIdx.x == 0) {
     int good = 1;
-    atomicAdd(&bar->sum[k & 3], partial);
+    atomicAdd(&bar->sum[k & 3], (double)partial);
     red_add_release(&bar->count, 1u);
     const unsigned target = (k + 1) * gridDim.x;
     long long spins = 0;
@@ -343,6 +351,7 @@ __device__ __forceinline__ bool grid_reduce(pcg_bar* bar, unsigned& k, double pa
     tot = *(volatile double*)&bar->sum[k & 3];
     if (blockIdx.x == 0 && k > 0) bar->sum[(k - 1) & 3] = 0.0;
     ok = good && !*(volatile int*)&bar->abort;
+    if (ok) epi(tot);
   }
   __syncthreads();
   k += 1;
@@ -775,9 +784,17 @@ __global__ void __launch_bounds__(CFG::NTHR, CFG::MINB) k_pcg_persistent(pcg_arg
   V bs = block_sum_v<V>(acc);
   int done = 0, it = 0;
   double rz = 0.0;
-  if (!grid_reduce(a.bar, kbar, (double)bs, rz, a.spin_limit)) done = 3;
+  // single system: alpha, beta and the stopping test are thread 0's work,
+  // handed to the block through shared memory
+  __shared__ V s_alpha, s_beta;
+  __shared__ int s_done;
+  if (threadIdx.x == 0) s_done = 0;
+  if (!grid_reduce(a.bar, kbar, bs, rz, a.spin_limit, [&](double t) {
+        if (!BATCH && !(t > 0.0)) s_done = 1;
+      }))
+    done = 3;
   const double rz0 = rz;
-  double beta = 0.0;
+  V vb_next = 0;  // single system: beta of the next iteration
   int cp = 0, cpp = 0;  // batches: ring rows of the last and the previous r^T z
   if constexpr (BATCH) {
     if (!done) {
@@ -796,7 +813,7 @@ __global__ void __launch_bounds__(CFG::NTHR, CFG::MINB) k_pcg_persistent(pcg_arg
       if (sh_active == 0) done = 1;
     }
   } else {
-    if (!done && !(rz > 0.0)) done = 1;
+    if (!done) done = s_done;
   }
 
   V apend = 0;            // single system: x += apend * dpend still to do on own nodes
@@ -804,7 +821,7 @@ __global__ void __launch_bounds__(CFG::NTHR, CFG::MINB) k_pcg_persistent(pcg_arg
   while (!done && it < a.maxit) {
     V* d = (it & 1) ? a.d1 : a.d0;   // previous direction
     V* dn = (it & 1) ? a.d0 : a.d1;  // this iteration's direction
-    const V vb = (V)beta;
+    const V vb = vb_next;
     const scene_view<T, V> sv{&a, cp, cpp, (int)(kbar & 7)};
     // batches: beta of scene sc (0 in the first iteration and once finished)
     auto beta_of = [&](int sc) -> V {
@@ -897,13 +914,21 @@ __global__ void __launch_bounds__(CFG::NTHR, CFG::MINB) k_pcg_persistent(pcg_arg
     if (clock0) { const unsigned long long t = global_ns(); tph[1] += t - tlast; tlast = t; }
     double dHd = 0.0;
     const int kb = (int)(kbar & 7);
-    if (!grid_reduce(a.bar, kbar, (double)bs, dHd, a.spin_limit)) { done = 3; break; }
+    if (!grid_reduce(a.bar, kbar, bs, dHd, a.spin_limit, [&](double t) {
+          if constexpr (!BATCH) {
+            if (!(t > 0.0)) s_done = 2;
+            else s_alpha = (V)(rz / t);
+          }
+        })) {
+      done = 3;
+      break;
+    }
     after_barrier(kbar - 1);
     if (clock0) { const unsigned long long t = global_ns(); tph[2] += t - tlast; tlast = t; }
     V alpha = 0;
     if constexpr (!BATCH) {
-      if (!(dHd > 0.0)) { done = 2; break; }
-      alpha = (V)(rz / dHd);
+      if (s_done) { done = s_done; break; }
+      alpha = s_alpha;
     }
     // batches: alpha of scene sc (0 once finished; a breakdown finishes it)
     auto alpha_of = [&](int sc) -> V {
@@ -959,14 +984,22 @@ __global__ void __launch_bounds__(CFG::NTHR, CFG::MINB) k_pcg_persistent(pcg_arg
     if (clock0) { const unsigned long long t = global_ns(); tph[3] += t - tlast; tlast = t; }
     double rz_new = 0.0;
     const int kc = (int)(kbar & 7);
-    if (!grid_reduce(a.bar, kbar, (double)bs, rz_new, a.spin_limit)) { done = 3; break; }
+    if (!grid_reduce(a.bar, kbar, bs, rz_new, a.spin_limit, [&](double t) {
+          if constexpr (!BATCH) {
+            s_beta = (V)(t / rz);
+            if (t <= a.tol2 * rz0) s_done = 1;
+          }
+        })) {
+      done = 3;
+      break;
+    }
     after_barrier(kbar - 1);
     if (clock0) { const unsigned long long t = global_ns(); tph[4] += t - tlast; tlast = t; }
     ++it;
     if constexpr (!BATCH) {
-      beta = rz_new / rz;
-      rz = rz_new;
-      if (rz <= a.tol2 * rz0) done = 1;
+      vb_next = s_beta;
+      rz = rz_new;  // a register copy; only thread 0 of block 0 reports it
+      done = s_done;
     } else {
       // iterations per scene: scenes that were still running this iteration
       if (blockIdx.x == 0)
