@@ -1600,14 +1600,26 @@ OR_EXPORT double or_ccd_bound(void* p, const double* x, const double* dir, int b
     }
   }
   /* PT and EE candidates: swept boxes over the full step, grown by dhat on
-   * the query side */
+   * the query side, taken in the frame that moves with the mean vertex
+   * displacement u (end positions P1 - u).  A translation common to every
+   * vertex changes no distance at any time of the step, so these boxes hold
+   * every pair that comes within dhat, as boxes swept in place do; the
+   * candidate set, and with it the bound, no longer depends on how fast the
+   * scene moves as a whole. */
+  double u[3] = {0.0, 0.0, 0.0};
+  for (int i = 0; i < nv; ++i)
+    for (int c = 0; c < 3; ++c) u[c] += D[3 * i + c];
+  for (int c = 0; c < 3; ++c) u[c] /= (nv > 0 ? nv : 1);
+  double* P1s = malloc(sizeof(double) * 3 * nv);
+  for (int i = 0; i < nv; ++i)
+    for (int c = 0; c < 3; ++c) P1s[3 * i + c] = P1[3 * i + c] - u[c];
   int nmax = S->nsv > S->nst ? S->nsv : S->nst;
   if (S->nse > nmax) nmax = S->nse;
   double *alo = malloc(sizeof(double) * 3 * (nmax + 1)), *ahi = malloc(sizeof(double) * 3 * (nmax + 1));
   double *blo = malloc(sizeof(double) * 3 * (nmax + 1)), *bhi = malloc(sizeof(double) * 3 * (nmax + 1));
   cand C = {0};
-  prim_boxes(P0, P1, S->sverts, S->nsv, 1, S->dhat, alo, ahi);
-  prim_boxes(P0, P1, S->stris, S->nst, 3, 0.0, blo, bhi);
+  prim_boxes(P0, P1s, S->sverts, S->nsv, 1, S->dhat, alo, ahi);
+  prim_boxes(P0, P1s, S->stris, S->nst, 3, 0.0, blo, bhi);
   box_pairs(S->nsv, alo, ahi, S->nst, blo, bhi, 0, brute, &C);
   for (long q = 0; q < C.n; ++q) {
     int v = S->sverts[C.a[q]];
@@ -1620,8 +1632,8 @@ OR_EXPORT double or_ccd_bound(void* p, const double* x, const double* dir, int b
     double tk = or_accd(0, xl, dl, S->gap_s, 1.0, S->ccd_max_iter, NULL);
     if (tk < t) t = tk;
   }
-  prim_boxes(P0, P1, S->sedges, S->nse, 2, S->dhat, alo, ahi);
-  prim_boxes(P0, P1, S->sedges, S->nse, 2, 0.0, blo, bhi);
+  prim_boxes(P0, P1s, S->sedges, S->nse, 2, S->dhat, alo, ahi);
+  prim_boxes(P0, P1s, S->sedges, S->nse, 2, 0.0, blo, bhi);
   box_pairs(S->nse, alo, ahi, S->nse, blo, bhi, 1, brute, &C);
   for (long q = 0; q < C.n; ++q) {
     const int *e = S->sedges + 2 * C.a[q], *f = S->sedges + 2 * C.b[q];
@@ -1634,7 +1646,7 @@ OR_EXPORT double or_ccd_bound(void* p, const double* x, const double* dir, int b
     if (tk < t) t = tk;
   }
   free(C.a); free(C.b); free(alo); free(ahi); free(blo); free(bhi);
-  free(P0); free(P1); free(D); free(x1);
+  free(P0); free(P1); free(P1s); free(D); free(x1);
   return t;
 }
 

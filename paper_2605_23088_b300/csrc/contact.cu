@@ -20,6 +20,7 @@
 //  * the CCD step bound: additive CCD (Li, Kaufman and Jiang 2021, ACCD) on
 //    swept-box candidates, exact for point-plane pairs.
 #include <algorithm>
+#include <cfloat>
 #include <cmath>
 
 #include "common.cuh"
@@ -59,6 +60,14 @@ struct boxw {
   // across scenes are excluded anyway, so this only saves work
   const int* vscene;
   double spacing;
+  // swept boxes: per-scene sums of the vertex displacements (x, y, z, count
+  // in rows of nsc) or null.  The end positions are moved back by their
+  // scene's mean displacement: a common translation of every vertex changes
+  // no distance at any time of the step, so boxes swept in that moving frame
+  // are as conservative as boxes swept in place, and much smaller when a
+  // scene moves as a whole (a falling pile)
+  const double* shift;
+  int nsc;
   operator boxes() const { return boxes{lo, hi, lof, hif}; }
 };
 __device__ __forceinline__ void scene_offset(int sc, double spacing, double* off) {
@@ -82,13 +91,29 @@ __global__ void k_boxes(int n, int k, const int* __restrict__ idx, const double*
     for (int c = 0; c < 3; ++c) { l[c] = fmin(l[c], P0[3 * v + c]); h[c] = fmax(h[c], P0[3 * v + c]); }
   }
   if (P1) {
+    double u[3] = {0.0, 0.0, 0.0};
+    if (out.shift) {
+      const int sc = out.vscene ? out.vscene[v0] : 0;
+      const double cnt = out.shift[3 * out.nsc + sc];
+      if (cnt > 0.0)
+        for (int c = 0; c < 3; ++c) u[c] = out.shift[c * out.nsc + sc] / cnt;
+    }
     double l1[3], h1[3];
-    for (int c = 0; c < 3; ++c) l1[c] = h1[c] = P1[3 * v0 + c];
+    for (int c = 0; c < 3; ++c) l1[c] = h1[c] = P1[3 * v0 + c] - u[c];
     for (int a = 1; a < k; ++a) {
       const int v = idx[k * e + a];
-      for (int c = 0; c < 3; ++c) { l1[c] = fmin(l1[c], P1[3 * v + c]); h1[c] = fmax(h1[c], P1[3 * v + c]); }
+      for (int c = 0; c < 3; ++c) {
+        const double q = P1[3 * v + c] - u[c];
+        l1[c] = fmin(l1[c], q);
+        h1[c] = fmax(h1[c], q);
+      }
     }
-    for (int c = 0; c < 3; ++c) { l[c] = fmin(l[c], l1[c]); h[c] = fmax(h[c], h1[c]); }
+    for (int c = 0; c < 3; ++c) {
+      // the rounding of P1 - u: a few ulps of the operands
+      const double r = out.shift ? 4.0 * DBL_EPSILON * (fmax(fabs(l1[c]), fabs(h1[c])) + fabs(u[c])) : 0.0;
+      l[c] = fmin(l[c], l1[c] - r);
+      h[c] = fmax(h[c], h1[c] + r);
+    }
   }
   double off[3] = {0.0, 0.0, 0.0};
   if (out.vscene) scene_offset(out.vscene[v0], out.spacing, off);
@@ -98,6 +123,43 @@ __global__ void k_boxes(int n, int k, const int* __restrict__ idx, const double*
     hi[3 * e + c] = hc;
     out.lof[3 * e + c] = __double2float_rd(lc);
     out.hif[3 * e + c] = __double2float_ru(hc);
+  }
+}
+
+// per-scene sums of the vertex displacements D and vertex counts into
+// acc[4][ns] (rows x, y, z, count).  One scene: per-block sums, one atomic per
+// block and row; batches (vertices sorted by scene): one atomic per run of a
+// scene within a warp
+__global__ void k_disp_sum(int nv, const double* __restrict__ D, const int* __restrict__ vscene, int ns,
+                           double* __restrict__ acc) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  const int lane = threadIdx.x & 31;
+  if (!vscene) {
+    double t[4] = {0.0, 0.0, 0.0, 0.0};
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < nv; i += stride) {
+      for (int c = 0; c < 3; ++c) t[c] += D[3 * i + c];
+      t[3] += 1.0;
+    }
+    __shared__ double sh[4][32];
+    for (int c = 0; c < 4; ++c) {
+      double v = t[c];
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (lane == 0) sh[c][threadIdx.x >> 5] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 4) {
+      double v = 0.0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += sh[threadIdx.x][w];
+      atomicAdd(acc + threadIdx.x, v);
+    }
+    return;
+  }
+  for (long long base = ((long long)blockIdx.x * blockDim.x + threadIdx.x) & ~31LL; base < nv; base += stride) {
+    const long long i = base + lane;
+    const bool in = i < nv;
+    const int key = in ? vscene[i] : -1;
+    for (int c = 0; c < 3; ++c) seg_add_global(acc + (size_t)c * ns, key, in ? D[3 * i + c] : 0.0);
+    seg_add_global(acc + 3 * (size_t)ns, key, in ? 1.0 : 0.0);
   }
 }
 
@@ -550,22 +612,132 @@ struct bar_ws {
   T cs[6], sn[6];
   double W[4][16];
   double db, d2b;
+  dist::wn_scratch wn;  // point-plane / line-line derivatives, formed by the whole warp
+  d3 yl[4];
   int ids[4], loc[4];
-  int n, active, m, node[16];
+  int n, active, m, node[16], dtype;
 };
 
+// Project(A) = V max(Lambda, 0) V^T for the N x N symmetric A in shared
+// memory (row-major), by one warp: cyclic Jacobi with N/2 disjoint rotations
+// per step in the round-robin order (N - 1 steps per sweep), the same rotation
+// formula and stopping rule as project_psd; then the product, upper triangle
+// first, mirrored.  N is a compile-time size (6, 9, 12: PP, PE, PT/EE), so the
+// index arithmetic of the sweeps is constant divisions.
+template <typename T, int N>
+__device__ void warp_project(T* A, T* V, T* cs, T* sn, int lane) {
+  constexpr int NP = N + (N & 1);  // even count for the round-robin (index N is a dummy when N is odd)
+  constexpr int M = NP / 2;
+  for (int e = lane; e < N * N; e += 32) V[e] = (e / N == e % N) ? T(1) : T(0);
+  __syncwarp();
+  // the pair (a, b), a < b, of rotation i in step st
+  auto rot = [](int st, int i, int& pp, int& qq) {
+    const int a = (i == 0) ? 0 : 1 + (st + i) % (NP - 1);
+    const int b = (i == 0) ? 1 + st : 1 + (st - i + NP - 1) % (NP - 1);
+    pp = min(a, b);
+    qq = max(a, b);
+  };
+  for (int sweep = 0; sweep < eig_traits<T>::max_sweeps; ++sweep) {
+    T off = 0, tot = 0;
+    for (int e = lane; e < N * N; e += 32) {
+      const int r = e / N, c = e % N;
+      const T a = A[e];
+      if (r == c) tot += a * a;
+      else if (r < c) off += a * a;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      off += __shfl_xor_sync(0xffffffffu, off, o);
+      tot += __shfl_xor_sync(0xffffffffu, tot, o);
+    }
+    tot += T(2) * off;
+    if (!(off > eig_traits<T>::rel_eps2 * tot)) break;
+    for (int st = 0; st < NP - 1; ++st) {
+      if (lane < M) {
+        int pp, qq;
+        rot(st, lane, pp, qq);
+        T c = 1, sg = 0;
+        if (qq < N) {
+          const T apq = A[pp * N + qq];
+          if (apq != T(0)) {
+            const T theta = (A[qq * N + qq] - A[pp * N + pp]) / (T(2) * apq);
+            const T t = (theta >= T(0) ? T(1) : T(-1)) / (fabs(theta) + sqrt(theta * theta + T(1)));
+            c = jacobi_c(t);
+            sg = t * c;
+          }
+        }
+        cs[lane] = c;
+        sn[lane] = sg;
+      }
+      __syncwarp();
+      // columns of A and V: A <- A J, V <- V J
+      for (int e = lane; e < M * N; e += 32) {
+        const int i = e / N, k = e % N;
+        int pp, qq;
+        rot(st, i, pp, qq);
+        const T c = cs[i], sg = sn[i];
+        if (qq >= N || sg == T(0)) continue;
+        const T akp = A[k * N + pp], akq = A[k * N + qq];
+        A[k * N + pp] = c * akp - sg * akq;
+        A[k * N + qq] = sg * akp + c * akq;
+        const T vkp = V[k * N + pp], vkq = V[k * N + qq];
+        V[k * N + pp] = c * vkp - sg * vkq;
+        V[k * N + qq] = sg * vkp + c * vkq;
+      }
+      __syncwarp();
+      // rows of A: A <- J^T A
+      for (int e = lane; e < M * N; e += 32) {
+        const int i = e / N, k = e % N;
+        int pp, qq;
+        rot(st, i, pp, qq);
+        const T c = cs[i], sg = sn[i];
+        if (qq >= N || sg == T(0)) continue;
+        const T apk = A[pp * N + k], aqk = A[qq * N + k];
+        A[pp * N + k] = c * apk - sg * aqk;
+        A[qq * N + k] = sg * apk + c * aqk;
+      }
+      __syncwarp();
+    }
+  }
+  T lam[N];
+#pragma unroll
+  for (int k = 0; k < N; ++k) lam[k] = (A[k * N + k] > T(0)) ? A[k * N + k] : T(0);
+  __syncwarp();
+  constexpr int NO = (N * N + 31) / 32;  // entries a lane visits (upper ones kept)
+  T outv[NO];
+  int oute[NO];
+  int no = 0;
+  for (int e = lane; e < N * N; e += 32) {
+    const int r = e / N, c = e % N;
+    if (r > c) continue;
+    T acc = 0;
+#pragma unroll
+    for (int k = 0; k < N; ++k) acc += V[r * N + k] * lam[k] * V[c * N + k];
+    outv[no] = acc;
+    oute[no] = e;
+    ++no;
+  }
+  __syncwarp();
+  for (int q = 0; q < no; ++q) {
+    const int e = oute[q], r = e / N, c = e % N;
+    A[r * N + c] = outv[q];
+    A[c * N + r] = outv[q];
+  }
+  __syncwarp();
+}
+
 template <typename T>
-__global__ void __launch_bounds__(128) k_barrier_w(int kind, int npairs, int pair_base, const int* __restrict__ pairs,
+__global__ void __launch_bounds__(32) k_barrier_w(int kind, int npairs, int pair_base, const int* __restrict__ pairs,
                                                    topo Tp, const double* __restrict__ vr, const double* __restrict__ P,
                                                    double sh, double kappa, int form, int project,
                                                    const int* __restrict__ koff, const int* __restrict__ dslot,
                                                    double* __restrict__ g, T* __restrict__ diag, T* __restrict__ vals,
                                                    int* status) {
-  __shared__ bar_ws<T> wsa[4];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const int p = blockIdx.x * 4 + wid;
+  // one pair per block of one warp: a few hundred pairs still reach every SM
+  __shared__ bar_ws<T> w;
+  const int lane = threadIdx.x & 31;
+  const int p = blockIdx.x;
   if (p >= npairs) return;  // warp-uniform
-  bar_ws<T>& w = wsa[wid];
   if (lane == 0) {
     int k;
     pair_vertices(kind, p, pairs, Tp, w.ids, &k);
@@ -581,17 +753,14 @@ __global__ void __launch_bounds__(128) k_barrier_w(int kind, int npairs, int pai
       w.db = bd.db;
       w.d2b = bd.d2b;
       w.n = dc.n;
-      d3 yl[4];
       for (int q = 0; q < dc.n; ++q) {
-        yl[q] = y[dc.loc[q]];
+        w.yl[q] = y[dc.loc[q]];
         w.loc[q] = dc.loc[q];
       }
-      switch (dc.dtype) {
-        case dist::PP: dist::ds_pp(yl, w.gs, w.Hs); break;
-        case dist::PE: dist::ds_pe(yl, w.gs, w.Hs); break;
-        case dist::PT: dist::ds_pt(yl, w.gs, w.Hs); break;
-        default: dist::ds_ee(yl, w.gs, w.Hs); break;
-      }
+      w.dtype = dc.dtype;
+      // point-plane and line-line derivatives are formed by the whole warp below
+      if (dc.dtype == dist::PP) dist::ds_pp(w.yl, w.gs, w.Hs);
+      else if (dc.dtype == dist::PE) dist::ds_pe(w.yl, w.gs, w.Hs);
       // merged node set and the UNION weights of the classified vertices
       const nodeset S = pair_nodes(w.ids, k, Tp.vnode, Tp.vbody, vr);
       w.m = S.m;
@@ -609,109 +778,24 @@ __global__ void __launch_bounds__(128) k_barrier_w(int kind, int npairs, int pai
   }
   __syncwarp();
   if (!w.active) return;  // warp-uniform
+  if (w.dtype == dist::PT) {
+    const double coef[3][4] = {{1, -1, 0, 0}, {0, -1, 1, 0}, {0, -1, 0, 1}};
+    dist::ds_wn_warp(w.yl[0] - w.yl[1], w.yl[2] - w.yl[1], w.yl[3] - w.yl[1], coef, w.wn, w.gs, w.Hs, lane);
+  } else if (w.dtype == dist::EE) {
+    const double coef[3][4] = {{1, 0, -1, 0}, {-1, 1, 0, 0}, {0, 0, -1, 1}};
+    dist::ds_wn_warp(w.yl[0] - w.yl[2], w.yl[1] - w.yl[0], w.yl[3] - w.yl[2], coef, w.wn, w.gs, w.Hs, lane);
+  }
   const int n3 = 3 * w.n;
   const double db = w.db, d2b = w.d2b;
   for (int e = lane; e < n3 * n3; e += 32) {
     const int r = e / n3, c = e % n3;
     w.A[e] = (T)(kappa * (d2b * w.gs[r] * w.gs[c] + db * w.Hs[e]));
-    w.V[e] = (r == c) ? T(1) : T(0);
   }
   __syncwarp();
   if (project) {
-    const int np = n3 + (n3 & 1);  // even count for the round-robin (index n3 is a dummy when n3 is odd)
-    const int m = np / 2;
-    for (int sweep = 0; sweep < eig_traits<T>::max_sweeps; ++sweep) {
-      T off = 0, tot = 0;
-      for (int e = lane; e < n3 * n3; e += 32) {
-        const int r = e / n3, c = e % n3;
-        const T a = w.A[e];
-        if (r == c) tot += a * a;
-        else if (r < c) off += a * a;
-      }
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        off += __shfl_xor_sync(0xffffffffu, off, o);
-        tot += __shfl_xor_sync(0xffffffffu, tot, o);
-      }
-      tot += T(2) * off;
-      if (!(off > eig_traits<T>::rel_eps2 * tot)) break;
-      for (int step = 0; step < np - 1; ++step) {
-        // rotation i of this step: indices (a_i, b_i), disjoint over i
-        if (lane < m) {
-          int a = (lane == 0) ? 0 : 1 + (step + lane) % (np - 1);
-          int b = (lane == 0) ? 1 + step : 1 + (step - lane + np - 1) % (np - 1);
-          const int pp = min(a, b), qq = max(a, b);
-          T c = 1, sn = 0;
-          if (qq < n3) {
-            const T apq = w.A[pp * n3 + qq];
-            if (apq != T(0)) {
-              const T theta = (w.A[qq * n3 + qq] - w.A[pp * n3 + pp]) / (T(2) * apq);
-              const T t = (theta >= T(0) ? T(1) : T(-1)) / (fabs(theta) + sqrt(theta * theta + T(1)));
-              c = jacobi_c(t);
-              sn = t * c;
-            }
-          }
-          w.cs[lane] = c;
-          w.sn[lane] = sn;
-        }
-        __syncwarp();
-        // columns of A and V: A <- A J, V <- V J
-        for (int e = lane; e < m * n3; e += 32) {
-          const int i = e / n3, k = e % n3;
-          const int a = (i == 0) ? 0 : 1 + (step + i) % (np - 1);
-          const int b = (i == 0) ? 1 + step : 1 + (step - i + np - 1) % (np - 1);
-          const int pp = min(a, b), qq = max(a, b);
-          if (qq >= n3) continue;
-          const T c = w.cs[i], sn = w.sn[i];
-          if (sn == T(0)) continue;
-          const T akp = w.A[k * n3 + pp], akq = w.A[k * n3 + qq];
-          w.A[k * n3 + pp] = c * akp - sn * akq;
-          w.A[k * n3 + qq] = sn * akp + c * akq;
-          const T vkp = w.V[k * n3 + pp], vkq = w.V[k * n3 + qq];
-          w.V[k * n3 + pp] = c * vkp - sn * vkq;
-          w.V[k * n3 + qq] = sn * vkp + c * vkq;
-        }
-        __syncwarp();
-        // rows of A: A <- J^T A
-        for (int e = lane; e < m * n3; e += 32) {
-          const int i = e / n3, k = e % n3;
-          const int a = (i == 0) ? 0 : 1 + (step + i) % (np - 1);
-          const int b = (i == 0) ? 1 + step : 1 + (step - i + np - 1) % (np - 1);
-          const int pp = min(a, b), qq = max(a, b);
-          if (qq >= n3) continue;
-          const T c = w.cs[i], sn = w.sn[i];
-          if (sn == T(0)) continue;
-          const T apk = w.A[pp * n3 + k], aqk = w.A[qq * n3 + k];
-          w.A[pp * n3 + k] = c * apk - sn * aqk;
-          w.A[qq * n3 + k] = sn * apk + c * aqk;
-        }
-        __syncwarp();
-      }
-    }
-    // Project(H) = V max(Lambda, 0) V^T, written back over A (upper, then mirrored)
-    T lam[12];
-#pragma unroll
-    for (int k = 0; k < 12; ++k) lam[k] = (k < n3 && w.A[k * n3 + k] > T(0)) ? w.A[k * n3 + k] : T(0);
-    __syncwarp();
-    T outv[5];
-    int outi[5];
-    int no = 0;
-    for (int e = lane; e < n3 * n3; e += 32) {
-      const int r = e / n3, c = e % n3;
-      if (r > c) continue;
-      T acc = 0;
-      for (int k = 0; k < n3; ++k) acc += w.V[r * n3 + k] * lam[k] * w.V[c * n3 + k];
-      outv[no] = acc;
-      outi[no] = e;
-      ++no;
-    }
-    __syncwarp();
-    for (int q = 0; q < no; ++q) {
-      const int e = outi[q], r = e / n3, c = e % n3;
-      w.A[r * n3 + c] = outv[q];
-      w.A[c * n3 + r] = outv[q];
-    }
-    __syncwarp();
+    if (n3 == 12) warp_project<T, 12>(w.A, w.V, w.cs, w.sn, lane);
+    else if (n3 == 9) warp_project<T, 9>(w.A, w.V, w.cs, w.sn, lane);
+    else warp_project<T, 6>(w.A, w.V, w.cs, w.sn, lane);
   }
   // gradient rows of the merged nodes
   const int M = w.m;
@@ -1159,6 +1243,8 @@ yasps_status alloc_boxes(yasps_system* s, boxbufs* bb) {
     w.hif = w.lof + 3 * nmax;
     w.vscene = s->nscene > 1 ? as<int>(s->vscene) : nullptr;
     w.spacing = s->scene_spacing;
+    w.shift = nullptr;
+    w.nsc = s->nscene;
   }
   return YASPS_OK;
 }
@@ -1188,15 +1274,15 @@ yasps_status eval_barrier_t(yasps_system* s, int project) {
   const double* P = as<double>(s->P);
   const int* koff = as<int>(s->pair_key_off);
   const int* dslot = as<int>(s->dyn_slot);
-  // one warp per pair (4 pairs per block of 128)
+  // one warp per pair, one pair per block
   if (s->npt) {
-    k_barrier_w<T><<<blocks_for(s->npt, 4), 128, 0, s->stream>>>(0, s->npt, 0, as<int>(s->pt), Tp, as<double>(s->vr), P,
+    k_barrier_w<T><<<s->npt, 32, 0, s->stream>>>(0, s->npt, 0, as<int>(s->pt), Tp, as<double>(s->vr), P,
                                                                 sh, s->prm.kappa, s->prm.barrier_form, project, koff,
                                                                 dslot, g, diag, vals, st);
     LAUNCH_CHECK(s, "k_barrier_w(PT)");
   }
   if (s->nee) {
-    k_barrier_w<T><<<blocks_for(s->nee, 4), 128, 0, s->stream>>>(1, s->nee, s->npt, as<int>(s->ee), Tp,
+    k_barrier_w<T><<<s->nee, 32, 0, s->stream>>>(1, s->nee, s->npt, as<int>(s->ee), Tp,
                                                                 as<double>(s->vr), P, sh, s->prm.kappa,
                                                                 s->prm.barrier_form, project, koff, dslot, g, diag,
                                                                 vals, st);
@@ -1357,10 +1443,13 @@ yasps_status swept_candidates(yasps_system* s, const double* x, const double* p)
   const topo Tp = make_topo(s);
   const size_t nv3 = 3 * (size_t)s->nv;
   ENSURE(s, s->stepv[3], sizeof(double) * (3 * (size_t)s->nn + 1));
-  ENSURE(s, s->stepv[4], sizeof(double) * (2 * nv3 + 2));
+  const int ns = s->nscene;
+  // P1, D, the step bound (one scene: D + nv3), the per-scene displacement sums
+  ENSURE(s, s->stepv[4], sizeof(double) * (2 * nv3 + 2 + 4 * (size_t)ns + 2));
   double* x1 = as<double>(s->stepv[3]);
   double* P1 = as<double>(s->stepv[4]);
   double* D = P1 + nv3;
+  double* dsum = D + nv3 + 2;
   double* P0 = as<double>(s->P);
   RC(launch_positions(s, x, P0));
   k_sub<<<blocks_for(3LL * s->nn, 256), 256, 0, s->stream>>>(3 * s->nn, x, p, x1);
@@ -1368,6 +1457,10 @@ yasps_status swept_candidates(yasps_system* s, const double* x, const double* p)
   RC(launch_positions(s, x1, P1));
   k_sub<<<blocks_for((long long)nv3, 256), 256, 0, s->stream>>>((int)nv3, P1, P0, D);
   LAUNCH_CHECK(s, "k_sub");
+  CK(s, cudaMemsetAsync(dsum, 0, sizeof(double) * 4 * (size_t)ns, s->stream));
+  k_disp_sum<<<std::min(148 * 4, std::max(1, blocks_for(s->nv, 256))), 256, 0, s->stream>>>(
+      s->nv, D, ns > 1 ? as<int>(s->vscene) : nullptr, ns, dsum);
+  LAUNCH_CHECK(s, "k_disp_sum");
   s->ncpt = s->ncee = 0;
   for (int kind = 0; kind < 2; ++kind) {
     const int nA = kind == 0 ? s->nsv : s->nse;
@@ -1375,6 +1468,7 @@ yasps_status swept_candidates(yasps_system* s, const double* x, const double* p)
     if (nA == 0 || nB == 0 || (kind == 1 && nA < 2)) continue;
     boxbufs bb;
     RC(alloc_boxes(s, &bb));
+    bb.a.shift = bb.b.shift = dsum;
     if (kind == 0) {
       k_boxes<<<blocks_for(nA, 256), 256, 0, s->stream>>>(nA, 1, as<int>(s->svert), P0, P1, s->prm.dhat, bb.a);
       LAUNCH_CHECK(s, "k_boxes");

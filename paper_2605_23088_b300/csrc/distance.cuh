@@ -286,6 +286,95 @@ YASPS_D void map_wn_to_verts(const double (&coef)[3][4], const double* g9, const
         }
 }
 
+// ---- warp-cooperative form of ds_wn + map_wn_to_verts (the same formulas):
+// the scalars are formed by every lane, the 18 entries of Hwn and Hnn, the 81
+// of H9 and the 144 of H by different lanes.  One lane doing all of it issues
+// a few thousand FP64 instructions; a warp instruction with a single active
+// lane costs about as much FP64 pipe time as a full one, so spreading the
+// entries over the lanes cuts the pipe time about 16 times.
+struct wn_scratch {
+  double Hwn[9], Hnn[9], gw[3], gn[3], g9[9], H9[81];
+};
+YASPS_D double comp(const d3& v, int i) { return i == 0 ? v.x : (i == 1 ? v.y : v.z); }
+// entry c (0..5) of row k of Jn = [dn/de1 dn/de2] (3 x 6), as in ds_wn
+YASPS_D double jn(const d3& e1, const d3& e2, int k, int c) {
+  const d3& e = (c < 3) ? e2 : e1;
+  const double sg = (c < 3) ? -1.0 : 1.0;  // dn/de1 = -[e2]x, dn/de2 = [e1]x
+  const int a = c % 3;
+  if (k == a) return 0.0;
+  // [v]x (row k, column a) = -eps_kab v_b
+  const int b = 3 - k - a;
+  const double eps = ((k + 1) % 3 == a) ? 1.0 : -1.0;
+  return sg * (-eps) * comp(e, b);
+}
+// all 32 lanes call; g (12) and H (144) are written to shared memory
+YASPS_D void ds_wn_warp(d3 wv, d3 e1v, d3 e2v, const double (&coef)[3][4], wn_scratch& S, double* g, double* H,
+                        int lane) {
+  const d3 nv = cross(e1v, e2v);
+  const double t = dot(wv, nv), N = dot(nv, nv);
+  if (lane < 9) {
+    const int i = lane / 3, j = lane % 3;
+    const double d = (i == j) ? 1.0 : 0.0;
+    S.Hwn[lane] = 2.0 * (comp(nv, i) * comp(wv, j) + t * d) / N - 4.0 * t * comp(nv, i) * comp(nv, j) / (N * N);
+  } else if (lane < 18) {
+    const int i = (lane - 9) / 3, j = (lane - 9) % 3;
+    const double d = (i == j) ? 1.0 : 0.0;
+    const double wi = comp(wv, i), wj = comp(wv, j), ni = comp(nv, i), nj = comp(nv, j);
+    S.Hnn[lane - 9] = 2.0 * wi * wj / N - 4.0 * t * (wi * nj + ni * wj) / (N * N) - 2.0 * t * t * d / (N * N) +
+                      8.0 * t * t * ni * nj / (N * N * N);
+  } else if (lane < 21) {
+    const int i = lane - 18;
+    S.gw[i] = 2.0 * t * comp(nv, i) / N;
+  } else if (lane < 24) {
+    const int i = lane - 21;
+    S.gn[i] = 2.0 * t * comp(wv, i) / N - 2.0 * t * t * comp(nv, i) / (N * N);
+  }
+  __syncwarp();
+  if (lane < 9) S.g9[lane] = lane < 3 ? S.gw[lane]
+                                      : S.gn[0] * jn(e1v, e2v, 0, lane - 3) + S.gn[1] * jn(e1v, e2v, 1, lane - 3) +
+                                            S.gn[2] * jn(e1v, e2v, 2, lane - 3);
+  for (int e = lane; e < 81; e += 32) {
+    const int r = e / 9, c = e % 9;
+    double h;
+    if (r < 3 && c < 3) {
+      h = 2.0 * comp(nv, r) * comp(nv, c) / N;
+    } else if (r < 3 || c < 3) {
+      const int i = r < 3 ? r : c, cc = (r < 3 ? c : r) - 3;
+      h = S.Hwn[3 * i] * jn(e1v, e2v, 0, cc) + S.Hwn[3 * i + 1] * jn(e1v, e2v, 1, cc) +
+          S.Hwn[3 * i + 2] * jn(e1v, e2v, 2, cc);
+    } else {
+      const int rr = r - 3, cc = c - 3;
+      double T3[3];
+#pragma unroll
+      for (int k = 0; k < 3; ++k)
+        T3[k] = S.Hnn[3 * k] * jn(e1v, e2v, 0, cc) + S.Hnn[3 * k + 1] * jn(e1v, e2v, 1, cc) +
+                S.Hnn[3 * k + 2] * jn(e1v, e2v, 2, cc);
+      h = jn(e1v, e2v, 0, rr) * T3[0] + jn(e1v, e2v, 1, rr) * T3[1] + jn(e1v, e2v, 2, rr) * T3[2];
+      // curvature of n: block (e1, e2) and its transpose, M = sum_k gn_k eps_kij
+      // (row e1_i, column e2_j or its transpose; eps_kij = +1 when j = i + 1 mod 3)
+      const int i = rr < 3 ? rr : cc, j = rr < 3 ? cc - 3 : rr - 3;
+      if ((rr < 3) != (cc < 3) && i != j) h += S.gn[3 - i - j] * (((i + 1) % 3 == j) ? 1.0 : -1.0);
+    }
+    S.H9[e] = h;
+  }
+  __syncwarp();
+  if (lane < 12) {
+    const int v = lane / 3, i = lane % 3;
+    g[lane] = coef[0][v] * S.g9[i] + coef[1][v] * S.g9[3 + i] + coef[2][v] * S.g9[6 + i];
+  }
+  for (int e = lane; e < 144; e += 32) {
+    const int row = e / 12, col = e % 12;
+    const int v = row / 3, i = row % 3, u = col / 3, j = col % 3;
+    double acc = 0;
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+      for (int q = 0; q < 3; ++q) acc += coef[r][v] * coef[q][u] * S.H9[9 * (3 * r + i) + 3 * q + j];
+    H[e] = acc;
+  }
+  __syncwarp();
+}
+
 // PT (point-plane): w = p - a, e1 = b - a, e2 = c - a
 YASPS_D void ds_pt(const d3* y, double* g, double* H) {
   double g9[9], H9[81];

@@ -196,6 +196,26 @@ def test_ccd_bound_parity(cubes):
         assert a == pytest.approx(ar, rel=1e-14, abs=0.0)
 
 
+def test_ccd_bound_moving_frame_parity(yb):
+    """Swept boxes in the frame of the mean displacement: two cubes rising
+    together while closing in (to 3 mm: no candidate, full step; to 0.5 mm:
+    bounded), the same with the common rise removed, and a horizontal drift
+    added to everything."""
+    s = scenes.cubes_scene(n=2)
+    O = oracle.OracleSystem(s)
+    G = yb.System(s)
+    x, _ = O.initial_state()
+    x = x.copy()
+    n = len(x) // 2
+    x[n:, 1] += 0.048
+    for lower in (0.147, 0.1495):
+        D = np.zeros_like(x)
+        D[:n, 1] = lower
+        D[n:, 1] = 0.100
+        for d in (D, D - D.mean(0), D + np.array([0.2, 0.0, -0.3])):
+            assert G.ccd_bound(T(x), T(-d)) == pytest.approx(O.ccd_bound(x, -d), rel=1e-14, abs=0.0)
+
+
 def test_step_teacher_forced(cubes, yb):
     s, O, G, states = cubes
     for (x0, v0), (x1, v1) in zip(states[:-1], states[1:]):

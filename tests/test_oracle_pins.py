@@ -323,6 +323,51 @@ def cubes_contact():
     return s, O, x, v
 
 
+def test_ccd_bound_invariant_under_common_translation(cubes_contact):
+    """The distance between two primitives at any time of the step does not
+    change when every vertex gets the same extra displacement, so neither does
+    a time of impact.  The swept-box candidates are taken in the frame that
+    moves with the mean displacement, which makes the bound (CCD over those
+    candidates) invariant too; a horizontal shift also leaves the ground plane
+    distances unchanged.  The grid broadphase gives the brute-force bound."""
+    s, O, x, v = cubes_contact
+    assert len(s["fixed"]) == 0 and len(s["body_mass"]) == 0  # every vertex is a free node
+    xt = O.xtilde(x, v)
+    p, _, _ = O.pcg(O.assemble(x, xt), tol=1e-10)
+    c = np.broadcast_to(np.array([0.3, 0.0, -0.2]), x.shape)
+    for scale in (1.0, 20.0, 200.0):
+        a0 = O.ccd_bound(x, scale * p)
+        assert 0.0 < a0 <= 1.0
+        assert O.ccd_bound(x, scale * p, brute=True) == a0
+        assert O.ccd_bound(x, scale * p - c) == pytest.approx(a0, rel=1e-9)
+    assert O.ccd_bound(x, 200.0 * p) < 1.0  # the large steps are bounded
+
+
+def test_ccd_bound_depends_on_relative_motion_only():
+    """Two cubes 50 mm apart rise together by 100 mm while the lower one closes
+    in to 3 mm of the upper one: ACCD (gap 0.1) would stop that approach, but
+    the pair never comes within dhat, so it is no candidate and the step is
+    not bounded.  Seen from the frame that removes the common rise the motion
+    is the same, and so is the bound; boxes swept in place would overlap in the
+    first view only (their union covers the common rise) and bound the step
+    there."""
+    s = scenes.cubes_scene(n=2)
+    O = oracle.OracleSystem(s)
+    x, _ = O.initial_state()
+    x = x.copy()
+    n = len(x) // 2  # cube 0 (lower) first, every vertex a free node
+    x[n:, 1] += 0.048
+    D = np.zeros_like(x)
+    D[:n, 1] = 0.147
+    D[n:, 1] = 0.100
+    a = O.ccd_bound(x, -D)
+    assert a == 1.0
+    assert O.ccd_bound(x, -(D - D.mean(0))) == a
+    # the same approach ending 0.5 mm apart (within dhat) is bounded
+    D[:n, 1] = 0.1495
+    assert O.ccd_bound(x, -D) < 1.0
+
+
 def test_dof_layout_sizes():
     g = json.load(open(os.path.join(GOLDEN, "paper_sizes.json")))["gradient_length"]
     s = scenes.mixed_scene(sphere_h=0.03, cloth_n=5, n_boxes=1)
