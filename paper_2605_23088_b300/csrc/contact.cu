@@ -244,9 +244,11 @@ struct grid_dev {
 };
 
 // Visit every B box overlapping A box i once (min-corner rule on the FP32
-// boxes, then the exact FP64 overlap test).
+// boxes, then the exact FP64 overlap test).  upper: only B ids above i (a set
+// queried against itself, each unordered pair once), skipped on the record's
+// id before its box is read.
 template <class F>
-__device__ __forceinline__ void grid_visit(const grid_dev& g, const boxes& A, int i, F&& f) {
+__device__ __forceinline__ void grid_visit(const grid_dev& g, const boxes& A, int i, F&& f, bool upper = false) {
   const float* alf = A.lof + 3 * i;
   const float* ahf = A.hif + 3 * i;
   const double* alo = A.lo + 3 * i;
@@ -259,8 +261,10 @@ __device__ __forceinline__ void grid_visit(const grid_dev& g, const boxes& A, in
         const long long id = ((long long)z * g.G.dim[1] + y) * g.G.dim[0] + x;
         const int qe = g.start[id + 1];
         for (int q = g.start[id]; q < qe; ++q) {
-          const float4 r0 = g.pk[2 * (size_t)q], r1 = g.pk[2 * (size_t)q + 1];
+          const float4 r0 = g.pk[2 * (size_t)q];
           const int j = __float_as_int(r0.w);
+          if (upper && j <= i) continue;
+          const float4 r1 = g.pk[2 * (size_t)q + 1];
           const float blf[3] = {r0.x, r0.y, r0.z};
           const float bhf[3] = {r1.x, r1.y, r1.z};
           if (ahf[0] < blf[0] || bhf[0] < alf[0] || ahf[1] < blf[1] || bhf[1] < alf[1] || ahf[2] < blf[2] ||
@@ -331,6 +335,48 @@ __device__ __forceinline__ double pair_lb2(int kind, d3 y0, d3 y1, d3 y2, d3 y3)
 }
 __device__ __forceinline__ bool surely_apart(double lb2, double sh) { return lb2 > sh * (1.0 + 1e-9); }
 
+// A second conservative test for pairs the box bound keeps: the distance
+// between two convex sets is at least their gap along any axis u, and the
+// projections of a point, a segment or a triangle are extreme at its
+// vertices.  Two axes: the common normal (triangle normal; e1 x e2 for two
+// segments) and the direction between the primitives' centres.  The gap is
+// formed relative to y0 in FP64 and compared with the same 1e-9 relative
+// margin; an axis of zero length is skipped.  Most candidate pairs lie a few
+// millimetres apart, beyond dhat, and stop here instead of in the exact
+// classification.
+__device__ __forceinline__ bool sat_apart(int kind, d3 y0, d3 y1, d3 y2, d3 y3, double sh) {
+  const d3 a1 = y1 - y0, b0 = y2 - y0, b1 = y3 - y0;  // y0 at the origin
+  d3 ax[2];
+  if (kind == 0) {  // point y0, triangle y1 y2 y3
+    ax[0] = cross(b0 - a1, b1 - a1);
+    ax[1] = a1 + b0 + b1;  // three times the centroid
+  } else {  // segments y0 y1 and y2 y3
+    ax[0] = cross(a1, b1 - b0);
+    ax[1] = (b0 + b1) - a1;  // twice the centre difference
+  }
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const d3 u = ax[k];
+    const double n2 = dot(u, u);
+    if (!(n2 > 0.0)) continue;
+    const double pa0 = 0.0, pa1 = dot(u, a1), pb0 = dot(u, b0), pb1 = dot(u, b1);
+    double lo_a, hi_a, lo_b, hi_b;
+    if (kind == 0) {  // the point alone on one side, the triangle's three vertices on the other
+      lo_a = hi_a = pa0;
+      lo_b = fmin(pa1, fmin(pb0, pb1));
+      hi_b = fmax(pa1, fmax(pb0, pb1));
+    } else {
+      lo_a = fmin(pa0, pa1);
+      hi_a = fmax(pa0, pa1);
+      lo_b = fmin(pb0, pb1);
+      hi_b = fmax(pb0, pb1);
+    }
+    const double gap = fmax(lo_b - hi_a, lo_a - hi_b);
+    if (gap > 0.0 && gap * gap > sh * n2 * (1.0 + 1e-9)) return true;
+  }
+  return false;
+}
+
 // ---------------------------------------------------------------- barrier scalar
 struct bder {
   double b, db, d2b;
@@ -361,7 +407,7 @@ __global__ void k_pt_query(int total, int nsv, topo T, const double* __restrict_
       const int t0 = T.stri[3 * t], t1 = T.stri[3 * t + 1], t2 = T.stri[3 * t + 2];
       if (pt_excluded(T, v, t0, t1, t2)) return;
       const d3 q0 = ld3(P, t0), q1 = ld3(P, t1), q2 = ld3(P, t2);
-      if (surely_apart(pair_lb2(0, p, q0, q1, q2), sh)) return;
+      if (surely_apart(pair_lb2(0, p, q0, q1, q2), sh) || sat_apart(0, p, q0, q1, q2, sh)) return;
       double s;
       const int st = dist::pt_classify(p, q0, q1, q2, &s);
       if (!(s < sh)) return;
@@ -413,7 +459,7 @@ __global__ void k_ee_query(int total, int nse, topo T, const double* __restrict_
       const int f0 = T.sedge[2 * j], f1 = T.sedge[2 * j + 1];
       if (ee_excluded(T, e0, e1, f0, f1)) return;
       const d3 b0 = ld3(P, f0), b1 = ld3(P, f1);
-      if (surely_apart(pair_lb2(1, a0, a1, b0, b1), sh)) return;
+      if (surely_apart(pair_lb2(1, a0, a1, b0, b1), sh) || sat_apart(1, a0, a1, b0, b1, sh)) return;
       double s;
       const int st = dist::ee_classify(a0, a1, b0, b1, &s);
       if (!(s < sh)) return;
@@ -425,7 +471,7 @@ __global__ void k_ee_query(int total, int nse, topo T, const double* __restrict_
         kadd(acc, kappa * barrier_fn(s, sh, form).b);
       }
       ++c;
-    });
+    }, true);
     if (mode == 0) cnt[i] = c;
     if (mode == 1) {
       c = min(c, lim - base);
@@ -1011,7 +1057,7 @@ __global__ void k_cand_query(int total, int kind, int nA, topo T, grid_dev g, bo
       tmp[(size_t)i * kCandSlots + c] = j;
     }
     ++c;
-  });
+  }, kind == 1);
   if (mode == 0 || mode == 3) cnt[i] = c;
   if (mode == 1) {
     c = min(c, lim - base);
@@ -1110,7 +1156,7 @@ __global__ void k_energy_cand(int kind, int n, const int* __restrict__ cand, top
       int ids[4];
       cand_vertices(kind, cand, (size_t)k, T, ids);
       const d3 y0 = ld3(P, ids[0]), y1 = ld3(P, ids[1]), y2 = ld3(P, ids[2]), y3 = ld3(P, ids[3]);
-      if (!surely_apart(pair_lb2(kind, y0, y1, y2, y3), sh)) {
+      if (!surely_apart(pair_lb2(kind, y0, y1, y2, y3), sh) && !sat_apart(kind, y0, y1, y2, y3, sh)) {
         double s;
         if (kind == 0) dist::pt_classify(y0, y1, y2, y3, &s);
         else dist::ee_classify(y0, y1, y2, y3, &s);
@@ -1136,7 +1182,7 @@ __global__ void k_filter_cand(int kind, int n, const int* __restrict__ cand, top
   int ids[4];
   cand_vertices(kind, cand, (size_t)k, T, ids);
   const d3 y0 = ld3(P, ids[0]), y1 = ld3(P, ids[1]), y2 = ld3(P, ids[2]), y3 = ld3(P, ids[3]);
-  if (surely_apart(pair_lb2(kind, y0, y1, y2, y3), sh)) {
+  if (surely_apart(pair_lb2(kind, y0, y1, y2, y3), sh) || sat_apart(kind, y0, y1, y2, y3, sh)) {
     flag[k] = 0;
     sub[k] = 0;
     return;
