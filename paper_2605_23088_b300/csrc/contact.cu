@@ -344,7 +344,7 @@ __device__ __forceinline__ bool surely_apart(double lb2, double sh) { return lb2
 // margin; an axis of zero length is skipped.  Most candidate pairs lie a few
 // millimetres apart, beyond dhat, and stop here instead of in the exact
 // classification.
-__device__ __forceinline__ bool sat_apart(int kind, d3 y0, d3 y1, d3 y2, d3 y3, double sh) {
+__device__ __forceinline__ double sat_lb2(int kind, d3 y0, d3 y1, d3 y2, d3 y3) {
   const d3 a1 = y1 - y0, b0 = y2 - y0, b1 = y3 - y0;  // y0 at the origin
   d3 ax[2];
   if (kind == 0) {  // point y0, triangle y1 y2 y3
@@ -354,6 +354,7 @@ __device__ __forceinline__ bool sat_apart(int kind, d3 y0, d3 y1, d3 y2, d3 y3, 
     ax[0] = cross(a1, b1 - b0);
     ax[1] = (b0 + b1) - a1;  // twice the centre difference
   }
+  double best = 0.0;
 #pragma unroll
   for (int k = 0; k < 2; ++k) {
     const d3 u = ax[k];
@@ -372,9 +373,12 @@ __device__ __forceinline__ bool sat_apart(int kind, d3 y0, d3 y1, d3 y2, d3 y3, 
       hi_b = fmax(pb0, pb1);
     }
     const double gap = fmax(lo_b - hi_a, lo_a - hi_b);
-    if (gap > 0.0 && gap * gap > sh * n2 * (1.0 + 1e-9)) return true;
+    if (gap > 0.0) best = fmax(best, gap * gap / n2);
   }
-  return false;
+  return best;  // a squared lower bound of the distance (0: no axis separates)
+}
+__device__ __forceinline__ bool sat_apart(int kind, d3 y0, d3 y1, d3 y2, d3 y3, double sh) {
+  return surely_apart(sat_lb2(kind, y0, y1, y2, y3), sh);
 }
 
 // ---------------------------------------------------------------- barrier scalar
@@ -1120,10 +1124,31 @@ __global__ void k_ccd_cand(int kind, int n, const int* __restrict__ cand, topo T
     // ACCD's first advance is (1 - gap) d0 / lp with lp its bound on the
     // relative motion: when that already exceeds the whole step the answer is
     // the full step, so skip the exact distances
-    const double lp = accd_motion_bound(kind, dx);
-    const double lb2 = pair_lb2(kind, x[0], x[1], x[2], x[3]);
-    if (!(lp == 0.0) && !((1.0 - gap) * (1.0 - gap) * lb2 > lp * lp * (1.0 + 1e-9)))
-      best = accd(kind, x, dx, gap, 1.0, max_iter, &capped);
+    // Any lower bound lb of d0 will do: lp <= 2 max_k |dx_k - m| (no square
+    // roots) decides most pairs, then the separating-axis bound, then lp itself
+    double m[3] = {0.0, 0.0, 0.0};
+    for (int i = 0; i < 4; ++i) {
+      m[0] = dist::add(m[0], dist::mul(0.25, dx[i].x));
+      m[1] = dist::add(m[1], dist::mul(0.25, dx[i].y));
+      m[2] = dist::add(m[2], dist::mul(0.25, dx[i].z));
+    }
+    double mx2 = 0.0;
+    for (int i = 0; i < 4; ++i) {
+      const d3 c = d3{dx[i].x - m[0], dx[i].y - m[1], dx[i].z - m[2]};
+      mx2 = fmax(mx2, dot(c, c));
+    }
+    const double g1 = (1.0 - gap) * (1.0 - gap);
+    if (mx2 > 0.0) {  // lp == 0 exactly when every relative motion is 0
+      double lb2 = pair_lb2(kind, x[0], x[1], x[2], x[3]);
+      if (!(g1 * lb2 > 4.0 * mx2 * (1.0 + 1e-9))) {
+        lb2 = fmax(lb2, sat_lb2(kind, x[0], x[1], x[2], x[3]));
+        if (!(g1 * lb2 > 4.0 * mx2 * (1.0 + 1e-9))) {
+          const double lp = accd_motion_bound(kind, dx);
+          if (!(lp == 0.0) && !(g1 * lb2 > lp * lp * (1.0 + 1e-9)))
+            best = accd(kind, x, dx, gap, 1.0, max_iter, &capped);
+        }
+      }
+    }
   }
   if (capped) dev_flag(status, DEV_ITERCAP);
   if (T.vscene) {  // batches: one bound per scene

@@ -229,6 +229,37 @@ __global__ void k_inertia_body(int nb, int nfree, const double* __restrict__ Mb,
 }
 
 // ---------------------------------------------------------------- shared scatter
+// d[0..8] += B[0..8] for one 3x3 block.  FP32: vector atomics (16- and 8-byte
+// reductions) where the block's address allows; a block starts at 36 bytes
+// times its index, so at one of four offsets mod 16 and in 3 or 4 operations
+// instead of 9.  FP64: scalar atomics.
+__device__ __forceinline__ void add_block9(double* d, const double* B) {
+#pragma unroll
+  for (int t = 0; t < 9; ++t) atomicAdd(d + t, B[t]);
+}
+__device__ __forceinline__ void add_block9(float* d, const float* B) {
+  const int off = (int)((reinterpret_cast<uintptr_t>(d) >> 2) & 3);  // floats past a 16-byte boundary
+  if (off == 0) {  // 4 + 4 + 1
+    atomicAdd(reinterpret_cast<float4*>(d), make_float4(B[0], B[1], B[2], B[3]));
+    atomicAdd(reinterpret_cast<float4*>(d + 4), make_float4(B[4], B[5], B[6], B[7]));
+    atomicAdd(d + 8, B[8]);
+  } else if (off == 1) {  // 1 + 2 + 4 + 2
+    atomicAdd(d, B[0]);
+    atomicAdd(reinterpret_cast<float2*>(d + 1), make_float2(B[1], B[2]));
+    atomicAdd(reinterpret_cast<float4*>(d + 3), make_float4(B[3], B[4], B[5], B[6]));
+    atomicAdd(reinterpret_cast<float2*>(d + 7), make_float2(B[7], B[8]));
+  } else if (off == 2) {  // 2 + 4 + 2 + 1
+    atomicAdd(reinterpret_cast<float2*>(d), make_float2(B[0], B[1]));
+    atomicAdd(reinterpret_cast<float4*>(d + 2), make_float4(B[2], B[3], B[4], B[5]));
+    atomicAdd(reinterpret_cast<float2*>(d + 6), make_float2(B[6], B[7]));
+    atomicAdd(d + 8, B[8]);
+  } else {  // 1 + 4 + 4
+    atomicAdd(d, B[0]);
+    atomicAdd(reinterpret_cast<float4*>(d + 1), make_float4(B[1], B[2], B[3], B[4]));
+    atomicAdd(reinterpret_cast<float4*>(d + 5), make_float4(B[5], B[6], B[7], B[8]));
+  }
+}
+
 // Add the k x k grid of 3x3 blocks  Bab = scale * sum_{j,l} w[a][j] w[b][l] Hf[(i,j),(m,l)]
 // (Hf in an F-space of dimension 3*nc, nc = 3 for tets, 2 for membranes)
 // for every local pair a <= b into diag / vals.
@@ -263,17 +294,19 @@ __device__ __forceinline__ void scatter_fspace(const T* Hf, const double (*w)[NC
           B[3 * i + m] = (T)scale * s;
         }
       if (a == b) {
-        T* d = diag + 9 * (size_t)nodes[a];
-#pragma unroll
-        for (int t = 0; t < 9; ++t) atomicAdd(d + t, B[t]);
+        add_block9(diag + 9 * (size_t)nodes[a], B);
       } else {
         const int sl = slots[(K == 4) ? pair_index4(a, b) : pair_index3(a, b)];
-        T* d = vals + 9 * (size_t)sl;
-        const bool tr = nodes[a] > nodes[b];
+        if (nodes[a] > nodes[b]) {  // the stored block is the transpose
+          T Bt[9];
 #pragma unroll
-        for (int i = 0; i < 3; ++i)
+          for (int i = 0; i < 3; ++i)
 #pragma unroll
-          for (int m = 0; m < 3; ++m) atomicAdd(d + 3 * i + m, tr ? B[3 * m + i] : B[3 * i + m]);
+            for (int m = 0; m < 3; ++m) Bt[3 * i + m] = B[3 * m + i];
+          add_block9(vals + 9 * (size_t)sl, Bt);
+        } else {
+          add_block9(vals + 9 * (size_t)sl, B);
+        }
       }
     }
   }
