@@ -4,6 +4,7 @@
 // compressed upper-triangular block layout (App. B, "Global Hessian
 // Compression").
 #include <algorithm>
+#include <climits>
 
 #include "common.cuh"
 #include "internal.h"
@@ -186,9 +187,53 @@ yasps_status scan_exclusive(yasps_system* s, const int* in, int* out, int n, int
   return YASPS_OK;
 }
 
+// Small arrays (the dynamic contact keys: typically a few hundred to a few
+// thousand): one block sorts (key, value) pairs in shared memory with a
+// bitonic network, padded to a power of two with maximal entries.  Equal keys
+// are ordered by value, so the result is a deterministic sort by key; one
+// launch instead of a histogram, scan and scatter per 8-bit digit.
+constexpr int kSmallSort = 4096;
+__global__ void __launch_bounds__(1024) k_sort_small(uint64_t* __restrict__ keys, int* __restrict__ vals, int n) {
+  __shared__ uint64_t sk[kSmallSort];
+  __shared__ int sv[kSmallSort];
+  int m = 1;
+  while (m < n) m <<= 1;
+  for (int i = threadIdx.x; i < m; i += blockDim.x) {
+    sk[i] = (i < n) ? keys[i] : ~0ull;
+    sv[i] = (i < n) ? vals[i] : INT_MAX;
+  }
+  __syncthreads();
+  for (int k = 2; k <= m; k <<= 1)
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int i = threadIdx.x; i < m; i += blockDim.x) {
+        const int l = i ^ j;
+        if (l > i) {
+          const bool up = (i & k) == 0;
+          const uint64_t ka = sk[i], kb = sk[l];
+          const int va = sv[i], vb = sv[l];
+          const bool gt = (ka > kb) || (ka == kb && va > vb);
+          if (gt == up) {
+            sk[i] = kb; sk[l] = ka;
+            sv[i] = vb; sv[l] = va;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    keys[i] = sk[i];
+    vals[i] = sv[i];
+  }
+}
+
 yasps_status radix_sort_pairs(yasps_system* s, uint64_t* keys, int* vals, uint64_t* keys_tmp, int* vals_tmp, int n,
                               int bits) {
   if (n <= 1) return YASPS_OK;
+  if (n <= kSmallSort) {
+    k_sort_small<<<1, 1024, 0, s->stream>>>(keys, vals, n);
+    LAUNCH_CHECK(s, "k_sort_small");
+    return YASPS_OK;
+  }
   const int nblk = (n + RS_TILE - 1) / RS_TILE;
   gbuf& hist = s->ws[9];
   ENSURE(s, hist, sizeof(int) * 256 * (size_t)nblk);
