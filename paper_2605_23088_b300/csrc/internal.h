@@ -88,6 +88,7 @@ struct yasps_system {
   gbuf diag;                // T [nn][9]
   gbuf grad;                // double [nn][3]
   gbuf minv;                // T [nfree][9] then [nb][144]
+  gbuf dsym;                // T [nn][6] D then [nfree][6] M^-1, packed symmetric for the PCG kernel
   gbuf P;                   // double [nv][3] vertex positions at the last evaluation
 
   // contact pairs, int [n][3] = (a, b, subtype), sorted by (a, b)

@@ -281,6 +281,9 @@ struct pcg_args {
   double tol2;
   const int *row_s, *col_s, *row_d, *col_d;
   const T *val_s, *val_d, *D, *Mi;
+  // D (all nodes) and M^-1 (free nodes) packed symmetric, 6 per node:
+  // (00, 01, 02, 11, 12, 22), the mean of the two mirrored entries
+  const T *Ds, *Ms;
   const double* rhs;
   V *x, *r, *z, *q;  // written and read across blocks: plain (coherent) loads only
   V *d0, *d1;        // the direction, ping-ponged between iterations
@@ -542,6 +545,17 @@ __device__ __forceinline__ V apply_blk(int r, int c, const T* b, const gath<V>& 
   return part;
 }
 
+// y = S x for a symmetric 3x3 S packed as (00, 01, 02, 11, 12, 22)
+template <typename T, typename V>
+__device__ __forceinline__ void sym3_apply(const T* S, V x0, V x1, V x2, V& y0, V& y1, V& y2) {
+  T m[6];
+#pragma unroll
+  for (int t = 0; t < 6; ++t) m[t] = __ldg(S + t);
+  y0 = (V)m[0] * x0 + (V)m[1] * x1 + (V)m[2] * x2;
+  y1 = (V)m[1] * x0 + (V)m[3] * x1 + (V)m[4] * x2;
+  y2 = (V)m[2] * x0 + (V)m[4] * x1 + (V)m[5] * x2;
+}
+
 // unit i: a free node (3 DOF) or an affine body (its 4 nodes, 12 DOF)
 __device__ __forceinline__ void unit_range(int i, int nfree, int& cnt, size_t& o) {
   cnt = (i < nfree) ? 3 : 12;
@@ -555,10 +569,10 @@ __device__ __forceinline__ void unit_range(int i, int nfree, int& cnt, size_t& o
 template <typename T, typename V, bool DEFER>
 __device__ __forceinline__ V diag_node(const pcg_args<T, V>& a, long long i, V beta, V alpha_prev, const V* d,
                                        V* dn) {
-  const T* B = a.D + 9 * (size_t)i;
-  T m[9];
+  const T* B = a.Ds + 6 * (size_t)i;
+  T m[6];
 #pragma unroll
-  for (int t = 0; t < 9; ++t) m[t] = __ldg(B + t);
+  for (int t = 0; t < 6; ++t) m[t] = __ldg(B + t);
   const V z0 = a.z[3 * i], z1 = a.z[3 * i + 1], z2 = a.z[3 * i + 2];
   const V e0 = d[3 * i], e1 = d[3 * i + 1], e2 = d[3 * i + 2];
   if constexpr (DEFER) {
@@ -572,8 +586,8 @@ __device__ __forceinline__ V diag_node(const pcg_args<T, V>& a, long long i, V b
   }
   const V d0 = dnew(z0, beta, e0), d1 = dnew(z1, beta, e1), d2 = dnew(z2, beta, e2);
   const V q0 = (V)m[0] * d0 + (V)m[1] * d1 + (V)m[2] * d2;
-  const V q1 = (V)m[3] * d0 + (V)m[4] * d1 + (V)m[5] * d2;
-  const V q2 = (V)m[6] * d0 + (V)m[7] * d1 + (V)m[8] * d2;
+  const V q1 = (V)m[1] * d0 + (V)m[3] * d1 + (V)m[4] * d2;
+  const V q2 = (V)m[2] * d0 + (V)m[4] * d1 + (V)m[5] * d2;
   dn[3 * i] = d0; dn[3 * i + 1] = d1; dn[3 * i + 2] = d2;
   q_add3(a.q, (int)i, q0, q1, q2);
   return d0 * q0 + d1 * q1 + d2 * q2;
@@ -582,10 +596,10 @@ __device__ __forceinline__ V diag_node(const pcg_args<T, V>& a, long long i, V b
 // z = M^-1 r, q = 0; r^T z
 template <typename T, typename V, bool DEFER>
 __device__ __forceinline__ V update_free(const pcg_args<T, V>& a, long long i, V alpha, const V* dn) {
-  const T* M = a.Mi + 9 * (size_t)i;
-  T m[9];
+  const T* M = a.Ms + 6 * (size_t)i;
+  T m[6];
 #pragma unroll
-  for (int t = 0; t < 9; ++t) m[t] = __ldg(M + t);
+  for (int t = 0; t < 6; ++t) m[t] = __ldg(M + t);
   V xv[3], dv[3], rv[3], qv[3];
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
@@ -602,11 +616,11 @@ __device__ __forceinline__ V update_free(const pcg_args<T, V>& a, long long i, V
     if constexpr (!DEFER) xv[c] += alpha * dv[c];
     rv[c] -= alpha * qv[c];
   }
+  zv[0] = (V)m[0] * rv[0] + (V)m[1] * rv[1] + (V)m[2] * rv[2];
+  zv[1] = (V)m[1] * rv[0] + (V)m[3] * rv[1] + (V)m[4] * rv[2];
+  zv[2] = (V)m[2] * rv[0] + (V)m[4] * rv[1] + (V)m[5] * rv[2];
 #pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    zv[c] = (V)m[3 * c] * rv[0] + (V)m[3 * c + 1] * rv[1] + (V)m[3 * c + 2] * rv[2];
-    acc += zv[c] * rv[c];
-  }
+  for (int c = 0; c < 3; ++c) acc += zv[c] * rv[c];
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
     if constexpr (!DEFER) a.x[3 * i + c] = xv[c];
@@ -614,6 +628,20 @@ __device__ __forceinline__ V update_free(const pcg_args<T, V>& a, long long i, V
     a.z[3 * i + c] = zv[c];
   }
   return acc;
+}
+
+// z = M^-1 r for unit i inside the PCG kernel: free nodes from the packed
+// symmetric M^-1, bodies from their 12x12 block
+template <typename T, typename V>
+__device__ __forceinline__ V precond_unit(const pcg_args<T, V>& a, int i) {
+  if (i >= a.nfree) return precond_row<T, V>(i, a.nfree, a.Mi, a.r, a.z);
+  V z0, z1, z2;
+  const V r0 = a.r[3 * (size_t)i], r1 = a.r[3 * (size_t)i + 1], r2 = a.r[3 * (size_t)i + 2];
+  sym3_apply<T, V>(a.Ms + 6 * (size_t)i, r0, r1, r2, z0, z1, z2);
+  a.z[3 * (size_t)i] = z0;
+  a.z[3 * (size_t)i + 1] = z1;
+  a.z[3 * (size_t)i + 2] = z2;
+  return z0 * r0 + z1 * r1 + z2 * r2;
 }
 
 // ---- batches: per-scene sums
@@ -757,7 +785,7 @@ __global__ void __launch_bounds__(CFG::NTHR, CFG::MINB) k_pcg_persistent(pcg_arg
         a.d0[o + c] = 0;
         a.q[q_idx<V>(o + c)] = 0;
       }
-      acc += precond_row<T, V>((int)i, a.nfree, a.Mi, a.r, a.z);
+      acc += precond_unit(a, (int)i);
     }
   } else {
     for (long long base = tid & ~31LL; base < nu; base += nthr) {
@@ -774,7 +802,7 @@ __global__ void __launch_bounds__(CFG::NTHR, CFG::MINB) k_pcg_persistent(pcg_arg
           a.d0[o + c] = 0;
           a.q[q_idx<V>(o + c)] = 0;
         }
-        v = precond_row<T, V>((int)i, a.nfree, a.Mi, a.r, a.z);
+        v = precond_unit(a, (int)i);
         key = a.node_scene[i < a.nfree ? i : a.nfree + 4 * (i - a.nfree)];
       }
       seg_add_shared(shs, key, v, lane);
@@ -1118,6 +1146,24 @@ struct scene_out {
 
 // PCG in precision (T, V) on H dx = rhs (FP64 rhs); dx accumulated into p (FP64).
 // Batches: stol2 (device, per scene) or null, per-scene iterations / flags out.
+// D (nn nodes) and the free nodes' M^-1 packed symmetric for the PCG kernel
+template <typename T>
+__global__ void k_pack_sym(int nn, int nfree, const T* __restrict__ D, const T* __restrict__ Mi, T* __restrict__ Ds,
+                           T* __restrict__ Ms) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nn) return;
+  auto pack = [](const T* A, T* S) {
+    S[0] = A[0];
+    S[1] = (T)0.5 * (A[1] + A[3]);
+    S[2] = (T)0.5 * (A[2] + A[6]);
+    S[3] = A[4];
+    S[4] = (T)0.5 * (A[5] + A[7]);
+    S[5] = A[8];
+  };
+  pack(D + 9 * (size_t)i, Ds + 6 * (size_t)i);
+  if (i < nfree) pack(Mi + 9 * (size_t)i, Ms + 6 * (size_t)i);
+}
+
 template <typename T, typename V, bool BATCH, typename CFG>
 yasps_status pcg_launch_cfg(yasps_system* s, const double* rhs, double* p, double tol, int maxit, const double* stol2,
                             int* iters, int* state, double* rel, scene_out* so) {
@@ -1150,6 +1196,15 @@ yasps_status pcg_launch_cfg(yasps_system* s, const double* rhs, double* p, doubl
   a.val_d = as<T>(s->Hd.vals);
   a.D = as<T>(s->diag);
   a.Mi = as<T>(s->minv);
+  ENSURE(s, s->dsym, sizeof(T) * 6 * (2 * (size_t)s->nn + 1));
+  T* ds = as<T>(s->dsym);
+  a.Ds = ds;
+  a.Ms = ds + 6 * (size_t)s->nn;
+  if (s->nn > 0) {
+    k_pack_sym<T><<<blocks_for(s->nn, 256), 256, 0, s->stream>>>(s->nn, s->nfree, a.D, a.Mi, ds,
+                                                                 ds + 6 * (size_t)s->nn);
+    LAUNCH_CHECK(s, "k_pack_sym");
+  }
   a.rhs = rhs;
   a.x = as<V>(s->vec[0]);
   a.r = as<V>(s->vec[1]);

@@ -63,7 +63,7 @@ static void all_bufs(yasps_system* s, std::vector<gbuf*>& v) {
                  &s->tet_v, &s->tet_n, &s->tet_rest, &s->tet_E, &s->tet_nu, &s->vscene, &s->node_scene, &s->scene_buf, &s->tet_slot, &s->tri_v, &s->tri_n, &s->tri_rest, &s->tri_slot,
                  &s->hinge_v, &s->hinge_n, &s->hinge_rest, &s->hinge_slot, &s->body_kv, &s->body_slot, &s->stri,
                  &s->sedge, &s->svert, &s->planes, &s->Hs.row_ptr, &s->Hs.col, &s->Hs.row, &s->Hs.vals,
-                 &s->Hd.row_ptr, &s->Hd.col, &s->Hd.row, &s->Hd.vals, &s->diag, &s->grad, &s->minv, &s->P, &s->pt,
+                 &s->Hd.row_ptr, &s->Hd.col, &s->Hd.row, &s->Hd.vals, &s->diag, &s->grad, &s->minv, &s->dsym, &s->P, &s->pt,
                  &s->ee, &s->pg, &s->cpt, &s->cee, &s->pair_key_off, &s->dyn_slot, &s->status, &s->scal, &s->red, &s->scan_tmp};
   for (gbuf* b : one) v.push_back(b);
   for (auto& b : s->ws) v.push_back(&b);
