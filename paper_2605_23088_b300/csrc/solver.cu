@@ -1243,9 +1243,10 @@ yasps_status pcg_launch_cfg(yasps_system* s, const double* rhs, double* p, doubl
     const double es = sizeof(T), vs = sizeof(V), nn = s->nn;
     const double nnzb = (double)s->Hs.nnzb + s->Hd.nnzb;
     // H d phase: blocks + column index + row pointer, D, z and d read, d' and q written
-    const double spmv_bytes = nnzb * (9 * es + 4) + nn * 4 + nn * 9 * es + 3 * vs * nn * 4;
+    // (D and M^-1 at 6 values per node: symmetric, read packed)
+    const double spmv_bytes = nnzb * (9 * es + 4) + nn * 4 + nn * 6 * es + 3 * vs * nn * 4;
     // whole iteration: H d phase + update (x, d', r, q read; x, r, z, q written; M^-1)
-    const double iter_bytes = spmv_bytes + 3 * vs * nn * 8 + nn * 9 * es;
+    const double iter_bytes = spmv_bytes + 3 * vs * nn * 8 + nn * 6 * es;
     s->prof_acc[YASPS_STAGE_PCG_KERNEL].bytes += iter_bytes * h.iters;
     auto& sp = s->prof_acc[YASPS_STAGE_SPMV];
     sp.count += h.iters;
