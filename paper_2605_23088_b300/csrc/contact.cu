@@ -249,10 +249,17 @@ struct grid_dev {
 // id before its box is read.
 template <class F>
 __device__ __forceinline__ void grid_visit(const grid_dev& g, const boxes& A, int i, F&& f, bool upper = false) {
-  const float* alf = A.lof + 3 * i;
-  const float* ahf = A.hif + 3 * i;
-  const double* alo = A.lo + 3 * i;
-  const double* ahi = A.hi + 3 * i;
+  // the query box in registers (f writes through pointers the compiler cannot
+  // tell apart from it)
+  float alf[3], ahf[3];
+  double alo[3], ahi[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    alf[c] = A.lof[3 * i + c];
+    ahf[c] = A.hif[3 * i + c];
+    alo[c] = A.lo[3 * i + c];
+    ahi[c] = A.hi[3 * i + c];
+  }
   int c0[3], c1[3];
   cell_range(g.G, alf, ahf, c0, c1);
   for (int z = c0[2]; z <= c1[2]; ++z)
@@ -260,11 +267,21 @@ __device__ __forceinline__ void grid_visit(const grid_dev& g, const boxes& A, in
       for (int x = c0[0]; x <= c1[0]; ++x) {
         const long long id = ((long long)z * g.G.dim[1] + y) * g.G.dim[0] + x;
         const int qe = g.start[id + 1];
-        for (int q = g.start[id]; q < qe; ++q) {
-          const float4 r0 = g.pk[2 * (size_t)q];
+        int q = g.start[id];
+        // one record ahead: the next record's 32 bytes load while this one is tested
+        float4 n0 = make_float4(0.f, 0.f, 0.f, 0.f), n1 = n0;
+        if (q < qe) {
+          n0 = g.pk[2 * (size_t)q];
+          n1 = g.pk[2 * (size_t)q + 1];
+        }
+        for (; q < qe; ++q) {
+          const float4 r0 = n0, r1 = n1;
+          if (q + 1 < qe) {
+            n0 = g.pk[2 * (size_t)q + 2];
+            n1 = g.pk[2 * (size_t)q + 3];
+          }
           const int j = __float_as_int(r0.w);
           if (upper && j <= i) continue;
-          const float4 r1 = g.pk[2 * (size_t)q + 1];
           const float blf[3] = {r0.x, r0.y, r0.z};
           const float bhf[3] = {r1.x, r1.y, r1.z};
           if (ahf[0] < blf[0] || bhf[0] < alf[0] || ahf[1] < blf[1] || bhf[1] < alf[1] || ahf[2] < blf[2] ||
