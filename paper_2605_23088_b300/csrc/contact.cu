@@ -76,14 +76,11 @@ __device__ __forceinline__ void scene_offset(int sc, double spacing, double* off
   off[2] = (double)(sc >> 6) * spacing;
 }
 
-// boxes of k-vertex primitives at positions P0 (and P1 when swept), grown by infl
-__global__ void k_boxes(int n, int k, const int* __restrict__ idx, const double* __restrict__ P0,
-                        const double* __restrict__ P1, double infl, boxw out) {
-  double* __restrict__ lo = out.lo;
-  double* __restrict__ hi = out.hi;
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= n) return;
-  double l[3], h[3];
+// box of k-vertex primitive e at positions P0 (and P1 when swept), before
+// growth: l, h; off: its scene's lattice offset
+__device__ __forceinline__ void prim_hull(int e, int k, const int* __restrict__ idx, const double* __restrict__ P0,
+                                          const double* __restrict__ P1, const boxw& out, double* l, double* h,
+                                          double* off) {
   const int v0 = idx[k * e];
   for (int c = 0; c < 3; ++c) l[c] = h[c] = P0[3 * v0 + c];
   for (int a = 1; a < k; ++a) {
@@ -115,15 +112,39 @@ __global__ void k_boxes(int n, int k, const int* __restrict__ idx, const double*
       h[c] = fmax(h[c], h1[c] + r);
     }
   }
-  double off[3] = {0.0, 0.0, 0.0};
+  for (int c = 0; c < 3; ++c) off[c] = 0.0;
   if (out.vscene) scene_offset(out.vscene[v0], out.spacing, off);
+}
+// the box grown by infl: FP64 and outward-rounded FP32
+__device__ __forceinline__ void put_box(const boxw& out, int e, const double* l, const double* h, const double* off,
+                                        double infl) {
   for (int c = 0; c < 3; ++c) {
     const double lc = l[c] - infl + off[c], hc = h[c] + infl + off[c];
-    lo[3 * e + c] = lc;
-    hi[3 * e + c] = hc;
+    out.lo[3 * e + c] = lc;
+    out.hi[3 * e + c] = hc;
     out.lof[3 * e + c] = __double2float_rd(lc);
     out.hif[3 * e + c] = __double2float_ru(hc);
   }
+}
+// boxes of k-vertex primitives at positions P0 (and P1 when swept), grown by infl
+__global__ void k_boxes(int n, int k, const int* __restrict__ idx, const double* __restrict__ P0,
+                        const double* __restrict__ P1, double infl, boxw out) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n) return;
+  double l[3], h[3], off[3];
+  prim_hull(e, k, idx, P0, P1, out, l, h, off);
+  put_box(out, e, l, h, off, infl);
+}
+// a set queried against itself (edges): its query boxes (grown by infl) and
+// its grid boxes (not grown) from one hull
+__global__ void k_boxes_self(int n, int k, const int* __restrict__ idx, const double* __restrict__ P0,
+                             const double* __restrict__ P1, double infl, boxw query, boxw grid) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n) return;
+  double l[3], h[3], off[3];
+  prim_hull(e, k, idx, P0, P1, query, l, h, off);
+  put_box(query, e, l, h, off, infl);
+  put_box(grid, e, l, h, off, 0.0);
 }
 
 // per-scene sums of the vertex displacements D and vertex counts into
@@ -845,24 +866,77 @@ __global__ void __launch_bounds__(32) k_barrier_w(int kind, int npairs, int pair
   }
   __syncwarp();
   if (!w.active) return;  // warp-uniform
-  if (w.dtype == dist::PT) {
-    const double coef[3][4] = {{1, -1, 0, 0}, {0, -1, 1, 0}, {0, -1, 0, 1}};
-    dist::ds_wn_warp(w.yl[0] - w.yl[1], w.yl[2] - w.yl[1], w.yl[3] - w.yl[1], coef, w.wn, w.gs, w.Hs, lane);
-  } else if (w.dtype == dist::EE) {
-    const double coef[3][4] = {{1, 0, -1, 0}, {-1, 1, 0, 0}, {0, 0, -1, 1}};
-    dist::ds_wn_warp(w.yl[0] - w.yl[2], w.yl[1] - w.yl[0], w.yl[3] - w.yl[2], coef, w.wn, w.gs, w.Hs, lane);
-  }
+  // point-plane / line-line: (w, e1, e2) = C y with C = coef (x) I3 (9 x 12)
+  const double coef_pt[3][4] = {{1, -1, 0, 0}, {0, -1, 1, 0}, {0, -1, 0, 1}};
+  const double coef_ee[3][4] = {{1, 0, -1, 0}, {-1, 1, 0, 0}, {0, 0, -1, 1}};
+  const bool wn = w.dtype == dist::PT || w.dtype == dist::EE;
+  if (w.dtype == dist::PT)
+    dist::ds_wn_warp(w.yl[0] - w.yl[1], w.yl[2] - w.yl[1], w.yl[3] - w.yl[1], coef_pt, w.wn, w.gs, w.Hs, lane);
+  else if (w.dtype == dist::EE)
+    dist::ds_wn_warp(w.yl[0] - w.yl[2], w.yl[1] - w.yl[0], w.yl[3] - w.yl[2], coef_ee, w.wn, w.gs, w.Hs, lane);
   const int n3 = 3 * w.n;
   const double db = w.db, d2b = w.d2b;
-  for (int e = lane; e < n3 * n3; e += 32) {
-    const int r = e / n3, c = e % n3;
-    w.A[e] = (T)(kappa * (d2b * w.gs[r] * w.gs[c] + db * w.Hs[e]));
-  }
-  __syncwarp();
-  if (project) {
-    if (n3 == 12) warp_project<T, 12>(w.A, w.V, w.cs, w.sn, lane);
-    else if (n3 == 9) warp_project<T, 9>(w.A, w.V, w.cs, w.sn, lane);
-    else warp_project<T, 6>(w.A, w.V, w.cs, w.sn, lane);
+  if (project && wn) {
+    // The 12x12 Hessian is C^T H9 C with H9 = kappa (b'' g9 g9^T + b' d2s) in
+    // (w, e1, e2).  With C C^T = L L^T (L = chol(coef coef^T) (x) I3) the rows
+    // of Q = L^-1 C are orthonormal and C^T H9 C = Q^T (L^T H9 L) Q, so the
+    // projection of the 12x12 is Q^T Project(K) Q with the 9x9 K = L^T H9 L:
+    // the same matrix up to rounding, from a Jacobi solve on 9 instead of 12.
+    const double(&coef)[3][4] = (w.dtype == dist::PT) ? coef_pt : coef_ee;
+    double G[3][3], L[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}}, Mq[3][4];
+    for (int r = 0; r < 3; ++r)
+      for (int q = 0; q < 3; ++q) {
+        double t = 0.0;
+        for (int v = 0; v < 4; ++v) t += coef[r][v] * coef[q][v];
+        G[r][q] = t;
+      }
+    L[0][0] = sqrt(G[0][0]);
+    L[1][0] = G[1][0] / L[0][0];
+    L[2][0] = G[2][0] / L[0][0];
+    L[1][1] = sqrt(G[1][1] - L[1][0] * L[1][0]);
+    L[2][1] = (G[2][1] - L[2][0] * L[1][0]) / L[1][1];
+    L[2][2] = sqrt(G[2][2] - L[2][0] * L[2][0] - L[2][1] * L[2][1]);
+    for (int v = 0; v < 4; ++v) {  // Mq = L^-1 coef (forward substitution)
+      Mq[0][v] = coef[0][v] / L[0][0];
+      Mq[1][v] = (coef[1][v] - L[1][0] * Mq[0][v]) / L[1][1];
+      Mq[2][v] = (coef[2][v] - L[2][0] * Mq[0][v] - L[2][1] * Mq[1][v]) / L[2][2];
+    }
+    for (int e = lane; e < 81; e += 32) {
+      const int ra = e / 9, ca = e % 9, rb = ra / 3, i = ra % 3, qb = ca / 3, j = ca % 3;
+      double acc = 0.0;
+      for (int r2 = rb; r2 < 3; ++r2)
+        for (int q2 = qb; q2 < 3; ++q2) {
+          const int a9 = 3 * r2 + i, b9 = 3 * q2 + j;
+          const double h9 = kappa * (d2b * w.wn.g9[a9] * w.wn.g9[b9] + db * w.wn.H9[9 * a9 + b9]);
+          acc += L[r2][rb] * L[q2][qb] * h9;
+        }
+      w.A[e] = (T)acc;
+    }
+    __syncwarp();
+    warp_project<T, 9>(w.A, w.V, w.cs, w.sn, lane);  // A (9 x 9) <- Project(K)
+    for (int e = lane; e < 144; e += 32) {
+      const int row = e / 12, col = e % 12, v = row / 3, i = row % 3, u = col / 3, j = col % 3;
+      T acc = 0;
+#pragma unroll
+      for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int q = 0; q < 3; ++q) acc += (T)(Mq[r][v] * Mq[q][u]) * w.A[9 * (3 * r + i) + 3 * q + j];
+      w.V[e] = acc;
+    }
+    __syncwarp();
+    for (int e = lane; e < 144; e += 32) w.A[e] = w.V[e];
+    __syncwarp();
+  } else {
+    for (int e = lane; e < n3 * n3; e += 32) {
+      const int r = e / n3, c = e % n3;
+      w.A[e] = (T)(kappa * (d2b * w.gs[r] * w.gs[c] + db * w.Hs[e]));
+    }
+    __syncwarp();
+    if (project) {
+      if (n3 == 12) warp_project<T, 12>(w.A, w.V, w.cs, w.sn, lane);
+      else if (n3 == 9) warp_project<T, 9>(w.A, w.V, w.cs, w.sn, lane);
+      else warp_project<T, 6>(w.A, w.V, w.cs, w.sn, lane);
+    }
   }
   // gradient rows of the merged nodes
   const int M = w.m;
@@ -1421,11 +1495,9 @@ yasps_status detect_pairs(yasps_system* s, const double* P) {
   if (s->nse > 1) {
     boxbufs bb;
     RC(alloc_boxes(s, &bb));
-    k_boxes<<<blocks_for(s->nse, 256), 256, 0, s->stream>>>(s->nse, 2, as<int>(s->sedge), P, nullptr, s->prm.dhat,
-                                                           bb.a);
-    LAUNCH_CHECK(s, "k_boxes");
-    k_boxes<<<blocks_for(s->nse, 256), 256, 0, s->stream>>>(s->nse, 2, as<int>(s->sedge), P, nullptr, 0.0, bb.b);
-    LAUNCH_CHECK(s, "k_boxes");
+    k_boxes_self<<<blocks_for(s->nse, 256), 256, 0, s->stream>>>(s->nse, 2, as<int>(s->sedge), P, nullptr,
+                                                               s->prm.dhat, bb.a, bb.b);
+    LAUNCH_CHECK(s, "k_boxes_self");
     grid_dev g;
     RC(build_grid(s, s->nse, bb.b, &g));
     RC(two_pass(s, s->nse, [&](int mode, int total, int* cnt, const int* off, int* out) -> yasps_status {
@@ -1502,11 +1574,9 @@ yasps_status barrier_energy(yasps_system* s, const double* P, double* E_host) {
   if (s->nse > 1) {
     boxbufs bb;
     RC(alloc_boxes(s, &bb));
-    k_boxes<<<blocks_for(s->nse, 256), 256, 0, s->stream>>>(s->nse, 2, as<int>(s->sedge), P, nullptr, s->prm.dhat,
-                                                           bb.a);
-    LAUNCH_CHECK(s, "k_boxes");
-    k_boxes<<<blocks_for(s->nse, 256), 256, 0, s->stream>>>(s->nse, 2, as<int>(s->sedge), P, nullptr, 0.0, bb.b);
-    LAUNCH_CHECK(s, "k_boxes");
+    k_boxes_self<<<blocks_for(s->nse, 256), 256, 0, s->stream>>>(s->nse, 2, as<int>(s->sedge), P, nullptr,
+                                                               s->prm.dhat, bb.a, bb.b);
+    LAUNCH_CHECK(s, "k_boxes_self");
     grid_dev g;
     RC(build_grid(s, s->nse, bb.b, &g));
     k_ee_query<<<nblk_e, 128, 0, s->stream>>>(0, s->nse, Tp, P, g, bb.a, sh, 2, nullptr, nullptr, nullptr,
@@ -1563,10 +1633,9 @@ yasps_status swept_candidates(yasps_system* s, const double* x, const double* p)
       k_boxes<<<blocks_for(nB, 256), 256, 0, s->stream>>>(nB, 3, as<int>(s->stri), P0, P1, 0.0, bb.b);
       LAUNCH_CHECK(s, "k_boxes");
     } else {
-      k_boxes<<<blocks_for(nA, 256), 256, 0, s->stream>>>(nA, 2, as<int>(s->sedge), P0, P1, s->prm.dhat, bb.a);
-      LAUNCH_CHECK(s, "k_boxes");
-      k_boxes<<<blocks_for(nB, 256), 256, 0, s->stream>>>(nB, 2, as<int>(s->sedge), P0, P1, 0.0, bb.b);
-      LAUNCH_CHECK(s, "k_boxes");
+      k_boxes_self<<<blocks_for(nA, 256), 256, 0, s->stream>>>(nA, 2, as<int>(s->sedge), P0, P1,
+                                                                 s->prm.dhat, bb.a, bb.b);
+      LAUNCH_CHECK(s, "k_boxes_self");
     }
     grid_dev g;
     RC(build_grid(s, nB, bb.b, &g));
