@@ -187,17 +187,16 @@ yasps_status scan_exclusive(yasps_system* s, const int* in, int* out, int n, int
   return YASPS_OK;
 }
 
-// Small arrays (the dynamic contact keys: typically a few hundred to a few
-// thousand): one block sorts (key, value) pairs in shared memory with a
-// bitonic network, padded to a power of two with maximal entries.  Equal keys
-// are ordered by value, so the result is a deterministic sort by key; one
-// launch instead of a histogram, scan and scatter per 8-bit digit.
-constexpr int kSmallSort = 4096;
-__global__ void __launch_bounds__(1024) k_sort_small(uint64_t* __restrict__ keys, int* __restrict__ vals, int n) {
-  __shared__ uint64_t sk[kSmallSort];
-  __shared__ int sv[kSmallSort];
-  int m = 1;
-  while (m < n) m <<= 1;
+// Small arrays (the dynamic contact keys: typically a few thousand): one
+// block sorts (key, value) pairs in shared memory with a bitonic network,
+// padded to a power of two with maximal entries.  Equal keys are ordered by
+// value, so the result is a deterministic sort by key; one launch instead of
+// a histogram, scan and scatter per 8-bit digit.
+constexpr int kSmallSort = 16384;  // 12 bytes per entry: 192 KB of shared memory at most
+__global__ void __launch_bounds__(1024) k_sort_small(uint64_t* __restrict__ keys, int* __restrict__ vals, int n, int m) {
+  extern __shared__ __align__(16) unsigned char sort_smem[];
+  uint64_t* sk = reinterpret_cast<uint64_t*>(sort_smem);
+  int* sv = reinterpret_cast<int*>(sk + m);
   for (int i = threadIdx.x; i < m; i += blockDim.x) {
     sk[i] = (i < n) ? keys[i] : ~0ull;
     sv[i] = (i < n) ? vals[i] : INT_MAX;
@@ -230,7 +229,12 @@ yasps_status radix_sort_pairs(yasps_system* s, uint64_t* keys, int* vals, uint64
                               int bits) {
   if (n <= 1) return YASPS_OK;
   if (n <= kSmallSort) {
-    k_sort_small<<<1, 1024, 0, s->stream>>>(keys, vals, n);
+    int m = 1;
+    while (m < n) m <<= 1;  // padded size (a power of two)
+    const size_t smem = (size_t)m * (sizeof(uint64_t) + sizeof(int));
+    CK(s, cudaFuncSetAttribute(k_sort_small, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)((size_t)kSmallSort * (sizeof(uint64_t) + sizeof(int)))));
+    k_sort_small<<<1, 1024, smem, s->stream>>>(keys, vals, n, m);
     LAUNCH_CHECK(s, "k_sort_small");
     return YASPS_OK;
   }
