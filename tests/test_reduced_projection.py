@@ -1,0 +1,47 @@
+"""The identity behind the 9x9 projection of point-plane / line-line barrier
+Hessians (CPU only, numpy).
+
+A pair's Hessian in its 12 vertex coordinates is C^T H9 C, where H9 lives in
+the 9 variables (w, e1, e2) = C y and C = coef (x) I3.  With C C^T = L L^T the
+rows of Q = L^-1 C are orthonormal and C = L Q, so the PSD projection of the
+12x12 equals Q^T Project(L^T H9 L) Q.  Checked here against numpy.linalg.eigh
+on the 12x12 for random symmetric H9 of both types, including ones that are
+already PSD or entirely negative.
+"""
+import numpy as np
+import pytest
+
+COEF = {
+    "point-plane": np.array([[1, -1, 0, 0], [0, -1, 1, 0], [0, -1, 0, 1]], float),
+    "line-line": np.array([[1, 0, -1, 0], [-1, 1, 0, 0], [0, 0, -1, 1]], float),
+}
+
+
+def project(A):
+    lam, V = np.linalg.eigh(0.5 * (A + A.T))
+    return (V * np.maximum(lam, 0.0)) @ V.T
+
+
+@pytest.mark.parametrize("kind", sorted(COEF))
+@pytest.mark.parametrize("shift", [0.0, 5.0, -5.0])
+def test_projection_through_the_reduced_space(kind, shift):
+    rng = np.random.default_rng(7)
+    C = np.kron(COEF[kind], np.eye(3))  # 9 x 12, rows (variable group, component)
+    L = np.linalg.cholesky(C @ C.T)
+    Q = np.linalg.solve(L, C)
+    assert np.allclose(Q @ Q.T, np.eye(9), atol=1e-14)
+    assert np.allclose(L @ Q, C, atol=1e-14)
+    for _ in range(20):
+        B = rng.normal(size=(9, 9))
+        H9 = 0.5 * (B + B.T) + shift * np.eye(9)
+        full = project(C.T @ H9 @ C)
+        reduced = Q.T @ project(L.T @ H9 @ L) @ Q
+        assert np.abs(full - reduced).max() <= 1e-12 * max(np.abs(full).max(), 1.0)
+
+
+def test_factor_is_block_constant():
+    """L is chol(coef coef^T) (x) I3: one 3x3 factor per distance type."""
+    for coef in COEF.values():
+        L3 = np.linalg.cholesky(coef @ coef.T)
+        L = np.linalg.cholesky(np.kron(coef @ coef.T, np.eye(3)))
+        assert np.allclose(L, np.kron(L3, np.eye(3)), atol=1e-15)
