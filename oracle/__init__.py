@@ -58,6 +58,7 @@ def lib():
         _lib.or_accd.restype = ctypes.c_double
         _lib.or_pg_ccd.restype = ctypes.c_double
         _lib.or_ccd_bound.restype = ctypes.c_double
+        _lib.or_get_kappa.restype = ctypes.c_double
     return _lib
 
 
@@ -383,6 +384,21 @@ class OracleSystem:
         rc = lib().or_pcg(self.h, _dp(_f64(rhs)), _dp(x), ctypes.c_double(tol), ctypes.c_int(maxit), ctypes.byref(it))
         return x, it.value, rc
 
+    def set_kappa_adaptive(self, on=True, kappa_min=1e-6, kappa_max=1e12, dmin=None):
+        """Adaptive barrier stiffness (reading c5): chosen at each step's start,
+        frozen for the step.  The first step that starts with contact pairs
+        balances the barrier gradient against the rest, clamped to
+        [kappa_min, kappa_max]; later steps double kappa (up to kappa_max) when
+        the smallest pair distance is below ``dmin`` (default dhat / 10) and
+        smaller than at the previous step's start."""
+        d = self.scene["dhat"] / 10.0 if dmin is None else dmin
+        lib().or_set_kappa_adaptive(self.h, ctypes.c_int(int(on)), ctypes.c_double(kappa_min),
+                                    ctypes.c_double(kappa_max), ctypes.c_double(d))
+
+    @property
+    def kappa(self):
+        return lib().or_get_kappa(self.h)
+
     def ccd_bound(self, x, direction, brute=False):
         return lib().or_ccd_bound(self.h, _dp(_f64(x)), _dp(_f64(direction)), ctypes.c_int(int(brute)))
 
@@ -390,9 +406,9 @@ class OracleSystem:
         """One implicit time step in place on copies; returns (x, v, rc, stats dict)."""
         x = _f64(x).copy()
         v = _f64(v).copy()
-        st = np.zeros(8)
+        st = np.zeros(9)
         rc = lib().or_step(self.h, _dp(x), _dp(v), ctypes.c_int(int(brute)), _dp(st))
-        keys = ["newton_iters", "pcg_iters", "alpha", "p_inf", "n_pt", "n_ee", "n_pg", "ls_fail"]
+        keys = ["newton_iters", "pcg_iters", "alpha", "p_inf", "n_pt", "n_ee", "n_pg", "ls_fail", "kappa"]
         return x, v, rc, dict(zip(keys, st.tolist()))
 
 

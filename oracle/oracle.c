@@ -734,6 +734,9 @@ typedef struct {
   double* xfix;   /* current positions of fixed vertices (3 per vertex, others unused) */
   double* nodemass; /* free nodes: m; bodies: 4x4 scalar mass matrix (16 per body) */
   double *tmu, *tlam, *cmu, *clam;
+  /* adaptive barrier stiffness (off unless set): bounds, distance threshold, state */
+  int kadapt, kinit;
+  double kmin, kmax, kdmin, dmin_prev;
 } osys;
 
 static void* dupa(const void* p, size_t bytes) {
@@ -1651,10 +1654,93 @@ OR_EXPORT double or_ccd_bound(void* p, const double* x, const double* dir, int b
 }
 
 /* ------------------------------------------------------------------------ */
+/* adaptive barrier stiffness (reading c5).  kappa is chosen at the start   */
+/* of a step and frozen for it.  The first step that starts with contact    */
+/* pairs takes the kappa that best balances the barrier gradient g_B        */
+/* (kappa = 1) against the gradient of the rest of the potential g_E,       */
+/* argmin_k |g_E + k g_B| = -g_E.g_B / g_B.g_B, clamped to [kmin, kmax]     */
+/* (kmin until then).  Later steps double it, up to kmax, when the smallest */
+/* pair distance at the step's start is below kdmin and smaller than at the */
+/* previous step's start.  Off by default: kappa stays the parameter.       */
+/* ------------------------------------------------------------------------ */
+OR_EXPORT void or_set_kappa_adaptive(void* p, int on, double kmin, double kmax, double kdmin) {
+  osys* S = p;
+  S->kadapt = on;
+  S->kinit = 0;
+  S->kmin = kmin;
+  S->kmax = kmax;
+  S->kdmin = kdmin;
+  S->dmin_prev = INFINITY;
+}
+OR_EXPORT double or_get_kappa(void* p) { return ((const osys*)p)->kappa; }
+
+/* smallest distance over the pairs within dhat at positions P (INFINITY if none) */
+static double min_pair_distance(const osys* S, const double* P, int brute) {
+  plist PT = {0}, EE = {0}, PG = {0};
+  detect(S, P, brute, &PT, &EE, &PG);
+  double m2 = INFINITY;
+  for (int q = 0; q < PT.n; ++q) {
+    const int v = PT.p[q].a;
+    const int* tv = S->stris + 3 * PT.p[q].b;
+    double s2;
+    or_pt_classify(P + 3 * v, P + 3 * tv[0], P + 3 * tv[1], P + 3 * tv[2], &s2);
+    if (s2 < m2) m2 = s2;
+  }
+  for (int q = 0; q < EE.n; ++q) {
+    const int *e = S->sedges + 2 * EE.p[q].a, *f = S->sedges + 2 * EE.p[q].b;
+    double s2;
+    or_ee_classify(P + 3 * e[0], P + 3 * e[1], P + 3 * f[0], P + 3 * f[1], &s2);
+    if (s2 < m2) m2 = s2;
+  }
+  for (int q = 0; q < PG.n; ++q) {
+    const double* pl = S->planes + 4 * PG.p[q].b;
+    const double d = vdot(pl, P + 3 * PG.p[q].a) - pl[3];
+    if (d * d < m2) m2 = d * d;
+  }
+  free(PT.p); free(EE.p); free(PG.p);
+  return sqrt(m2);
+}
+
+static void kappa_update(osys* S, const double* x, const double* xtil, int brute) {
+  const int n = 3 * S->nn;
+  double* P = malloc(sizeof(double) * 3 * S->nv);
+  or_vertex_positions(S, x, P);
+  const double dmin = min_pair_distance(S, P, brute);
+  if (!S->kinit) {
+    if (isfinite(dmin)) {
+      double *gE = malloc(sizeof(double) * n), num = 0.0, den = 0.0;
+      S->kappa = 0.0;
+      or_assemble(S, x, xtil, brute, 0);
+      memcpy(gE, G_ASM->g, sizeof(double) * n);
+      S->kappa = 1.0;
+      or_assemble(S, x, xtil, brute, 0);
+      for (int i = 0; i < n; ++i) {
+        const double gB = G_ASM->g[i] - gE[i];
+        num += gE[i] * gB;
+        den += gB * gB;
+      }
+      double k = (den > 0.0) ? -num / den : S->kmin;
+      if (!(k >= S->kmin)) k = S->kmin;
+      if (k > S->kmax) k = S->kmax;
+      S->kappa = k;
+      S->kinit = 1;
+      free(gE);
+    } else {
+      S->kappa = S->kmin;
+    }
+  } else if (dmin < S->kdmin && dmin < S->dmin_prev) {
+    S->kappa = fmin(2.0 * S->kappa, S->kmax);
+  }
+  S->dmin_prev = dmin;
+  free(P);
+}
+
+/* ------------------------------------------------------------------------ */
 /* one implicit time step: Newton on the incremental potential              */
 /* ------------------------------------------------------------------------ */
 /* stats: [0] newton iters, [1] pcg iters total, [2] last alpha, [3] final ||p||inf,
- *        [4] n_pt, [5] n_ee, [6] n_pg, [7] line-search failures            */
+ *        [4] n_pt, [5] n_ee, [6] n_pg, [7] line-search failures,
+ *        [8] the step's barrier stiffness kappa                            */
 OR_EXPORT int or_step(void* p, double* x, double* v, int brute, double* stats) {
   osys* S = p;
   int n = 3 * S->nn;
@@ -1666,6 +1752,7 @@ OR_EXPORT int or_step(void* p, double* x, double* v, int brute, double* stats) {
          *dir = malloc(sizeof(double) * n), *xtrial = malloc(sizeof(double) * n);
   memcpy(xt, x, sizeof(double) * n);
   or_xtilde(S, x, v, xtil);
+  if (S->kadapt) kappa_update(S, x, xtil, brute);
   int rc = 0, it, pcg_total = 0, ls_fail = 0;
   double alpha = 0.0, pinf = 0.0;
   for (it = 0; it < S->newton_max; ++it) {
@@ -1697,6 +1784,7 @@ OR_EXPORT int or_step(void* p, double* x, double* v, int brute, double* stats) {
     stats[0] = it; stats[1] = pcg_total; stats[2] = alpha; stats[3] = pinf;
     stats[4] = G_ASM ? G_ASM->PT.n : 0; stats[5] = G_ASM ? G_ASM->EE.n : 0; stats[6] = G_ASM ? G_ASM->PG.n : 0;
     stats[7] = ls_fail;
+    stats[8] = S->kappa;
   }
   free(xt); free(xtil); free(g); free(dir); free(xtrial);
   return rc;
