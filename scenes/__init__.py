@@ -389,6 +389,40 @@ def mixed_scene(sphere_r=0.1, sphere_h=0.0108, cloth_n=101, cloth_size=1.0, n_bo
     return finalize_scene(parts, "mixed", dt, dhat, kappa, n_steps, planes=[[0, 1, 0, 0]])
 
 
+def union_contact_scene(gap=3e-4, dhat=1e-3, kappa=1e4, dt=0.01, seed=0):
+    """A small scene where every UNION combination is in contact at rest.
+
+    Box A (affine) rests ``gap`` above the ground; box B (affine, turned 20
+    degrees about y) sits ``gap`` above A, so their faces and crossing edges
+    form body-body point-triangle and edge-edge pairs; a 3x3 cloth lies
+    ``gap`` above B (free vertex on body triangle) and box C (affine) lies
+    ``gap`` above the cloth (body vertex on free triangle); a one-hex soft
+    block (6 tets) stands ``gap`` from A's +x face and ``gap`` above the ground
+    (free vertex on body triangle, free point-ground).
+    """
+    parts = _empty_parts()
+    sa, sb, sc = 0.04, 0.03, 0.008
+    av, af = box_surface(sa, (0.0, gap + sa / 2, 0.0))
+    _add_body(parts, av, af, mass=1000.0 * sa ** 3, vol=sa ** 3, kappa=1e8)
+    c = np.cos(np.radians(20.0)); sn = np.sin(np.radians(20.0))
+    Ry = np.array([[c, 0.0, sn], [0.0, 1.0, 0.0], [-sn, 0.0, c]])
+    b_c = np.array([0.002, gap + sa + gap + sb / 2, 0.001])
+    bv, bf = box_surface(sb, (0.0, 0.0, 0.0))
+    _add_body(parts, bv @ Ry.T + b_c, bf, mass=1000.0 * sb ** 3, vol=sb ** 3, kappa=1e8)
+    top_b = b_c[1] + sb / 2
+    thick, E_c, nu_c = 1e-3, 1e6, 0.3
+    kb = E_c * thick ** 3 / (24 * (1 - nu_c ** 2))
+    cs = 0.016
+    cv, ct = cloth_grid(3, cs, (b_c[0] - cs / 2, top_b + gap, b_c[2] - cs / 2))
+    _add_cloth(parts, cv, ct, E_c, nu_c, thick, 1000.0, kb)
+    cvv, cf = box_surface(sc, (b_c[0] + 0.001, top_b + 2 * gap + sc / 2, b_c[2] - 0.001))
+    _add_body(parts, cvv, cf, mass=1000.0 * sc ** 3, vol=sc ** 3, kappa=1e8)
+    hs = 0.015
+    hv = hex_grid(1, 1, 1, hs, (sa / 2 + gap, gap, -hs / 2))
+    _add_soft(parts, hv, kuhn_tets(1, 1, 1), 1e5, 0.4, 1000.0)
+    return finalize_scene(parts, "union_contact", dt, dhat, kappa, 1, planes=[[0, 1, 0, 0]])
+
+
 def beam_scene(nx=52, ny=8, nz=8, length=1.0, width=0.1, lift=0.02, seed=0, dt=0.01, dhat=1e-3,
                kappa=1e4, n_steps=20, rho=1000.0, nu=0.4):
     """Clamped beam (x=0 face fixed) with log-uniform per-tet E and N(0,0.1) velocities."""
