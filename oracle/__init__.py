@@ -384,16 +384,23 @@ class OracleSystem:
         rc = lib().or_pcg(self.h, _dp(_f64(rhs)), _dp(x), ctypes.c_double(tol), ctypes.c_int(maxit), ctypes.byref(it))
         return x, it.value, rc
 
-    def set_kappa_adaptive(self, on=True, kappa_min=1e-6, kappa_max=1e12, dmin=None):
+    def set_kappa_adaptive(self, on=True, kappa_min=None, kappa_max=None, dmin=None):
         """Adaptive barrier stiffness (reading c5): chosen at each step's start,
         frozen for the step.  The first step that starts with contact pairs
         balances the barrier gradient against the rest, clamped to
         [kappa_min, kappa_max]; later steps double kappa (up to kappa_max) when
         the smallest pair distance is below ``dmin`` (default dhat / 10) and
-        smaller than at the previous step's start."""
+        smaller than at the previous step's start.  kappa_min None: the
+        stiffness at which the barrier holds an average vertex's weight at
+        dhat / 2; kappa_max None: 1e4 kappa_min."""
         d = self.scene["dhat"] / 10.0 if dmin is None else dmin
-        lib().or_set_kappa_adaptive(self.h, ctypes.c_int(int(on)), ctypes.c_double(kappa_min),
-                                    ctypes.c_double(kappa_max), ctypes.c_double(d))
+        lib().or_set_kappa_adaptive(self.h, ctypes.c_int(int(on)), ctypes.c_double(kappa_min or 0.0),
+                                    ctypes.c_double(kappa_max or 0.0), ctypes.c_double(d))
+
+    def kappa_bounds(self):
+        a, b = ctypes.c_double(), ctypes.c_double()
+        lib().or_get_kappa_bounds(self.h, ctypes.byref(a), ctypes.byref(b))
+        return a.value, b.value
 
     @property
     def kappa(self):

@@ -1662,15 +1662,39 @@ OR_EXPORT double or_ccd_bound(void* p, const double* x, const double* dir, int b
 /* (kmin until then).  Later steps double it, up to kmax, when the smallest */
 /* pair distance at the step's start is below kdmin and smaller than at the */
 /* previous step's start.  Off by default: kappa stays the parameter.       */
+/*                                                                          */
+/* kmin <= 0 derives the lower bound from the scene: the stiffness at which */
+/* the barrier alone holds the weight of an average vertex (total mass /    */
+/* vertex count) at half the activation distance.  In this potential the   */
+/* weight enters as m h^2 |g| (inertia term with x_tilde = x + h v + h^2 g) */
+/* and the barrier as kappa |db/dd|, d the distance, so                     */
+/*   kmin = m h^2 |g| / |db/dd (dhat / 2)|,  db/dd = 2 d b'(d^2).           */
+/* |g| = 0 takes standard gravity.  kmax <= 0 takes 1e4 kmin.               */
 /* ------------------------------------------------------------------------ */
+static double kappa_lower_bound(const osys* S) {
+  double m = 0.0;
+  for (int v = 0; v < S->nv; ++v) m += S->vmass[v];
+  m /= (S->nv > 0 ? S->nv : 1);
+  double gn = sqrt(S->grav[0] * S->grav[0] + S->grav[1] * S->grav[1] + S->grav[2] * S->grav[2]);
+  if (!(gn > 0.0)) gn = 9.80665;
+  const double d = 0.5 * S->dhat;
+  double b, db, d2b;
+  or_barrier_scalar(d * d, S->dhat * S->dhat, S->form, &b, &db, &d2b);
+  return m * S->dt * S->dt * gn / fabs(2.0 * d * db);
+}
 OR_EXPORT void or_set_kappa_adaptive(void* p, int on, double kmin, double kmax, double kdmin) {
   osys* S = p;
   S->kadapt = on;
   S->kinit = 0;
-  S->kmin = kmin;
-  S->kmax = kmax;
+  S->kmin = kmin > 0.0 ? kmin : kappa_lower_bound(S);
+  S->kmax = kmax > 0.0 ? kmax : 1e4 * S->kmin;
   S->kdmin = kdmin;
   S->dmin_prev = INFINITY;
+}
+OR_EXPORT void or_get_kappa_bounds(void* p, double* kmin, double* kmax) {
+  const osys* S = p;
+  *kmin = S->kmin;
+  *kmax = S->kmax;
 }
 OR_EXPORT double or_get_kappa(void* p) { return ((const osys*)p)->kappa; }
 

@@ -7,7 +7,9 @@ to [kappa_min, kappa_max]; later steps double it (up to kappa_max) when the
 smallest pair distance is below a threshold and smaller than at the previous
 step's start.  The pins check the argmin property with gradients taken from
 separate systems assembled at kappa = 0 and kappa = 1, the clamps, and the
-doubling rule against distances recomputed from the pair lists.
+doubling rule against distances recomputed from the pair lists.  The default
+lower bound (the stiffness that holds an average vertex's weight at dhat / 2)
+is pinned by the static equilibrium of such a vertex and by its scaling.
 """
 import numpy as np
 import pytest
@@ -115,3 +117,73 @@ def test_off_by_default():
     O = oracle.OracleSystem(s)
     x, v = O.initial_state()
     assert O.step(x, v)[3]["kappa"] == s["kappa"]
+
+
+def hanging_vertex_scene(dhat=1e-3, dt=0.01, rho=1000.0):
+    """One tet at rest with three vertices fixed 5 cm up and the fourth, free,
+    dhat / 2 above the ground: the free vertex's only contact is its
+    point-ground pair, and every vertex carries the same lumped mass."""
+    h = 0.05
+    verts = np.array([[0.0, dhat / 2, 0.0], [0.0, h, 0.0], [0.02, h, 0.0], [0.0, h, 0.02]])
+    tets = np.array([[0, 2, 1, 3]])
+    parts = scenes._empty_parts()
+    scenes._add_soft(parts, verts, tets, 1e5, 0.3, rho)
+    parts["fixed"].append([1, 2, 3])
+    parts["fixed_vel"].append(np.zeros((3, 3)))
+    s = scenes.finalize_scene(parts, "hanging", dt, dhat, 1e4, 1, planes=[[0, 1, 0, 0]])
+    return s
+
+
+@pytest.mark.parametrize("form", [0, 1])
+def test_derived_lower_bound_is_the_resting_equilibrium(form):
+    """kappa_min by default: the stiffness at which the barrier alone holds an
+    average vertex's weight at dhat / 2.  A free vertex of that mass resting at
+    dhat / 2 with zero velocity is then in static equilibrium: the first step
+    (contact at its start) balances the gradients to exactly kappa_min, the
+    incremental potential's gradient vanishes there, and the step leaves the
+    vertex where it is."""
+    s = hanging_vertex_scene()
+    vol = abs(np.linalg.det(np.array([[0.02, 0, 0], [0, 0, 0.02], [0, 0.05 - 5e-4, 0]]))) / 6.0
+    O = oracle.OracleSystem(s, pcg_tol=1e-12, barrier_form=form)
+    x, v = O.initial_state()
+    assert O.nn == 1 and len(O.pairs(x)[2]) == 1
+    O.set_kappa_adaptive(True)
+    kmin, kmax = O.kappa_bounds()
+    assert kmax == pytest.approx(1e4 * kmin, rel=1e-15)
+    # with kappa = kmin the assembled gradient at rest vanishes (equilibrium)
+    Ok = oracle.OracleSystem(s, kappa=kmin, barrier_form=form)
+    g = Ok.assemble(x, Ok.xtilde(x, v))
+    m = 1000.0 * vol / 4.0
+    assert np.abs(g).max() <= 1e-9 * m * s["dt"] ** 2 * 9.81
+    x1, v1, rc, st = O.step(x, v)
+    assert rc == 0 and st["kappa"] == pytest.approx(kmin, rel=1e-12)
+    assert np.abs(x1 - x).max() <= 1e-12 and np.abs(v1).max() <= 1e-10
+
+
+def test_derived_lower_bound_scales_with_mass_and_step():
+    """m h^2 |g| scaling: doubling the density doubles kappa_min, doubling dt
+    quadruples it."""
+    def kmin(**kw):
+        O = oracle.OracleSystem(hanging_vertex_scene(**kw))
+        O.set_kappa_adaptive(True)
+        return O.kappa_bounds()[0]
+    k0 = kmin()
+    assert kmin(rho=2000.0) == pytest.approx(2.0 * k0, rel=1e-12)
+    assert kmin(dt=0.02) == pytest.approx(4.0 * k0, rel=1e-12)
+
+
+def test_config1_rollout_with_derived_bounds():
+    """The first configuration (two cubes, kappa adaptive) runs its first steps
+    with every Newton solve converged, kappa non-decreasing from the lower bound."""
+    s = scenes.cubes_scene()
+    O = oracle.OracleSystem(s, pcg_tol=1e-8)
+    O.set_kappa_adaptive(True)
+    kmin, _ = O.kappa_bounds()
+    x, v = O.initial_state()
+    ks = []
+    for _ in range(4):
+        x, v, rc, st = O.step(x, v)
+        assert rc == 0
+        ks.append(st["kappa"])
+    assert ks[0] == kmin and all(b >= a for a, b in zip(ks, ks[1:])) and ks[-1] > kmin
+    assert O.positions(x)[:, 1].min() > 0

@@ -478,10 +478,22 @@ def test_step_no_interpenetration_and_descent(cubes_contact):
     assert O.energy(x1, xt) <= E0
     P = O.positions(x1)
     assert P[:, 1].min() > 0
+    # no crossing along the segment from x to x1: positions are linear in the
+    # DOFs, so P(t) = P0 + t (P1 - P0); every pair found at the samples keeps a
+    # positive distance (brute-force detection at each sample)
+    P0 = O.positions(x)
+    for t in np.linspace(0.0, 1.0, 33):
+        Pt = P0 + t * (P - P0)
+        xs = x + t * (x1 - x)
+        assert np.allclose(O.positions(xs), Pt, rtol=0, atol=1e-15)
+        pts, ees, pgs = O.pairs(xs, brute=True)
+        for a, b, sub in pts:
+            assert oracle.pt_classify(Pt[a], *Pt[s["surf_tris"][b]])[1] > 0
+        for a, b, sub in ees:
+            e, f = s["surf_edges"][a], s["surf_edges"][b]
+            assert oracle.ee_classify(Pt[e[0]], Pt[e[1]], Pt[f[0]], Pt[f[1]])[1] > 0
+        assert Pt[:, 1].min() > 0
     pt, ee, pg = O.pairs(x1)
-    for st_, pair in ((0, pt), (1, ee)):
-        for a, b, sub in pair:
-            pass
     # every detected pair has a strictly positive distance
     for a, b, sub in pt:
         tv = s["surf_tris"][b]
