@@ -20,7 +20,11 @@
 //    race on the array and give wrong results -- serialise them;
 //  * the first call on a device looks up the array's device address (once per
 //    device, with that device current); make that first call before any
-//    stream capture.
+//    stream capture;
+//  * a call cannot itself be captured into a CUDA graph: it reads its
+//    convergence scalars back to the host every 8 iterations;
+//  * p_dev must not alias rhs_dev or any other input (the call zeroes p before
+//    it has finished reading rhs).
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -47,8 +51,12 @@ static __device__ __align__(256) double g_pcg_scratch[kScratchDoubles];
 
 struct scal {  // lives at g_pcg_scratch + kOffScal
   double rz, rz0, alpha, beta, tol2;
-  int done, iters;
+  int done, iters;  // done: 0 running, 1 converged, 2 d^T H d <= 0, 3 iteration cap
+  int max_iter;
 };
+// bits of the flag word (the last double of the array)
+constexpr int kBadDiag = 1;   // a diagonal block that is not positive definite
+constexpr int kBadIndex = 2;  // an upper block outside 0 <= row < col < n_nodes
 static_assert(sizeof(scal) <= 16 * sizeof(double), "scalar block too large");
 
 __device__ double blk_sum(double v) {
@@ -67,7 +75,7 @@ __device__ double blk_sum(double v) {
 
 // invert the 3x3 diagonal blocks; r = rhs, p = 0, d = 0, z = M^-1 r, partial r.z
 __global__ void ks_init(int nn, const double* __restrict__ diag, const double* __restrict__ rhs, double* __restrict__ p,
-                        double* S, double tol2, int* bad) {
+                        double* S, double tol2, int max_iter, int* bad) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   double* r = S + kOffR;
   double* z = S + kOffZ;
@@ -79,12 +87,15 @@ __global__ void ks_init(int nn, const double* __restrict__ diag, const double* _
     const double c00 = A[4] * A[8] - A[5] * A[7], c01 = A[5] * A[6] - A[3] * A[8], c02 = A[3] * A[7] - A[4] * A[6];
     const double det = A[0] * c00 + A[1] * c01 + A[2] * c02;
     double inv[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
-    if (det > 0.0 && isfinite(det)) {
+    // Sylvester's criterion: a symmetric 3x3 block is positive definite iff
+    // its leading minors A00, A00 A11 - A01 A10 and det are all positive
+    const double m2 = A[0] * A[4] - A[1] * A[3];
+    if (A[0] > 0.0 && m2 > 0.0 && det > 0.0 && isfinite(det)) {
       inv[0] = c00 / det; inv[1] = (A[2] * A[7] - A[1] * A[8]) / det; inv[2] = (A[1] * A[5] - A[2] * A[4]) / det;
       inv[3] = c01 / det; inv[4] = (A[0] * A[8] - A[2] * A[6]) / det; inv[5] = (A[2] * A[3] - A[0] * A[5]) / det;
       inv[6] = c02 / det; inv[7] = (A[1] * A[6] - A[0] * A[7]) / det; inv[8] = (A[0] * A[4] - A[1] * A[3]) / det;
     } else {
-      atomicOr(bad, 1);
+      atomicOr(bad, kBadDiag);
     }
     for (int t = 0; t < 9; ++t) M[9 * (size_t)i + t] = inv[t];
     for (int a = 0; a < 3; ++a) {
@@ -106,6 +117,7 @@ __global__ void ks_init(int nn, const double* __restrict__ diag, const double* _
     sc->beta = 0.0;
     sc->iters = 0;
     sc->done = 0;
+    sc->max_iter = max_iter;
   }
 }
 
@@ -119,12 +131,17 @@ __global__ void ks_finish_rz(int nparts, double* S, int first) {
     if (first) {
       sc->rz = v;
       sc->rz0 = v;
-      if (!(v > 0.0)) sc->done = 1;
+      // r0 = 0 exactly: p = 0 is the solution; a negative or NaN r^T z means
+      // an indefinite preconditioner block or a non-finite right-hand side
+      if (v == 0.0) sc->done = 1;
+      else if (!(v > 0.0)) sc->done = 2;
     } else if (!sc->done) {
       sc->beta = v / sc->rz;
       sc->rz = v;
       sc->iters += 1;
       if (v <= sc->tol2 * sc->rz0) sc->done = 1;
+      else if (!(v == v)) sc->done = 2;
+      else if (sc->iters >= sc->max_iter) sc->done = 3;
     }
   }
 }
@@ -148,9 +165,11 @@ __global__ void ks_dir(int nn, const double* __restrict__ diag, double* S) {
   for (int a = 0; a < 3; ++a) q[3 * i + a] = B[3 * a] * dv[0] + B[3 * a + 1] * dv[1] + B[3 * a + 2] * dv[2];
 }
 
-// q += U d + U^T d over upper blocks (row < col), one block per thread
-__global__ void ks_upper(int nnzb, const int* __restrict__ row, const int* __restrict__ col,
-                         const double* __restrict__ vals, double* S) {
+// q += U d + U^T d over upper blocks (row < col), one block per thread; a
+// block outside 0 <= row < col < nn is skipped and flagged (the call then
+// fails with YASPS_E_INVAL), so a bad index never addresses the array
+__global__ void ks_upper(int nn, int nnzb, const int* __restrict__ row, const int* __restrict__ col,
+                         const double* __restrict__ vals, double* S, int* bad) {
   const scal* sc = reinterpret_cast<const scal*>(S + kOffScal);
   if (sc->done) return;
   const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -158,6 +177,10 @@ __global__ void ks_upper(int nnzb, const int* __restrict__ row, const int* __res
   const double* d = S + kOffD;
   double* q = S + kOffQ;
   const int r = row[k], c = col[k];
+  if (r < 0 || r >= c || c >= nn) {
+    atomicOr(bad, kBadIndex);
+    return;
+  }
   const double* B = vals + 9 * (size_t)k;
   for (int a = 0; a < 3; ++a) {
     atomicAdd(&q[3 * r + a], B[3 * a] * d[3 * c] + B[3 * a + 1] * d[3 * c + 1] + B[3 * a + 2] * d[3 * c + 2]);
@@ -233,6 +256,10 @@ extern "C" yasps_status yasps_pcg_solve_static(int n_nodes, int nnzb, const int*
     set_err(err, err_len, "yasps_pcg_solve_static: bad arguments");
     return YASPS_E_INVAL;
   }
+  if (n_nodes > 0 && (p_dev == rhs_dev || p_dev == diag_dev || (nnzb > 0 && p_dev == vals_dev))) {
+    set_err(err, err_len, "yasps_pcg_solve_static: p_dev must not alias an input");
+    return YASPS_E_INVAL;
+  }
   if (n_nodes > kMaxNodes) {
     char m[160];
     snprintf(m, sizeof m, "yasps_pcg_solve_static: %d nodes exceed the fixed scratch capacity of %d nodes", n_nodes,
@@ -275,18 +302,17 @@ extern "C" yasps_status yasps_pcg_solve_static(int n_nodes, int nnzb, const int*
     set_err(err, err_len, "yasps_pcg_solve_static: cudaMemsetAsync failed");
     return YASPS_E_CUDA;
   }
-  ks_init<<<nblk, kThreads, 0, st>>>(n_nodes, diag_dev, rhs_dev, p_dev, S, rel_tol * rel_tol, bad);
+  ks_init<<<nblk, kThreads, 0, st>>>(n_nodes, diag_dev, rhs_dev, p_dev, S, rel_tol * rel_tol, max_iter, bad);
   ks_finish_rz<<<1, kThreads, 0, st>>>(nblk, S, 1);
-  struct {
-    double rz, rz0, alpha, beta, tol2;
-    int done, iters;
-  } h{};
+  scal h{};
   int bad_h = 0;
   int launched = 0;
   for (;;) {
     for (int k = 0; k < 8; ++k) {
       ks_dir<<<nblk, kThreads, 0, st>>>(n_nodes, diag_dev, S);
-      if (nnzb > 0) ks_upper<<<(nnzb + kThreads - 1) / kThreads, kThreads, 0, st>>>(nnzb, row_dev, col_dev, vals_dev, S);
+      if (nnzb > 0)
+        ks_upper<<<(nnzb + kThreads - 1) / kThreads, kThreads, 0, st>>>(n_nodes, nnzb, row_dev, col_dev, vals_dev, S,
+                                                                        bad);
       ks_dot_dq<<<kDotBlocks, kThreads, 0, st>>>(n3, S);
       ks_alpha<<<1, kThreads, 0, st>>>(kDotBlocks, S);
       ks_update<<<nblk, kThreads, 0, st>>>(n_nodes, p_dev, S);
@@ -302,13 +328,19 @@ extern "C" yasps_status yasps_pcg_solve_static(int n_nodes, int nnzb, const int*
       set_err(err, err_len, cudaGetErrorString(e));
       return YASPS_E_CUDA;
     }
-    if (h.done || h.iters >= max_iter || launched >= max_iter) break;
+    if (h.done || (bad_h & kBadIndex) || launched >= max_iter) break;
   }
   if (iters) *iters = h.iters;
   const double rr = (h.rz0 > 0.0) ? std::sqrt(std::fmax(h.rz, 0.0) / h.rz0) : 0.0;
   if (rel_res) *rel_res = rr;
-  if (bad_h || h.done == 2) {
-    set_err(err, err_len, "yasps_pcg_solve_static: matrix not positive definite (singular diagonal block or d^T H d <= 0)");
+  if (bad_h & kBadIndex) {
+    set_err(err, err_len, "yasps_pcg_solve_static: an upper block is outside 0 <= row < col < n_nodes");
+    return YASPS_E_INVAL;
+  }
+  if ((bad_h & kBadDiag) || h.done == 2) {
+    set_err(err, err_len,
+            "yasps_pcg_solve_static: matrix not positive definite or non-finite input (indefinite diagonal block, "
+            "r^T z <= 0 or NaN, or d^T H d <= 0)");
     return YASPS_E_NAN;
   }
   if (h.done != 1 && rr > rel_tol) {
