@@ -83,6 +83,26 @@ typedef struct {
                          previous direction the line search did not take, (1 - alpha) p;
                          PCG then stops when r^T z <= tol^2 g^T M^-1 g (the same accuracy
                          relative to the right-hand side g as a cold start) */
+  /* Adaptive barrier stiffness (the adaptive stiffness of IPC, Li et al. 2020,
+   * restated per time step; single scenes only).  With kappa_adaptive != 0,
+   * yasps_step chooses kappa at the start of each step and keeps it for the
+   * whole step: the first step that starts with contact pairs takes
+   * argmin_k |g_E + k g_B| = -g_E.g_B / g_B.g_B (g_B: barrier gradient at
+   * kappa = 1, g_E: gradient of the rest of the potential) clamped to
+   * [kappa_min, kappa_max], and kappa_min before that; every later step
+   * doubles kappa (at most kappa_max) when the smallest pair distance at its
+   * start is below kappa_dmin (<= 0: dhat / 10) and below the previous
+   * step's.  kappa_min <= 0
+   * derives the lower bound from the scene: the stiffness at which the
+   * barrier alone holds an average vertex's weight (total mass / vertex
+   * count) at dhat / 2, m h^2 |g| / (2 d |b'(d^2)|) with d = dhat / 2 (|g| = 0:
+   * standard gravity); kappa_max <= 0 takes 1e4 times the lower bound.  The
+   * kappa of the last step is in yasps_step_stats.kappa and the state can be
+   * read and restored with yasps_get_kappa_state / yasps_set_kappa_state. */
+  int kappa_adaptive;
+  double kappa_min, kappa_max, kappa_dmin;
+  double ls_armijo;   /* line search: accept E(x - alpha p) <= E(x) - ls_armijo alpha g^T p
+                         (0: any decrease, up to the rounding of the energy sums) */
 } yasps_params;
 
 /* Scene, host pointers, copied at build.  Index arrays are int32, 0-based.
@@ -143,11 +163,31 @@ typedef struct {
   double p_inf;         /* ||p||_inf at exit */
   double t_eval_ms, t_pcg_ms, t_ccd_ms, t_ls_ms; /* stage times (CUDA events) */
   int n_cand_pt, n_cand_ee; /* swept-box candidates of the last line search */
+  double kappa;         /* barrier stiffness the step used */
 } yasps_step_stats;
+
+/* One record per Newton iteration of the last yasps_step on a single scene
+ * (the convergence diagnostics of Sec. "Solver": why a step needed the
+ * iterations it did).  Iteration k: the direction p solved at x_k, its
+ * infinity norm and the node holding it, the PCG effort, the CCD bound
+ * alpha_ccd along x_k - alpha p, the accepted alpha after ls_halvings
+ * halvings, the energies E(x_k) and E(x_k - alpha p), and the active pair
+ * counts at x_k.  s_min is the smallest squared pair distance at x_k (-1 when
+ * yasps_newton_trace_enable was not on, +inf with no pair).  The last record
+ * of a converged step has alpha = 0 (no line search ran). */
+typedef struct {
+  int pcg_iters, ls_halvings;
+  int n_pt, n_ee, n_pg, n_cand_pt, n_cand_ee;
+  int pinf_node;
+  double p_inf, pcg_rel_res, alpha_ccd, alpha, E0, E1, s_min;
+  double g_dot_p;     /* g^T p: the decrease the quadratic model predicts for alpha = 1 is g^T p / 2 */
+  double p_at_max[3]; /* p at pinf_node */
+} yasps_newton_record;
 
 /* Fill *p with defaults (FP64, dt 0.01, dhat 1e-3, kappa 1e4, g = (0,-9.81,0),
  * newton_tol 1e-6, pcg_rel_tol 1e-4, newton_max_iter 100, ls_max_iter 30,
- * barrier_form 0, ccd_gap 0.1, ccd_max_iter 100000, refine_sweeps 4, pcg_warm_start 1). */
+ * barrier_form 0, ccd_gap 0.1, ccd_max_iter 100000, refine_sweeps 4, pcg_warm_start 1,
+ * kappa_adaptive 0, kappa_min, kappa_max and kappa_dmin 0 (derived), ls_armijo 0). */
 void yasps_default_params(yasps_params* p);
 
 /* Build a system: uploads the scene, computes rest-shape quantities
@@ -225,7 +265,10 @@ yasps_status yasps_energy(yasps_system* sys, const double* x_dev, const double* 
  * block-Jacobi inverse (App. D; only when YASPS_TERM_INERTIA is in the mask,
  * since the inverse needs the mass-regularised full Hessian).  Uses the pair lists of the last
  * yasps_detect_pairs, which must have been called at the same x.  Zeroes g and
- * H first.  Asynchronous. */
+ * H first.  Synchronises (reads the device status).  Errors: E_NAN for a
+ * non-finite value, or (project != 0) a diagonal block that is not positive
+ * definite; with project == 0 such a block is not an error (exact Hessians can
+ * be indefinite) but the block-Jacobi preconditioner is then not usable. */
 yasps_status yasps_eval_local(yasps_system* sys, const double* x_dev, const double* xtilde_dev, int term_mask,
                               int project);
 
@@ -265,6 +308,25 @@ yasps_status yasps_ccd_bound(yasps_system* sys, const double* x_dev, const doubl
  * the last accepted iterate). */
 yasps_status yasps_step(yasps_system* sys, double* x_dev, double* v_dev, yasps_step_stats* stats);
 
+/* Newton records of the last yasps_step (single scenes; see
+ * yasps_newton_record).  capacity: room in out (host); *count receives the
+ * number of records of the step (which may exceed capacity; only
+ * min(count, capacity) are written).  yasps_newton_trace_enable(sys, 1)
+ * adds the smallest pair distance to every record at the cost of one small
+ * kernel and a host read per Newton iteration. */
+yasps_status yasps_newton_trace(const yasps_system* sys, int capacity, yasps_newton_record* out_host, int* count);
+yasps_status yasps_newton_trace_enable(yasps_system* sys, int enable);
+
+/* Adaptive-kappa state (kappa_adaptive): the current kappa, whether it has
+ * been initialised by gradient balance, and the smallest pair distance at the
+ * start of the previous step (+inf: none); kappa_lo / kappa_hi receive the
+ * bounds in force (kappa_min / kappa_max or the derived ones).  Any output
+ * pointer may be NULL.  Read the state to checkpoint a rollout, write it to
+ * resume one. */
+yasps_status yasps_get_kappa_state(yasps_system* sys, double* kappa, int* initialised, double* dmin_prev,
+                                   double* kappa_lo, double* kappa_hi);
+yasps_status yasps_set_kappa_state(yasps_system* sys, double kappa, int initialised, double dmin_prev);
+
 /* Prescribed positions of fixed vertices (host [n_verts][3]; only fixed rows
  * are read / written). */
 yasps_status yasps_set_fixed_positions(yasps_system* sys, const double* P_host);
@@ -283,6 +345,17 @@ yasps_status yasps_get_fixed_positions(yasps_system* sys, double* P_host);
 #define YASPS_PCG_VARIANTS 5
 yasps_status yasps_autotune_pcg(yasps_system* sys, int iters, int* variant, double* us_per_iter);
 yasps_status yasps_set_pcg_variant(yasps_system* sys, int variant);
+
+/* Bound of the PCG kernel's device-side waits (its grid barriers and tile
+ * copies): after `polls` polls a waiting block raises the kernel's abort flag,
+ * every block leaves at its next wait (each still waiting for its own copies
+ * in flight), and the solve returns YASPS_E_TIMEOUT with the system still
+ * usable.  0 restores the default (2^22 polls, a few seconds).
+ * unmet_next != 0 is for testing that path: the next PCG launch's grid
+ * barriers wait for one arrival more than the grid has (a count nothing
+ * completes), so every block runs into the bound; the setting is cleared by
+ * that launch. */
+yasps_status yasps_set_wait_limit(yasps_system* sys, long long polls, int unmet_next);
 
 /* Per-scene results of the last yasps_step on a batch (host arrays of
  * n_scenes, each nullable): Newton iterations, PCG iterations summed over the
@@ -374,6 +447,14 @@ yasps_status yasps_profile_get(yasps_system* sys, int stage, yasps_stage_stats* 
  * block of the grid needs beyond the first. */
 yasps_status yasps_pcg_phase_ms(const yasps_system* sys, double* out);
 
+/* Measured FMA throughput of the current device's FP64 (precision 0) or FP32
+ * (precision 1) pipe in TFLOP/s (2 flops per FMA), from a kernel of
+ * independent register FMA chains on every SM, best of three timed launches
+ * on the legacy default stream (synchronises the device).  These are the
+ * peaks the element and barrier kernels' ALU rooflines are measured against.
+ * Errors: E_INVAL, E_CUDA. */
+yasps_status yasps_probe_fma_tflops(int precision, double* tflops_host);
+
 /* Block-Jacobi PCG that allocates no device memory (the paper has no
  * counterpart; it is an interface for callers that cannot allocate).
  * Some callers may not call cudaMalloc / cudaFree at solve time -- code inside
@@ -393,8 +474,16 @@ yasps_status yasps_pcg_phase_ms(const yasps_system* sys, double* out);
  * larger problems get YASPS_E_CAPACITY.  All calls share that array: calls
  * whose work overlaps on the GPU race and must be serialised.  The first call
  * on a device looks up the array's device address; make it before any stream
- * capture.  Work runs on cuda_stream; the call returns after synchronising it.
- * Errors: E_INVAL, E_CAPACITY, E_NAN (not positive definite), E_NOCONV, E_CUDA. */
+ * capture.  A call cannot itself be captured into a CUDA graph: it reads its
+ * convergence scalars back every 8 iterations.  p_dev must not alias rhs_dev
+ * or any other input (equal pointers get E_INVAL).  Work runs on cuda_stream;
+ * the call returns after synchronising it.
+ * Errors: E_INVAL (bad arguments, aliasing, or an upper block outside
+ * 0 <= row < col < n_nodes, which is skipped on the device and reported),
+ * E_CAPACITY, E_NAN (a diagonal block that is not positive definite by
+ * Sylvester's criterion, r^T z < 0 or NaN from a non-finite rhs, or
+ * d^T H d <= 0), E_NOCONV (max_iter reached; p holds the last iterate), E_CUDA.
+ * A zero rhs returns YASPS_OK with p = 0. */
 yasps_status yasps_pcg_solve_static(int n_nodes, int nnzb, const int* row_dev, const int* col_dev,
                                     const double* vals_dev, const double* diag_dev, const double* rhs_dev,
                                     double* p_dev, double rel_tol, int max_iter, void* cuda_stream, int* iters,

@@ -28,7 +28,9 @@ EXPORTS = [
     "yasps_detect_pairs", "yasps_export_pairs", "yasps_energy", "yasps_eval_local", "yasps_assemble",
     "yasps_export_bsr", "yasps_export_gradient", "yasps_spmv", "yasps_pcg_solve", "yasps_ccd_bound", "yasps_step",
     "yasps_set_fixed_positions", "yasps_get_fixed_positions", "yasps_set_tet_young", "yasps_adjoint_step", "yasps_scene_stats", "yasps_autotune_pcg", "yasps_set_pcg_variant", "yasps_kernel_launches", "yasps_profile_enable",
-    "yasps_profile_get", "yasps_pcg_phase_ms", "yasps_pcg_solve_static",
+    "yasps_profile_get", "yasps_pcg_phase_ms", "yasps_pcg_solve_static", "yasps_newton_trace",
+    "yasps_newton_trace_enable", "yasps_get_kappa_state", "yasps_set_kappa_state", "yasps_set_wait_limit",
+    "yasps_probe_fma_tflops",
 ]
 STAGE_SPMV, STAGE_TET, STAGE_BARRIER, STAGE_PCG, STAGE_DETECT, STAGE_EVAL, STAGE_CCD, STAGE_LS, STAGE_PCG_KERNEL = range(9)
 STAGE_NAMES = ["spmv", "tet", "barrier", "pcg", "detect", "eval", "ccd", "line_search", "pcg_kernel"]
@@ -47,7 +49,9 @@ class Params(ctypes.Structure):
                 ("kappa", ctypes.c_double), ("gravity", ctypes.c_double * 3), ("newton_tol", ctypes.c_double),
                 ("pcg_rel_tol", ctypes.c_double), ("pcg_max_iter", ctypes.c_int), ("newton_max_iter", ctypes.c_int),
                 ("ls_max_iter", ctypes.c_int), ("barrier_form", ctypes.c_int), ("ccd_gap", ctypes.c_double),
-                ("ccd_max_iter", ctypes.c_int), ("refine_sweeps", ctypes.c_int), ("pcg_warm_start", ctypes.c_int)]
+                ("ccd_max_iter", ctypes.c_int), ("refine_sweeps", ctypes.c_int), ("pcg_warm_start", ctypes.c_int),
+                ("kappa_adaptive", ctypes.c_int), ("kappa_min", ctypes.c_double), ("kappa_max", ctypes.c_double),
+                ("kappa_dmin", ctypes.c_double), ("ls_armijo", ctypes.c_double)]
 
 
 _PD = ctypes.POINTER(ctypes.c_double)
@@ -72,10 +76,19 @@ class StepStats(ctypes.Structure):
                 ("n_ee", ctypes.c_int), ("n_pg", ctypes.c_int), ("status", ctypes.c_int),
                 ("alpha_last", ctypes.c_double), ("p_inf", ctypes.c_double), ("t_eval_ms", ctypes.c_double),
                 ("t_pcg_ms", ctypes.c_double), ("t_ccd_ms", ctypes.c_double), ("t_ls_ms", ctypes.c_double),
-                ("n_cand_pt", ctypes.c_int), ("n_cand_ee", ctypes.c_int)]
+                ("n_cand_pt", ctypes.c_int), ("n_cand_ee", ctypes.c_int), ("kappa", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class NewtonRecord(ctypes.Structure):
+    _fields_ = [("pcg_iters", ctypes.c_int), ("ls_halvings", ctypes.c_int), ("n_pt", ctypes.c_int),
+                ("n_ee", ctypes.c_int), ("n_pg", ctypes.c_int), ("n_cand_pt", ctypes.c_int),
+                ("n_cand_ee", ctypes.c_int), ("pinf_node", ctypes.c_int), ("p_inf", ctypes.c_double),
+                ("pcg_rel_res", ctypes.c_double), ("alpha_ccd", ctypes.c_double), ("alpha", ctypes.c_double),
+                ("E0", ctypes.c_double), ("E1", ctypes.c_double), ("s_min", ctypes.c_double),
+                ("g_dot_p", ctypes.c_double), ("p_at_max", ctypes.c_double * 3)]
 
 
 class StageStats(ctypes.Structure):
@@ -124,22 +137,43 @@ def _ptr(t):
     return ctypes.c_void_p(t.data_ptr())
 
 
-def pcg_solve_static(n_nodes, row, col, vals, diag, rhs, rel_tol=1e-4, max_iter=0, stream=None):
+def probe_fma_tflops(precision):
+    """Measured FMA throughput of the current GPU's FP64 (0) or FP32 (1) pipe, TFLOP/s."""
+    t = ctypes.c_double()
+    rc = lib().yasps_probe_fma_tflops(ctypes.c_int(precision), ctypes.byref(t))
+    if rc != YASPS_OK:
+        raise YaspsError(rc, "FMA probe failed")
+    return t.value
+
+
+def pcg_solve_static(n_nodes, row, col, vals, diag, rhs, rel_tol=1e-4, max_iter=0, stream=None, out=None):
     """Block-Jacobi PCG that allocates no device memory (yasps_pcg_solve_static).
 
-    For callers that may not allocate at solve time: every argument is a CUDA
-    tensor the caller owns (row/col int32 [nnzb], vals float64 [nnzb,3,3], diag
-    float64 [n_nodes,3,3], rhs float64 [n_nodes,3]); the temporaries live in a
-    fixed device array inside the library (at most 65536 nodes).  Returns
-    (p, iters, rel_res) with p a new tensor like rhs.
+    For callers that may not allocate at solve time: every argument is a
+    contiguous CUDA tensor the caller owns (row/col int32 [nnzb], vals float64
+    [nnzb,3,3], diag float64 [n_nodes,3,3], rhs float64 [n_nodes,3]); the
+    temporaries live in a fixed device array inside the library (at most 65536
+    nodes).  ``out`` (float64 [n_nodes,3], not aliasing rhs) receives p; without
+    it a new tensor is made here (which allocates, on the caller's side).
+    Returns (p, iters, rel_res).
     """
     import torch
 
-    p = torch.empty_like(rhs)
+    nnzb = int(row.numel())
+    want = [("row", row, torch.int32, (nnzb,)), ("col", col, torch.int32, (nnzb,)),
+            ("vals", vals, torch.float64, (nnzb, 3, 3)), ("diag", diag, torch.float64, (n_nodes, 3, 3)),
+            ("rhs", rhs, torch.float64, (n_nodes, 3))]
+    if out is not None:
+        want.append(("out", out, torch.float64, (n_nodes, 3)))
+    for name, t, dt, shape in want:
+        if not isinstance(t, torch.Tensor) or t.dtype != dt or not t.is_cuda or not t.is_contiguous():
+            raise ValueError(f"pcg_solve_static: {name} must be a contiguous CUDA {dt} tensor")
+        if tuple(t.shape) != shape and not (t.numel() == 0 and 0 in shape):
+            raise ValueError(f"pcg_solve_static: {name} has shape {tuple(t.shape)}, expected {shape}")
+    p = torch.empty_like(rhs) if out is None else out
     it, rel = ctypes.c_int(), ctypes.c_double()
     err = ctypes.create_string_buffer(256)
     s = stream if stream is not None else torch.cuda.current_stream()
-    nnzb = int(row.numel())
     null = ctypes.c_void_p(0)
     rc = lib().yasps_pcg_solve_static(ctypes.c_int(n_nodes), ctypes.c_int(nnzb), _ptr(row) if nnzb else null,
                                       _ptr(col) if nnzb else null, _ptr(vals) if nnzb else null, _ptr(diag),
@@ -339,6 +373,35 @@ class System:
         d["rc"] = rc
         return d
 
+    def newton_trace(self):
+        """Per-Newton-iteration records of the last step (list of dicts, yasps_newton_trace)."""
+        n = ctypes.c_int()
+        self._check(lib().yasps_newton_trace(self.h, ctypes.c_int(0), None, ctypes.byref(n)))
+        recs = (NewtonRecord * max(n.value, 1))()
+        self._check(lib().yasps_newton_trace(self.h, ctypes.c_int(n.value), recs, ctypes.byref(n)))
+        out = []
+        for r in recs[:n.value]:
+            d = {k: getattr(r, k) for k, _ in NewtonRecord._fields_}
+            d["p_at_max"] = list(r.p_at_max)
+            out.append(d)
+        return out
+
+    def newton_trace_enable(self, on=True):
+        """Also record the smallest pair distance of every Newton iteration."""
+        self._check(lib().yasps_newton_trace_enable(self.h, ctypes.c_int(int(on))))
+
+    def kappa_state(self):
+        """(kappa, initialised, smallest pair distance at the previous step's start,
+        lower bound, upper bound) of the adaptive barrier stiffness."""
+        k, i, d, lo, hi = ctypes.c_double(), ctypes.c_int(), ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        self._check(lib().yasps_get_kappa_state(self.h, ctypes.byref(k), ctypes.byref(i), ctypes.byref(d),
+                                                ctypes.byref(lo), ctypes.byref(hi)))
+        return k.value, bool(i.value), d.value, lo.value, hi.value
+
+    def set_kappa_state(self, kappa, initialised, dmin_prev):
+        self._check(lib().yasps_set_kappa_state(self.h, ctypes.c_double(kappa), ctypes.c_int(int(initialised)),
+                                                ctypes.c_double(dmin_prev)))
+
     def set_fixed_positions(self, P):
         P = np.ascontiguousarray(P, dtype=np.float64)
         self._check(lib().yasps_set_fixed_positions(self.h, P.ctypes.data_as(_PD)))
@@ -355,6 +418,12 @@ class System:
         us = np.zeros(PCG_VARIANTS)
         self._check(lib().yasps_autotune_pcg(self.h, ctypes.c_int(iters), ctypes.byref(v), us.ctypes.data_as(_PD)))
         return v.value, us
+
+    def set_wait_limit(self, polls, unmet_next=False):
+        """Polls a PCG-kernel wait may spend before the solve gives up with E_TIMEOUT
+        (0: default); unmet_next makes the next launch's barriers wait for an
+        arrival that never comes (testing the timeout path)."""
+        self._check(lib().yasps_set_wait_limit(self.h, ctypes.c_longlong(int(polls)), ctypes.c_int(int(unmet_next))))
 
     def set_pcg_variant(self, variant):
         self._check(lib().yasps_set_pcg_variant(self.h, ctypes.c_int(variant)))

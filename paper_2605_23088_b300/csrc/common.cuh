@@ -16,6 +16,7 @@ enum : int {
   DEV_BADINDEX = 4,  // index out of range
   DEV_ITERCAP = 8,   // an iteration cap was reached (ACCD)
   DEV_TIMEOUT = 16,  // a bounded grid-barrier wait gave up
+  DEV_INDEFINITE = 32,  // a block-Jacobi block is not positive definite (exact Hessians can be)
 };
 
 YASPS_D void dev_flag(int* status, int code) { atomicOr(status, code); }

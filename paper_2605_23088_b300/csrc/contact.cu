@@ -22,6 +22,7 @@
 #include <algorithm>
 #include <cfloat>
 #include <cmath>
+#include <cstring>
 
 #include "common.cuh"
 #include "distance.cuh"
@@ -423,7 +424,7 @@ __device__ __forceinline__ bool sat_apart(int kind, d3 y0, d3 y1, d3 y2, d3 y3, 
 struct bder {
   double b, db, d2b;
 };
-__device__ __forceinline__ bder barrier_fn(double s, double sh, int form) {
+__host__ __device__ __forceinline__ bder barrier_fn(double s, double sh, int form) {
   if (!(s < sh)) return {0.0, 0.0, 0.0};
   const double d = s - sh, L = log(s / sh);
   if (form == 1)
@@ -682,29 +683,54 @@ __device__ __forceinline__ void project_n(T* H) {
   project_psd<N, T>(H);
 }
 
-// PT / EE barrier pairs (kind 0 = PT, 1 = EE), one warp per pair.  Lane 0 classifies
-// the pair and forms the distance derivatives; the warp then builds the
-// position-space Hessian, projects it with a parallel-ordering Jacobi EVD in
-// shared memory (n/2 disjoint rotations per step, round-robin over the n - 1
-// steps of a sweep; the same rotation formula and stopping rule as
-// project_psd, so Project(H), which is unique, agrees to rounding), and
-// scatters through the merged UNION Jacobians.  Pair counts are often small
-// (hundreds to thousands): a thread per pair would leave the GPU idle while
-// each thread runs a 12x12 EVD out of local memory.
+// PT / EE barrier pairs (kind 0 = PT, 1 = EE) in two passes.
+//
+// k_barrier_prep, one thread per pair: the exact FP64 classification (closest
+// feature), the squared distance and the barrier derivatives b'(s), b''(s).
+// FP64 is scarce on this part and a warp instruction costs about the same
+// FP64 pipe time with one active lane as with 32, so this scalar work runs 32
+// pairs per warp instruction instead of on one lane of a warp per pair.
+//
+// k_barrier_pair, one warp per pair: every distance type is written in
+// reduced variables z = C y (PP: w = p - a; PE: w = p - a, e = b - a; PT and
+// EE: (w, e1, e2) as in the distance functions), C = coef (x) I3 with k = 1,
+// 2, 3 rows of small integers over the n = k + 1 classified vertices.  The
+// position-space Hessian is C^T H_z C with H_z = kappa (b'' g_z g_z^T + b'
+// d2s/dz2) (R x R, R = 3k).  With C C^T = L L^T (L = chol(coef coef^T) (x) I3)
+// the rows of Q = L^-1 C are orthonormal, C = L Q, and
+//   Project(C^T H_z C) = Q^T Project(L^T H_z L) Q
+// exactly: a Jacobi solve on R = 3, 6, 9 instead of 6, 9, 12, and no
+// position-space Hessian is formed before the projection.  The gradient stays
+// FP64 (g_y = C^T g_z); in the FP32-mixed form the R x R Hessians, the
+// projection and the product are FP32.  The result is then mapped through the
+// UNION weights of the pair's vertices, duplicate nodes merged, and scattered.
 template <typename T>
 struct bar_ws {
-  double gs[12];
-  double Hs[144];
-  T A[144];
-  T V[144];
-  T cs[6], sn[6];
+  double gz[9];    // ds/dz
+  T gzf[9];        // the same in T
+  T Hz[81];        // kappa (b'' gz gz^T + b' d2s/dz2), then K = L^T Hz L, then Project(K)
+  T V[81];         // Jacobi rotations
+  T Hy[144];       // Q^T Project(K) Q (n3 x n3)
+  T cs[5], sn[5];
   double W[4][16];
-  double db, d2b;
-  dist::wn_scratch wn;  // point-plane / line-line derivatives, formed by the whole warp
-  d3 yl[4];
-  int ids[4], loc[4];
-  int n, active, m, node[16], dtype;
+  int node[16];
+  int m;
 };
+
+// reduced-coordinate constants per distance type (PP, PE, PT, EE): coef (k x
+// n), L = chol(coef coef^T) (k x k, lower) and Q = L^-1 coef (k x n)
+struct bar_tables {
+  double coef[4][3][4];
+  double L[4][3][3];
+  double Q[4][3][4];
+  float Lf[4][3][3];
+  float Qf[4][3][4];
+  int k[4];
+};
+__device__ __forceinline__ double tab_L(const bar_tables& t, double, int d, int r, int a) { return t.L[d][r][a]; }
+__device__ __forceinline__ float tab_L(const bar_tables& t, float, int d, int r, int a) { return t.Lf[d][r][a]; }
+__device__ __forceinline__ double tab_Q(const bar_tables& t, double, int d, int r, int v) { return t.Q[d][r][v]; }
+__device__ __forceinline__ float tab_Q(const bar_tables& t, float, int d, int r, int v) { return t.Qf[d][r][v]; }
 
 // Project(A) = V max(Lambda, 0) V^T for the N x N symmetric A in shared
 // memory (row-major), by one warp: cyclic Jacobi with N/2 disjoint rotations
@@ -814,145 +840,239 @@ __device__ void warp_project(T* A, T* V, T* cs, T* sn, int lane) {
   __syncwarp();
 }
 
+// one thread per PT / EE pair: info[p] = active | dtype << 1 | loc0 << 3 | loc1
+// << 5 | loc2 << 7 | loc3 << 9 (loc: the classified vertices among the pair's
+// four), bd[p] = (b'(s), b''(s)).  Pairs are PT then EE (kind by index).
+__global__ void k_barrier_prep(int npt, int nee, const int* __restrict__ pt, const int* __restrict__ ee, topo Tp,
+                               const double* __restrict__ P, double sh, int form, int* __restrict__ info,
+                               double2* __restrict__ bd) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= npt + nee) return;
+  const int kind = p < npt ? 0 : 1;
+  int ids[4], k;
+  pair_vertices(kind, kind == 0 ? p : p - npt, kind == 0 ? pt : ee, Tp, ids, &k);
+  d3 y[4];
+  for (int a = 0; a < 4; ++a) y[a] = ld3(P, ids[a]);
+  double sd;
+  dist::dclass dc;
+  if (kind == 0) dc = dist::pt_dclass(dist::pt_classify(y[0], y[1], y[2], y[3], &sd));
+  else dc = dist::ee_dclass(dist::ee_classify(y[0], y[1], y[2], y[3], &sd));
+  const bool active = (sd < sh) && (sd > 0.0);
+  int code = active ? 1 : 0;
+  code |= dc.dtype << 1;
+  for (int q = 0; q < 4; ++q) code |= (q < dc.n ? dc.loc[q] : 0) << (3 + 2 * q);
+  info[p] = code;
+  if (active) {
+    const bder b = barrier_fn(sd, sh, form);
+    bd[p] = make_double2(b.db, b.d2b);
+  }
+}
+
+// ds/dz and d2s/dz2 (times kappa b', plus kappa b'' gz gz^T) of one pair in its
+// reduced variables z, by the lanes of one warp; gz (FP64) and Hz (T) in
+// shared memory.  z: PP w (3); PE (w, e) (6); PT / EE (w, e1, e2) (9).
 template <typename T>
-__global__ void __launch_bounds__(32) k_barrier_w(int kind, int npairs, int pair_base, const int* __restrict__ pairs,
-                                                   topo Tp, const double* __restrict__ vr, const double* __restrict__ P,
-                                                   double sh, double kappa, int form, int project,
-                                                   const int* __restrict__ koff, const int* __restrict__ dslot,
-                                                   double* __restrict__ g, T* __restrict__ diag, T* __restrict__ vals,
-                                                   int* status) {
-  // one pair per block of one warp: a few hundred pairs still reach every SM
-  __shared__ bar_ws<T> w;
-  const int lane = threadIdx.x & 31;
-  const int p = blockIdx.x;
-  if (p >= npairs) return;  // warp-uniform
-  if (lane == 0) {
-    int k;
-    pair_vertices(kind, p, pairs, Tp, w.ids, &k);
-    d3 y[4];
-    for (int a = 0; a < 4; ++a) y[a] = ld3(P, w.ids[a]);
-    double sd;
-    dist::dclass dc;
-    if (kind == 0) dc = dist::pt_dclass(dist::pt_classify(y[0], y[1], y[2], y[3], &sd));
-    else dc = dist::ee_dclass(dist::ee_classify(y[0], y[1], y[2], y[3], &sd));
-    w.active = (sd < sh) && (sd > 0.0);
-    if (w.active) {
-      const bder bd = barrier_fn(sd, sh, form);
-      w.db = bd.db;
-      w.d2b = bd.d2b;
-      w.n = dc.n;
-      for (int q = 0; q < dc.n; ++q) {
-        w.yl[q] = y[dc.loc[q]];
-        w.loc[q] = dc.loc[q];
+__device__ void bar_reduced(int dtype, const d3* yl, double kappa, double db, double d2b, bar_ws<T>& w, int lane) {
+  using dist::comp;
+  if (dtype == dist::PP) {
+    const d3 wv = yl[0] - yl[1];
+    if (lane < 3) {
+      w.gz[lane] = 2.0 * comp(wv, lane);
+      w.gzf[lane] = (T)w.gz[lane];
+    }
+    __syncwarp();
+    if (lane < 9) {
+      const int i = lane / 3, j = lane % 3;
+      w.Hz[lane] = (T)kappa * ((T)d2b * w.gzf[i] * w.gzf[j] + (T)db * ((i == j) ? T(2) : T(0)));
+    }
+  } else if (dtype == dist::PE) {
+    // s = |w|^2 - (w.e)^2 / |e|^2
+    const d3 wv = yl[0] - yl[1], ev = yl[2] - yl[1];
+    const double u = dot(wv, ev), L = dot(ev, ev), iLd = 1.0 / L;
+    if (lane < 3) w.gz[lane] = 2.0 * comp(wv, lane) - 2.0 * u * comp(ev, lane) * iLd;
+    else if (lane < 6) {
+      const int i = lane - 3;
+      w.gz[lane] = -2.0 * u * comp(wv, i) * iLd + 2.0 * u * u * comp(ev, i) * iLd * iLd;
+    }
+    if (lane < 6) w.gzf[lane] = (T)w.gz[lane];
+    __syncwarp();
+    // blocks (w,w), (w,e), (e,w), (e,e) of the 6 x 6 Hessian, in T
+    const T uf = (T)u, iL = (T)iLd;
+    for (int e = lane; e < 36; e += 32) {
+      const int r = e / 6, c = e % 6, i = r % 3, j = c % 3;
+      const T wi = (T)comp(wv, i), wj = (T)comp(wv, j), ei = (T)comp(ev, i), ej = (T)comp(ev, j);
+      const T d = (i == j) ? T(1) : T(0);
+      T h;
+      if (r < 3 && c < 3) h = T(2) * d - T(2) * ei * ej * iL;
+      else if (r < 3) h = -T(2) * ei * wj * iL - T(2) * uf * d * iL + T(4) * uf * ei * ej * iL * iL;
+      else if (c < 3) h = -T(2) * ej * wi * iL - T(2) * uf * d * iL + T(4) * uf * ej * ei * iL * iL;
+      else
+        h = -T(2) * wi * wj * iL + T(4) * uf * (wi * ej + ei * wj) * iL * iL + T(2) * uf * uf * d * iL * iL -
+            T(8) * uf * uf * ei * ej * iL * iL * iL;
+      w.Hz[e] = (T)kappa * ((T)d2b * w.gzf[r] * w.gzf[c] + (T)db * h);
+    }
+  } else {
+    // s = (w.n)^2 / (n.n), n = e1 x e2
+    d3 wv, e1v, e2v;
+    if (dtype == dist::PT) {
+      wv = yl[0] - yl[1]; e1v = yl[2] - yl[1]; e2v = yl[3] - yl[1];
+    } else {
+      wv = yl[0] - yl[2]; e1v = yl[1] - yl[0]; e2v = yl[3] - yl[2];
+    }
+    const d3 nv = cross(e1v, e2v);
+    const double t = dot(wv, nv), N = dot(nv, nv), iNd = 1.0 / N;
+    // gradient (FP64): lanes 0-2 dw, 3-8 de1, de2 through dn/de = [-[e2]x, [e1]x]
+    if (lane < 9) {
+      double g;
+      if (lane < 3) g = 2.0 * t * comp(nv, lane) * iNd;
+      else {
+        const int c = lane - 3;
+        g = 0.0;
+        for (int q = 0; q < 3; ++q)
+          g += (2.0 * t * comp(wv, q) * iNd - 2.0 * t * t * comp(nv, q) * iNd * iNd) * dist::jn(e1v, e2v, q, c);
       }
-      w.dtype = dc.dtype;
-      // point-plane and line-line derivatives are formed by the whole warp below
-      if (dc.dtype == dist::PP) dist::ds_pp(w.yl, w.gs, w.Hs);
-      else if (dc.dtype == dist::PE) dist::ds_pe(w.yl, w.gs, w.Hs);
-      // merged node set and the UNION weights of the classified vertices
-      const nodeset S = pair_nodes(w.ids, k, Tp.vnode, Tp.vbody, vr);
-      w.m = S.m;
-      for (int u = 0; u < S.m; ++u) w.node[u] = S.node[u];
-      for (int q = 0; q < dc.n; ++q) {
-        for (int u = 0; u < S.m; ++u) w.W[q][u] = 0.0;
-        const vmapd vm = vertex_map(w.ids[dc.loc[q]], Tp.vnode, Tp.vbody, vr);
-        for (int a = 0; a < vm.n; ++a) {
-          int u = 0;
-          while (S.node[u] != vm.node[a]) ++u;
-          w.W[q][u] += vm.w[a];
+      w.gz[lane] = g;
+      w.gzf[lane] = (T)g;
+    }
+    __syncwarp();
+    // Hessian entries in T from T copies of the FP64 vectors and scalars
+    const T tf = (T)t, iN = (T)iNd;
+    const T wf[3] = {(T)wv.x, (T)wv.y, (T)wv.z}, nf[3] = {(T)nv.x, (T)nv.y, (T)nv.z};
+    const T e1f[3] = {(T)e1v.x, (T)e1v.y, (T)e1v.z}, e2f[3] = {(T)e2v.x, (T)e2v.y, (T)e2v.z};
+    // entry (q, c) of Jn = dn/d(e1, e2) (3 x 6)
+    auto jnf = [&](int q, int c) -> T {
+      const T* e = (c < 3) ? e2f : e1f;
+      const T sg = (c < 3) ? T(-1) : T(1);
+      const int a = c % 3;
+      if (q == a) return T(0);
+      const int b = 3 - q - a;
+      const T eps = ((q + 1) % 3 == a) ? T(1) : T(-1);
+      return sg * (-eps) * e[b];
+    };
+    auto hwn = [&](int i, int j) -> T {
+      return T(2) * (nf[i] * wf[j] + (i == j ? tf : T(0))) * iN - T(4) * tf * nf[i] * nf[j] * iN * iN;
+    };
+    auto hnn = [&](int i, int j) -> T {
+      return T(2) * wf[i] * wf[j] * iN - T(4) * tf * (wf[i] * nf[j] + nf[i] * wf[j]) * iN * iN -
+             (i == j ? T(2) * tf * tf * iN * iN : T(0)) + T(8) * tf * tf * nf[i] * nf[j] * iN * iN * iN;
+    };
+    for (int e = lane; e < 81; e += 32) {
+      const int r = e / 9, c = e % 9;
+      T h;
+      if (r < 3 && c < 3) {
+        h = T(2) * nf[r] * nf[c] * iN;
+      } else if (r < 3 || c < 3) {
+        const int i = r < 3 ? r : c, cc = (r < 3 ? c : r) - 3;
+        h = hwn(i, 0) * jnf(0, cc) + hwn(i, 1) * jnf(1, cc) + hwn(i, 2) * jnf(2, cc);
+      } else {
+        const int rr = r - 3, cc = c - 3;
+        T t3[3];
+        for (int q = 0; q < 3; ++q) t3[q] = hnn(q, 0) * jnf(0, cc) + hnn(q, 1) * jnf(1, cc) + hnn(q, 2) * jnf(2, cc);
+        h = jnf(0, rr) * t3[0] + jnf(1, rr) * t3[1] + jnf(2, rr) * t3[2];
+        // curvature of n: the (e1, e2) block and its transpose, sum_k gn_k eps_kij
+        const int i = rr < 3 ? rr : cc, j = rr < 3 ? cc - 3 : rr - 3;
+        if ((rr < 3) != (cc < 3) && i != j) {
+          const int kk = 3 - i - j;
+          const T gn = T(2) * tf * wf[kk] * iN - T(2) * tf * tf * nf[kk] * iN * iN;
+          h += gn * (((i + 1) % 3 == j) ? T(1) : T(-1));
         }
       }
+      w.Hz[e] = (T)kappa * ((T)d2b * w.gzf[r] * w.gzf[c] + (T)db * h);
     }
   }
   __syncwarp();
-  if (!w.active) return;  // warp-uniform
-  // point-plane / line-line: (w, e1, e2) = C y with C = coef (x) I3 (9 x 12)
-  const double coef_pt[3][4] = {{1, -1, 0, 0}, {0, -1, 1, 0}, {0, -1, 0, 1}};
-  const double coef_ee[3][4] = {{1, 0, -1, 0}, {-1, 1, 0, 0}, {0, 0, -1, 1}};
-  const bool wn = w.dtype == dist::PT || w.dtype == dist::EE;
-  if (w.dtype == dist::PT)
-    dist::ds_wn_warp(w.yl[0] - w.yl[1], w.yl[2] - w.yl[1], w.yl[3] - w.yl[1], coef_pt, w.wn, w.gs, w.Hs, lane);
-  else if (w.dtype == dist::EE)
-    dist::ds_wn_warp(w.yl[0] - w.yl[2], w.yl[1] - w.yl[0], w.yl[3] - w.yl[2], coef_ee, w.wn, w.gs, w.Hs, lane);
-  const int n3 = 3 * w.n;
-  const double db = w.db, d2b = w.d2b;
-  if (project && wn) {
-    // The 12x12 Hessian is C^T H9 C with H9 = kappa (b'' g9 g9^T + b' d2s) in
-    // (w, e1, e2).  With C C^T = L L^T (L = chol(coef coef^T) (x) I3) the rows
-    // of Q = L^-1 C are orthonormal and C^T H9 C = Q^T (L^T H9 L) Q, so the
-    // projection of the 12x12 is Q^T Project(K) Q with the 9x9 K = L^T H9 L:
-    // the same matrix up to rounding, from a Jacobi solve on 9 instead of 12.
-    const double(&coef)[3][4] = (w.dtype == dist::PT) ? coef_pt : coef_ee;
-    double G[3][3], L[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}}, Mq[3][4];
-    for (int r = 0; r < 3; ++r)
-      for (int q = 0; q < 3; ++q) {
-        double t = 0.0;
-        for (int v = 0; v < 4; ++v) t += coef[r][v] * coef[q][v];
-        G[r][q] = t;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(128) k_barrier_pair(int npairs, int npt, const int* __restrict__ pt,
+                                                       const int* __restrict__ ee, topo Tp,
+                                                       const double* __restrict__ vr, const double* __restrict__ P,
+                                                       const int* __restrict__ info, const double2* __restrict__ bd,
+                                                       double kappa, int project, bar_tables tb,
+                                                       const int* __restrict__ koff, const int* __restrict__ dslot,
+                                                       double* __restrict__ g, T* __restrict__ diag,
+                                                       T* __restrict__ vals, int* status) {
+  __shared__ bar_ws<T> wsp[4];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int p = blockIdx.x * 4 + wid;
+  if (p >= npairs) return;  // warp-uniform
+  const int code = info[p];
+  if (!(code & 1)) return;  // warp-uniform: not within dhat
+  bar_ws<T>& w = wsp[wid];
+  const int dtype = (code >> 1) & 3;
+  const int kind = p < npt ? 0 : 1;
+  int ids[4], kv;
+  pair_vertices(kind, kind == 0 ? p : p - npt, kind == 0 ? pt : ee, Tp, ids, &kv);
+  const int nloc = (dtype == dist::PP) ? 2 : (dtype == dist::PE ? 3 : 4);
+  int loc[4];
+  d3 yl[4];
+  for (int q = 0; q < 4; ++q) {
+    loc[q] = (code >> (3 + 2 * q)) & 3;
+    yl[q] = ld3(P, ids[loc[q]]);
+  }
+  const double2 b2 = bd[p];
+  // merged node set and the UNION weights of the classified vertices (integer
+  // work and loads; lane 0)
+  if (lane == 0) {
+    const nodeset S = pair_nodes(ids, kv, Tp.vnode, Tp.vbody, vr);
+    w.m = S.m;
+    for (int u = 0; u < S.m; ++u) w.node[u] = S.node[u];
+    for (int q = 0; q < nloc; ++q) {
+      for (int u = 0; u < S.m; ++u) w.W[q][u] = 0.0;
+      const vmapd vm = vertex_map(ids[loc[q]], Tp.vnode, Tp.vbody, vr);
+      for (int a = 0; a < vm.n; ++a) {
+        int u = 0;
+        while (S.node[u] != vm.node[a]) ++u;
+        w.W[q][u] += vm.w[a];
       }
-    L[0][0] = sqrt(G[0][0]);
-    L[1][0] = G[1][0] / L[0][0];
-    L[2][0] = G[2][0] / L[0][0];
-    L[1][1] = sqrt(G[1][1] - L[1][0] * L[1][0]);
-    L[2][1] = (G[2][1] - L[2][0] * L[1][0]) / L[1][1];
-    L[2][2] = sqrt(G[2][2] - L[2][0] * L[2][0] - L[2][1] * L[2][1]);
-    for (int v = 0; v < 4; ++v) {  // Mq = L^-1 coef (forward substitution)
-      Mq[0][v] = coef[0][v] / L[0][0];
-      Mq[1][v] = (coef[1][v] - L[1][0] * Mq[0][v]) / L[1][1];
-      Mq[2][v] = (coef[2][v] - L[2][0] * Mq[0][v] - L[2][1] * Mq[1][v]) / L[2][2];
-    }
-    for (int e = lane; e < 81; e += 32) {
-      const int ra = e / 9, ca = e % 9, rb = ra / 3, i = ra % 3, qb = ca / 3, j = ca % 3;
-      double acc = 0.0;
-      for (int r2 = rb; r2 < 3; ++r2)
-        for (int q2 = qb; q2 < 3; ++q2) {
-          const int a9 = 3 * r2 + i, b9 = 3 * q2 + j;
-          const double h9 = kappa * (d2b * w.wn.g9[a9] * w.wn.g9[b9] + db * w.wn.H9[9 * a9 + b9]);
-          acc += L[r2][rb] * L[q2][qb] * h9;
-        }
-      w.A[e] = (T)acc;
-    }
-    __syncwarp();
-    warp_project<T, 9>(w.A, w.V, w.cs, w.sn, lane);  // A (9 x 9) <- Project(K)
-    for (int e = lane; e < 144; e += 32) {
-      const int row = e / 12, col = e % 12, v = row / 3, i = row % 3, u = col / 3, j = col % 3;
-      T acc = 0;
-#pragma unroll
-      for (int r = 0; r < 3; ++r)
-#pragma unroll
-        for (int q = 0; q < 3; ++q) acc += (T)(Mq[r][v] * Mq[q][u]) * w.A[9 * (3 * r + i) + 3 * q + j];
-      w.V[e] = acc;
-    }
-    __syncwarp();
-    for (int e = lane; e < 144; e += 32) w.A[e] = w.V[e];
-    __syncwarp();
-  } else {
-    for (int e = lane; e < n3 * n3; e += 32) {
-      const int r = e / n3, c = e % n3;
-      w.A[e] = (T)(kappa * (d2b * w.gs[r] * w.gs[c] + db * w.Hs[e]));
-    }
-    __syncwarp();
-    if (project) {
-      if (n3 == 12) warp_project<T, 12>(w.A, w.V, w.cs, w.sn, lane);
-      else if (n3 == 9) warp_project<T, 9>(w.A, w.V, w.cs, w.sn, lane);
-      else warp_project<T, 6>(w.A, w.V, w.cs, w.sn, lane);
     }
   }
-  // gradient rows of the merged nodes
+  bar_reduced<T>(dtype, yl, kappa, b2.x, b2.y, w, lane);
+  const int k = tb.k[dtype], R = 3 * k, n3 = 3 * nloc;
+  // K = L^T Hz L (R x R), into V as scratch, then back into Hz
+  for (int e = lane; e < R * R; e += 32) {
+    const int ra = e / R, ca = e % R, a = ra / 3, i = ra % 3, b = ca / 3, j = ca % 3;
+    T acc = 0;
+    for (int r = a; r < k; ++r)
+      for (int q = b; q < k; ++q) acc += tab_L(tb, T(), dtype, r, a) * tab_L(tb, T(), dtype, q, b) * w.Hz[R * (3 * r + i) + 3 * q + j];
+    w.V[e] = acc;
+  }
+  __syncwarp();
+  for (int e = lane; e < R * R; e += 32) w.Hz[e] = w.V[e];
+  __syncwarp();
+  if (project) {
+    if (R == 9) warp_project<T, 9>(w.Hz, w.V, w.cs, w.sn, lane);
+    else if (R == 6) warp_project<T, 6>(w.Hz, w.V, w.cs, w.sn, lane);
+    else warp_project<T, 3>(w.Hz, w.V, w.cs, w.sn, lane);
+  }
+  // position space: Hy = Q^T K Q (n3 x n3)
+  for (int e = lane; e < n3 * n3; e += 32) {
+    const int row = e / n3, col = e % n3, v = row / 3, i = row % 3, u = col / 3, j = col % 3;
+    T acc = 0;
+    for (int r = 0; r < k; ++r)
+      for (int q = 0; q < k; ++q) acc += tab_Q(tb, T(), dtype, r, v) * tab_Q(tb, T(), dtype, q, u) * w.Hz[R * (3 * r + i) + 3 * q + j];
+    w.Hy[e] = acc;
+  }
+  __syncwarp();
+  // gradient rows of the merged nodes (FP64): g_y = C^T g_z, times kappa b'
   const int M = w.m;
   if (lane < M) {
     double gu[3] = {0, 0, 0};
     bool any = false;
-    for (int q = 0; q < w.n; ++q)
+    for (int q = 0; q < nloc; ++q)
       if (w.W[q][lane] != 0.0) {
         any = true;
-        for (int i = 0; i < 3; ++i) gu[i] += w.W[q][lane] * kappa * db * w.gs[3 * q + i];
+        for (int i = 0; i < 3; ++i) {
+          double gq = 0.0;
+          for (int r = 0; r < k; ++r) gq += tb.coef[dtype][r][q] * w.gz[3 * r + i];
+          gu[i] += w.W[q][lane] * kappa * b2.x * gq;
+        }
       }
     if (any)
       for (int i = 0; i < 3; ++i) atomicAdd(&g[3 * w.node[lane] + i], gu[i]);
   }
   // Hessian blocks (u <= w) of the merged nodes, one per lane at a time
-  const int kbase = koff[pair_base + p];
+  const int kbase = koff[p];
   const int nb = M * (M + 1) / 2;
   for (int e = lane; e < nb; e += 32) {
     int u = 0, rem = e;
@@ -960,14 +1080,15 @@ __global__ void __launch_bounds__(32) k_barrier_w(int kind, int npairs, int pair
     const int v2 = u + rem;
     T B[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
     bool any = false;
-    for (int q = 0; q < w.n; ++q) {
+    for (int q = 0; q < nloc; ++q) {
       if (w.W[q][u] == 0.0) continue;
-      for (int r = 0; r < w.n; ++r) {
+      for (int r = 0; r < nloc; ++r) {
         const double f = w.W[q][u] * w.W[r][v2];
         if (f == 0.0) continue;
         any = true;
+        const T ff = (T)f;
         for (int i = 0; i < 3; ++i)
-          for (int j = 0; j < 3; ++j) B[3 * i + j] += (T)f * w.A[(3 * q + i) * n3 + 3 * r + j];
+          for (int j = 0; j < 3; ++j) B[3 * i + j] += ff * w.Hy[(3 * q + i) * n3 + 3 * r + j];
       }
     }
     if (!any) continue;
@@ -980,6 +1101,37 @@ __global__ void __launch_bounds__(32) k_barrier_w(int kind, int npairs, int pair
     }
     for (int t = 0; t < 9; ++t) atomicAdd(d + t, B[t]);
   }
+}
+
+// smallest squared distance over the PT, EE and PG pair lists (the adaptive
+// barrier stiffness and the Newton records).  Squared distances are
+// non-negative, so their bit patterns order like their values.
+__global__ void k_pairs_min_s(int npt, int nee, int npg, const int* __restrict__ pt, const int* __restrict__ ee,
+                              const int* __restrict__ pg, topo T, const double* __restrict__ P,
+                              const double* __restrict__ planes, unsigned long long* __restrict__ out) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  double sd = __builtin_huge_val();
+  if (p < npt + nee) {
+    const int kind = p < npt ? 0 : 1;
+    int ids[4], k;
+    pair_vertices(kind, kind == 0 ? p : p - npt, kind == 0 ? pt : ee, T, ids, &k);
+    d3 y[4];
+    for (int a = 0; a < 4; ++a) y[a] = ld3(P, ids[a]);
+    if (kind == 0) dist::pt_classify(y[0], y[1], y[2], y[3], &sd);
+    else dist::ee_classify(y[0], y[1], y[2], y[3], &sd);
+  } else if (p < npt + nee + npg) {
+    const int q = p - npt - nee;
+    const double* pl = planes + 4 * pg[3 * q + 1];
+    const double d = dist::sub(dist::vdot(d3{pl[0], pl[1], pl[2]}, ld3(P, pg[3 * q])), pl[3]);
+    sd = dist::mul(d, d);
+  }
+  unsigned long long b = (unsigned long long)__double_as_longlong(sd);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long bo = __shfl_xor_sync(0xffffffffu, b, o);
+    b = bo < b ? bo : b;
+  }
+  if ((threadIdx.x & 31) == 0 && p - (int)(threadIdx.x & 31) < npt + nee + npg) atomicMin(out, b);
 }
 
 // point-plane pairs: s = d^2, grad s = 2 d n, hess s = 2 n n^T; the position-
@@ -1425,8 +1577,53 @@ yasps_status two_pass(yasps_system* s, int nA, Launch&& launch, gbuf& outbuf, in
   return YASPS_OK;
 }
 
+// coef, L = chol(coef coef^T) and Q = L^-1 coef of the four distance types
+bar_tables make_bar_tables() {
+  bar_tables t{};
+  const double c[4][3][4] = {{{1, -1, 0, 0}},
+                             {{1, -1, 0, 0}, {0, -1, 1, 0}},
+                             {{1, -1, 0, 0}, {0, -1, 1, 0}, {0, -1, 0, 1}},
+                             {{1, 0, -1, 0}, {-1, 1, 0, 0}, {0, 0, -1, 1}}};
+  const int k[4] = {1, 2, 3, 3};
+  for (int d = 0; d < 4; ++d) {
+    t.k[d] = k[d];
+    double G[3][3] = {}, L[3][3] = {};
+    for (int r = 0; r < k[d]; ++r)
+      for (int q = 0; q < k[d]; ++q)
+        for (int v = 0; v < 4; ++v) G[r][q] += c[d][r][v] * c[d][q][v];
+    for (int j = 0; j < k[d]; ++j) {
+      double sjj = G[j][j];
+      for (int m = 0; m < j; ++m) sjj -= L[j][m] * L[j][m];
+      L[j][j] = std::sqrt(sjj);
+      for (int i = j + 1; i < k[d]; ++i) {
+        double sij = G[i][j];
+        for (int m = 0; m < j; ++m) sij -= L[i][m] * L[j][m];
+        L[i][j] = sij / L[j][j];
+      }
+    }
+    for (int v = 0; v < 4; ++v)
+      for (int r = 0; r < k[d]; ++r) {  // forward substitution L Q = coef
+        double acc = c[d][r][v];
+        for (int m = 0; m < r; ++m) acc -= L[r][m] * t.Q[d][m][v];
+        t.Q[d][r][v] = acc / L[r][r];
+      }
+    for (int r = 0; r < 3; ++r) {
+      for (int q = 0; q < 3; ++q) {
+        t.L[d][r][q] = L[r][q];
+        t.Lf[d][r][q] = (float)L[r][q];
+      }
+      for (int v = 0; v < 4; ++v) {
+        t.coef[d][r][v] = c[d][r][v];
+        t.Qf[d][r][v] = (float)t.Q[d][r][v];
+      }
+    }
+  }
+  return t;
+}
+
 template <typename T>
 yasps_status eval_barrier_t(yasps_system* s, int project) {
+  static const bar_tables tb = make_bar_tables();
   const topo Tp = make_topo(s);
   const double sh = s->prm.dhat * s->prm.dhat;
   int* st = as<int>(s->status);
@@ -1436,19 +1633,19 @@ yasps_status eval_barrier_t(yasps_system* s, int project) {
   const double* P = as<double>(s->P);
   const int* koff = as<int>(s->pair_key_off);
   const int* dslot = as<int>(s->dyn_slot);
-  // one warp per pair, one pair per block
-  if (s->npt) {
-    k_barrier_w<T><<<s->npt, 32, 0, s->stream>>>(0, s->npt, 0, as<int>(s->pt), Tp, as<double>(s->vr), P,
-                                                                sh, s->prm.kappa, s->prm.barrier_form, project, koff,
-                                                                dslot, g, diag, vals, st);
-    LAUNCH_CHECK(s, "k_barrier_w(PT)");
-  }
-  if (s->nee) {
-    k_barrier_w<T><<<s->nee, 32, 0, s->stream>>>(1, s->nee, s->npt, as<int>(s->ee), Tp,
-                                                                as<double>(s->vr), P, sh, s->prm.kappa,
-                                                                s->prm.barrier_form, project, koff, dslot, g, diag,
-                                                                vals, st);
-    LAUNCH_CHECK(s, "k_barrier_w(EE)");
+  const int np = s->npt + s->nee;
+  if (np) {
+    // per-pair classification (a thread per pair), then the derivatives (a warp per pair)
+    ENSURE(s, s->bar_prep, (sizeof(double2) + sizeof(int)) * ((size_t)np + 1) + 16);
+    double2* bd = as<double2>(s->bar_prep);
+    int* info = reinterpret_cast<int*>(bd + np + 1);
+    k_barrier_prep<<<blocks_for(np, 128), 128, 0, s->stream>>>(s->npt, s->nee, as<int>(s->pt), as<int>(s->ee), Tp, P,
+                                                              sh, s->prm.barrier_form, info, bd);
+    LAUNCH_CHECK(s, "k_barrier_prep");
+    k_barrier_pair<T><<<blocks_for(np, 4), 128, 0, s->stream>>>(np, s->npt, as<int>(s->pt), as<int>(s->ee), Tp,
+                                                               as<double>(s->vr), P, info, bd, s->prm.kappa, project,
+                                                               tb, koff, dslot, g, diag, vals, st);
+    LAUNCH_CHECK(s, "k_barrier_pair");
   }
   if (s->npg) {
     k_barrier_pg<T><<<blocks_for(s->npg, 128), 128, 0, s->stream>>>(s->npg, s->npt + s->nee, as<int>(s->pg), Tp,
@@ -1508,6 +1705,29 @@ yasps_status detect_pairs(yasps_system* s, const double* P) {
     }, s->ee, &s->nee));
   }
   return build_dynamic_bsr(s);
+}
+
+double barrier_db(double s, double sh, int form) { return barrier_fn(s, sh, form).db; }
+
+yasps_status pairs_min_dist2(yasps_system* s, const double* P, double* s_min_host) {
+  const int np = s->npt + s->nee + s->npg;
+  *s_min_host = __builtin_huge_val();
+  if (np == 0) return YASPS_OK;
+  ENSURE(s, s->ws[11], sizeof(unsigned long long) * 2);
+  unsigned long long* d = as<unsigned long long>(s->ws[11]);
+  const double inf = __builtin_huge_val();
+  unsigned long long init;
+  std::memcpy(&init, &inf, sizeof init);
+  CK(s, cudaMemcpyAsync(d, &init, sizeof init, cudaMemcpyHostToDevice, s->stream));
+  const topo Tp = make_topo(s);
+  k_pairs_min_s<<<blocks_for(np, 128), 128, 0, s->stream>>>(s->npt, s->nee, s->npg, as<int>(s->pt), as<int>(s->ee),
+                                                          as<int>(s->pg), Tp, P, as<double>(s->planes), d);
+  LAUNCH_CHECK(s, "k_pairs_min_s");
+  unsigned long long h = init;
+  CK(s, cudaMemcpyAsync(&h, d, sizeof h, cudaMemcpyDeviceToHost, s->stream));
+  CK(s, cudaStreamSynchronize(s->stream));
+  std::memcpy(s_min_host, &h, sizeof h);
+  return YASPS_OK;
 }
 
 yasps_status build_dynamic_bsr(yasps_system* s) {

@@ -267,6 +267,14 @@ template <typename T, int K, int NC>
 __device__ __forceinline__ void scatter_fspace(const T* Hf, const double (*w)[NC], double scale, const int* nodes,
                                                const int* slots, T* diag, T* vals) {
   constexpr int NF = 3 * NC;
+  // the weights and the scale in T once: in the FP32-mixed form every
+  // double-to-float conversion is an instruction on the (scarce) FP64 pipe
+  T wt[K][NC];
+#pragma unroll
+  for (int a = 0; a < K; ++a)
+#pragma unroll
+    for (int j = 0; j < NC; ++j) wt[a][j] = (T)w[a][j];
+  const T sct = (T)scale;
   // Y[a][i][(m,l)] = sum_j w[a][j] Hf[(i,j),(m,l)]
 #pragma unroll
   for (int a = 0; a < K; ++a) {
@@ -277,7 +285,7 @@ __device__ __forceinline__ void scatter_fspace(const T* Hf, const double (*w)[NC
       for (int q = 0; q < NF; ++q) {
         T s = 0;
 #pragma unroll
-        for (int j = 0; j < NC; ++j) s += (T)w[a][j] * Hf[(NC * i + j) * NF + q];
+        for (int j = 0; j < NC; ++j) s += wt[a][j] * Hf[(NC * i + j) * NF + q];
         Y[i][q] = s;
       }
 #pragma unroll
@@ -290,8 +298,8 @@ __device__ __forceinline__ void scatter_fspace(const T* Hf, const double (*w)[NC
         for (int m = 0; m < 3; ++m) {
           T s = 0;
 #pragma unroll
-          for (int l = 0; l < NC; ++l) s += Y[i][NC * m + l] * (T)w[b][l];
-          B[3 * i + m] = (T)scale * s;
+          for (int l = 0; l < NC; ++l) s += Y[i][NC * m + l] * wt[b][l];
+          B[3 * i + m] = sct * s;
         }
       if (a == b) {
         add_block9(diag + 9 * (size_t)nodes[a], B);

@@ -49,6 +49,8 @@ struct yasps_system {
   gbuf node_scene; // int [nn] scene of each node (batches only)
   double scene_spacing = 0.0;  // lattice spacing of the scenes' broadphase boxes (batches)
   int pcg_variant = 0;         // launch configuration of the PCG kernel (yasps_autotune_pcg)
+  long long wait_limit = 0;    // polls of a device-side wait before it gives up (0: default)
+  bool wait_unmet = false;     // the next PCG launch's barriers wait for an arrival that never comes (tests)
   // per-scene results of the last yasps_step (batches)
   std::vector<int> scene_newton, scene_status, scene_pcg;
   gbuf scene_buf;  // per-scene device scratch (sums, tolerances, step bounds)
@@ -100,6 +102,7 @@ struct yasps_system {
   bool cand_valid = false;
   gbuf pair_key_off;  // int [npt + nee + 1] offsets of each pair's dynamic keys
   gbuf dyn_slot;      // int [nkeys] dynamic BSR slot per key
+  gbuf bar_prep;      // per PT / EE pair: barrier derivatives (double2) then classification codes (int)
   int nkeys = 0;
 
   // workspaces
@@ -123,6 +126,15 @@ struct yasps_system {
   std::vector<cudaEvent_t> prof_pool;
   yasps_stage_stats prof_acc[YASPS_NUM_STAGES] = {};
   double pcg_phase_ms[8] = {};  // yasps_pcg_phase_ms
+
+  // Newton records of the last yasps_step (yasps_newton_trace)
+  std::vector<yasps_newton_record> trace;
+  bool trace_smin = false;  // also record the smallest pair distance (one extra kernel per iteration)
+  // adaptive barrier stiffness (kappa_adaptive): initialised by gradient
+  // balance, and the smallest pair distance at the previous step's start
+  bool kappa_init = false;
+  double kappa_lo = 0.0, kappa_hi = 0.0;  // resolved bounds (kappa_min / kappa_max, or derived)
+  double kappa_dmin_prev = __builtin_huge_val();  // +inf until a step has started
 };
 
 // stage profiler: prof_begin returns an event recorded on the stream (or null
@@ -205,6 +217,11 @@ yasps_status ccd_candidates(yasps_system* s, double* alpha_host);
 // sacc (device [nscene], batches): per-scene sums added there, E_host untouched
 yasps_status barrier_energy_candidates(yasps_system* s, const double* P, double* E_host, double* sacc = nullptr);
 yasps_status detect_from_candidates(yasps_system* s, const double* P);
+// smallest squared distance over the current pair lists at vertex positions P
+// (+inf without pairs); synchronises
+yasps_status pairs_min_dist2(yasps_system* s, const double* P, double* s_min_host);
+// b'(s) of the barrier form (host)
+double barrier_db(double s, double sh, int form);
 
 // ---------------------------------------------------------------- solver.cu
 yasps_status alloc_hessian(yasps_system* s);
@@ -214,6 +231,9 @@ yasps_status spmv64(yasps_system* s, const double* x, double* y);
 // x0 (nullable): initial guess; the stopping test is relative to rhs either way
 yasps_status pcg_solve(yasps_system* s, const double* rhs, double* p, double tol, int maxit, int* iters,
                        double* rel_res, const double* x0 = nullptr);
-yasps_status inf_norm(yasps_system* s, const double* x, int n, double* out_host);
+// max |x_i| over n values; arg_host (nullable) receives an index i holding it
+yasps_status inf_norm(yasps_system* s, const double* x, int n, double* out_host, int* arg_host = nullptr);
+// (a.b, b.b) over n FP64 values; synchronises
+yasps_status dot2(yasps_system* s, const double* a, const double* b, int n, double* ab_host, double* bb_host);
 yasps_status read_status(yasps_system* s, int* bits);  // synchronises, clears the device word
 yasps_status autotune_pcg(yasps_system* s, int iters, int* variant, double* us);

@@ -129,8 +129,10 @@ __global__ void k_bj_free(int nfree, const T* __restrict__ D, T* __restrict__ Mi
   for (int t = 0; t < 9; ++t) A[t] = (double)D[9 * (size_t)i + t];
   const double c00 = A[4] * A[8] - A[5] * A[7], c01 = A[5] * A[6] - A[3] * A[8], c02 = A[3] * A[7] - A[4] * A[6];
   const double det = A[0] * c00 + A[1] * c01 + A[2] * c02;
-  if (!(det > 0.0) || !isfinite(det)) {
-    dev_flag(status, DEV_NAN);
+  // positive definite by Sylvester's criterion (leading minors A00, the 2x2
+  // one and det); otherwise the identity stands in and the block is reported
+  if (!(A[0] > 0.0) || !(A[0] * A[4] - A[1] * A[3] > 0.0) || !(det > 0.0) || !isfinite(det)) {
+    dev_flag(status, isfinite(det) ? DEV_INDEFINITE : DEV_NAN);
     for (int t = 0; t < 9; ++t) Mi[9 * (size_t)i + t] = (t % 4 == 0) ? T(1) : T(0);
     return;
   }
@@ -186,7 +188,7 @@ __global__ void k_bj_body(int nb, int nfree, const T* __restrict__ D, const int*
         t = I[c * 12 + j]; I[c * 12 + j] = I[piv * 12 + j]; I[piv * 12 + j] = t;
       }
     const double d = A[c * 12 + c];
-    if (!(fabs(d) > 0.0)) { dev_flag(status, DEV_NAN); return; }
+    if (!(fabs(d) > 0.0)) { dev_flag(status, isfinite(d) ? DEV_INDEFINITE : DEV_NAN); return; }
     for (int j = 0; j < 12; ++j) { A[c * 12 + j] /= d; I[c * 12 + j] /= d; }
     for (int r = 0; r < 12; ++r)
       if (r != c) {
@@ -291,6 +293,8 @@ struct pcg_args {
   pcg_bar* bar;
   int* status;
   long long spin_limit;
+  double rscale;   // r0 = rscale * rhs (the FP32 inner solves work on a normalised residual)
+  unsigned unmet;  // extra arrivals every grid barrier waits for (0; 1 makes the waits run out, for tests)
   // batches (nscene > 1): per-scene alpha, beta and stopping test
   int nscene;
   const int* node_scene;  // [nn]
@@ -335,7 +339,7 @@ struct no_epilogue {
 // FP64 arithmetic repeated by every thread of the grid is slow on this part.
 template <typename P, typename F = no_epilogue>
 __device__ __forceinline__ bool grid_reduce(pcg_bar* bar, unsigned& k, P partial, double& total,
-                                            long long spin_limit, F epi = F{}) {
+                                            long long spin_limit, unsigned unmet, F epi = F{}) {
   __shared__ int ok;
   __shared__ double tot;
   __syncthreads();
@@ -343,7 +347,7 @@ __device__ __forceinline__ bool grid_reduce(pcg_bar* bar, unsigned& k, P partial
     int good = 1;
     atomicAdd(&bar->sum[k & 3], (double)partial);
     red_add_release(&bar->count, 1u);
-    const unsigned target = (k + 1) * gridDim.x;
+    const unsigned target = (k + 1) * gridDim.x + unmet;  // unmet > 0: a count no grid reaches (tests)
     long long spins = 0;
     while (ld_acquire(&bar->count) < target) {
       if ((++spins & 255) == 0) {
@@ -404,6 +408,7 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned by
                "l"(src), "r"(bytes), "r"(smem_u32(m))
                : "memory");
 }
+constexpr long long kDrainPolls = 1LL << 24;  // polls allowed for copies in flight at exit
 // bounded wait on one buffer's mbarrier; false after spin_limit polls
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* m, unsigned parity, long long spin_limit) {
   for (long long k = 0; k < spin_limit; ++k)
@@ -780,7 +785,7 @@ __global__ void __launch_bounds__(CFG::NTHR, CFG::MINB) k_pcg_persistent(pcg_arg
       size_t o;
       unit_range((int)i, a.nfree, cnt, o);
       for (int c = 0; c < cnt; ++c) {
-        a.r[o + c] = (V)a.rhs[o + c];
+        a.r[o + c] = (V)(a.rhs[o + c] * a.rscale);
         a.x[o + c] = 0;
         a.d0[o + c] = 0;
         a.q[q_idx<V>(o + c)] = 0;
@@ -797,7 +802,7 @@ __global__ void __launch_bounds__(CFG::NTHR, CFG::MINB) k_pcg_persistent(pcg_arg
         size_t o;
         unit_range((int)i, a.nfree, cnt, o);
         for (int c = 0; c < cnt; ++c) {
-          a.r[o + c] = (V)a.rhs[o + c];
+          a.r[o + c] = (V)(a.rhs[o + c] * a.rscale);
           a.x[o + c] = 0;
           a.d0[o + c] = 0;
           a.q[q_idx<V>(o + c)] = 0;
@@ -817,7 +822,7 @@ __global__ void __launch_bounds__(CFG::NTHR, CFG::MINB) k_pcg_persistent(pcg_arg
   __shared__ V s_alpha, s_beta;
   __shared__ int s_done;
   if (threadIdx.x == 0) s_done = 0;
-  if (!grid_reduce(a.bar, kbar, bs, rz, a.spin_limit, [&](double t) {
+  if (!grid_reduce(a.bar, kbar, bs, rz, a.spin_limit, a.unmet, [&](double t) {
         if (!BATCH && !(t > 0.0)) s_done = 1;
       }))
     done = 3;
@@ -889,9 +894,14 @@ __global__ void __launch_bounds__(CFG::NTHR, CFG::MINB) k_pcg_persistent(pcg_arg
     bool ok = true;
     for (int j = 0; j < sh.tt; ++j) {
       const int b = j & 1;
-      if (!mbar_wait_bounded(&mbar[b], (parity >> b) & 1u, a.spin_limit >> 3)) ok = false;
-      parity ^= 1u << b;
-      inflight &= ~(1u << b);
+      // a wait that gives up leaves the buffer's copy marked in flight (and
+      // its parity unchanged) so that the drain below still waits for it
+      if (mbar_wait_bounded(&mbar[b], (parity >> b) & 1u, a.spin_limit >> 3)) {
+        parity ^= 1u << b;
+        inflight &= ~(1u << b);
+      } else {
+        ok = false;
+      }
       if (__syncthreads_or(!ok)) { ok = false; break; }
       const unsigned char* buf = smem + b * L::BUF;
       const int cnt = tile_of(a, sh, j, L::NT).cnt;
@@ -942,7 +952,7 @@ __global__ void __launch_bounds__(CFG::NTHR, CFG::MINB) k_pcg_persistent(pcg_arg
     if (clock0) { const unsigned long long t = global_ns(); tph[1] += t - tlast; tlast = t; }
     double dHd = 0.0;
     const int kb = (int)(kbar & 7);
-    if (!grid_reduce(a.bar, kbar, bs, dHd, a.spin_limit, [&](double t) {
+    if (!grid_reduce(a.bar, kbar, bs, dHd, a.spin_limit, a.unmet, [&](double t) {
           if constexpr (!BATCH) {
             if (!(t > 0.0)) s_done = 2;
             else s_alpha = (V)(rz / t);
@@ -1012,7 +1022,7 @@ __global__ void __launch_bounds__(CFG::NTHR, CFG::MINB) k_pcg_persistent(pcg_arg
     if (clock0) { const unsigned long long t = global_ns(); tph[3] += t - tlast; tlast = t; }
     double rz_new = 0.0;
     const int kc = (int)(kbar & 7);
-    if (!grid_reduce(a.bar, kbar, bs, rz_new, a.spin_limit, [&](double t) {
+    if (!grid_reduce(a.bar, kbar, bs, rz_new, a.spin_limit, a.unmet, [&](double t) {
           if constexpr (!BATCH) {
             s_beta = (V)(t / rz);
             if (t <= a.tol2 * rz0) s_done = 1;
@@ -1047,10 +1057,12 @@ __global__ void __launch_bounds__(CFG::NTHR, CFG::MINB) k_pcg_persistent(pcg_arg
         for (int c = 0; c < 3; ++c) a.x[3 * i + c] += apend * dpend[3 * i + c];
   }
   // a block that gave up may still have tile copies in flight: wait for them
-  // (bounded) before the block exits
+  // before the block exits (bounded, but by a fixed limit far above a copy's
+  // duration, independent of the barrier's wait limit)
   if (threadIdx.x == 0)
     for (int b = 0; b < 2; ++b)
-      if ((inflight >> b) & 1u) mbar_wait_bounded(&mbar[b], (parity >> b) & 1u, a.spin_limit);
+      if ((inflight >> b) & 1u) mbar_wait_bounded(&mbar[b], (parity >> b) & 1u, kDrainPolls);
+  __syncthreads();
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     a.sc->rz = rz;
     a.sc->rz0 = rz0;
@@ -1063,26 +1075,74 @@ __global__ void __launch_bounds__(CFG::NTHR, CFG::MINB) k_pcg_persistent(pcg_arg
 }
 
 template <typename V>
-__global__ void k_add_to(int n, double* __restrict__ p, const V* __restrict__ dx) {
+__global__ void k_add_to(int n, double* __restrict__ p, const V* __restrict__ dx, double c) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) p[i] += (double)dx[i];
+  if (i < n) p[i] += c * (double)dx[i];
 }
 __global__ void k_sub_from(int n, const double* __restrict__ a, double* __restrict__ y) {  // y = a - y
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) y[i] = a[i] - y[i];
 }
+// per-block max |x_i| into part[b] and an index holding it into part[nblk + b]
+// (as a double; exact below 2^53)
 __global__ void k_absmax(int n, const double* __restrict__ x, double* __restrict__ part) {
   double m = 0.0;
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-    m = fmax(m, fabs(x[i]));
+  long long at = 0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const double a = fabs(x[i]);
+    if (a > m) {
+      m = a;
+      at = i;
+    }
+  }
   __shared__ double sh[32];
-  m = warp_max(m);
-  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = m;
+  __shared__ long long shi[32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const double mo = __shfl_xor_sync(0xffffffffu, m, o);
+    const long long ao = __shfl_xor_sync(0xffffffffu, at, o);
+    if (mo > m || (mo == m && ao < at)) {
+      m = mo;
+      at = ao;
+    }
+  }
+  if ((threadIdx.x & 31) == 0) {
+    sh[threadIdx.x >> 5] = m;
+    shi[threadIdx.x >> 5] = at;
+  }
   __syncthreads();
   if (threadIdx.x < 32) {
-    double v = (threadIdx.x < (blockDim.x >> 5)) ? sh[threadIdx.x] : 0.0;
-    v = warp_max(v);
-    if (threadIdx.x == 0) part[blockIdx.x] = v;
+    const bool in = threadIdx.x < (blockDim.x >> 5);
+    double v = in ? sh[threadIdx.x] : 0.0;
+    long long a = in ? shi[threadIdx.x] : 0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const double vo = __shfl_xor_sync(0xffffffffu, v, o);
+      const long long ao = __shfl_xor_sync(0xffffffffu, a, o);
+      if (vo > v || (vo == v && ao < a)) {
+        v = vo;
+        a = ao;
+      }
+    }
+    if (threadIdx.x == 0) {
+      part[blockIdx.x] = v;
+      part[gridDim.x + blockIdx.x] = (double)a;
+    }
+  }
+}
+// per-block (a.b, b.b) partials into part[2 b], part[2 b + 1]
+__global__ void k_dot2(int n, const double* __restrict__ a, const double* __restrict__ b, double* __restrict__ part) {
+  double ab = 0.0, bb = 0.0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const double bi = b[i];
+    ab += a[i] * bi;
+    bb += bi * bi;
+  }
+  ab = block_sum(ab);
+  bb = block_sum(bb);
+  if (threadIdx.x == 0) {
+    part[2 * blockIdx.x] = ab;
+    part[2 * blockIdx.x + 1] = bb;
   }
 }
 // r^T M^-1 r in FP64 (the refinement check of the FP32-mixed form)
@@ -1166,7 +1226,7 @@ __global__ void k_pack_sym(int nn, int nfree, const T* __restrict__ D, const T* 
 
 template <typename T, typename V, bool BATCH, typename CFG>
 yasps_status pcg_launch_cfg(yasps_system* s, const double* rhs, double* p, double tol, int maxit, const double* stol2,
-                            int* iters, int* state, double* rel, scene_out* so) {
+                            int* iters, int* state, double* rel, scene_out* so, double rscale) {
   const int n3 = 3 * s->nn;
   for (int k = 0; k < 5; ++k) ENSURE(s, s->vec[k], sizeof(V) * (n3 + 4));
   ENSURE(s, s->vec[4], sizeof(V) * 4 * ((size_t)s->nn + 1));  // q: qlay<V>::S per node
@@ -1215,7 +1275,10 @@ yasps_status pcg_launch_cfg(yasps_system* s, const double* rhs, double* p, doubl
   a.sc = sc;
   a.bar = bar;
   a.status = as<int>(s->status);
-  a.spin_limit = 1LL << 22;  // a few seconds of polling per wait
+  a.spin_limit = s->wait_limit > 0 ? s->wait_limit : (1LL << 22);  // a few seconds of polling per wait
+  a.rscale = rscale;
+  a.unmet = s->wait_unmet ? 1u : 0u;
+  s->wait_unmet = false;
   a.nscene = ns;
   a.node_scene = BATCH ? as<int>(s->node_scene) : nullptr;
   a.ring = BATCH ? reinterpret_cast<double*>(base + 256) : nullptr;
@@ -1255,7 +1318,7 @@ yasps_status pcg_launch_cfg(yasps_system* s, const double* rhs, double* p, doubl
     sp.bytes += spmv_bytes * h.iters;
   }
   if (h.done == 3) SYS_FAIL(s, YASPS_E_TIMEOUT, "PCG grid barrier timed out");
-  k_add_to<V><<<blocks_for(n3, 256), 256, 0, s->stream>>>(n3, p, a.x);
+  k_add_to<V><<<blocks_for(n3, 256), 256, 0, s->stream>>>(n3, p, a.x, 1.0 / rscale);
   LAUNCH_CHECK(s, "k_add_to");
   *iters = h.iters;
   *state = h.done;
@@ -1266,30 +1329,30 @@ yasps_status pcg_launch_cfg(yasps_system* s, const double* rhs, double* p, doubl
 // the launch configuration the system uses (s->pcg_variant)
 template <typename T, typename V, bool BATCH>
 yasps_status pcg_launch(yasps_system* s, const double* rhs, double* p, double tol, int maxit, const double* stol2,
-                        int* iters, int* state, double* rel, scene_out* so) {
+                        int* iters, int* state, double* rel, scene_out* so, double rscale = 1.0) {
   switch (s->pcg_variant) {
     case 1:
       return pcg_launch_cfg<T, V, BATCH, typename pcg_variant<T, 1>::C>(s, rhs, p, tol, maxit, stol2, iters, state,
-                                                                        rel, so);
+                                                                        rel, so, rscale);
     case 2:
       return pcg_launch_cfg<T, V, BATCH, typename pcg_variant<T, 2>::C>(s, rhs, p, tol, maxit, stol2, iters, state,
-                                                                        rel, so);
+                                                                        rel, so, rscale);
     case 3:
       return pcg_launch_cfg<T, V, BATCH, typename pcg_variant<T, 3>::C>(s, rhs, p, tol, maxit, stol2, iters, state,
-                                                                        rel, so);
+                                                                        rel, so, rscale);
     case 4:
       return pcg_launch_cfg<T, V, BATCH, typename pcg_variant<T, 4>::C>(s, rhs, p, tol, maxit, stol2, iters, state,
-                                                                        rel, so);
+                                                                        rel, so, rscale);
     default:
       return pcg_launch_cfg<T, V, BATCH, typename pcg_variant<T, 0>::C>(s, rhs, p, tol, maxit, stol2, iters, state,
-                                                                        rel, so);
+                                                                        rel, so, rscale);
   }
 }
 
 template <typename T, typename V>
 yasps_status pcg_inner(yasps_system* s, const double* rhs, double* p, double tol, int maxit, int* iters, int* state,
-                       double* rel) {
-  return pcg_launch<T, V, false>(s, rhs, p, tol, maxit, nullptr, iters, state, rel, nullptr);
+                       double* rel, double rscale = 1.0) {
+  return pcg_launch<T, V, false>(s, rhs, p, tol, maxit, nullptr, iters, state, rel, nullptr, rscale);
 }
 
 // r^T M^-1 r per scene in FP64 (the refinement check of a batch): warp-segmented
@@ -1448,16 +1511,21 @@ static yasps_status pcg_solve_batch(yasps_system* s, const double* rhs, double* 
   bool all = false, broke = false;
   const int sweeps = std::max(1, s->prm.refine_sweeps);
   for (int sw = 0; sw < sweeps && !all; ++sw) {
+    double live = 0.0;  // r^T M^-1 r of the scenes still solving
     for (int k = 0; k < ns; ++k) {
       const bool fin = !(rz[k] > tol * tol * rz0[k]);
       const double inner = fin ? 1.0 : std::max(tol * std::sqrt(rz0[k] / rz[k]), 5e-6);
       stol2[k] = inner * inner;
+      if (!fin) live += rz[k];
     }
+    // the FP32 solve works on the residual scaled to unit M^-1 norm over the
+    // scenes still solving (kept away from FP32 underflow); scaled back in FP64
+    const double rscale = live > 0.0 ? 1.0 / std::sqrt(live) : 1.0;
     ENSURE(s, s->scene_buf, sizeof(double) * (2 * (size_t)ns + 4));
     double* st_dev = as<double>(s->scene_buf) + ns;
     CK(s, cudaMemcpyAsync(st_dev, stol2.data(), sizeof(double) * ns, cudaMemcpyHostToDevice, s->stream));
     RC((pcg_launch<float, float, true>(s, sw == 0 ? rhs : res, p, tol, maxit - total, st_dev, &it, &state, &rel,
-                                       &so)));
+                                       &so, rscale)));
     total += it;
     broke |= take(so);
     RC(spmv64(s, p, res));
@@ -1494,6 +1562,9 @@ yasps_status pcg_solve_impl(yasps_system* s, const double* rhs, double* p, doubl
   // the stopping test is relative to the right-hand side: r^T z <= tol^2 g^T M^-1 g
   double rz0 = 0.0, rz = 0.0;
   RC(mixed ? rz64<float>(s, rhs, &rz0) : rz64<double>(s, rhs, &rz0));
+  // g^T M^-1 g: NaN from a non-finite right-hand side, negative from an
+  // indefinite preconditioner block; exactly 0 means p = 0 solves it
+  if (!(rz0 >= 0.0)) SYS_FAIL(s, YASPS_E_NAN, "PCG: non-finite right-hand side or indefinite preconditioner");
   if (!(rz0 > 0.0)) {
     CK(s, cudaMemsetAsync(p, 0, sizeof(double) * n3, s->stream));
     if (iters) *iters = 0;
@@ -1528,7 +1599,10 @@ yasps_status pcg_solve_impl(yasps_system* s, const double* rhs, double* p, doubl
   const int sweeps = std::max(1, s->prm.refine_sweeps);
   for (int sw = 0; sw < sweeps && rz > tol * tol * rz0; ++sw) {
     const double inner_tol = std::max(tol * std::sqrt(rz0 / rz), 5e-6);
-    RC((pcg_inner<float, float>(s, r_cur, p, inner_tol, maxit - total, &it, &state, &rel)));
+    // the FP32 solve sees the residual scaled to unit M^-1 norm (its vectors and
+    // d^T H d stay far from FP32 underflow however small the residual gets);
+    // the correction is scaled back in FP64
+    RC((pcg_inner<float, float>(s, r_cur, p, inner_tol, maxit - total, &it, &state, &rel, 1.0 / std::sqrt(rz))));
     total += it;
     // FP64 residual res = rhs - H p
     RC(spmv64(s, p, res));
@@ -1602,17 +1676,41 @@ yasps_status autotune_pcg(yasps_system* s, int iters, int* variant, double* us) 
                : autotune_t<double, double, false>(s, iters, variant, us);
 }
 
-yasps_status inf_norm(yasps_system* s, const double* x, int n, double* out_host) {
+yasps_status inf_norm(yasps_system* s, const double* x, int n, double* out_host, int* arg_host) {
   const int nblk = std::min(148 * 2, blocks_for(std::max(n, 1), 256));
-  ENSURE(s, s->red, sizeof(double) * (nblk + 8));
+  ENSURE(s, s->red, sizeof(double) * (2 * nblk + 8));
   k_absmax<<<nblk, 256, 0, s->stream>>>(n, x, as<double>(s->red));
   LAUNCH_CHECK(s, "k_absmax");
-  std::vector<double> h(nblk);
-  CK(s, cudaMemcpyAsync(h.data(), s->red.p, sizeof(double) * nblk, cudaMemcpyDeviceToHost, s->stream));
+  std::vector<double> h(2 * nblk);
+  CK(s, cudaMemcpyAsync(h.data(), s->red.p, sizeof(double) * 2 * nblk, cudaMemcpyDeviceToHost, s->stream));
   CK(s, cudaStreamSynchronize(s->stream));
   double m = 0.0;
-  for (double v : h) m = std::max(m, v);
+  int at = 0;
+  for (int b = 0; b < nblk; ++b)
+    if (h[b] > m) {
+      m = h[b];
+      at = (int)h[nblk + b];
+    }
   *out_host = m;
+  if (arg_host) *arg_host = at;
+  return YASPS_OK;
+}
+
+yasps_status dot2(yasps_system* s, const double* a, const double* b, int n, double* ab_host, double* bb_host) {
+  const int nblk = std::min(148 * 2, blocks_for(std::max(n, 1), 256));
+  ENSURE(s, s->red, sizeof(double) * (2 * nblk + 8));
+  k_dot2<<<nblk, 256, 0, s->stream>>>(n, a, b, as<double>(s->red));
+  LAUNCH_CHECK(s, "k_dot2");
+  std::vector<double> h(2 * nblk);
+  CK(s, cudaMemcpyAsync(h.data(), s->red.p, sizeof(double) * 2 * nblk, cudaMemcpyDeviceToHost, s->stream));
+  CK(s, cudaStreamSynchronize(s->stream));
+  double ab = 0.0, bb = 0.0;
+  for (int k = 0; k < nblk; ++k) {
+    ab += h[2 * k];
+    bb += h[2 * k + 1];
+  }
+  *ab_host = ab;
+  *bb_host = bb;
   return YASPS_OK;
 }
 

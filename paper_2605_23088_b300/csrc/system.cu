@@ -64,7 +64,7 @@ static void all_bufs(yasps_system* s, std::vector<gbuf*>& v) {
                  &s->hinge_v, &s->hinge_n, &s->hinge_rest, &s->hinge_slot, &s->body_kv, &s->body_slot, &s->stri,
                  &s->sedge, &s->svert, &s->planes, &s->Hs.row_ptr, &s->Hs.col, &s->Hs.row, &s->Hs.vals,
                  &s->Hd.row_ptr, &s->Hd.col, &s->Hd.row, &s->Hd.vals, &s->diag, &s->grad, &s->minv, &s->dsym, &s->P, &s->pt,
-                 &s->ee, &s->pg, &s->cpt, &s->cee, &s->pair_key_off, &s->dyn_slot, &s->status, &s->scal, &s->red, &s->scan_tmp};
+                 &s->ee, &s->pg, &s->cpt, &s->cee, &s->pair_key_off, &s->dyn_slot, &s->bar_prep, &s->status, &s->scal, &s->red, &s->scan_tmp};
   for (gbuf* b : one) v.push_back(b);
   for (auto& b : s->ws) v.push_back(&b);
   for (auto& b : s->vec) v.push_back(&b);
@@ -152,6 +152,11 @@ void yasps_default_params(yasps_params* p) {
   p->ccd_max_iter = 100000;
   p->refine_sweeps = 4;
   p->pcg_warm_start = 1;
+  p->kappa_adaptive = 0;
+  p->kappa_min = 0.0;
+  p->kappa_max = 0.0;
+  p->kappa_dmin = 0.0;
+  p->ls_armijo = 0.0;
 }
 
 const char* yasps_build_error(void) { return g_build_error.c_str(); }
@@ -524,6 +529,10 @@ yasps_status yasps_eval_local(yasps_system* s, const double* x_dev, const double
   int bits = 0;
   RC(read_status(s, &bits));
   if (bits & (DEV_NAN | DEV_BADINDEX)) SYS_FAIL(s, YASPS_E_NAN, "device error during local evaluation");
+  // an exact (unprojected) Hessian may have indefinite diagonal blocks: the
+  // assembly stands, only the block-Jacobi preconditioner is then not built
+  if (project && (bits & DEV_INDEFINITE))
+    SYS_FAIL(s, YASPS_E_NAN, "projected Hessian has a diagonal block that is not positive definite");
   return YASPS_OK;
 }
 
@@ -632,6 +641,113 @@ static float elapsed(cudaEvent_t a, cudaEvent_t b) {
 
 static yasps_status step_batched(yasps_system* s, double* x, double* v, yasps_step_stats* stats);
 
+// Adaptive barrier stiffness at the start of a step (kappa_adaptive): pairs
+// and their smallest distance at x; the first step with pairs balances the
+// barrier gradient g_B (kappa = 1) against the gradient g_E of the other
+// terms, argmin_k |g_E + k g_B| = -g_E.g_B / g_B.g_B, clamped to
+// [kappa_min, kappa_max] (kappa_min before that step); later steps double
+// kappa, up to kappa_max, when the smallest distance is below kappa_dmin and
+// below the previous step's.  kappa is then frozen for the step.
+// The bounds of the adaptive stiffness: kappa_min > 0 and kappa_max > 0 as
+// given; kappa_min <= 0 takes the stiffness at which the barrier alone holds
+// the weight of an average vertex (total mass / vertex count) at half the
+// activation distance: the weight enters this potential as m h^2 |g| and the
+// barrier as kappa |db/dd| = kappa 2 d |b'(d^2)|, so
+// kappa_min = m h^2 |g| / (2 d |b'(d^2)|) at d = dhat / 2 (|g| = 0: standard
+// gravity); kappa_max <= 0 takes 1e4 kappa_min.
+static yasps_status kappa_bounds(yasps_system* s) {
+  double lo = s->prm.kappa_min;
+  if (!(lo > 0.0)) {
+    std::vector<double> vm(std::max(s->nv, 1), 0.0);
+    if (s->nv)
+      CK(s, cudaMemcpyAsync(vm.data(), s->vmass.p, sizeof(double) * s->nv, cudaMemcpyDeviceToHost, s->stream));
+    CK(s, cudaStreamSynchronize(s->stream));
+    double m = 0.0;
+    for (int v = 0; v < s->nv; ++v) m += vm[v];
+    m /= std::max(s->nv, 1);
+    const double* gv = s->prm.gravity;
+    double gn = std::sqrt(gv[0] * gv[0] + gv[1] * gv[1] + gv[2] * gv[2]);
+    if (!(gn > 0.0)) gn = 9.80665;
+    const double d = 0.5 * s->prm.dhat;
+    const double db = barrier_db(d * d, s->prm.dhat * s->prm.dhat, s->prm.barrier_form);
+    lo = m * s->prm.dt * s->prm.dt * gn / std::fabs(2.0 * d * db);
+  }
+  s->kappa_lo = lo;
+  s->kappa_hi = s->prm.kappa_max > 0.0 ? s->prm.kappa_max : 1e4 * lo;
+  return YASPS_OK;
+}
+
+static yasps_status kappa_update(yasps_system* s, const double* x, const double* xtil) {
+  RC(launch_positions(s, x, as<double>(s->P)));
+  RC(detect_pairs(s, as<double>(s->P)));
+  double s2 = 0.0;
+  RC(pairs_min_dist2(s, as<double>(s->P), &s2));
+  const double dmin = std::sqrt(s2);
+  if (!s->kappa_init) {
+    RC(kappa_bounds(s));
+    if (std::isfinite(dmin)) {
+      const int n3 = 3 * s->nn;
+      ENSURE(s, s->stepv[5], sizeof(double) * (n3 + 4));
+      double* gE = as<double>(s->stepv[5]);
+      RC(eval_impl(s, x, xtil, YASPS_TERM_ALL & ~YASPS_TERM_BARRIER, 0));
+      CK(s, cudaMemcpyAsync(gE, s->grad.p, sizeof(double) * n3, cudaMemcpyDeviceToDevice, s->stream));
+      const double keep = s->prm.kappa;
+      s->prm.kappa = 1.0;
+      yasps_status rc = eval_impl(s, x, xtil, YASPS_TERM_BARRIER, 0);
+      s->prm.kappa = keep;
+      RC(rc);
+      double num = 0.0, den = 0.0;
+      RC(dot2(s, gE, as<double>(s->grad), n3, &num, &den));
+      double k = den > 0.0 ? -num / den : s->kappa_lo;
+      if (!(k >= s->kappa_lo)) k = s->kappa_lo;
+      if (k > s->kappa_hi) k = s->kappa_hi;
+      s->prm.kappa = k;
+      s->kappa_init = true;
+    } else {
+      s->prm.kappa = s->kappa_lo;
+    }
+  } else if (dmin < (s->prm.kappa_dmin > 0.0 ? s->prm.kappa_dmin : 0.1 * s->prm.dhat) && dmin < s->kappa_dmin_prev) {
+    s->prm.kappa = std::min(2.0 * s->prm.kappa, s->kappa_hi);
+  }
+  s->kappa_dmin_prev = dmin;
+  return YASPS_OK;
+}
+
+extern "C" yasps_status yasps_get_kappa_state(yasps_system* s, double* kappa, int* initialised, double* dmin_prev,
+                                              double* kappa_lo, double* kappa_hi) {
+  if (!s) return YASPS_E_INVAL;
+  RC(kappa_bounds(s));
+  if (kappa) *kappa = s->prm.kappa;
+  if (initialised) *initialised = s->kappa_init ? 1 : 0;
+  if (dmin_prev) *dmin_prev = s->kappa_dmin_prev;
+  if (kappa_lo) *kappa_lo = s->kappa_lo;
+  if (kappa_hi) *kappa_hi = s->kappa_hi;
+  return YASPS_OK;
+}
+
+extern "C" yasps_status yasps_set_kappa_state(yasps_system* s, double kappa, int initialised, double dmin_prev) {
+  if (!s || !(kappa >= 0.0) || std::isnan(dmin_prev)) return YASPS_E_INVAL;
+  RC(kappa_bounds(s));
+  s->prm.kappa = kappa;
+  s->kappa_init = initialised != 0;
+  s->kappa_dmin_prev = dmin_prev;
+  return YASPS_OK;
+}
+
+extern "C" yasps_status yasps_newton_trace(const yasps_system* s, int capacity, yasps_newton_record* out, int* count) {
+  if (!s || capacity < 0 || (capacity > 0 && !out)) return YASPS_E_INVAL;
+  const int n = (int)s->trace.size();
+  for (int k = 0; k < std::min(n, capacity); ++k) out[k] = s->trace[k];
+  if (count) *count = n;
+  return YASPS_OK;
+}
+
+extern "C" yasps_status yasps_newton_trace_enable(yasps_system* s, int enable) {
+  if (!s) return YASPS_E_INVAL;
+  s->trace_smin = enable != 0;
+  return YASPS_OK;
+}
+
 extern "C" yasps_status yasps_step(yasps_system* s, double* x, double* v, yasps_step_stats* stats) {
   if (!s || !x || !v) return YASPS_E_INVAL;
   if (s->nscene > 1) return step_batched(s, x, v, stats);
@@ -655,6 +771,9 @@ extern "C" yasps_status yasps_step(yasps_system* s, double* x, double* v, yasps_
   CK(s, cudaMemcpyAsync(xt, x, sizeof(double) * n3, cudaMemcpyDeviceToDevice, s->stream));
   RC(launch_xtilde(s, x, v, xtil));
   s->cand_valid = false;
+  s->trace.clear();
+  if (s->prm.kappa_adaptive) RC(kappa_update(s, x, xtil));
+  st.kappa = s->prm.kappa;
   yasps_status rc = YASPS_OK;
   int it = 0;
   double pinf = 0.0, alpha = 1.0;
@@ -689,12 +808,29 @@ extern "C" yasps_status yasps_step(yasps_system* s, double* x, double* v, yasps_
     cudaEventRecord(s->ev[2], s->stream);
     int bits = 0;
     RC(read_status(s, &bits));
-    if (bits & (DEV_NAN | DEV_BADINDEX)) {
+    if (bits & (DEV_NAN | DEV_BADINDEX | DEV_INDEFINITE)) {
       s->err = "device error during evaluation";
       rc = YASPS_E_NAN;
       break;
     }
-    RC(inf_norm(s, p, n3, &pinf));
+    yasps_newton_record rec{};
+    rec.pcg_iters = pit;
+    rec.pcg_rel_res = rel;
+    rec.n_pt = s->npt; rec.n_ee = s->nee; rec.n_pg = s->npg;
+    rec.s_min = -1.0;
+    if (s->trace_smin) RC(pairs_min_dist2(s, as<double>(s->P), &rec.s_min));
+    RC(inf_norm(s, p, n3, &pinf, &rec.pinf_node));
+    rec.pinf_node /= 3;
+    rec.p_inf = pinf;
+    double gp = 0.0, pp = 0.0;
+    RC(dot2(s, as<double>(s->grad), p, n3, &gp, &pp));
+    rec.g_dot_p = gp;
+    if (s->trace_smin) {
+      CK(s, cudaMemcpyAsync(rec.p_at_max, p + 3 * (size_t)rec.pinf_node, sizeof(double) * 3, cudaMemcpyDeviceToHost,
+                            s->stream));
+      CK(s, cudaStreamSynchronize(s->stream));
+    }
+    s->trace.push_back(rec);
     if (!std::isfinite(pinf)) {
       s->err = "non-finite Newton direction";
       rc = YASPS_E_NAN;
@@ -708,6 +844,9 @@ extern "C" yasps_status yasps_step(yasps_system* s, double* x, double* v, yasps_
     cudaEvent_t pc = prof_begin(s);
     RC(ccd_bound(s, x, p, &alpha));
     prof_end(s, YASPS_STAGE_CCD, pc, 0.0);
+    s->trace.back().alpha_ccd = alpha;
+    s->trace.back().n_cand_pt = s->ncpt;
+    s->trace.back().n_cand_ee = s->ncee;
     st.n_cand_pt = s->ncpt;
     st.n_cand_ee = s->ncee;
     cudaEventRecord(s->ev[4], s->stream);
@@ -724,7 +863,7 @@ extern "C" yasps_status yasps_step(yasps_system* s, double* x, double* v, yasps_
       RC(energy_impl(s, xtrial, xtil, &E1, nullptr, true));
       // a decrease, up to the rounding of the energy sums: FP64 element
       // energies do not resolve differences below 1e-12 |E0|
-      if (E1 <= E0 + 1e-12 * std::fabs(E0)) break;
+      if (E1 <= E0 + 1e-12 * std::fabs(E0) - s->prm.ls_armijo * alpha * gp) break;
       alpha *= 0.5;
     }
     prof_end(s, YASPS_STAGE_LS, pl, 0.0);
@@ -732,6 +871,10 @@ extern "C" yasps_status yasps_step(yasps_system* s, double* x, double* v, yasps_
     cudaEventSynchronize(s->ev[5]);
     st.t_ccd_ms += elapsed(s->ev[3], s->ev[4]);
     st.t_ls_ms += elapsed(s->ev[4], s->ev[5]);
+    s->trace.back().ls_halvings = ls;
+    s->trace.back().alpha = ls == s->prm.ls_max_iter ? 0.0 : alpha;
+    s->trace.back().E0 = E0;
+    s->trace.back().E1 = E1;
     if (ls == s->prm.ls_max_iter) {
       s->err = "line search found no decreasing step";
       rc = YASPS_E_LINESEARCH;
@@ -825,7 +968,7 @@ extern "C" yasps_status yasps_adjoint_step(yasps_system* s, const double* x_t, c
   RC(eval_impl(s, x_next, xtil, YASPS_TERM_ALL, 0));
   int bits = 0;
   RC(read_status(s, &bits));
-  if (bits & (DEV_NAN | DEV_BADINDEX))
+  if (bits & (DEV_NAN | DEV_BADINDEX | DEV_INDEFINITE))
     SYS_FAIL(s, YASPS_E_NAN, "exact Hessian at the step solution has a non-positive diagonal block");
   k_adj_rhs<<<blocks_for(n3, 256), 256, 0, s->stream>>>(n3, xbar, vbar, 1.0 / h, rhs);
   LAUNCH_CHECK(s, "k_adj_rhs");
@@ -897,7 +1040,10 @@ static yasps_status energy_scenes(yasps_system* s, const double* x, const double
 static yasps_status step_batched(yasps_system* s, double* x, double* v, yasps_step_stats* stats) {
   const int n3 = 3 * s->nn, ns = s->nscene;
   const double h = s->prm.dt;
+  if (s->prm.kappa_adaptive) SYS_FAIL(s, YASPS_E_INVAL, "adaptive kappa is available for single scenes only");
+  s->trace.clear();
   yasps_step_stats st{};
+  st.kappa = s->prm.kappa;
   for (int k = 0; k < 4; ++k) ENSURE(s, s->stepv[k], sizeof(double) * (n3 + 4));
   double* xt = as<double>(s->stepv[0]);
   double* xtil = as<double>(s->stepv[1]);
@@ -951,7 +1097,7 @@ static yasps_status step_batched(yasps_system* s, double* x, double* v, yasps_st
     if (rc != YASPS_OK) break;
     int bits = 0;
     RC(read_status(s, &bits));
-    if (bits & (DEV_NAN | DEV_BADINDEX)) {
+    if (bits & (DEV_NAN | DEV_BADINDEX | DEV_INDEFINITE)) {
       s->err = "device error during evaluation";
       rc = YASPS_E_NAN;
       break;
@@ -1067,6 +1213,13 @@ extern "C" yasps_status yasps_autotune_pcg(yasps_system* s, int iters, int* vari
   if (!s) return YASPS_E_INVAL;
   if (s->hess_precision < 0) SYS_FAIL(s, YASPS_E_INVAL, "nothing assembled yet");
   return autotune_pcg(s, iters, variant, us_per_iter);
+}
+
+extern "C" yasps_status yasps_set_wait_limit(yasps_system* s, long long polls, int unmet_next) {
+  if (!s || polls < 0) return YASPS_E_INVAL;
+  s->wait_limit = polls;
+  s->wait_unmet = unmet_next != 0;
+  return YASPS_OK;
 }
 
 extern "C" yasps_status yasps_set_pcg_variant(yasps_system* s, int variant) {
