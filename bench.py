@@ -352,6 +352,9 @@ def native(args):
             "gpu_launches": fp64["launches"], "clocks": fp64["clocks"]}
         if dx is not None:
             line["fp64_plain"]["max_dx_vs_fp32_mixed_m"] = dx
+    if not args.skip_spmv_study:
+        line["spmv_study"] = spmv_study(G)
+        line["projection_study"] = projection_study()
     if not args.skip_batch:
         line["batch"] = batch_bench(args, dev)
     if rank == 0 and world == 1 and not args.skip_cpu:
@@ -363,6 +366,180 @@ def native(args):
     if bad:
         print(f"bench: {len(bad)} timed step(s) did not converge (statuses {sorted(set(bad))})", file=sys.stderr)
         sys.exit(3)
+
+
+# ---------------------------------------------------------------------------
+def spmv_layouts(row_u, col_u, vals_u, diag, perm=None):
+    """The four layouts of the SpMV study from the upper blocks of a symmetric
+    block matrix (host arrays), optionally after renumbering node i as
+    perm[i]: (diag, {layout: (row, col, vals)}).  Upper layouts keep row <
+    col (a block that the renumbering turns around is transposed), the full
+    ones carry both triangles; BSR and BCOO layouts are the same sorted
+    arrays, read by different kernels."""
+    row_u, col_u = np.asarray(row_u, np.int64), np.asarray(col_u, np.int64)
+    vals_u = np.asarray(vals_u).reshape(-1, 3, 3)
+    if perm is not None:
+        r, c = perm[row_u], perm[col_u]
+        swap = r > c
+        vals_u = vals_u.copy()
+        vals_u[swap] = vals_u[swap].transpose(0, 2, 1)
+        row_u, col_u = np.where(swap, c, r), np.where(swap, r, c)
+        d = np.empty_like(diag)
+        d[perm] = diag
+        diag = d
+    o = np.lexsort((col_u, row_u))
+    upper = (row_u[o].astype(np.int32), col_u[o].astype(np.int32), np.ascontiguousarray(vals_u[o]))
+    R = np.concatenate([row_u, col_u])
+    C = np.concatenate([col_u, row_u])
+    V = np.concatenate([vals_u, vals_u.transpose(0, 2, 1)])
+    o2 = np.lexsort((C, R))
+    full = (R[o2].astype(np.int32), C[o2].astype(np.int32), np.ascontiguousarray(V[o2]))
+    return diag, {"upper_bsr": upper, "full_bsr": full, "full_bcoo": full, "upper_bcoo": upper}
+
+
+def spmv_study(G, reps=20):
+    """Time y = A x on the system's current matrix in every layout and
+    precision, natural node order and a seeded random renumbering, with L2
+    flushed before every timed call; GB/s of algorithmic bytes (blocks and
+    their indices, diagonal, x and y once) against the measured HBM peak."""
+    import torch
+
+    import paper_2605_23088_b300 as yb
+
+    n = G.n_nodes
+    rows, cols, vals = [], [], []
+    diag = None
+    for which in (0, 1):
+        rp, col, blk, dg = G.export_bsr(which)
+        rows.append(np.repeat(np.arange(n), np.diff(rp)))
+        cols.append(col)
+        vals.append(blk)
+        if which == 0:
+            diag = dg
+    row_u, col_u, vals_u = np.concatenate(rows), np.concatenate(cols), np.concatenate(vals)
+    peak, kind = load_peaks()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")  # twice the L2
+    stream = torch.cuda.current_stream()
+    rng = np.random.default_rng(3)
+    x64 = rng.normal(size=(n, 3))
+    out = {"n_nodes": n, "upper_blocks": int(len(row_u)), "peak_gbs": peak, "peak_kind": kind, "reps": reps,
+           "l2": "flushed before every call (256 MB write)"}
+    ref = None
+    for order in ("natural", "permuted"):
+        perm = None if order == "natural" else rng.permutation(n)
+        d, lay = spmv_layouts(row_u, col_u, vals_u, diag, perm)
+        xo = x64 if perm is None else x64[np.argsort(perm)]  # x in the new numbering: x'[perm[i]] = x[i]
+        for prec, dt, nbyte in ((1, torch.float32, 4), (0, torch.float64, 8)):
+            X = torch.as_tensor(xo, dtype=dt, device="cuda")
+            D = torch.as_tensor(d, dtype=dt, device="cuda")
+            for name in yb.SPMV_FORMATS:
+                r_, c_, v_ = lay[name]
+                R_ = torch.as_tensor(r_, device="cuda")
+                C_ = torch.as_tensor(c_, device="cuda")
+                V_ = torch.as_tensor(v_, dtype=dt, device="cuda")
+                Y = torch.empty_like(X)
+                flag = torch.zeros(1, dtype=torch.int32, device="cuda")
+                fmt = yb.SPMV_FORMATS.index(name)
+                yb.spmv_format(fmt, n, R_, C_, V_, D, X, Y, flag)
+                ms = []
+                for _ in range(reps):
+                    flush.zero_()
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    yb.spmv_format(fmt, n, R_, C_, V_, D, X, Y, flag)
+                    e1.record(stream)
+                    torch.cuda.synchronize()
+                    ms.append(e0.elapsed_time(e1))
+                y = Y.double().cpu().numpy()
+                if perm is not None:
+                    y = y[perm]  # back to the natural numbering
+                if ref is None:
+                    ref = y
+                err = float(np.abs(y - ref).max() / np.abs(ref).max())
+                nb = len(r_)
+                algo = nb * (9 * nbyte + 8) + n * 9 * nbyte + 2 * 3 * nbyte * n
+                t = statistics.median(ms) * 1e-3
+                out[f"{order}_{'fp32' if prec else 'fp64'}_{name}"] = {
+                    "us": t * 1e6, "gbs": algo / t / 1e9, "frac": algo / t / 1e9 / peak, "bytes": algo,
+                    "max_rel_diff_vs_first": err, "flag": int(flag.item())}
+    return out
+
+
+# ---------------------------------------------------------------------------
+def pp_barrier_hessians(count, dhat=1e-3, kappa=1e4, seed=5):
+    """Synthetic point-point barrier Hessians (the projection study's inputs):
+    pairs at distances 0.1-0.9 dhat in random directions; position-space 6 x 6
+    Hessians kappa (b'' grad s grad s^T + b' hess s) of the barrier
+    -(s - sh)^2 ln(s / sh), s = |p - a|^2, and their node-space images through
+    the UNION Jacobians for a free and an affine vertex (15 x 15) and for two
+    affine vertices (24 x 24), with body-relative offsets r of a few cm."""
+    rng = np.random.default_rng(seed)
+    sh = dhat * dhat
+    d = dhat * rng.uniform(0.1, 0.9, count)
+    u = rng.normal(size=(count, 3))
+    u /= np.linalg.norm(u, axis=1, keepdims=True)
+    w = d[:, None] * u
+    s_ = d * d
+    L = np.log(s_ / sh)
+    db = -2.0 * (s_ - sh) * L - (s_ - sh) ** 2 / s_
+    d2b = -2.0 * L - 4.0 * (s_ - sh) / s_ + (s_ - sh) ** 2 / s_ ** 2
+    g = np.concatenate([2 * w, -2 * w], axis=1)
+    I3 = np.eye(3)
+    hs = 2.0 * np.block([[I3, -I3], [-I3, I3]])
+    H6 = kappa * (d2b[:, None, None] * g[:, :, None] * g[:, None, :] + db[:, None, None] * hs[None])
+    def union_J(r):  # 3 x 12: [I3, r1 I3, r2 I3, r3 I3]
+        return np.concatenate([I3] + [ri * I3 for ri in r], axis=1)
+    r1 = rng.uniform(-0.05, 0.05, (count, 3))
+    r2 = rng.uniform(-0.05, 0.05, (count, 3))
+    H15 = np.empty((count, 15, 15))
+    H24 = np.empty((count, 24, 24))
+    for k in range(count):
+        J15 = np.zeros((6, 15))
+        J15[:3, :3] = I3
+        J15[3:, 3:] = union_J(r1[k])
+        H15[k] = J15.T @ H6[k] @ J15
+        J24 = np.zeros((6, 24))
+        J24[:3, :12] = union_J(r1[k])
+        J24[3:, 12:] = union_J(r2[k])
+        H24[k] = J24.T @ H6[k] @ J24
+    # the library's PP form: the 3 x 3 in w = p - a (K = 2 H_w)
+    H3 = kappa * (d2b[:, None, None] * 4 * w[:, :, None] * w[:, None, :] + db[:, None, None] * 2 * I3[None]) * 2
+    return {24: H24, 15: H15, 6: H6, 3: H3}
+
+
+def projection_study(count=16384, reps=5):
+    """EVD micro-benchmark (Sec. "Eigendecomposition: Automatic Optimization",
+    the 24 / 15 / 6 sizes): time of projecting point-point barrier Hessians
+    in node space (24 x 24 between two affine vertices, 15 x 15 between a free
+    and an affine one), in position space (6 x 6) and in the reduced variable
+    w = p - a (3 x 3, what the library's barrier kernel does), per precision."""
+    import torch
+
+    import paper_2605_23088_b300 as yb
+
+    mats = pp_barrier_hessians(count)
+    stream = torch.cuda.current_stream()
+    out = {"pairs": count, "reps": reps}
+    for prec, dt in ((1, torch.float32), (0, torch.float64)):
+        t = {}
+        for n, H in mats.items():
+            Hd = torch.as_tensor(H, dtype=dt, device="cuda")
+            Od = torch.empty_like(Hd)
+            yb.project_batch(Hd, Od)
+            ms = []
+            for _ in range(reps):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                yb.project_batch(Hd, Od)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ms.append(e0.elapsed_time(e1))
+            t[n] = statistics.median(ms) * 1e3 / count  # microseconds per pair
+        name = "fp32" if prec else "fp64"
+        out[name] = {"us_per_pair": {str(k): v for k, v in t.items()},
+                     "speedup_24_to_6": t[24] / t[6], "speedup_15_to_6": t[15] / t[6], "speedup_6_to_3": t[6] / t[3],
+                     "speedup_24_to_3": t[24] / t[3]}
+    return out
 
 
 # ---------------------------------------------------------------------------
@@ -599,6 +776,7 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=3, help="timed FP64 steps (the first of the timed steps)")
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-batch", action="store_true", help="leave out the batching-form measurement")
+    ap.add_argument("--skip-spmv-study", action="store_true", help="leave out the SpMV layout study")
     ap.add_argument("--batch-steps", type=int, default=2)
     ap.add_argument("--save-state", default=None, help="write the post-pre-roll state (.npz) for --load-state")
     ap.add_argument("--load-state", default=None, help="start from a state written by --save-state")

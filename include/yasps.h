@@ -150,6 +150,18 @@ typedef struct {
    * 1024 scenes (YASPS_E_CAPACITY beyond). */
   int n_scenes;
   const int* vert_scene;    /* [n_verts] or NULL when n_scenes <= 1 */
+  /* Cloth model of the membrane triangles: 0 StVK (tri_E, tri_nu: Young's
+   * modulus and Poisson ratio, plane stress); 1 Baraff-Witkin stretch and
+   * shear (Baraff and Witkin 1998 in F-space, the cloth of the paper's
+   * benchmarks, Sec. "Cloths on Bunny on Cloth"): with F = [f_u f_v] (3x2)
+   * the deformation gradient over the rest (u, v) frame,
+   *   Psi = k_st/2 ((|f_u| - 1)^2 + (|f_v| - 1)^2) + k_sh/2 (f_u . f_v)^2,
+   * energy = area * thickness * Psi, k_st = tri_E (stretch stiffness, Pa)
+   * and k_sh = tri_shear (shear stiffness, Pa); tri_nu is not read.  The
+   * Hessian is projected in the 6x6 F-space (Sec. "Eigendecomposition:
+   * Manual Optimization").  tri_shear may be NULL for model 0. */
+  int cloth_model;
+  const double* tri_shear;  /* [n_tris] shear stiffness (Pa), model 1 */
 } yasps_scene_desc;
 
 /* Per-call statistics of yasps_step (the paper's counters, Sec. "Simulation
@@ -443,9 +455,51 @@ yasps_status yasps_profile_get(yasps_system* sys, int stage, yasps_stage_stats* 
  * kernel's first block): out[0] the block's own nodes (new direction and
  * diagonal product), out[1] the upper BSR blocks, out[2] the wait for the
  * grid's d^T H d, out[3] the update + preconditioner phase, out[4] the wait
- * for the grid's r^T z; out[5..7] = 0.  Waits include the time the slowest
- * block of the grid needs beyond the first. */
+ * for the grid's r^T z; out[5], out[6] the mean and the largest over the
+ * grid's blocks of a block's own-node + upper-block time (the load balance of
+ * the H d phase); out[7] = 0.  Waits include the time the slowest block of
+ * the grid needs beyond the first. */
 yasps_status yasps_pcg_phase_ms(const yasps_system* sys, double* out);
+
+/* The SpMV layout study (Sec. "Evaluation", the SpMV experiment; App.
+ * "SpMV"): y = (D + A_off) x for a symmetric matrix of 3x3 blocks given in
+ * one of four layouts, on caller arrays (all device, asynchronous on
+ * cuda_stream, no allocation):
+ *   YASPS_SPMV_UPPER_BSR   the library's storage: the nnzb upper blocks
+ *                          (row < col) sorted by row, each with its row and
+ *                          column; rows reduced by a warp-segmented shuffle,
+ *                          the transposed products added by atomics;
+ *   YASPS_SPMV_FULL_BSR    every off-diagonal block (both triangles) sorted
+ *                          by row: the same segmented reduction, no transposes;
+ *   YASPS_SPMV_FULL_BCOO   every off-diagonal block in any order, each adding
+ *                          its product to y by atomics;
+ *   YASPS_SPMV_UPPER_BCOO  the upper blocks in any order, each adding its
+ *                          product and its transpose's by atomics.
+ * row_dev, col_dev: int [nnzb]; vals_dev: [nnzb][9] row-major blocks;
+ * diag_dev [n_nodes][9]; x_dev, y_dev [n_nodes][3] (y overwritten), all FP64
+ * (precision 0) or FP32 (precision 1).  flag_dev (device int, caller-zeroed):
+ * set to 1 when a block lies outside the layout (index out of range, row >= col
+ * for the upper layouts, row == col for the full ones); such blocks are
+ * skipped.  Errors: E_INVAL for bad arguments, E_CUDA for a launch failure. */
+#define YASPS_SPMV_UPPER_BSR 0
+#define YASPS_SPMV_FULL_BSR 1
+#define YASPS_SPMV_FULL_BCOO 2
+#define YASPS_SPMV_UPPER_BCOO 3
+yasps_status yasps_spmv_format(int format, int precision, int n_nodes, int nnzb, const int* row_dev,
+                               const int* col_dev, const void* vals_dev, const void* diag_dev, const void* x_dev,
+                               void* y_dev, int* flag_dev, void* cuda_stream);
+
+/* PSD projection of count symmetric n x n matrices (row-major, contiguous,
+ * FP64 for precision 0, FP32 for 1): out = V max(Lambda, 0) V^T (Sec. "EVD
+ * and PSD Projection"), one warp per matrix with the parallel-ordering Jacobi
+ * of the barrier kernel; n in {3, 6, 9, 12, 15, 24} -- the sizes of the
+ * paper's projection comparison (Sec. "Eigendecomposition: Automatic
+ * Optimization": a point-point barrier in node space is 24 x 24 between two
+ * affine vertices and 15 x 15 between a free and an affine one, 6 x 6 in
+ * position space).  Device pointers, asynchronous on cuda_stream, no
+ * allocation.  Errors: E_INVAL (other n, bad arguments), E_CUDA. */
+yasps_status yasps_project_batch(int n, int count, int precision, const void* in_dev, void* out_dev,
+                                 void* cuda_stream);
 
 /* Measured FMA throughput of the current device's FP64 (precision 0) or FP32
  * (precision 1) pipe in TFLOP/s (2 flops per FMA), from a kernel of

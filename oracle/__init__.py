@@ -178,6 +178,11 @@ def ee_classify(a0, a1, b0, b1):
     return st, s.value
 
 
+def bw_local(x, X, kst, ksh, thick, project=True):
+    """Baraff-Witkin stretch + shear membrane triangle: (energy, gradient 9, Hessian 9x9)."""
+    return _local(lib().or_bw_local, 9, x, X, kst, ksh, thick, project=project)
+
+
 def pair_local(kind, xloc, plane=None, kappa=1.0, shat=1e-6, form=0, project=True):
     """kind 0 = PT, 1 = EE, 2 = PG; returns (E, g, H, subtype) in position space."""
     xl = _f64(xloc).ravel()
@@ -246,6 +251,8 @@ class OracleSystem:
             ctypes.c_int(len(s["planes"])), _dp(k(s["planes"], _f64)),
             _dp(self.fparams), _ip(self.iparams))
         self.h = ctypes.c_void_p(self.h)
+        if int(s.get("cloth_model", 0)) == 1:
+            L.or_set_cloth_model(self.h, ctypes.c_int(1), _dp(k(s["tri_shear"], _f64)))
         self.nn = L.or_num_nodes(self.h)
         self.nfree = L.or_num_free(self.h)
         self.nv = len(s["rest_pos"])

@@ -339,15 +339,35 @@ static jet stvk_psi_jet(const double* F /*3x2 row-major*/, double mu, double lam
   return jadd(jscale(nrm, mu), jscale(jsq(tr), 0.5 * lam));
 }
 
-OR_EXPORT int or_stvk_local(const double* x, const double* X, double mu, double lam, double thick, int project,
-                            double* E, double* g, double* H) {
+/* Baraff-Witkin stretch and shear (Baraff and Witkin 1998) as a function of
+ * the 3x2 deformation gradient F = [f_u f_v] over the rest (u, v) frame:
+ *   Psi = kst/2 ((|f_u| - 1)^2 + (|f_v| - 1)^2) + ksh/2 (f_u . f_v)^2,
+ * the cloth of the paper's benchmarks (Sec. "Cloths on Bunny on Cloth");
+ * projected in its 6x6 F-space (Sec. "Eigendecomposition: Manual
+ * Optimization"). */
+static jet bw_psi_jet(const double* F /*3x2 row-major*/, double kst, double ksh) {
+  JN = 6;
+  jet f[6];
+  for (int i = 0; i < 6; ++i) f[i] = jvar(F[i], i);
+  jet lu = jsqrt(jadd(jadd(jsq(f[0]), jsq(f[2])), jsq(f[4])));
+  jet lv = jsqrt(jadd(jadd(jsq(f[1]), jsq(f[3])), jsq(f[5])));
+  jet c = jadd(jadd(jmul(f[0], f[1]), jmul(f[2], f[3])), jmul(f[4], f[5]));
+  jet st = jadd(jsq(jaddc(lu, -1.0)), jsq(jaddc(lv, -1.0)));
+  return jadd(jscale(st, 0.5 * kst), jscale(jsq(c), 0.5 * ksh));
+}
+
+/* membrane element (model 0 StVK with Lame constants a = mu, b = lam;
+ * model 1 Baraff-Witkin with a = kst, b = ksh): energy area * thick * Psi(F),
+ * F = [x1 - x0, x2 - x0] Dm^-1, Hessian J_F^T Project(d2Psi/dF2) J_F */
+static int membrane_local(int model, const double* x, const double* X, double a, double b, double thick,
+                          int project, double* E, double* g, double* H) {
   double Dminv[4], area;
   if (or_tri_rest(X, Dminv, &area)) return -1;
   double F[6];
   for (int i = 0; i < 3; ++i)
     for (int j = 0; j < 2; ++j)
       F[2 * i + j] = (x[3 + i] - x[i]) * Dminv[0 * 2 + j] + (x[6 + i] - x[i]) * Dminv[1 * 2 + j];
-  jet r = stvk_psi_jet(F, mu, lam);
+  jet r = model == 1 ? bw_psi_jet(F, a, b) : stvk_psi_jet(F, a, b);
   double Jf[6 * 9];
   memset(Jf, 0, sizeof Jf);
   for (int i = 0; i < 3; ++i)
@@ -362,7 +382,7 @@ OR_EXPORT int or_stvk_local(const double* x, const double* X, double mu, double 
   if (g)
     for (int c = 0; c < 9; ++c) {
       double s = 0.0;
-      for (int a = 0; a < 6; ++a) s += Jf[a * 9 + c] * r.g[a];
+      for (int q = 0; q < 6; ++q) s += Jf[q * 9 + c] * r.g[q];
       g[c] = k * s;
     }
   if (H) {
@@ -372,6 +392,14 @@ OR_EXPORT int or_stvk_local(const double* x, const double* X, double mu, double 
     for (int i = 0; i < 81; ++i) H[i] *= k;
   }
   return 0;
+}
+OR_EXPORT int or_stvk_local(const double* x, const double* X, double mu, double lam, double thick, int project,
+                            double* E, double* g, double* H) {
+  return membrane_local(0, x, X, mu, lam, thick, project, E, g, H);
+}
+OR_EXPORT int or_bw_local(const double* x, const double* X, double kst, double ksh, double thick, int project,
+                          double* E, double* g, double* H) {
+  return membrane_local(1, x, X, kst, ksh, thick, project, E, g, H);
 }
 
 /* ======================================================================== */
@@ -734,6 +762,8 @@ typedef struct {
   double* xfix;   /* current positions of fixed vertices (3 per vertex, others unused) */
   double* nodemass; /* free nodes: m; bodies: 4x4 scalar mass matrix (16 per body) */
   double *tmu, *tlam, *cmu, *clam;
+  int cmodel;  /* membrane model: 0 StVK (cmu, clam), 1 Baraff-Witkin (cE stretch, cshear) */
+  double* cshear;
   /* adaptive barrier stiffness (off unless set): bounds, distance threshold, state */
   int kadapt, kinit;
   double kmin, kmax, kdmin, dmin_prev;
@@ -850,13 +880,23 @@ OR_EXPORT void or_destroy(void* p) {
   if (!S) return;
   void* ptrs[] = {S->rest, S->vbody, S->tets, S->tE, S->tnu, S->trho, S->tris, S->cE, S->cnu, S->cth, S->crho, S->hinges,
                   S->hkb, S->bmass, S->bvol, S->bkappa, S->stris, S->sedges, S->sverts, S->planes, S->fixed, S->fixvel,
-                  S->vnode, S->vfixed, S->vr, S->vmass, S->xfix, S->nodemass, S->tmu, S->tlam, S->cmu, S->clam};
+                  S->vnode, S->vfixed, S->vr, S->vmass, S->xfix, S->nodemass, S->tmu, S->tlam, S->cmu, S->clam,
+                  S->cshear};
   for (size_t i = 0; i < sizeof ptrs / sizeof ptrs[0]; ++i) free(ptrs[i]);
   free(S);
 }
 
 OR_EXPORT int or_num_nodes(void* p) { return ((osys*)p)->nn; }
 OR_EXPORT int or_num_free(void* p) { return ((osys*)p)->nfree; }
+/* membrane model of the cloth triangles: 0 StVK (default), 1 Baraff-Witkin
+ * with the stretch stiffness in tri_E and shear[e] the shear stiffness */
+OR_EXPORT void or_set_cloth_model(void* p, int model, const double* shear) {
+  osys* S = p;
+  S->cmodel = model;
+  free(S->cshear);
+  S->cshear = NULL;
+  if (model == 1) S->cshear = dupa(shear, sizeof(double) * (S->nc > 0 ? S->nc : 1));
+}
 OR_EXPORT void or_vertex_info(void* p, int* vnode, double* vr, double* vmass) {
   osys* S = p;
   memcpy(vnode, S->vnode, sizeof(int) * S->nv);
@@ -1178,7 +1218,8 @@ static void energy_terms(const osys* S, const double* x, const double* xtil, con
     double xl[9], Xl[9], E;
     gather_pos(S, P, S->tris + 3 * e, 3, xl);
     gather_pos(S, S->rest, S->tris + 3 * e, 3, Xl);
-    or_stvk_local(xl, Xl, S->cmu[e], S->clam[e], S->cth[e], 0, &E, NULL, NULL);
+    if (S->cmodel == 1) or_bw_local(xl, Xl, S->cE[e], S->cshear[e], S->cth[e], 0, &E, NULL, NULL);
+    else or_stvk_local(xl, Xl, S->cmu[e], S->clam[e], S->cth[e], 0, &E, NULL, NULL);
     kadd(&k[2], h2 * E);
   }
   for (int e = 0; e < S->nh; ++e) {
@@ -1388,7 +1429,8 @@ OR_EXPORT int or_assemble(void* p, const double* x, const double* xtil, int brut
     double xl[9], Xl[9], gl[9], Hl[81];
     gather_pos(S, P, S->tris + 3 * e, 3, xl);
     gather_pos(S, S->rest, S->tris + 3 * e, 3, Xl);
-    or_stvk_local(xl, Xl, S->cmu[e], S->clam[e], S->cth[e], project, NULL, gl, Hl);
+    if (S->cmodel == 1) or_bw_local(xl, Xl, S->cE[e], S->cshear[e], S->cth[e], project, NULL, gl, Hl);
+    else or_stvk_local(xl, Xl, S->cmu[e], S->clam[e], S->cth[e], project, NULL, gl, Hl);
     for (int i = 0; i < 9; ++i) gl[i] *= h2;
     for (int i = 0; i < 81; ++i) Hl[i] *= h2;
     scatter_local(S, S->tris + 3 * e, 3, gl, Hl, A->g, &Ls);

@@ -30,12 +30,14 @@ EXPORTS = [
     "yasps_set_fixed_positions", "yasps_get_fixed_positions", "yasps_set_tet_young", "yasps_adjoint_step", "yasps_scene_stats", "yasps_autotune_pcg", "yasps_set_pcg_variant", "yasps_kernel_launches", "yasps_profile_enable",
     "yasps_profile_get", "yasps_pcg_phase_ms", "yasps_pcg_solve_static", "yasps_newton_trace",
     "yasps_newton_trace_enable", "yasps_get_kappa_state", "yasps_set_kappa_state", "yasps_set_wait_limit",
-    "yasps_probe_fma_tflops",
+    "yasps_probe_fma_tflops", "yasps_spmv_format", "yasps_project_batch",
 ]
+SPMV_UPPER_BSR, SPMV_FULL_BSR, SPMV_FULL_BCOO, SPMV_UPPER_BCOO = range(4)
+SPMV_FORMATS = ["upper_bsr", "full_bsr", "full_bcoo", "upper_bcoo"]
 STAGE_SPMV, STAGE_TET, STAGE_BARRIER, STAGE_PCG, STAGE_DETECT, STAGE_EVAL, STAGE_CCD, STAGE_LS, STAGE_PCG_KERNEL = range(9)
 STAGE_NAMES = ["spmv", "tet", "barrier", "pcg", "detect", "eval", "ccd", "line_search", "pcg_kernel"]
 PCG_VARIANTS = 5  # YASPS_PCG_VARIANTS
-PCG_PHASES = ["own_nodes", "upper_blocks", "wait_dHd", "update", "wait_rz", "unused5", "unused6", "unused7"]
+PCG_PHASES = ["own_nodes", "upper_blocks", "wait_dHd", "update", "wait_rz", "hd_busy_mean", "hd_busy_max", "unused7"]
 
 
 class YaspsError(RuntimeError):
@@ -68,7 +70,8 @@ class SceneDesc(ctypes.Structure):
                 ("n_bodies", ctypes.c_int), ("body_mass", _PD), ("body_vol", _PD), ("body_kappa", _PD),
                 ("n_surf_tris", ctypes.c_int), ("surf_tri2v", _PI), ("n_surf_edges", ctypes.c_int),
                 ("surf_edge2v", _PI), ("n_surf_verts", ctypes.c_int), ("surf_verts", _PI),
-                ("n_planes", ctypes.c_int), ("planes", _PD), ("n_scenes", ctypes.c_int), ("vert_scene", _PI)]
+                ("n_planes", ctypes.c_int), ("planes", _PD), ("n_scenes", ctypes.c_int), ("vert_scene", _PI),
+                ("cloth_model", ctypes.c_int), ("tri_shear", _PD)]
 
 
 class StepStats(ctypes.Structure):
@@ -135,6 +138,42 @@ def default_params(**kw):
 
 def _ptr(t):
     return ctypes.c_void_p(t.data_ptr())
+
+
+def spmv_format(fmt, n_nodes, row, col, vals, diag, x, y, flag, stream=None):
+    """y = (D + A_off) x in one of the four layouts of the SpMV study
+    (yasps_spmv_format); every argument a contiguous CUDA tensor (row, col,
+    flag int32; vals [nnzb,3,3], diag [n,3,3], x, y [n,3] all float64 or all
+    float32).  Asynchronous on the stream."""
+    import torch
+
+    prec = 0 if x.dtype == torch.float64 else 1
+    s = stream if stream is not None else torch.cuda.current_stream()
+    nnzb = int(row.numel())
+    null = ctypes.c_void_p(0)
+    rc = lib().yasps_spmv_format(ctypes.c_int(fmt), ctypes.c_int(prec), ctypes.c_int(n_nodes), ctypes.c_int(nnzb),
+                                 _ptr(row) if nnzb else null, _ptr(col) if nnzb else null,
+                                 _ptr(vals) if nnzb else null, _ptr(diag), _ptr(x), _ptr(y), _ptr(flag),
+                                 ctypes.c_void_p(s.cuda_stream))
+    if rc != YASPS_OK:
+        raise YaspsError(rc, "yasps_spmv_format failed")
+
+
+def project_batch(H, out=None, stream=None):
+    """PSD projection of a batch of symmetric matrices H (CUDA tensor [count, n, n],
+    float64 or float32, n in 3, 6, 9, 12, 15, 24) by the library's warp Jacobi."""
+    import torch
+
+    if out is None:
+        out = torch.empty_like(H)
+    count, n = int(H.shape[0]), int(H.shape[1])
+    prec = 0 if H.dtype == torch.float64 else 1
+    s = stream if stream is not None else torch.cuda.current_stream()
+    rc = lib().yasps_project_batch(ctypes.c_int(n), ctypes.c_int(count), ctypes.c_int(prec), _ptr(H), _ptr(out),
+                                   ctypes.c_void_p(s.cuda_stream))
+    if rc != YASPS_OK:
+        raise YaspsError(rc, "yasps_project_batch failed")
+    return out
 
 
 def probe_fma_tflops(precision):
@@ -227,6 +266,9 @@ class System:
         d.n_surf_edges = len(s["surf_edges"]); d.surf_edge2v = arr(s["surf_edges"], np.int32)
         d.n_surf_verts = len(s["surf_verts"]); d.surf_verts = arr(s["surf_verts"], np.int32)
         d.n_planes = len(s["planes"]); d.planes = arr(s["planes"], np.float64)
+        d.cloth_model = int(s.get("cloth_model", 0))
+        if d.cloth_model:
+            d.tri_shear = arr(s["tri_shear"], np.float64)
         if s.get("vert_scene") is not None and int(s.get("n_scenes", 1)) > 1:
             d.n_scenes = int(s["n_scenes"]); d.vert_scene = arr(s["vert_scene"], np.int32)
         self.n_scenes = max(1, int(d.n_scenes))

@@ -1657,6 +1657,42 @@ yasps_status eval_barrier_t(yasps_system* s, int project) {
   return YASPS_OK;
 }
 
+// Projection of a batch of symmetric N x N matrices (row-major), one warp per
+// matrix, four per block: the EVD micro-benchmark of the projection sizes
+// (yasps_project_batch) with the same warp Jacobi the barrier kernel uses.
+template <typename T, int N>
+__global__ void __launch_bounds__(128) k_project_batch(int count, const T* __restrict__ in, T* __restrict__ out) {
+  constexpr int NP = N + (N & 1);
+  __shared__ T A[4][N * N], V[4][N * N];
+  __shared__ T cs[4][NP / 2], sn[4][NP / 2];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const long long m = (long long)blockIdx.x * 4 + w;
+  if (m >= count) return;  // warp-uniform
+  const T* src = in + (size_t)m * N * N;
+  for (int e = lane; e < N * N; e += 32) A[w][e] = src[e];
+  __syncwarp();
+  warp_project<T, N>(A[w], V[w], cs[w], sn[w], lane);
+  T* dst = out + (size_t)m * N * N;
+  for (int e = lane; e < N * N; e += 32) dst[e] = A[w][e];
+}
+
+template <typename T>
+yasps_status project_batch_t(int n, int count, const void* in, void* out, cudaStream_t st) {
+  const T* I = static_cast<const T*>(in);
+  T* O = static_cast<T*>(out);
+  const int g = blocks_for(count, 4);
+  switch (n) {
+    case 3: k_project_batch<T, 3><<<g, 128, 0, st>>>(count, I, O); break;
+    case 6: k_project_batch<T, 6><<<g, 128, 0, st>>>(count, I, O); break;
+    case 9: k_project_batch<T, 9><<<g, 128, 0, st>>>(count, I, O); break;
+    case 12: k_project_batch<T, 12><<<g, 128, 0, st>>>(count, I, O); break;
+    case 15: k_project_batch<T, 15><<<g, 128, 0, st>>>(count, I, O); break;
+    case 24: k_project_batch<T, 24><<<g, 128, 0, st>>>(count, I, O); break;
+    default: return YASPS_E_INVAL;
+  }
+  return cudaGetLastError() == cudaSuccess ? YASPS_OK : YASPS_E_CUDA;
+}
+
 }  // namespace
 
 // ======================================================================== API
@@ -1979,4 +2015,13 @@ yasps_status detect_from_candidates(yasps_system* s, const double* P) {
     nout = total;
   }
   return build_dynamic_bsr(s);
+}
+
+extern "C" yasps_status yasps_project_batch(int n, int count, int precision, const void* in_dev, void* out_dev,
+                                            void* cuda_stream) {
+  if (count < 0 || (count > 0 && (!in_dev || !out_dev)) || (precision != 0 && precision != 1)) return YASPS_E_INVAL;
+  if (count == 0) return YASPS_OK;
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  return precision == 0 ? project_batch_t<double>(n, count, in_dev, out_dev, st)
+                        : project_batch_t<float>(n, count, in_dev, out_dev, st);
 }

@@ -58,8 +58,8 @@ __global__ void k_rest_tet(int nt, const int* __restrict__ tv, const double* __r
 
 __global__ void k_rest_tri(int nc, const int* __restrict__ tv, const double* __restrict__ rest,
                            const double* __restrict__ E, const double* __restrict__ nu, const double* __restrict__ th,
-                           const double* __restrict__ rho, double* __restrict__ out, double* __restrict__ vmass,
-                           int* status) {
+                           const double* __restrict__ rho, int model, double* __restrict__ out,
+                           double* __restrict__ vmass, int* status) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= nc) return;
   const int v0 = tv[3 * e], v1 = tv[3 * e + 1], v2 = tv[3 * e + 2];
@@ -77,9 +77,15 @@ __global__ void k_rest_tri(int nc, const int* __restrict__ tv, const double* __r
   o[0] = D11 / det; o[1] = -D01 / det; o[2] = -D10 / det; o[3] = D00 / det;
   const double area = 0.5 * ln;
   o[4] = area * th[e];
-  o[5] = E[e] / (2.0 * (1.0 + nu[e]));          // mu
-  o[6] = E[e] * nu[e] / (1.0 - nu[e] * nu[e]);  // plane-stress lambda
-  o[7] = 0.0;
+  if (model == 1) {  // Baraff-Witkin: stretch and shear stiffness (nu holds the shear stiffness)
+    o[5] = E[e];
+    o[6] = nu[e];
+    o[7] = 1.0;
+  } else {
+    o[5] = E[e] / (2.0 * (1.0 + nu[e]));          // mu
+    o[6] = E[e] * nu[e] / (1.0 - nu[e] * nu[e]);  // plane-stress lambda
+    o[7] = 0.0;
+  }
   const double m = rho[e] * area * th[e] / 3.0;
   atomicAdd(&vmass[v0], m); atomicAdd(&vmass[v1], m); atomicAdd(&vmass[v2], m);
 }
@@ -623,11 +629,59 @@ __global__ void __launch_bounds__(128) k_membrane(int nc, const int* __restrict_
   for (int i = 0; i < 3; ++i)
 #pragma unroll
     for (int j = 0; j < 2; ++j) F[2 * i + j] = A1[i] * Dm[j] + A2[i] * Dm[2 + j];
-  const double E00 = 0.5 * (F[0] * F[0] + F[2] * F[2] + F[4] * F[4] - 1.0);
-  const double E11 = 0.5 * (F[1] * F[1] + F[3] * F[3] + F[5] * F[5] - 1.0);
-  const double E01 = 0.5 * (F[0] * F[1] + F[2] * F[3] + F[4] * F[5]);
-  const double tr = E00 + E11;
-  const double S[4] = {2 * mu * E00 + lam * tr, 2 * mu * E01, 2 * mu * E01, 2 * mu * E11 + lam * tr};
+  // first Piola-Kirchhoff stress P = dPsi/dF (3x2) and d2Psi/dF2 (6x6, index 2 i + j)
+  double Pk[6];
+  T Hf[36];
+  if (R[7] == 0.0) {
+    // StVK: E = (F^T F - I) / 2, S = 2 mu E + lam tr(E) I, P = F S;
+    // d2Psi/dF2 [(i,j),(k,l)] = d_ik S_lj + mu (F_il F_kj + (F F^T)_ik d_jl) + lam F_ij F_kl
+    const double E00 = 0.5 * (F[0] * F[0] + F[2] * F[2] + F[4] * F[4] - 1.0);
+    const double E11 = 0.5 * (F[1] * F[1] + F[3] * F[3] + F[5] * F[5] - 1.0);
+    const double E01 = 0.5 * (F[0] * F[1] + F[2] * F[3] + F[4] * F[5]);
+    const double tr = E00 + E11;
+    const double S[4] = {2 * mu * E00 + lam * tr, 2 * mu * E01, 2 * mu * E01, 2 * mu * E11 + lam * tr};
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 2; ++j) Pk[2 * i + j] = F[2 * i] * S[j] + F[2 * i + 1] * S[2 + j];
+#pragma unroll
+    for (int r = 0; r < 6; ++r)
+#pragma unroll
+      for (int q = 0; q < 6; ++q) {
+        const int i = r / 2, j = r % 2, k = q / 2, l = q % 2;
+        const double FFt = F[2 * i] * F[2 * k] + F[2 * i + 1] * F[2 * k + 1];
+        double v = (i == k ? S[2 * l + j] : 0.0) + mu * (F[2 * i + l] * F[2 * k + j] + (j == l ? FFt : 0.0)) +
+                   lam * F[2 * i + j] * F[2 * k + l];
+        Hf[6 * r + q] = (T)v;
+      }
+  } else {
+    // Baraff-Witkin: Psi = kst/2 ((|fu| - 1)^2 + (|fv| - 1)^2) + ksh/2 (fu.fv)^2 (mu, lam hold kst, ksh)
+    const double kst = mu, ksh = lam;
+    const double fu[3] = {F[0], F[2], F[4]}, fv[3] = {F[1], F[3], F[5]};
+    const double nu_ = fmax(sqrt(fu[0] * fu[0] + fu[1] * fu[1] + fu[2] * fu[2]), 1e-12);
+    const double nv_ = fmax(sqrt(fv[0] * fv[0] + fv[1] * fv[1] + fv[2] * fv[2]), 1e-12);
+    const double c = fu[0] * fv[0] + fu[1] * fv[1] + fu[2] * fv[2];
+    const double su = kst * (1.0 - 1.0 / nu_), sv = kst * (1.0 - 1.0 / nv_);
+    const double tu = kst / (nu_ * nu_ * nu_), tv = kst / (nv_ * nv_ * nv_);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      Pk[2 * i] = su * fu[i] + ksh * c * fv[i];
+      Pk[2 * i + 1] = sv * fv[i] + ksh * c * fu[i];
+    }
+#pragma unroll
+    for (int r = 0; r < 6; ++r)
+#pragma unroll
+      for (int q = 0; q < 6; ++q) {
+        const int i = r / 2, j = r % 2, k = q / 2, l = q % 2;
+        const double d = (i == k) ? 1.0 : 0.0;
+        double v;
+        if (j == 0 && l == 0) v = su * d + tu * fu[i] * fu[k] + ksh * fv[i] * fv[k];
+        else if (j == 1 && l == 1) v = sv * d + tv * fv[i] * fv[k] + ksh * fu[i] * fu[k];
+        else if (j == 0) v = ksh * (fv[i] * fu[k] + c * d);
+        else v = ksh * (fu[i] * fv[k] + c * d);
+        Hf[6 * r + q] = (T)v;
+      }
+  }
   double w[3][2];
 #pragma unroll
   for (int j = 0; j < 2; ++j) { w[1][j] = Dm[j]; w[2][j] = Dm[2 + j]; w[0][j] = -(Dm[j] + Dm[2 + j]); }
@@ -637,24 +691,12 @@ __global__ void __launch_bounds__(128) k_membrane(int nc, const int* __restrict_
     if (nodes[a] < 0) continue;
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-      double s = 0.0;
+      double sg = 0.0;
 #pragma unroll
-      for (int j = 0; j < 2; ++j) s += (F[2 * i] * S[j] + F[2 * i + 1] * S[2 + j]) * w[a][j];
-      atomicAdd(&g[3 * nodes[a] + i], sc * s);
+      for (int j = 0; j < 2; ++j) sg += Pk[2 * i + j] * w[a][j];
+      atomicAdd(&g[3 * nodes[a] + i], sc * sg);
     }
   }
-  // d2Psi/dF2 [(i,j),(k,l)] = d_ik S_lj + mu (F_il F_kj + (F F^T)_ik d_jl) + lam F_ij F_kl
-  T Hf[36];
-#pragma unroll
-  for (int r = 0; r < 6; ++r)
-#pragma unroll
-    for (int q = 0; q < 6; ++q) {
-      const int i = r / 2, j = r % 2, k = q / 2, l = q % 2;
-      const double FFt = F[2 * i] * F[2 * k] + F[2 * i + 1] * F[2 * k + 1];
-      double v = (i == k ? S[2 * l + j] : 0.0) + mu * (F[2 * i + l] * F[2 * k + j] + (j == l ? FFt : 0.0)) +
-                 lam * F[2 * i + j] * F[2 * k + l];
-      Hf[6 * r + q] = (T)v;
-    }
   if (project) project_psd<6, T>(Hf);
   int slots[3] = {cslot[3 * e], cslot[3 * e + 1], cslot[3 * e + 2]};
   scatter_fspace<T, 3, 2>(Hf, w, sc, nodes, slots, diag, vals);
@@ -820,9 +862,15 @@ __global__ void k_energy_membrane(int nc, const int* __restrict__ cv, const doub
       const v3<double> x0 = ld3(P, cv[3 * e]);
       const v3<double> a1 = ld3(P, cv[3 * e + 1]) - x0, a2 = ld3(P, cv[3 * e + 2]) - x0;
       const v3<double> f0 = R[0] * a1 + R[2] * a2, f1 = R[1] * a1 + R[3] * a2;  // columns of F
-      const double E00 = 0.5 * (dot(f0, f0) - 1.0), E11 = 0.5 * (dot(f1, f1) - 1.0), E01 = 0.5 * dot(f0, f1);
-      const double tr = E00 + E11;
-      const double psi = R[5] * (E00 * E00 + E11 * E11 + 2.0 * E01 * E01) + 0.5 * R[6] * tr * tr;
+      double psi;
+      if (R[7] == 0.0) {  // StVK
+        const double E00 = 0.5 * (dot(f0, f0) - 1.0), E11 = 0.5 * (dot(f1, f1) - 1.0), E01 = 0.5 * dot(f0, f1);
+        const double tr = E00 + E11;
+        psi = R[5] * (E00 * E00 + E11 * E11 + 2.0 * E01 * E01) + 0.5 * R[6] * tr * tr;
+      } else {  // Baraff-Witkin stretch and shear
+        const double su = sqrt(dot(f0, f0)) - 1.0, sv = sqrt(dot(f1, f1)) - 1.0, c = dot(f0, f1);
+        psi = 0.5 * R[5] * (su * su + sv * sv) + 0.5 * R[6] * c * c;
+      }
       val = h2 * R[4] * psi;
       key = sa.acc ? sa.vscene[cv[3 * e]] : 0;
     }
@@ -949,7 +997,8 @@ yasps_status setup_rest(yasps_system* s, const double* tE, const double* tnu, co
   }
   if (s->nc > 0) {
     k_rest_tri<<<blocks_for(s->nc, 128), 128, 0, s->stream>>>(s->nc, as<int>(s->tri_v), as<double>(s->rest), cE, cnu,
-                                                             cth, crho, as<double>(s->tri_rest), as<double>(s->vmass), st);
+                                                             cth, crho, s->cloth_model, as<double>(s->tri_rest),
+                                                             as<double>(s->vmass), st);
     LAUNCH_CHECK(s, "k_rest_tri");
     k_nodes_of<<<blocks_for(3LL * s->nc, 256), 256, 0, s->stream>>>(s->nc, 3, as<int>(s->tri_v), as<int>(s->vnode),
                                                                    as<int>(s->vbody), as<int>(s->tri_n), st);

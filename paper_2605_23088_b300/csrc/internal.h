@@ -45,6 +45,7 @@ struct yasps_system {
   double bbox_diag = 1.0;
   int nbits = 1;  // bits of a node id in packed (row, col) keys; node 2^nbits - 1 is the sentinel
   int nscene = 1;  // independent scenes in this system (batching)
+  int cloth_model = 0;  // membrane triangles: 0 StVK, 1 Baraff-Witkin
   gbuf vscene;     // int [nv] scene of each vertex (batches only)
   gbuf node_scene; // int [nn] scene of each node (batches only)
   double scene_spacing = 0.0;  // lattice spacing of the scenes' broadphase boxes (batches)
@@ -72,7 +73,7 @@ struct yasps_system {
   gbuf tet_nu;    // double [nt] Poisson ratios
   gbuf tet_slot;  // int [nt][6] static BSR slot of local pairs (01,02,03,12,13,23), -1 none
   gbuf tri_v, tri_n;  // int [nc][3]
-  gbuf tri_rest;      // double [nc][8]: Dm^-1 (4), area*thick, mu, lam, 0
+  gbuf tri_rest;      // double [nc][8]: Dm^-1 (4), area*thick, mu, lam, 0 (StVK) | k_st, k_sh, 1 (Baraff-Witkin)
   gbuf tri_slot;      // int [nc][3] (01, 02, 12)
   gbuf hinge_v, hinge_n;  // int [nh][4]
   gbuf hinge_rest;        // double [nh][2]: theta0, kb * 3|e|^2 / (A1 + A2)
@@ -102,6 +103,7 @@ struct yasps_system {
   bool cand_valid = false;
   gbuf pair_key_off;  // int [npt + nee + 1] offsets of each pair's dynamic keys
   gbuf dyn_slot;      // int [nkeys] dynamic BSR slot per key
+  gbuf pcg_bt;        // per-block busy time of the PCG kernel's H d' phase (profiling)
   gbuf bar_prep;      // per PT / EE pair: barrier derivatives (double2) then classification codes (int)
   int nkeys = 0;
 

@@ -294,6 +294,7 @@ struct pcg_args {
   int* status;
   long long spin_limit;
   double rscale;   // r0 = rscale * rhs (the FP32 inner solves work on a normalised residual)
+  unsigned long long* bt;  // per-block busy time of the H d' phase (own nodes + upper blocks), or null
   unsigned unmet;  // extra arrivals every grid barrier waits for (0; 1 makes the waits run out, for tests)
   // batches (nscene > 1): per-scene alpha, beta and stopping test
   int nscene;
@@ -742,7 +743,7 @@ __global__ void __launch_bounds__(CFG::NTHR, CFG::MINB) k_pcg_persistent(pcg_arg
   // 2 wait + d^T H d, 3 update, 4 wait + r^T z
   __shared__ unsigned long long tph[5];
   __shared__ int sh_active;
-  unsigned long long tlast = 0;
+  unsigned long long tlast = 0, tbusy = 0, tbusy0 = 0;
   if (threadIdx.x < 5) tph[threadIdx.x] = 0;
   if constexpr (BATCH)
     for (int t = threadIdx.x; t < a.nscene; t += blockDim.x) shs[t] = 0.0;
@@ -863,6 +864,7 @@ __global__ void __launch_bounds__(CFG::NTHR, CFG::MINB) k_pcg_persistent(pcg_arg
       return (V)(sv.rz(sc) / sv.rz_old(sc));
     };
     if (clock0) tlast = global_ns();
+    if (a.bt && threadIdx.x == 0) tbusy0 = global_ns();
     // the first two tiles travel while the block does its own nodes
     if (threadIdx.x == 0)
       for (int j = 0; j < 2 && j < sh.tt; ++j) {
@@ -950,6 +952,7 @@ __global__ void __launch_bounds__(CFG::NTHR, CFG::MINB) k_pcg_persistent(pcg_arg
     }
     bs = block_sum_v<V>(acc);
     if (clock0) { const unsigned long long t = global_ns(); tph[1] += t - tlast; tlast = t; }
+    if (a.bt && threadIdx.x == 0) tbusy += global_ns() - tbusy0;
     double dHd = 0.0;
     const int kb = (int)(kbar & 7);
     if (!grid_reduce(a.bar, kbar, bs, dHd, a.spin_limit, a.unmet, [&](double t) {
@@ -1063,6 +1066,7 @@ __global__ void __launch_bounds__(CFG::NTHR, CFG::MINB) k_pcg_persistent(pcg_arg
     for (int b = 0; b < 2; ++b)
       if ((inflight >> b) & 1u) mbar_wait_bounded(&mbar[b], (parity >> b) & 1u, kDrainPolls);
   __syncthreads();
+  if (a.bt && threadIdx.x == 0) a.bt[blockIdx.x] = tbusy;
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     a.sc->rz = rz;
     a.sc->rz0 = rz0;
@@ -1277,6 +1281,11 @@ yasps_status pcg_launch_cfg(yasps_system* s, const double* rhs, double* p, doubl
   a.status = as<int>(s->status);
   a.spin_limit = s->wait_limit > 0 ? s->wait_limit : (1LL << 22);  // a few seconds of polling per wait
   a.rscale = rscale;
+  a.bt = nullptr;
+  if (s->prof_on) {
+    ENSURE(s, s->pcg_bt, sizeof(unsigned long long) * ((size_t)G + 1));
+    a.bt = as<unsigned long long>(s->pcg_bt);
+  }
   a.unmet = s->wait_unmet ? 1u : 0u;
   s->wait_unmet = false;
   a.nscene = ns;
@@ -1314,8 +1323,19 @@ yasps_status pcg_launch_cfg(yasps_system* s, const double* rhs, double* p, doubl
     auto& sp = s->prof_acc[YASPS_STAGE_SPMV];
     sp.count += h.iters;
     sp.ms += (h.t_ns[0] + h.t_ns[1] + h.t_ns[2]) * 1e-6;
-    for (int k = 0; k < 8; ++k) s->pcg_phase_ms[k] += h.t_ns[k] * 1e-6;
+    for (int k = 0; k < 5; ++k) s->pcg_phase_ms[k] += h.t_ns[k] * 1e-6;
     sp.bytes += spmv_bytes * h.iters;
+    // load balance of the H d' phase: mean and max over the blocks of their busy time
+    std::vector<unsigned long long> bt(G);
+    CK(s, cudaMemcpyAsync(bt.data(), a.bt, sizeof(unsigned long long) * G, cudaMemcpyDeviceToHost, s->stream));
+    CK(s, cudaStreamSynchronize(s->stream));
+    double mean = 0.0, mx = 0.0;
+    for (int b = 0; b < G; ++b) {
+      mean += (double)bt[b];
+      mx = std::max(mx, (double)bt[b]);
+    }
+    s->pcg_phase_ms[5] += mean / G * 1e-6;
+    s->pcg_phase_ms[6] += mx * 1e-6;
   }
   if (h.done == 3) SYS_FAIL(s, YASPS_E_TIMEOUT, "PCG grid barrier timed out");
   k_add_to<V><<<blocks_for(n3, 256), 256, 0, s->stream>>>(n3, p, a.x, 1.0 / rscale);

@@ -64,7 +64,7 @@ static void all_bufs(yasps_system* s, std::vector<gbuf*>& v) {
                  &s->hinge_v, &s->hinge_n, &s->hinge_rest, &s->hinge_slot, &s->body_kv, &s->body_slot, &s->stri,
                  &s->sedge, &s->svert, &s->planes, &s->Hs.row_ptr, &s->Hs.col, &s->Hs.row, &s->Hs.vals,
                  &s->Hd.row_ptr, &s->Hd.col, &s->Hd.row, &s->Hd.vals, &s->diag, &s->grad, &s->minv, &s->dsym, &s->P, &s->pt,
-                 &s->ee, &s->pg, &s->cpt, &s->cee, &s->pair_key_off, &s->dyn_slot, &s->bar_prep, &s->status, &s->scal, &s->red, &s->scan_tmp};
+                 &s->ee, &s->pg, &s->cpt, &s->cee, &s->pair_key_off, &s->dyn_slot, &s->bar_prep, &s->pcg_bt, &s->status, &s->scal, &s->red, &s->scan_tmp};
   for (gbuf* b : one) v.push_back(b);
   for (auto& b : s->ws) v.push_back(&b);
   for (auto& b : s->vec) v.push_back(&b);
@@ -169,6 +169,9 @@ static yasps_status build_impl(yasps_system* s, const yasps_scene_desc* d) {
       d->n_surf_tris < 0 || d->n_surf_edges < 0 || d->n_surf_verts < 0 || d->n_planes < 0)
     SYS_FAIL(s, YASPS_E_INVAL, "negative size in the scene");
   if (nv > 0 && (!d->rest_pos || !d->vert_body)) SYS_FAIL(s, YASPS_E_INVAL, "rest_pos / vert_body missing");
+  if (d->cloth_model != 0 && d->cloth_model != 1) SYS_FAIL(s, YASPS_E_INVAL, "cloth_model must be 0 or 1");
+  if (d->cloth_model == 1 && d->n_tris > 0 && !d->tri_shear)
+    SYS_FAIL(s, YASPS_E_INVAL, "tri_shear missing for the Baraff-Witkin cloth");
   auto bad_idx = [&](const int* a, long long n, int hi) {
     for (long long i = 0; i < n; ++i)
       if (a[i] < 0 || a[i] >= hi) return true;
@@ -327,15 +330,19 @@ static yasps_status build_impl(yasps_system* s, const yasps_scene_desc* d) {
   ENSURE(s, s->P, sizeof(double) * (3 * (size_t)nv + 1));
 
   // per-element material inputs (temporaries)
-  gbuf tmp[8];
-  struct { const double* p; size_t n; } mats[8] = {{d->tet_E, (size_t)s->nt},     {d->tet_nu, (size_t)s->nt},
+  gbuf tmp[9];
+  const bool bw = d->cloth_model == 1;
+  // Baraff-Witkin: the second membrane constant is the shear stiffness
+  struct { const double* p; size_t n; } mats[9] = {{d->tet_E, (size_t)s->nt},     {d->tet_nu, (size_t)s->nt},
                                                   {d->tet_rho, (size_t)s->nt},   {d->tri_E, (size_t)s->nc},
-                                                  {d->tri_nu, (size_t)s->nc},    {d->tri_thick, (size_t)s->nc},
-                                                  {d->tri_rho, (size_t)s->nc},   {d->hinge_kb, (size_t)s->nh}};
+                                                  {bw ? d->tri_shear : d->tri_nu, (size_t)s->nc},
+                                                  {d->tri_thick, (size_t)s->nc}, {d->tri_rho, (size_t)s->nc},
+                                                  {d->hinge_kb, (size_t)s->nh},  {nullptr, 0}};
   yasps_status rc = YASPS_OK;
   for (int k = 0; k < 8 && rc == YASPS_OK; ++k) rc = upload(s, tmp[k], mats[k].p, mats[k].n);
   if (rc == YASPS_OK) rc = upload(s, s->tet_E, d->tet_E, (size_t)s->nt);
   if (rc == YASPS_OK) rc = upload(s, s->tet_nu, d->tet_nu, (size_t)s->nt);
+  s->cloth_model = bw ? 1 : 0;
   if (rc == YASPS_OK)
     rc = setup_rest(s, as<double>(tmp[0]), as<double>(tmp[1]), as<double>(tmp[2]), as<double>(tmp[3]),
                     as<double>(tmp[4]), as<double>(tmp[5]), as<double>(tmp[6]), as<double>(tmp[7]));

@@ -215,7 +215,7 @@ def random_rotations(rng, n):
 # --------------------------------------------------------------------------
 def _empty_parts():
     return dict(verts=[], vel=[], body=[], tets=[], tet_E=[], tet_nu=[], tet_rho=[],
-                tris=[], tri_E=[], tri_nu=[], tri_thick=[], tri_rho=[], hinges=[], hinge_kb=[],
+                tris=[], tri_E=[], tri_nu=[], tri_thick=[], tri_rho=[], tri_shear=[], hinges=[], hinge_kb=[],
                 surf_tris=[], fixed=[], fixed_vel=[], body_mass=[], body_vol=[], body_kappa=[], nv=0, nb=0)
 
 
@@ -235,7 +235,7 @@ def _add_soft(parts, verts, tets, E, nu, rho, vel=None):
     return off
 
 
-def _add_cloth(parts, verts, tris, E, nu, thick, rho, kb):
+def _add_cloth(parts, verts, tris, E, nu, thick, rho, kb, shear=0.0):
     off = parts["nv"]
     nv = len(verts)
     parts["verts"].append(verts)
@@ -245,6 +245,7 @@ def _add_cloth(parts, verts, tris, E, nu, thick, rho, kb):
     nc = len(tris)
     parts["tri_E"].append(np.full(nc, E)); parts["tri_nu"].append(np.full(nc, nu))
     parts["tri_thick"].append(np.full(nc, thick)); parts["tri_rho"].append(np.full(nc, rho))
+    parts["tri_shear"].append(np.full(nc, shear))
     h = cloth_hinges(tris)
     parts["hinges"].append(h + off)
     parts["hinge_kb"].append(np.full(len(h), kb))
@@ -282,7 +283,7 @@ def finalize_scene(parts, name, dt, dhat, kappa, n_steps, planes, gravity=(0.0, 
     s["fixed"] = _cat([np.asarray(f, np.int64) for f in parts["fixed"]], (), np.int32)
     s["fixed_vel"] = _cat([np.asarray(f, np.float64).reshape(-1, 3) for f in parts["fixed_vel"]], (3,), np.float64)
     s["tets"] = _cat(parts["tets"], (4,), np.int32)
-    for k in ("tet_E", "tet_nu", "tet_rho", "tri_E", "tri_nu", "tri_thick", "tri_rho", "hinge_kb"):
+    for k in ("tet_E", "tet_nu", "tet_rho", "tri_E", "tri_nu", "tri_thick", "tri_rho", "tri_shear", "hinge_kb"):
         s[k] = _cat(parts[k], (), np.float64)
     s["tris"] = _cat(parts["tris"], (3,), np.int32)
     s["hinges"] = _cat(parts["hinges"], (4,), np.int32)
@@ -294,6 +295,7 @@ def finalize_scene(parts, name, dt, dhat, kappa, n_steps, planes, gravity=(0.0, 
     s["surf_edges"] = unique_edges(st).astype(np.int32) if len(st) else np.zeros((0, 2), np.int32)
     s["surf_verts"] = np.unique(st).astype(np.int32) if len(st) else np.zeros((0,), np.int32)
     s["planes"] = np.asarray(planes, np.float64).reshape(-1, 4)
+    s["cloth_model"] = int(parts.get("cloth_model", 0))
     s["dt"] = float(dt)
     s["dhat"] = float(dhat)
     s["kappa"] = float(kappa)
@@ -423,6 +425,50 @@ def union_contact_scene(gap=3e-4, dhat=1e-3, kappa=1e4, dt=0.01, seed=0):
     return finalize_scene(parts, "union_contact", dt, dhat, kappa, 1, planes=[[0, 1, 0, 0]])
 
 
+def blob_mesh(h, radius=0.05, seed=0):
+    """A voxelised lumpy blob (the stand-in for the bunny of the paper's cloth
+    scenes): a sphere of the given radius with two smaller spheres attached."""
+    rng = np.random.default_rng(seed)
+    centres = [(0.0, 0.0, 0.0), (0.6 * radius, 0.55 * radius, 0.0), (-0.5 * radius, 0.3 * radius, 0.45 * radius)]
+    radii = [radius, 0.55 * radius, 0.45 * radius * (1.0 + 0.1 * rng.random())]
+
+    def inside(p):
+        ok = np.zeros(len(p), bool)
+        for c, r in zip(centres, radii):
+            ok |= np.linalg.norm(p - np.asarray(c), axis=1) <= r
+        return ok
+
+    lo = np.full(3, -1.2 * radius)
+    hi = np.full(3, 1.2 * radius)
+    return voxel_tets(inside, lo, hi, h)
+
+
+def bw_cloth_scene(cloth_n=101, cloth_size=1.0, layers=1, blob_h=0.01, blob_radius=0.12, seed=0, dt=0.01,
+                   dhat=1e-3, kappa=1e4, n_steps=200):
+    """The shape of the paper's first cloth benchmark (Sec. "Cloths on Bunny on
+    Cloth", Table 1) with synthetic inputs: a voxelised soft blob (stable
+    Neo-Hookean, E 10259 Pa, nu 0.205) held 2 cm above a Baraff-Witkin cloth
+    sheet pinned at its four corners (stretch 33570 Pa, shear 100607 Pa,
+    bending 0.055, 1 mm thick), and `layers` - 1 more sheets 3 cm apart above
+    the blob, free to fall onto it."""
+    parts = _empty_parts()
+    parts["cloth_model"] = 1
+    bv, bt = blob_mesh(blob_h, blob_radius, seed)
+    sheet_y = 0.3
+    bv = bv + np.array([0.0, sheet_y + 0.02 - bv[:, 1].min(), 0.0])
+    _add_soft(parts, bv, bt, 10259.0, 0.205, 1000.0)
+    top = bv[:, 1].max()
+    for k in range(layers):
+        y = sheet_y if k == 0 else top + 0.03 * k
+        cv, ct = cloth_grid(cloth_n, cloth_size, (-cloth_size / 2, y, -cloth_size / 2))
+        off = _add_cloth(parts, cv, ct, 33570.0, 0.0, 1e-3, 1000.0, 0.055, shear=100607.0)
+        if k == 0:
+            corners = [0, cloth_n - 1, cloth_n * (cloth_n - 1), cloth_n * cloth_n - 1]
+            parts["fixed"].append([off + c for c in corners])
+            parts["fixed_vel"].append(np.zeros((4, 3)))
+    return finalize_scene(parts, "bw_cloth", dt, dhat, kappa, n_steps, planes=[[0, 1, 0, 0]])
+
+
 def beam_scene(nx=52, ny=8, nz=8, length=1.0, width=0.1, lift=0.02, seed=0, dt=0.01, dhat=1e-3,
                kappa=1e4, n_steps=20, rho=1000.0, nu=0.4):
     """Clamped beam (x=0 face fixed) with log-uniform per-tet E and N(0,0.1) velocities."""
@@ -510,13 +556,13 @@ def concat_scenes(scenes, newton_tol=None):
            "kappa": first["kappa"], "gravity": first["gravity"].copy(), "n_steps": first["n_steps"]}
     voff, boff = 0, 0
     acc = {k: [] for k in ("rest_pos", "vel0", "vert_body", "fixed", "fixed_vel", "tets", "tet_E", "tet_nu", "tet_rho",
-                           "tris", "tri_E", "tri_nu", "tri_thick", "tri_rho", "hinges", "hinge_kb", "body_mass",
+                           "tris", "tri_E", "tri_nu", "tri_thick", "tri_rho", "tri_shear", "hinges", "hinge_kb", "body_mass",
                            "body_vol", "body_kappa", "surf_tris", "surf_edges", "surf_verts", "vert_scene")}
     for k, sc in enumerate(scenes):
         nv = len(sc["rest_pos"])
         for key in ("rest_pos", "vel0", "fixed_vel", "tet_E", "tet_nu", "tet_rho", "tri_E", "tri_nu", "tri_thick",
-                    "tri_rho", "hinge_kb", "body_mass", "body_vol", "body_kappa"):
-            acc[key].append(np.asarray(sc[key]))
+                    "tri_rho", "tri_shear", "hinge_kb", "body_mass", "body_vol", "body_kappa"):
+            acc[key].append(np.asarray(sc.get(key, np.zeros(len(sc["tris"])) if key == "tri_shear" else None)))
         vb = np.asarray(sc["vert_body"]).copy()
         vb[vb >= 0] += boff
         acc["vert_body"].append(vb)
@@ -528,6 +574,10 @@ def concat_scenes(scenes, newton_tol=None):
     ints = ("vert_body", "fixed", "tets", "tris", "hinges", "surf_tris", "surf_edges", "surf_verts", "vert_scene")
     for key, lst in acc.items():
         out[key] = np.ascontiguousarray(np.concatenate(lst, axis=0).astype(np.int32 if key in ints else np.float64))
+    models = {int(sc.get("cloth_model", 0)) for sc in scenes if len(sc["tris"])}
+    if len(models) > 1:
+        raise ValueError("scenes of a batch must share the cloth model")
+    out["cloth_model"] = models.pop() if models else 0
     out["n_scenes"] = len(scenes)
     out["scene_vert_offsets"] = np.cumsum([0] + [len(sc["rest_pos"]) for sc in scenes])
     out["bbox_diag"] = max(sc["bbox_diag"] for sc in scenes)
