@@ -170,11 +170,12 @@ def allreduce_sum(world, v):
 
 
 # ---------------------------------------------------------------------------
-def run_steps(system, x0, v0, steps, profile, world, host_io):
+def run_steps(system, x0, v0, steps, profile, world, host_io, label):
     """K implicit steps from (x0, v0).  host_io: every step copies x, v in from
     pinned host memory and the result back out (the end-to-end path through
     the C ABI with host buffers); the step itself is bracketed by CUDA events
-    on the launching stream, the whole iteration by the host clock."""
+    on the launching stream, the whole iteration by the host clock.  The
+    steps sit inside the NVTX range `label` (for ncu --nvtx-include)."""
     import torch
 
     import paper_2605_23088_b300 as yb
@@ -191,6 +192,7 @@ def run_steps(system, x0, v0, steps, profile, world, host_io):
     per = []
     with ClockSampler(int(os.environ.get("LOCAL_RANK", "0"))) as clk:
         torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push(label)
         for _ in range(steps):
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             t0 = time.perf_counter()
@@ -208,6 +210,7 @@ def run_steps(system, x0, v0, steps, profile, world, host_io):
             per.append({"rc": st["rc"], "newton": st["newton_iters"],
                         "passes": st["newton_iters"] + (1 if st["rc"] == 0 else 0), "pcg": st["pcg_iters_total"],
                         "pairs": [st["n_pt"], st["n_ee"], st["n_pg"]], "ms": e0.elapsed_time(e1), "e2e_ms": wall})
+        torch.cuda.nvtx.range_pop()
     launches = system.kernel_launches() - l0
     prof = {k: system.profile_get(i) for i, k in enumerate(yb.STAGE_NAMES)} if profile else None
     phases = system.pcg_phase_ms() if profile else None
@@ -272,7 +275,7 @@ def native(args):
 
     # FP32-mixed: the timed steps, each with its host copies (value: step time
     # on the device; e2e: the whole iteration through pinned host buffers)
-    mixed_run = run_steps(G, x0, v0, args.steps, True, world, host_io=True)
+    mixed_run = run_steps(G, x0, v0, args.steps, True, world, host_io=True, label="timed_fp32-mixed")
     mixed = summarize(mixed_run, world)
     bytes_state = 2 * x0.numel() * 8
 
@@ -284,7 +287,7 @@ def native(args):
         G64.step(xs, vs, raise_on_error=False)  # an assembly to tune on
         var, us = G64.autotune_pcg(30)
         tune["fp64"] = {"variant": var, "us_per_iter": [round(u, 2) for u in us]}
-        fp64_run = run_steps(G64, x0, v0, n64, True, world, host_io=False)
+        fp64_run = run_steps(G64, x0, v0, n64, True, world, host_io=False, label="timed_fp64")
         fp64 = summarize(fp64_run, world)
         fp64["prof"] = fp64_run["prof"]
         fp64["launches"] = fp64_run["launches"]

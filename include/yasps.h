@@ -111,7 +111,7 @@ typedef struct {
 typedef struct {
   int n_verts;
   const double* rest_pos;   /* [n_verts][3] undeformed world positions (also the initial state) */
-  const int* vert_body;     /* [n_verts] -1 or affine body id */
+  const int* vert_body;     /* [n_verts] -1 free, an affine body id (>= 0), or -2: embedded in a cage */
   int n_fixed;
   const int* fixed_verts;   /* [n_fixed] vertices with prescribed positions */
   const double* fixed_vel;  /* [n_fixed][3] prescribed velocity, applied at the start of each step */
@@ -162,6 +162,20 @@ typedef struct {
    * Manual Optimization").  tri_shear may be NULL for model 0. */
   int cloth_model;
   const double* tri_shear;  /* [n_tris] shear stiffness (Pa), model 1 */
+  /* Cage-embedded vertices (the cage parameterisation of Sec. "Caged Bunny"):
+   * vertex embed_verts[e] (vert_body -2; strictly increasing) sits at
+   * p = sum_k embed_w[e][k] x(embed_cage[e][k]) over the 8 vertices of the
+   * cage cell that encloses it (trilinear weights).  Cage vertices must be
+   * free (vert_body -1, not fixed, not embedded); embedded vertices carry no
+   * DOF, mass or elastic element of their own -- they take part in contact,
+   * and their UNION Jacobian (w_k I3 over up to 8 nodes) carries the contact
+   * forces to the cage, whose own elements (e.g. 6 tets per cell) hold it
+   * together.  A pair of embedded vertices then spans up to 16 nodes, a
+   * point-triangle or edge-edge pair up to 32. */
+  int n_embedded;
+  const int* embed_verts;   /* [n_embedded] */
+  const int* embed_cage;    /* [n_embedded][8] cage vertex ids */
+  const double* embed_w;    /* [n_embedded][8] weights (sum 1) */
 } yasps_scene_desc;
 
 /* Per-call statistics of yasps_step (the paper's counters, Sec. "Simulation
@@ -460,6 +474,16 @@ yasps_status yasps_profile_get(yasps_system* sys, int stage, yasps_stage_stats* 
  * the H d phase); out[7] = 0.  Waits include the time the slowest block of
  * the grid needs beyond the first. */
 yasps_status yasps_pcg_phase_ms(const yasps_system* sys, double* out);
+
+/* Load balance of the PCG kernel, block by block: for each block of the grid
+ * of the last launch profiled since yasps_profile_enable, its own-node +
+ * upper-block time in microseconds per iteration (summed over the profiled
+ * launches of that grid size, divided by their iterations) and the SM it ran
+ * on in that launch.  *n_blocks (host) receives the grid size (0 before any
+ * profiled launch); up to `capacity` entries go to us_per_iter and sm_ids
+ * (host arrays, each nullable).  For measurement only. */
+yasps_status yasps_pcg_block_busy(const yasps_system* sys, int capacity, int* n_blocks, double* us_per_iter,
+                                  int* sm_ids);
 
 /* The SpMV layout study (Sec. "Evaluation", the SpMV experiment; App.
  * "SpMV"): y = (D + A_off) x for a symmetric matrix of 3x3 blocks given in

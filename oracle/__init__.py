@@ -253,6 +253,9 @@ class OracleSystem:
         self.h = ctypes.c_void_p(self.h)
         if int(s.get("cloth_model", 0)) == 1:
             L.or_set_cloth_model(self.h, ctypes.c_int(1), _dp(k(s["tri_shear"], _f64)))
+        if len(s.get("embed_verts", ())):
+            L.or_set_embedding(self.h, ctypes.c_int(len(s["embed_verts"])), _ip(k(s["embed_verts"], _i32)),
+                               _ip(k(s["embed_cage"], _i32)), _dp(k(s["embed_w"], _f64)))
         self.nn = L.or_num_nodes(self.h)
         self.nfree = L.or_num_free(self.h)
         self.nv = len(s["rest_pos"])

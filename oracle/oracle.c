@@ -764,6 +764,10 @@ typedef struct {
   double *tmu, *tlam, *cmu, *clam;
   int cmodel;  /* membrane model: 0 StVK (cmu, clam), 1 Baraff-Witkin (cE stretch, cshear) */
   double* cshear;
+  int ne;        /* cage-embedded vertices (vert_body -2) */
+  int* emb_of;   /* [nv] embedding row or -1 */
+  int* emb_cage; /* [ne][8] cage vertex ids */
+  double* emb_w; /* [ne][8] trilinear weights */
   /* adaptive barrier stiffness (off unless set): bounds, distance threshold, state */
   int kadapt, kinit;
   double kmin, kmax, kdmin, dmin_prev;
@@ -815,7 +819,8 @@ OR_EXPORT void* or_create(int nv, const double* rest, const int* vbody,
   int nf = 0;
   for (int v = 0; v < nv; ++v) {
     if (S->vfixed[v]) S->vnode[v] = -1;
-    else if (vbody[v] < 0) S->vnode[v] = nf++;
+    else if (vbody[v] == -1) S->vnode[v] = nf++;
+    else if (vbody[v] <= -2) S->vnode[v] = -2; /* cage-embedded: or_set_embedding gives its map */
   }
   S->nfree = nf;
   S->nn = nf + 4 * nb;
@@ -858,7 +863,7 @@ OR_EXPORT void* or_create(int nv, const double* rest, const int* vbody,
   /* node mass: free m I3; body M_ab = sum_v m_v w_a w_b, w = (1, r1, r2, r3) */
   S->nodemass = calloc(nf + 16 * nb + 1, sizeof(double));
   for (int v = 0; v < nv; ++v) {
-    if (S->vfixed[v]) continue;
+    if (S->vfixed[v] || vbody[v] <= -2) continue; /* embedded vertices carry no mass */
     if (vbody[v] < 0) S->nodemass[S->vnode[v]] = S->vmass[v];
     else {
       double w[4] = {1.0, S->vr[3 * v], S->vr[3 * v + 1], S->vr[3 * v + 2]};
@@ -881,13 +886,25 @@ OR_EXPORT void or_destroy(void* p) {
   void* ptrs[] = {S->rest, S->vbody, S->tets, S->tE, S->tnu, S->trho, S->tris, S->cE, S->cnu, S->cth, S->crho, S->hinges,
                   S->hkb, S->bmass, S->bvol, S->bkappa, S->stris, S->sedges, S->sverts, S->planes, S->fixed, S->fixvel,
                   S->vnode, S->vfixed, S->vr, S->vmass, S->xfix, S->nodemass, S->tmu, S->tlam, S->cmu, S->clam,
-                  S->cshear};
+                  S->cshear, S->emb_of, S->emb_cage, S->emb_w};
   for (size_t i = 0; i < sizeof ptrs / sizeof ptrs[0]; ++i) free(ptrs[i]);
   free(S);
 }
 
 OR_EXPORT int or_num_nodes(void* p) { return ((osys*)p)->nn; }
 OR_EXPORT int or_num_free(void* p) { return ((osys*)p)->nfree; }
+/* cage embedding (Sec. "Caged Bunny"): vertex verts[e] (vert_body -2) sits
+ * at sum_k w[e][k] x(cage[e][k]) over its cage cell's 8 free vertices */
+OR_EXPORT void or_set_embedding(void* p, int ne, const int* verts, const int* cage, const double* w) {
+  osys* S = p;
+  S->ne = ne;
+  free(S->emb_of); free(S->emb_cage); free(S->emb_w);
+  S->emb_of = malloc(sizeof(int) * (S->nv + 1));
+  for (int v = 0; v < S->nv; ++v) S->emb_of[v] = -1;
+  for (int e = 0; e < ne; ++e) S->emb_of[verts[e]] = e;
+  S->emb_cage = dupa(cage, sizeof(int) * 8 * (ne > 0 ? ne : 1));
+  S->emb_w = dupa(w, sizeof(double) * 8 * (ne > 0 ? ne : 1));
+}
 /* membrane model of the cloth triangles: 0 StVK (default), 1 Baraff-Witkin
  * with the stretch stiffness in tri_E and shear[e] the shear stiffness */
 OR_EXPORT void or_set_cloth_model(void* p, int model, const double* shear) {
@@ -904,9 +921,17 @@ OR_EXPORT void or_vertex_info(void* p, int* vnode, double* vr, double* vmass) {
   memcpy(vmass, S->vmass, sizeof(double) * S->nv);
 }
 
-/* vertex -> (up to 4) node ids and weights; position p = sum w_k x[node_k] */
+/* vertex -> (up to 8) node ids and weights; position p = sum w_k x[node_k]
+ * (Sec. "UNION": free -> itself; affine -> (t, A1, A2, A3) with weights
+ * (1, r1, r2, r3); cage-embedded -> the 8 nodes of its cage cell with its
+ * trilinear weights, Sec. "Caged Bunny") */
 static int vmap(const osys* S, int v, int* nodes, double* w) {
   if (S->vfixed[v]) return 0;
+  if (S->vbody[v] <= -2) {
+    const int e = S->emb_of[v];
+    for (int k = 0; k < 8; ++k) { nodes[k] = S->vnode[S->emb_cage[8 * e + k]]; w[k] = S->emb_w[8 * e + k]; }
+    return 8;
+  }
   if (S->vbody[v] < 0) { nodes[0] = S->vnode[v]; w[0] = 1.0; return 1; }
   int b0 = S->vnode[v];
   for (int k = 0; k < 4; ++k) nodes[k] = b0 + k;
@@ -915,7 +940,7 @@ static int vmap(const osys* S, int v, int* nodes, double* w) {
 }
 static void vpos(const osys* S, const double* x, int v, double* p) {
   if (S->vfixed[v]) { memcpy(p, S->xfix + 3 * v, sizeof(double) * 3); return; }
-  int nodes[4]; double w[4];
+  int nodes[8]; double w[8];
   int m = vmap(S, v, nodes, w);
   p[0] = p[1] = p[2] = 0.0;
   for (int k = 0; k < m; ++k)
@@ -930,7 +955,7 @@ OR_EXPORT void or_initial_state(void* p, const double* vel0, double* x, double* 
   memset(x, 0, sizeof(double) * 3 * S->nn);
   memset(v, 0, sizeof(double) * 3 * S->nn);
   for (int i = 0; i < S->nv; ++i)
-    if (!S->vfixed[i] && S->vbody[i] < 0)
+    if (!S->vfixed[i] && S->vbody[i] == -1)
       for (int c = 0; c < 3; ++c) { x[3 * S->vnode[i] + c] = S->rest[3 * i + c]; v[3 * S->vnode[i] + c] = vel0[3 * i + c]; }
   for (int b = 0; b < S->nb; ++b) {
     int b0 = S->nfree + 4 * b;
@@ -1297,11 +1322,11 @@ static int cmp_contrib(const void* x, const void* y) {
  * r2 I3, r3 I3]); node blocks that several local vertices share are merged
  * before they are emitted (Sec. "Hessian Code Generation", local compression). */
 static void scatter_local(const osys* S, const int* verts, int k, const double* gl, const double* Hl, double* g, clist* L) {
-  int un[16], nu = 0;
-  double W[4][16];
+  int un[32], nu = 0;
+  double W[4][32];
   memset(W, 0, sizeof W);
   for (int i = 0; i < k; ++i) {
-    int nodes[4]; double w[4];
+    int nodes[8]; double w[8];
     int m = vmap(S, verts[i], nodes, w);
     for (int q = 0; q < m; ++q) {
       int u;
@@ -1923,8 +1948,8 @@ OR_EXPORT int or_adjoint_step(void* p, const double* xt, const double* vt, const
     or_snh_local(xl, Xl, S->tmu[e], S->tlam[e], 0, NULL, gl, Hl);
     double acc = 0.0;
     for (int a = 0; a < 4; ++a) {
-      int nodes[4];
-      double w[4];
+      int nodes[8];
+      double w[8];
       int m = vmap(S, S->tets[4 * e + a], nodes, w);
       for (int c = 0; c < 3; ++c) {
         double lv = 0.0;

@@ -28,7 +28,7 @@ EXPORTS = [
     "yasps_detect_pairs", "yasps_export_pairs", "yasps_energy", "yasps_eval_local", "yasps_assemble",
     "yasps_export_bsr", "yasps_export_gradient", "yasps_spmv", "yasps_pcg_solve", "yasps_ccd_bound", "yasps_step",
     "yasps_set_fixed_positions", "yasps_get_fixed_positions", "yasps_set_tet_young", "yasps_adjoint_step", "yasps_scene_stats", "yasps_autotune_pcg", "yasps_set_pcg_variant", "yasps_kernel_launches", "yasps_profile_enable",
-    "yasps_profile_get", "yasps_pcg_phase_ms", "yasps_pcg_solve_static", "yasps_newton_trace",
+    "yasps_profile_get", "yasps_pcg_phase_ms", "yasps_pcg_block_busy", "yasps_pcg_solve_static", "yasps_newton_trace",
     "yasps_newton_trace_enable", "yasps_get_kappa_state", "yasps_set_kappa_state", "yasps_set_wait_limit",
     "yasps_probe_fma_tflops", "yasps_spmv_format", "yasps_project_batch",
 ]
@@ -71,7 +71,8 @@ class SceneDesc(ctypes.Structure):
                 ("n_surf_tris", ctypes.c_int), ("surf_tri2v", _PI), ("n_surf_edges", ctypes.c_int),
                 ("surf_edge2v", _PI), ("n_surf_verts", ctypes.c_int), ("surf_verts", _PI),
                 ("n_planes", ctypes.c_int), ("planes", _PD), ("n_scenes", ctypes.c_int), ("vert_scene", _PI),
-                ("cloth_model", ctypes.c_int), ("tri_shear", _PD)]
+                ("cloth_model", ctypes.c_int), ("tri_shear", _PD), ("n_embedded", ctypes.c_int),
+                ("embed_verts", _PI), ("embed_cage", _PI), ("embed_w", _PD)]
 
 
 class StepStats(ctypes.Structure):
@@ -266,6 +267,9 @@ class System:
         d.n_surf_edges = len(s["surf_edges"]); d.surf_edge2v = arr(s["surf_edges"], np.int32)
         d.n_surf_verts = len(s["surf_verts"]); d.surf_verts = arr(s["surf_verts"], np.int32)
         d.n_planes = len(s["planes"]); d.planes = arr(s["planes"], np.float64)
+        if len(s.get("embed_verts", ())):
+            d.n_embedded = len(s["embed_verts"]); d.embed_verts = arr(s["embed_verts"], np.int32)
+            d.embed_cage = arr(s["embed_cage"], np.int32); d.embed_w = arr(s["embed_w"], np.float64)
         d.cloth_model = int(s.get("cloth_model", 0))
         if d.cloth_model:
             d.tri_shear = arr(s["tri_shear"], np.float64)
@@ -510,3 +514,15 @@ class System:
         out = np.zeros(8)
         self._check(lib().yasps_pcg_phase_ms(self.h, out.ctypes.data_as(_PD)))
         return dict(zip(PCG_PHASES, out.tolist()))
+
+    def pcg_block_busy(self):
+        """Per-block own-node + upper-block time of the PCG kernel (us per
+        iteration) and the SM of each block, over the launches profiled since
+        profile_enable(True)."""
+        n = ctypes.c_int()
+        self._check(lib().yasps_pcg_block_busy(self.h, 0, ctypes.byref(n), None, None))
+        us = np.zeros(max(n.value, 1))
+        sm = np.zeros(max(n.value, 1), np.int32)
+        self._check(lib().yasps_pcg_block_busy(self.h, n.value, ctypes.byref(n), us.ctypes.data_as(_PD),
+                                               sm.ctypes.data_as(_PI)))
+        return us[:n.value], sm[:n.value]

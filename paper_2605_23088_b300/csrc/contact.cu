@@ -328,6 +328,8 @@ struct topo {
   const int *vnode, *vbody, *stri, *sedge, *svert;
   int* status;
   const int* vscene;  // scene of each vertex in a batch, else null: pairs never cross scenes
+  const int* enode;   // [ne][8] cage nodes of embedded vertices
+  const double* ew;   // [ne][8] their weights
 };
 __device__ __forceinline__ bool pt_excluded(const topo& T, int v, int t0, int t1, int t2) {
   if (v == t0 || v == t1 || v == t2) return true;
@@ -582,35 +584,45 @@ __global__ void k_pg_query(int total, int nsv, int npl, topo T, const double* __
 
 // ---------------------------------------------------------------- pair node sets
 // Nodes and weights of a vertex through its UNION branch (App. A index rules):
-// free -> 1 node (w = 1); affine -> 4 nodes (t, A1, A2, A3; w = 1, r1, r2, r3);
-// fixed -> none.
+// The UNION map of a vertex: the nodes its position depends on and the
+// weights (its Jacobian is w_k I3 per node).  Free -> 1 node (w = 1); affine
+// -> 4 nodes (t, A1, A2, A3; w = 1, r1, r2, r3); cage-embedded -> the 8 nodes
+// of its cage cell (trilinear weights); fixed -> none.
+constexpr int kMaxVertNodes = 8;
+constexpr int kMaxPairNodes = 4 * kMaxVertNodes;  // before merging
 struct vmapd {
   int n;
-  int node[4];
-  double w[4];
+  int node[kMaxVertNodes];
+  double w[kMaxVertNodes];
 };
-__device__ __forceinline__ vmapd vertex_map(int v, const int* vnode, const int* vbody, const double* vr) {
+__device__ __forceinline__ vmapd vertex_map(int v, const topo& T, const double* vr) {
   vmapd m;
-  const int n = vnode[v];
+  const int n = T.vnode[v];
   if (n < 0) { m.n = 0; return m; }
-  if (vbody[v] < 0) { m.n = 1; m.node[0] = n; m.w[0] = 1.0; return m; }
+  const int b = T.vbody[v];
+  if (b == -1) { m.n = 1; m.node[0] = n; m.w[0] = 1.0; return m; }
+  if (b <= -2) {
+    const int e = -2 - b;
+    m.n = 8;
+    for (int k = 0; k < 8; ++k) { m.node[k] = T.enode[8 * e + k]; m.w[k] = T.ew[8 * e + k]; }
+    return m;
+  }
   m.n = 4;
   for (int k = 0; k < 4; ++k) m.node[k] = n + k;
   m.w[0] = 1.0; m.w[1] = vr[3 * v]; m.w[2] = vr[3 * v + 1]; m.w[3] = vr[3 * v + 2];
   return m;
 }
 
-// sorted unique node list of up to 4 vertices (<= 16 before merging)
+// sorted unique node list of up to 4 vertices (<= 32 before merging)
 struct nodeset {
   int m;
-  int node[16];
+  int node[kMaxPairNodes];
 };
-__device__ __forceinline__ nodeset pair_nodes(const int* ids, int k, const int* vnode, const int* vbody,
-                                              const double* vr) {
+__device__ __forceinline__ nodeset pair_nodes(const int* ids, int k, const topo& T, const double* vr) {
   nodeset S;
   S.m = 0;
   for (int a = 0; a < k; ++a) {
-    const vmapd vm = vertex_map(ids[a], vnode, vbody, vr);
+    const vmapd vm = vertex_map(ids[a], T, vr);
     for (int q = 0; q < vm.n; ++q) {
       const int nd = vm.node[q];
       int pos = 0;
@@ -655,7 +667,7 @@ __global__ void k_pair_nkeys(int npt, int nee, int npg, const int* __restrict__ 
   const int li = p - (kind == 0 ? 0 : (kind == 1 ? npt : npt + nee));
   int ids[4], k;
   pair_vertices(kind, li, kind == 0 ? pt : (kind == 1 ? ee : pg), T, ids, &k);
-  const nodeset S = pair_nodes(ids, k, T.vnode, T.vbody, vr);
+  const nodeset S = pair_nodes(ids, k, T, vr);
   nk[p] = S.m * (S.m - 1) / 2;
 }
 __global__ void k_pair_keys(int npt, int nee, int npg, const int* __restrict__ pt, const int* __restrict__ ee,
@@ -667,7 +679,7 @@ __global__ void k_pair_keys(int npt, int nee, int npg, const int* __restrict__ p
   const int li = p - (kind == 0 ? 0 : (kind == 1 ? npt : npt + nee));
   int ids[4], k;
   pair_vertices(kind, li, kind == 0 ? pt : (kind == 1 ? ee : pg), T, ids, &k);
-  const nodeset S = pair_nodes(ids, k, T.vnode, T.vbody, vr);
+  const nodeset S = pair_nodes(ids, k, T, vr);
   int o = koff[p];
   for (int u = 0; u < S.m; ++u)
     for (int w = u + 1; w < S.m; ++w) {
@@ -712,8 +724,8 @@ struct bar_ws {
   T V[81];         // Jacobi rotations
   T Hy[144];       // Q^T Project(K) Q (n3 x n3)
   T cs[5], sn[5];
-  double W[4][16];
-  int node[16];
+  double W[4][kMaxPairNodes];
+  int node[kMaxPairNodes];
   int m;
 };
 
@@ -1014,12 +1026,12 @@ __global__ void __launch_bounds__(128) k_barrier_pair(int npairs, int npt, const
   // merged node set and the UNION weights of the classified vertices (integer
   // work and loads; lane 0)
   if (lane == 0) {
-    const nodeset S = pair_nodes(ids, kv, Tp.vnode, Tp.vbody, vr);
+    const nodeset S = pair_nodes(ids, kv, Tp, vr);
     w.m = S.m;
     for (int u = 0; u < S.m; ++u) w.node[u] = S.node[u];
     for (int q = 0; q < nloc; ++q) {
       for (int u = 0; u < S.m; ++u) w.W[q][u] = 0.0;
-      const vmapd vm = vertex_map(ids[loc[q]], Tp.vnode, Tp.vbody, vr);
+      const vmapd vm = vertex_map(ids[loc[q]], Tp, vr);
       for (int a = 0; a < vm.n; ++a) {
         int u = 0;
         while (S.node[u] != vm.node[a]) ++u;
@@ -1154,7 +1166,13 @@ __global__ void k_barrier_pg(int npg, int pair_base, const int* __restrict__ pg,
   const double nv[3] = {pl[0], pl[1], pl[2]};
   const double lam = kappa * (4.0 * d * d * bd.d2b + 2.0 * bd.db);
   const double hc = (project && lam < 0.0) ? 0.0 : lam;
-  const vmapd vm = vertex_map(v, Tp.vnode, Tp.vbody, vr);
+  vmapd vm = vertex_map(v, Tp, vr);
+  // the pair's dynamic keys follow the sorted node order (a cage's nodes need not be sorted)
+  for (int a = 1; a < vm.n; ++a)
+    for (int b = a; b > 0 && vm.node[b - 1] > vm.node[b]; --b) {
+      const int tn = vm.node[b]; vm.node[b] = vm.node[b - 1]; vm.node[b - 1] = tn;
+      const double tw = vm.w[b]; vm.w[b] = vm.w[b - 1]; vm.w[b - 1] = tw;
+    }
   for (int a = 0; a < vm.n; ++a)
     for (int i = 0; i < 3; ++i) atomicAdd(&g[3 * vm.node[a] + i], vm.w[a] * kappa * bd.db * 2.0 * d * nv[i]);
   const int kbase = koff[pair_base + p];
@@ -1476,8 +1494,9 @@ __global__ void k_compact_cand(int n, const int* __restrict__ cand, const int* _
 
 // ======================================================================== host
 topo make_topo(yasps_system* s) {
-  return topo{as<int>(s->vnode), as<int>(s->vbody), as<int>(s->stri), as<int>(s->sedge), as<int>(s->svert),
-              as<int>(s->status), s->nscene > 1 ? as<int>(s->vscene) : nullptr};
+  return topo{as<int>(s->vnode),  as<int>(s->vbody),  as<int>(s->stri),
+              as<int>(s->sedge),  as<int>(s->svert),  as<int>(s->status),
+              s->nscene > 1 ? as<int>(s->vscene) : nullptr, as<int>(s->emb_node), as<double>(s->emb_w)};
 }
 
 // Build a grid on boxes (blo, bhi) of n primitives.  Buffers: ws[3] start,

@@ -117,7 +117,7 @@ __global__ void k_nodes_of(int n, int k, const int* __restrict__ ev, const int* 
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= (long long)n * k) return;
   const int v = ev[i];
-  if (vbody[v] >= 0) dev_flag(status, DEV_BADINDEX);  // elastic elements act on free / fixed vertices
+  if (vbody[v] != -1) dev_flag(status, DEV_BADINDEX);  // elastic elements act on free / fixed vertices
   en[i] = vnode[v];
 }
 
@@ -125,7 +125,7 @@ __global__ void k_free_nodemass(int nv, const int* __restrict__ vnode, const int
                                 const double* __restrict__ vmass, double* __restrict__ nodemass) {
   const int v = blockIdx.x * blockDim.x + threadIdx.x;
   if (v >= nv) return;
-  if (vbody[v] < 0 && vnode[v] >= 0) nodemass[vnode[v]] = vmass[v];
+  if (vbody[v] == -1 && vnode[v] >= 0) nodemass[vnode[v]] = vmass[v];
 }
 
 // ---------------------------------------------------------------- static sparsity keys
@@ -163,13 +163,21 @@ __global__ void k_body_keys(int nb, int nfree, int nbits, int id_base, uint64_t*
 // for fixed vertices.  Explicitly rounded, in a fixed order, so that positions
 // agree bit-for-bit with a plain evaluation of the same sum.
 __global__ void k_positions(int nv, const int* __restrict__ vnode, const int* __restrict__ vbody,
-                            const double* __restrict__ vr, const double* __restrict__ xfix, const double* __restrict__ x,
-                            double* __restrict__ P) {
+                            const double* __restrict__ vr, const int* __restrict__ enode,
+                            const double* __restrict__ ew, const double* __restrict__ xfix,
+                            const double* __restrict__ x, double* __restrict__ P) {
   const int v = blockIdx.x * blockDim.x + threadIdx.x;
   if (v >= nv) return;
   const int n = vnode[v];
   if (n < 0) {
     for (int c = 0; c < 3; ++c) P[3 * v + c] = xfix[3 * v + c];
+  } else if (vbody[v] <= -2) {  // cage-embedded: sum_k w_k x(cage node k), in order
+    const int e = -2 - vbody[v];
+    for (int c = 0; c < 3; ++c) {
+      double p = 0.0;
+      for (int k = 0; k < 8; ++k) p = __dadd_rn(p, __dmul_rn(ew[8 * e + k], x[3 * enode[8 * e + k] + c]));
+      P[3 * v + c] = p;
+    }
   } else if (vbody[v] < 0) {
     for (int c = 0; c < 3; ++c) P[3 * v + c] = x[3 * n + c];
   } else {
@@ -1082,7 +1090,8 @@ yasps_status static_sparsity(yasps_system* s) {
 yasps_status launch_positions(yasps_system* s, const double* x, double* P) {
   if (s->nv == 0) return YASPS_OK;
   k_positions<<<blocks_for(s->nv, 256), 256, 0, s->stream>>>(s->nv, as<int>(s->vnode), as<int>(s->vbody),
-                                                            as<double>(s->vr), as<double>(s->xfix), x, P);
+                                                             as<double>(s->vr), as<int>(s->emb_node),
+                                                             as<double>(s->emb_w), as<double>(s->xfix), x, P);
   LAUNCH_CHECK(s, "k_positions");
   return YASPS_OK;
 }

@@ -58,7 +58,10 @@ struct yasps_system {
 
   // scene, device
   gbuf vnode;     // int [nv] free: node; body: first node of its body; fixed: -1
-  gbuf vbody;     // int [nv]
+  gbuf vbody;     // int [nv] -1 free, >= 0 affine body, -2 - e cage-embedded (embedding row e)
+  int ne = 0;     // cage-embedded vertices
+  gbuf emb_node;  // int [ne][8] nodes of an embedded vertex's cage cell
+  gbuf emb_w;     // double [ne][8] its trilinear weights
   gbuf vr;        // double [nv][3] body-relative rest position (body vertices)
   gbuf vmass;     // double [nv]
   gbuf rest;      // double [nv][3]
@@ -128,6 +131,9 @@ struct yasps_system {
   std::vector<cudaEvent_t> prof_pool;
   yasps_stage_stats prof_acc[YASPS_NUM_STAGES] = {};
   double pcg_phase_ms[8] = {};  // yasps_pcg_phase_ms
+  std::vector<double> pcg_busy_ns;  // yasps_pcg_block_busy: per-block busy ns, summed
+  std::vector<int> pcg_busy_sm;     // SM of each block in the last profiled launch
+  long long pcg_busy_iters = 0;
 
   // Newton records of the last yasps_step (yasps_newton_trace)
   std::vector<yasps_newton_record> trace;

@@ -60,7 +60,7 @@ struct pcg_dev {
 struct pcg_bar {
   unsigned count;
   int abort;
-  int pad[2];
+  unsigned pool[2];  // claimed shared tiles of the H d' phase, iteration parity
   double sum[4];
 };
 
@@ -233,11 +233,6 @@ __device__ V block_sum_v(V v) {
   __syncthreads();
   return r;
 }
-__device__ double sum_partials(const double* part, int n) {
-  double v = 0.0;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) v += part[i];
-  return block_sum(v);
-}
 
 // z = M^-1 r on free nodes (3x3) and bodies (12x12); v_i = z_i, returns r_i . z_i partial
 template <typename T, typename V>
@@ -369,8 +364,9 @@ __device__ __forceinline__ bool grid_reduce(pcg_bar* bar, unsigned& k, P partial
 
 // ---- shared-memory staging of the upper blocks (bulk async copies)
 //
-// Each block owns an even, 4-aligned share of the static upper blocks and a
-// chunk of the dynamic ones, walked in tiles of two blocks per thread.  A
+// Each block owns an even, 4-aligned share of the first 80% of the upper
+// blocks (static, then dynamic; share_cut) and then claims tiles of the rest
+// from a shared pool; tiles hold BPT blocks per thread.  A
 // tile's values, rows and columns are contiguous, so thread 0 moves them into
 // shared memory with three cp.async.bulk copies completing on an mbarrier,
 // double-buffered: the next tile travels while the current one is multiplied,
@@ -419,22 +415,45 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* m, unsigned parity, 
 
 // this block's share of the upper blocks: static [s0, s1), dynamic [e0, e1)
 struct spmv_share {
-  int s0, s1, e0, e1, ts, tt;  // ts static tiles, tt tiles in all
+  int s0, s1, e0, e1, ts, tt;  // own tiles: ts in the static part, tt in all
+  int ps, pd, pts, ptt;        // shared pool: dynamic [pd, n_d) in pts tiles, then static [ps, n_s); ptt in all
 };
+// Block b's upper blocks: an equal share of the static blocks followed by the
+// dynamic ones (one sequence of n_s + n_d), cut at multiples of 4 within each
+// array so that every tile starts 16-byte aligned.  Only the block whose share
+// straddles the end of the static part gets tiles of both arrays.
+__device__ __forceinline__ void share_cut(long long n_s, long long n_d, long long b, long long G, long long& cs,
+                                          long long& cd) {
+  if (b >= G) { cs = n_s; cd = n_d; return; }
+  const long long v = b * (n_s + n_d) / G;
+  cs = (v < n_s ? v : n_s) & ~3LL;
+  cd = (v > n_s ? v - n_s : 0) & ~3LL;
+}
+// The blocks of a grid do not finish equal shares at the same time (blocks
+// sharing an SM are not scheduled evenly, and contact blocks gather from
+// farther away), so the last kPoolPct percent of the upper blocks form a pool
+// of tiles that the blocks claim from a counter once their own share is done.
+// Pool tiles are full tiles (smaller ones leave lanes idle while costing a
+// tile's latency), the dynamic ones first (they take longest).
+constexpr int kPoolPct = 20;
 template <typename T, typename V>
 __device__ __forceinline__ spmv_share share_of(const pcg_args<T, V>& a, int NT) {
   const long long G = gridDim.x, b = blockIdx.x;
+  const long long n_s = a.n_s, n_d = a.n_d, N = n_s + n_d;
+  const long long vp = N - N * kPoolPct / 100;  // the pool starts at this index of the sequence
   spmv_share o;
-  o.s0 = (int)((b * a.n_s / G) & ~3LL);
-  o.s1 = (b + 1 == G) ? a.n_s : (int)(((b + 1) * a.n_s / G) & ~3LL);
-  // dynamic blocks in 4-aligned chunks of at least 512, from the last block down
-  long long dc = (a.n_d + G - 1) / G;
-  dc = dc < 512 ? 512 : ((dc + 3) & ~3LL);
-  const long long c = G - 1 - b;
-  o.e0 = (int)(c * dc < a.n_d ? c * dc : a.n_d);
-  o.e1 = (int)((c + 1) * dc < a.n_d ? (c + 1) * dc : a.n_d);
+  const long long ps = vp < n_s ? (vp & ~3LL) : n_s;
+  const long long pd = vp < n_s ? 0 : ((vp - n_s) & ~3LL);
+  long long s0, d0, s1, d1;
+  share_cut(ps, pd, b, G, s0, d0);
+  share_cut(ps, pd, b + 1, G, s1, d1);
+  o.s0 = (int)s0; o.s1 = (int)s1;
+  o.e0 = (int)d0; o.e1 = (int)d1;
   o.ts = (o.s1 - o.s0 + NT - 1) / NT;
   o.tt = o.ts + (o.e1 - o.e0 + NT - 1) / NT;
+  o.ps = (int)ps; o.pd = (int)pd;
+  o.pts = (int)((n_d - pd + NT - 1) / NT);  // dynamic pool tiles (claimed first)
+  o.ptt = o.pts + (int)((n_s - ps + NT - 1) / NT);
   return o;
 }
 template <typename T, typename V>
@@ -443,6 +462,21 @@ struct tile_src {
   const int *row, *col;
   int base, cnt;
 };
+// tile t of the shared pool (t < sh.ptt): dynamic tiles, then static ones
+template <typename T, typename V>
+__device__ __forceinline__ tile_src<T, V> pool_tile(const pcg_args<T, V>& a, const spmv_share& sh, int t, int NT) {
+  tile_src<T, V> o;
+  if (t < sh.pts) {
+    o.vals = a.val_d; o.row = a.row_d; o.col = a.col_d;
+    o.base = sh.pd + t * NT;
+    o.cnt = min(NT, a.n_d - o.base);
+  } else {
+    o.vals = a.val_s; o.row = a.row_s; o.col = a.col_s;
+    o.base = sh.ps + (t - sh.pts) * NT;
+    o.cnt = min(NT, a.n_s - o.base);
+  }
+  return o;
+}
 template <typename T, typename V>
 __device__ __forceinline__ tile_src<T, V> tile_of(const pcg_args<T, V>& a, const spmv_share& sh, int j, int NT) {
   tile_src<T, V> o;
@@ -743,6 +777,7 @@ __global__ void __launch_bounds__(CFG::NTHR, CFG::MINB) k_pcg_persistent(pcg_arg
   // 2 wait + d^T H d, 3 update, 4 wait + r^T z
   __shared__ unsigned long long tph[5];
   __shared__ int sh_active;
+  __shared__ int s_tcnt[2];  // blocks in the tile requested into each buffer (0: none)
   unsigned long long tlast = 0, tbusy = 0, tbusy0 = 0;
   if (threadIdx.x < 5) tph[threadIdx.x] = 0;
   if constexpr (BATCH)
@@ -866,11 +901,42 @@ __global__ void __launch_bounds__(CFG::NTHR, CFG::MINB) k_pcg_persistent(pcg_arg
     if (clock0) tlast = global_ns();
     if (a.bt && threadIdx.x == 0) tbusy0 = global_ns();
     // the first two tiles travel while the block does its own nodes
-    if (threadIdx.x == 0)
-      for (int j = 0; j < 2 && j < sh.tt; ++j) {
-        issue_tile<L>(tile_of(a, sh, j, L::NT), smem + j * L::BUF, &mbar[j]);
-        inflight |= 1u << j;
+    unsigned* pool_ctr = &a.bar->pool[it & 1];
+    int nissued = 0, pend = -1;
+    bool pool_out = false;
+    // thread 0: request the block's next tile into buffer b (its own tiles
+    // first, then claims from the pool; the claim for the next pool tile is
+    // made one request ahead, so its round trip overlaps a tile's work)
+    auto issue_next = [&](int b) {
+      tile_src<T, V> src;
+      bool have = false;
+      if (nissued < sh.tt) {
+        src = tile_of(a, sh, nissued, L::NT);
+        have = true;
+      } else if (!pool_out) {
+        const int t = pend >= 0 ? pend : (int)atomicAdd(pool_ctr, 1u);
+        pend = -1;
+        if (t < sh.ptt) {
+          src = pool_tile(a, sh, t, L::NT);
+          have = true;
+          pend = (int)atomicAdd(pool_ctr, 1u);
+        } else {
+          pool_out = true;
+        }
       }
+      ++nissued;
+      if (have) {
+        issue_tile<L>(src, smem + b * L::BUF, &mbar[b]);
+        inflight |= 1u << b;
+        s_tcnt[b] = src.cnt;
+      } else {
+        s_tcnt[b] = 0;
+      }
+    };
+    if (threadIdx.x == 0) {
+      issue_next(0);
+      issue_next(1);
+    }
     acc = 0;
     wacc wa;
     if constexpr (!BATCH) {
@@ -892,10 +958,13 @@ __global__ void __launch_bounds__(CFG::NTHR, CFG::MINB) k_pcg_persistent(pcg_arg
       }
     }
     if (clock0) { const unsigned long long t = global_ns(); tph[0] += t - tlast; tlast = t; }
-    // upper blocks, tile by tile from shared memory
+    // upper blocks, tile by tile from shared memory, until a buffer gets none
     bool ok = true;
-    for (int j = 0; j < sh.tt; ++j) {
+    __syncthreads();  // s_tcnt of the first two tiles
+    for (int j = 0;; ++j) {
       const int b = j & 1;
+      const int cnt = s_tcnt[b];
+      if (cnt == 0) break;
       // a wait that gives up leaves the buffer's copy marked in flight (and
       // its parity unchanged) so that the drain below still waits for it
       if (mbar_wait_bounded(&mbar[b], (parity >> b) & 1u, a.spin_limit >> 3)) {
@@ -906,7 +975,6 @@ __global__ void __launch_bounds__(CFG::NTHR, CFG::MINB) k_pcg_persistent(pcg_arg
       }
       if (__syncthreads_or(!ok)) { ok = false; break; }
       const unsigned char* buf = smem + b * L::BUF;
-      const int cnt = tile_of(a, sh, j, L::NT).cnt;
       // BPT blocks per thread (k, k + NTHR, ...; each warp on 32 consecutive
       // blocks): all gathers are in flight before any is used
       const int* rows = reinterpret_cast<const int*>(buf + L::VB);
@@ -936,10 +1004,7 @@ __global__ void __launch_bounds__(CFG::NTHR, CFG::MINB) k_pcg_persistent(pcg_arg
         else acc += pu;
       }
       __syncthreads();  // every thread is done with buffer b
-      if (threadIdx.x == 0 && j + 2 < sh.tt) {
-        issue_tile<L>(tile_of(a, sh, j + 2, L::NT), smem + b * L::BUF, &mbar[b]);
-        inflight |= 1u << b;
-      }
+      if (threadIdx.x == 0) issue_next(b);
     }
     if (!ok) {
       if (threadIdx.x == 0) atomicExch(&a.bar->abort, 1);
@@ -965,6 +1030,9 @@ __global__ void __launch_bounds__(CFG::NTHR, CFG::MINB) k_pcg_persistent(pcg_arg
       break;
     }
     after_barrier(kbar - 1);
+    // the pool counter of the previous iteration is dead (its claims preceded
+    // the last barrier): clear it for the next one
+    if (blockIdx.x == 0 && threadIdx.x == 0) a.bar->pool[(it + 1) & 1] = 0u;
     if (clock0) { const unsigned long long t = global_ns(); tph[2] += t - tlast; tlast = t; }
     V alpha = 0;
     if constexpr (!BATCH) {
@@ -1066,7 +1134,12 @@ __global__ void __launch_bounds__(CFG::NTHR, CFG::MINB) k_pcg_persistent(pcg_arg
     for (int b = 0; b < 2; ++b)
       if ((inflight >> b) & 1u) mbar_wait_bounded(&mbar[b], (parity >> b) & 1u, kDrainPolls);
   __syncthreads();
-  if (a.bt && threadIdx.x == 0) a.bt[blockIdx.x] = tbusy;
+  if (a.bt && threadIdx.x == 0) {
+    unsigned smid;
+    asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
+    a.bt[blockIdx.x] = tbusy;
+    a.bt[gridDim.x + blockIdx.x] = smid;
+  }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     a.sc->rz = rz;
     a.sc->rz0 = rz0;
@@ -1239,7 +1312,10 @@ yasps_status pcg_launch_cfg(yasps_system* s, const double* rhs, double* p, doubl
   RC((pcg_grid<T, V, BATCH, CFG>(s, &G)));
   const int ns = s->nscene;
   // scalars, barrier, and for batches: ring [8][ns], srz0, siters, sflag
-  const size_t scal_bytes = 256 + (BATCH ? (size_t)ns * (8 * 8 + 8 + 4 + 4) + 64 : 0);
+  // pcg_dev (128 B), the barrier (cache-line aligned), then for batches the ring
+  static_assert(sizeof(pcg_dev) <= 128, "pcg_dev exceeds its slot");
+  constexpr size_t kHead = 128 + ((sizeof(pcg_bar) + 127) & ~(size_t)127);
+  const size_t scal_bytes = kHead + (BATCH ? (size_t)ns * (8 * 8 + 8 + 4 + 4) + 64 : 0);
   ENSURE(s, s->scal, scal_bytes);
   char* base = static_cast<char*>(s->scal.p);
   pcg_dev* sc = reinterpret_cast<pcg_dev*>(base);
@@ -1283,14 +1359,14 @@ yasps_status pcg_launch_cfg(yasps_system* s, const double* rhs, double* p, doubl
   a.rscale = rscale;
   a.bt = nullptr;
   if (s->prof_on) {
-    ENSURE(s, s->pcg_bt, sizeof(unsigned long long) * ((size_t)G + 1));
+    ENSURE(s, s->pcg_bt, sizeof(unsigned long long) * (2 * (size_t)G + 1));
     a.bt = as<unsigned long long>(s->pcg_bt);
   }
   a.unmet = s->wait_unmet ? 1u : 0u;
   s->wait_unmet = false;
   a.nscene = ns;
   a.node_scene = BATCH ? as<int>(s->node_scene) : nullptr;
-  a.ring = BATCH ? reinterpret_cast<double*>(base + 256) : nullptr;
+  a.ring = BATCH ? reinterpret_cast<double*>(base + kHead) : nullptr;
   a.srz0 = BATCH ? a.ring + 8 * (size_t)ns : nullptr;
   a.siters = BATCH ? reinterpret_cast<int*>(a.srz0 + ns) : nullptr;
   a.sflag = BATCH ? a.siters + ns : nullptr;
@@ -1326,14 +1402,22 @@ yasps_status pcg_launch_cfg(yasps_system* s, const double* rhs, double* p, doubl
     for (int k = 0; k < 5; ++k) s->pcg_phase_ms[k] += h.t_ns[k] * 1e-6;
     sp.bytes += spmv_bytes * h.iters;
     // load balance of the H d' phase: mean and max over the blocks of their busy time
-    std::vector<unsigned long long> bt(G);
-    CK(s, cudaMemcpyAsync(bt.data(), a.bt, sizeof(unsigned long long) * G, cudaMemcpyDeviceToHost, s->stream));
+    std::vector<unsigned long long> bt(2 * (size_t)G);
+    CK(s, cudaMemcpyAsync(bt.data(), a.bt, sizeof(unsigned long long) * 2 * G, cudaMemcpyDeviceToHost, s->stream));
     CK(s, cudaStreamSynchronize(s->stream));
     double mean = 0.0, mx = 0.0;
+    if ((int)s->pcg_busy_ns.size() != G) {
+      s->pcg_busy_ns.assign(G, 0.0);
+      s->pcg_busy_iters = 0;
+    }
+    s->pcg_busy_sm.resize(G);
     for (int b = 0; b < G; ++b) {
       mean += (double)bt[b];
       mx = std::max(mx, (double)bt[b]);
+      s->pcg_busy_ns[b] += (double)bt[b];
+      s->pcg_busy_sm[b] = (int)bt[G + b];
     }
+    s->pcg_busy_iters += h.iters;
     s->pcg_phase_ms[5] += mean / G * 1e-6;
     s->pcg_phase_ms[6] += mx * 1e-6;
   }

@@ -59,7 +59,7 @@ static yasps_status upload(yasps_system* s, gbuf& b, const T* host, size_t count
 }
 
 static void all_bufs(yasps_system* s, std::vector<gbuf*>& v) {
-  gbuf* one[] = {&s->vnode, &s->vbody, &s->vr, &s->vmass, &s->rest, &s->xfix, &s->fixed, &s->fixvel, &s->nodemass,
+  gbuf* one[] = {&s->vnode, &s->vbody, &s->vr, &s->emb_node, &s->emb_w, &s->vmass, &s->rest, &s->xfix, &s->fixed, &s->fixvel, &s->nodemass,
                  &s->tet_v, &s->tet_n, &s->tet_rest, &s->tet_E, &s->tet_nu, &s->vscene, &s->node_scene, &s->scene_buf, &s->tet_slot, &s->tri_v, &s->tri_n, &s->tri_rest, &s->tri_slot,
                  &s->hinge_v, &s->hinge_n, &s->hinge_rest, &s->hinge_slot, &s->body_kv, &s->body_slot, &s->stri,
                  &s->sedge, &s->svert, &s->planes, &s->Hs.row_ptr, &s->Hs.col, &s->Hs.row, &s->Hs.vals,
@@ -118,6 +118,22 @@ yasps_status yasps_profile_enable(yasps_system* s, int enable) {
   if (enable) {
     for (auto& a : s->prof_acc) a = yasps_stage_stats{0, 0.0, 0.0};
     for (auto& t : s->pcg_phase_ms) t = 0.0;
+    s->pcg_busy_ns.clear();
+    s->pcg_busy_sm.clear();
+    s->pcg_busy_iters = 0;
+  }
+  return YASPS_OK;
+}
+
+yasps_status yasps_pcg_block_busy(const yasps_system* s, int capacity, int* n_blocks, double* us_per_iter,
+                                  int* sm_ids) {
+  if (!s || !n_blocks || capacity < 0) return YASPS_E_INVAL;
+  const int G = (int)s->pcg_busy_ns.size();
+  *n_blocks = G;
+  const double it = s->pcg_busy_iters > 0 ? (double)s->pcg_busy_iters : 1.0;
+  for (int b = 0; b < G && b < capacity; ++b) {
+    if (us_per_iter) us_per_iter[b] = s->pcg_busy_ns[b] * 1e-3 / it;
+    if (sm_ids) sm_ids[b] = s->pcg_busy_sm[b];
   }
   return YASPS_OK;
 }
@@ -185,7 +201,22 @@ static yasps_status build_impl(yasps_system* s, const yasps_scene_desc* d) {
   for (int i = 1; i < d->n_surf_verts; ++i)
     if (d->surf_verts[i] <= d->surf_verts[i - 1]) SYS_FAIL(s, YASPS_E_INVAL, "surf_verts must be strictly increasing");
   for (int v = 0; v < nv; ++v)
-    if (d->vert_body[v] < -1 || d->vert_body[v] >= d->n_bodies) SYS_FAIL(s, YASPS_E_INVAL, "vert_body out of range");
+    if (d->vert_body[v] < -2 || d->vert_body[v] >= d->n_bodies) SYS_FAIL(s, YASPS_E_INVAL, "vert_body out of range");
+  // cage-embedded vertices: each listed once, its 8 cage vertices free
+  const int ne = d->n_embedded > 0 ? d->n_embedded : 0;
+  std::vector<int> emb_row(nv, -1);
+  if (ne > 0 && (!d->embed_verts || !d->embed_cage || !d->embed_w))
+    SYS_FAIL(s, YASPS_E_INVAL, "embed_verts / embed_cage / embed_w missing");
+  if (bad_idx(d->embed_verts, ne, nv) || bad_idx(d->embed_cage, 8LL * ne, nv))
+    SYS_FAIL(s, YASPS_E_INVAL, "embedding index out of range");
+  for (int e = 0; e < ne; ++e) {
+    const int v = d->embed_verts[e];
+    if (e > 0 && v <= d->embed_verts[e - 1]) SYS_FAIL(s, YASPS_E_INVAL, "embed_verts must be strictly increasing");
+    if (d->vert_body[v] != -2) SYS_FAIL(s, YASPS_E_INVAL, "an embedded vertex must have vert_body -2");
+    emb_row[v] = e;
+  }
+  for (int v = 0; v < nv; ++v)
+    if (d->vert_body[v] == -2 && emb_row[v] < 0) SYS_FAIL(s, YASPS_E_INVAL, "vert_body -2 without an embedding");
 
   // batching: scenes contiguous in vertex order, every element inside one scene
   const int ns = (d->n_scenes > 1) ? d->n_scenes : 1;
@@ -221,14 +252,24 @@ static yasps_status build_impl(yasps_system* s, const yasps_scene_desc* d) {
   std::vector<int> isfixed(nv, 0), vnode(nv, -1);
   for (int i = 0; i < d->n_fixed; ++i) isfixed[d->fixed_verts[i]] = 1;
   for (int v = 0; v < nv; ++v)
-    if (isfixed[v] && d->vert_body[v] >= 0) SYS_FAIL(s, YASPS_E_INVAL, "a fixed vertex cannot belong to an affine body");
+    if (isfixed[v] && d->vert_body[v] != -1) SYS_FAIL(s, YASPS_E_INVAL, "a fixed vertex must be free (not in a body or a cage)");
   int nf = 0;
   for (int v = 0; v < nv; ++v)
-    if (!isfixed[v] && d->vert_body[v] < 0) vnode[v] = nf++;
+    if (!isfixed[v] && d->vert_body[v] == -1) vnode[v] = nf++;
   s->nfree = nf;
   s->nn = nf + 4 * s->nb;
   for (int v = 0; v < nv; ++v)
     if (d->vert_body[v] >= 0) vnode[v] = nf + 4 * d->vert_body[v];
+  // embedded vertices: no node of their own; the node table lists their cage's
+  std::vector<int> emb_node(8 * (size_t)ne + 8, 0);
+  for (int e = 0; e < ne; ++e)
+    for (int k = 0; k < 8; ++k) {
+      const int c = d->embed_cage[8 * e + k];
+      if (d->vert_body[c] != -1 || isfixed[c]) SYS_FAIL(s, YASPS_E_INVAL, "a cage vertex must be free and not fixed");
+      emb_node[8 * e + k] = vnode[c];
+    }
+  for (int e = 0; e < ne; ++e) vnode[d->embed_verts[e]] = emb_node[8 * e];
+  s->ne = ne;
   int nbits = 1;
   while (((1LL << nbits) - 1) < (long long)s->nn + 1) ++nbits;
   if (nbits > 31) SYS_FAIL(s, YASPS_E_INVAL, "too many nodes");
@@ -236,7 +277,7 @@ static yasps_status build_impl(yasps_system* s, const yasps_scene_desc* d) {
   if (ns > 1) {
     std::vector<int> nscene(s->nn, 0);
     for (int v = 0; v < nv; ++v) {
-      if (isfixed[v]) continue;
+      if (isfixed[v] || d->vert_body[v] == -2) continue;  // an embedded vertex's nodes are its cage's
       if (d->vert_body[v] < 0) nscene[vnode[v]] = d->vert_scene[v];
       else
         for (int k = 0; k < 4; ++k) nscene[vnode[v] + k] = d->vert_scene[v];
@@ -297,7 +338,13 @@ static yasps_status build_impl(yasps_system* s, const yasps_scene_desc* d) {
   RC(upload(s, s->rest, d->rest_pos, 3 * (size_t)nv));
   RC(upload(s, s->xfix, d->rest_pos, 3 * (size_t)nv));
   RC(upload(s, s->vnode, vnode.data(), nv));
-  RC(upload(s, s->vbody, d->vert_body, nv));
+  // device body codes: -1 free, >= 0 affine body, -2 - e embedded with embedding row e
+  std::vector<int> vb(d->vert_body, d->vert_body + nv);
+  for (int v = 0; v < nv; ++v)
+    if (emb_row[v] >= 0) vb[v] = -2 - emb_row[v];
+  RC(upload(s, s->vbody, vb.data(), nv));
+  RC(upload(s, s->emb_node, emb_node.data(), 8 * (size_t)ne));
+  RC(upload(s, s->emb_w, d->embed_w, 8 * (size_t)ne));
   RC(upload(s, s->vr, vr.data(), 3 * (size_t)nv));
   RC(upload(s, s->vmass, bvm.data(), nv));
   RC(upload(s, s->fixed, d->fixed_verts, d->n_fixed));
@@ -430,7 +477,7 @@ yasps_status yasps_initial_state(yasps_system* s, const double* vel0, double* x_
   std::vector<int> cnt(s->nb, 0);
   for (int i = 0; i < s->nv; ++i) {
     const int n = vnode[i];
-    if (n < 0) continue;
+    if (n < 0 || vbody[i] <= -2) continue;  // fixed, or embedded (its cage carries the state)
     if (vbody[i] < 0) {
       for (int c = 0; c < 3; ++c) {
         x[3 * n + c] = rest[3 * i + c];

@@ -219,7 +219,7 @@ def _empty_parts():
                 surf_tris=[], fixed=[], fixed_vel=[], body_mass=[], body_vol=[], body_kappa=[], nv=0, nb=0)
 
 
-def _add_soft(parts, verts, tets, E, nu, rho, vel=None):
+def _add_soft(parts, verts, tets, E, nu, rho, vel=None, surface=True):
     off = parts["nv"]
     nv = len(verts)
     parts["verts"].append(verts)
@@ -230,7 +230,40 @@ def _add_soft(parts, verts, tets, E, nu, rho, vel=None):
     parts["tet_E"].append(np.broadcast_to(np.asarray(E, np.float64), (nt,)).copy())
     parts["tet_nu"].append(np.full(nt, nu, np.float64))
     parts["tet_rho"].append(np.full(nt, rho, np.float64))
-    parts["surf_tris"].append(boundary_faces(tets) + off)
+    if surface:
+        parts["surf_tris"].append(boundary_faces(tets) + off)
+    parts["nv"] += nv
+    return off
+
+
+def _add_embedded_surface(parts, verts, faces, cage_off, cage_origin, cage_h, cage_dims):
+    """A surface mesh embedded in a hex cage (the cage parameterisation): every
+    vertex is tied to the 8 corners of the cage cell that encloses it by
+    trilinear weights; vert_body -2, no mass and no element of its own."""
+    nx, ny, nz = cage_dims
+    off = parts["nv"]
+    nv = len(verts)
+    parts["verts"].append(verts)
+    parts["vel"].append(np.zeros((nv, 3)))
+    parts["body"].append(np.full(nv, -2, dtype=np.int64))
+    parts["surf_tris"].append(faces + off)
+    u = (verts - np.asarray(cage_origin)) / cage_h
+    cell = np.clip(np.floor(u).astype(np.int64), 0, np.array([nx - 1, ny - 1, nz - 1]))
+    f = u - cell
+    vid = lambda i, j, k: i + (nx + 1) * (j + (ny + 1) * k)
+    cage = np.zeros((nv, 8), np.int64)
+    w = np.zeros((nv, 8))
+    q = 0
+    for dk in (0, 1):
+        for dj in (0, 1):
+            for di in (0, 1):
+                cage[:, q] = cage_off + vid(cell[:, 0] + di, cell[:, 1] + dj, cell[:, 2] + dk)
+                w[:, q] = ((f[:, 0] if di else 1 - f[:, 0]) * (f[:, 1] if dj else 1 - f[:, 1]) *
+                           (f[:, 2] if dk else 1 - f[:, 2]))
+                q += 1
+    parts.setdefault("embed_verts", []).append(np.arange(off, off + nv))
+    parts.setdefault("embed_cage", []).append(cage)
+    parts.setdefault("embed_w", []).append(w)
     parts["nv"] += nv
     return off
 
@@ -296,6 +329,9 @@ def finalize_scene(parts, name, dt, dhat, kappa, n_steps, planes, gravity=(0.0, 
     s["surf_verts"] = np.unique(st).astype(np.int32) if len(st) else np.zeros((0,), np.int32)
     s["planes"] = np.asarray(planes, np.float64).reshape(-1, 4)
     s["cloth_model"] = int(parts.get("cloth_model", 0))
+    s["embed_verts"] = _cat(parts.get("embed_verts", []), (), np.int32)
+    s["embed_cage"] = _cat(parts.get("embed_cage", []), (8,), np.int32)
+    s["embed_w"] = _cat(parts.get("embed_w", []), (8,), np.float64)
     s["dt"] = float(dt)
     s["dhat"] = float(dhat)
     s["kappa"] = float(kappa)
@@ -467,6 +503,37 @@ def bw_cloth_scene(cloth_n=101, cloth_size=1.0, layers=1, blob_h=0.01, blob_radi
             parts["fixed"].append([off + c for c in corners])
             parts["fixed_vel"].append(np.zeros((4, 3)))
     return finalize_scene(parts, "bw_cloth", dt, dhat, kappa, n_steps, planes=[[0, 1, 0, 0]])
+
+
+def caged_blob_scene(blob_h=0.01, blob_radius=0.05, cage_h=0.025, E=3.17e4, nu=0.226, rho=1000.0, lift=3e-4,
+                     with_box=True, seed=0, dt=0.01, dhat=1e-3, kappa=1e4, n_steps=150):
+    """The cage example's shape (Sec. "Caged Bunny", Table "Caged Bunny"; the
+    bunny replaced by a voxelised blob): the blob's boundary surface, embedded
+    by trilinear weights in a uniform hex cage of spacing cage_h whose cells
+    are split into 6 stable Neo-Hookean tets each (E 31.7 kPa, nu 0.226); the
+    cage vertices are free and do not collide, the embedded surface does.  The
+    surface's lowest point starts `lift` above the ground; with_box adds an
+    affine box resting `lift` above the surface's highest point."""
+    parts = _empty_parts()
+    bv, bt = blob_mesh(blob_h, blob_radius, seed)
+    faces = boundary_faces(bt)
+    used = np.unique(faces)
+    remap = -np.ones(len(bv), np.int64)
+    remap[used] = np.arange(len(used))
+    sv, sf = bv[used], remap[faces]
+    sv = sv + np.array([0.0, lift - sv[:, 1].min(), 0.0])
+    lo, hi = sv.min(0) - 1e-3, sv.max(0) + 1e-3
+    dims = np.maximum(np.ceil((hi - lo) / cage_h).astype(int), 1)
+    cv = hex_grid(dims[0], dims[1], dims[2], cage_h, lo)
+    ct = kuhn_tets(dims[0], dims[1], dims[2])
+    coff = _add_soft(parts, cv, ct, E, nu, rho, surface=False)
+    _add_embedded_surface(parts, sv, sf, coff, lo, cage_h, tuple(dims))
+    if with_box:  # an affine box resting on the surface's highest point
+        size = 0.03
+        top = sv[np.argmax(sv[:, 1])]
+        bx, bf = box_surface(size, (top[0] + 0.004, top[1] + lift + size / 2, top[2] - 0.003))
+        _add_body(parts, bx, bf, mass=1000.0 * size ** 3, vol=size ** 3, kappa=1e8)
+    return finalize_scene(parts, "caged_blob", dt, dhat, kappa, n_steps, planes=[[0, 1, 0, 0]])
 
 
 def beam_scene(nx=52, ny=8, nz=8, length=1.0, width=0.1, lift=0.02, seed=0, dt=0.01, dhat=1e-3,

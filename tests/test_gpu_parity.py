@@ -189,6 +189,26 @@ def test_spmv_and_pcg(cubes):
     assert it > 0 and rr <= 1e-12
 
 
+def test_pcg_block_busy_profile(cubes):
+    """The per-block busy times of a profiled PCG launch: one entry per block of
+    its grid, positive, each on a valid SM; nothing before profiling."""
+    s, O, G, states = cubes
+    x, v = states[-1]
+    xt = O.xtilde(x, v)
+    g_ref = O.assemble(x, xt)
+    G.detect_pairs(T(x))
+    G.eval_local(T(x), T(xt))
+    G.profile_enable(True)
+    busy0, _ = G.pcg_block_busy()
+    assert len(busy0) == 0
+    G.pcg_solve(T(g_ref), rel_tol=1e-12)
+    busy, sm = G.pcg_block_busy()
+    G.profile_enable(False)
+    nsm = torch.cuda.get_device_properties(0).multi_processor_count
+    assert len(busy) >= nsm and np.all(busy > 0)
+    assert np.all((sm >= 0) & (sm < nsm)) and len(set(sm.tolist())) == nsm
+
+
 def test_energy_parity(cubes):
     s, O, G, states = cubes
     for xs, vs in states:
