@@ -59,6 +59,17 @@ def source_sha(*files):
     return h.hexdigest()[:16]
 
 
+def alu_counts(kernel_file):
+    """Per-tet FP64 / FP32 flop counts of the tet kernel from a committed ncu
+    counter capture (profiles/snh_kernel_counts.json), if it was taken on the
+    current source; else None."""
+    p = os.path.join(ROOT, "profiles", "snh_kernel_counts.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    return d if d.get("source_sha") == source_sha(kernel_file) else None
+
+
 def traffic_rate(kernel_files):
     """DRAM bytes per second of the PCG kernel from a committed ncu capture
     (dram__bytes_read.sum + dram__bytes_write.sum over gpu__time_duration.sum of
@@ -312,6 +323,31 @@ def native(args):
             "launches": pk["count"], "iterations_per_launch": mixed["pcg"] / max(pk["count"], 1),
             "spmv_phase_gbs": spmv_gbs}
 
+    # secondary rooflines: the assembly (HBM; the local evaluation with its
+    # scatter, fused) and the tet kernel (FP64 pipe, against the live FMA probe)
+    nnzb = G.bsr_nnzb(0) + G.bsr_nnzb(1)
+    pairs_mean = sum(sum(p["pairs"]) for p in mixed_run["per"]) / max(len(mixed_run["per"]), 1)
+    es = 4  # FP32 Hessian blocks in the mixed form; positions, material, gradient FP64
+    asm_bytes = n_tets * (16 + 96 + 96) + nnzb * 9 * es + G.n_nodes * (9 * es + 24) + pairs_mean * 12
+    ev = prof["eval"]
+    asm_s = ev["ms"] * 1e-3 / max(ev["count"], 1)
+    secondary = {"assembly": {"bound": "hbm", "kernels": "local evaluation + scatter (tet, barrier, inertia)",
+                              "bytes_per_eval": asm_bytes, "eval_us": asm_s * 1e6,
+                              "achieved": asm_bytes / asm_s / 1e9 if asm_s > 0 else None, "peak": peak,
+                              "unit": "GB/s", "frac": asm_bytes / asm_s / 1e9 / peak if asm_s > 0 else None}}
+    cnt = alu_counts("paper_2605_23088_b300/csrc/elements.cu")
+    tt = prof["tet"]
+    if cnt and tt["count"] and tt["ms"] > 0:
+        t_s = tt["ms"] * 1e-3 / tt["count"]
+        f64_peak, f32_peak = yb.probe_fma_tflops(0), yb.probe_fma_tflops(1)
+        a64 = cnt["fp64_flops_per_tet"] * n_tets / t_s / 1e12
+        a32 = cnt["fp32_flops_per_tet"] * n_tets / t_s / 1e12
+        secondary["k_snh<float>"] = {"bound": "alu", "pipe": "fp64", "achieved": a64, "peak": f64_peak,
+                                     "unit": "TFLOP/s", "frac": a64 / f64_peak, "launch_us": t_s * 1e6,
+                                     "fp32_achieved": a32, "fp32_peak": f32_peak, "fp32_frac": a32 / f32_peak,
+                                     "peak_kind": "measured (FMA probe, this run)",
+                                     "flops_per_tet": [cnt["fp64_flops_per_tet"], cnt["fp32_flops_per_tet"]]}
+
     value = mixed["passes_all"] / (mixed["ms_max"] * 1e-3)
     per_step = [{"rc": p["rc"], "newton": p["newton"], "pcg": p["pcg"], "pairs_pt_ee_pg": p["pairs"],
                  "ms": round(p["ms"], 2)} for p in mixed_run["per"]]
@@ -331,6 +367,7 @@ def native(args):
                    "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
         "spmv_gbs": spmv_gbs,
         "roofline": roof,
+        "secondary_rooflines": secondary,
         "stages_ms": {k: (v_["ms"], v_["count"]) for k, v_ in prof.items()},
         "pcg_phase_us_per_iter": {k: v_ * 1e3 / max(mixed["pcg"], 1) for k, v_ in mixed_run["phases"].items()},
         "e2e": {"value": mixed["passes_all"] / (mixed["e2e_max"] * 1e-3), "unit": "Newton iterations/s",

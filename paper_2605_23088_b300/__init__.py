@@ -374,6 +374,12 @@ class System:
     def assemble(self):
         self._check(lib().yasps_assemble(self.h))
 
+    def bsr_nnzb(self, which):
+        """Number of upper blocks of the static (0) or dynamic (1) BSR part."""
+        nnzb = ctypes.c_int()
+        self._check(lib().yasps_export_bsr(self.h, ctypes.c_int(which), ctypes.byref(nnzb), None, None, None, None))
+        return nnzb.value
+
     def export_bsr(self, which):
         nnzb = ctypes.c_int()
         self._check(lib().yasps_export_bsr(self.h, ctypes.c_int(which), ctypes.byref(nnzb), None, None, None, None))
