@@ -105,15 +105,19 @@ __global__ void __launch_bounds__(256) k_spmv_upper(int nnzb, const int* __restr
     atomicAdd(&y[3 * c + 1], (V)b[1] * xr0 + (V)b[4] * xr1 + (V)b[7] * xr2);
     atomicAdd(&y[3 * c + 2], (V)b[2] * xr0 + (V)b[5] * xr1 + (V)b[8] * xr2);
   }
-  // segmented suffix reduction of the U x contributions within the warp
+  // the U x contributions: FP32 by a segmented suffix reduction within the
+  // warp; FP64 by one atomic per block and component (in L2, off the FP64 pipe)
+  if constexpr (sizeof(V) == 4) {
 #pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const int ro = __shfl_down_sync(0xffffffffu, r, o);
-    const V b0 = shfl_down_v(a0, o), b1 = shfl_down_v(a1, o), b2 = shfl_down_v(a2, o);
-    if (lane + o < 32 && ro == r) { a0 += b0; a1 += b1; a2 += b2; }
+    for (int o = 1; o < 32; o <<= 1) {
+      const int ro = __shfl_down_sync(0xffffffffu, r, o);
+      const V b0 = shfl_down_v(a0, o), b1 = shfl_down_v(a1, o), b2 = shfl_down_v(a2, o);
+      if (lane + o < 32 && ro == r) { a0 += b0; a1 += b1; a2 += b2; }
+    }
+    const int rp = __shfl_up_sync(0xffffffffu, r, 1);
+    if (!(r >= 0 && (lane == 0 || rp != r))) return;
   }
-  const int rp = __shfl_up_sync(0xffffffffu, r, 1);
-  if (r >= 0 && (lane == 0 || rp != r)) {
+  if (r >= 0) {
     atomicAdd(&y[3 * r], a0);
     atomicAdd(&y[3 * r + 1], a1);
     atomicAdd(&y[3 * r + 2], a2);
@@ -559,8 +563,12 @@ __device__ __forceinline__ void q_take3(double* q, long long node, double* out) 
   }
 }
 
-// q += B d'_c into the row (segmented over the warp), q += B^T d'_r into the
-// column; returns the block's share 2 d'_r^T B d'_c of d'^T U d'
+// q += B d'_c into the row, q += B^T d'_r into the column; returns the
+// block's share 2 d'_r^T B d'_c of d'^T U d'.  FP32 reduces the rows over the
+// warp (segmented shuffle, one vector atomic per row segment); FP64 adds
+// every block's row part with atomics, which execute in L2: the segmented
+// reduction's FP64 additions (15 per block) would run on the SM's FP64 pipe,
+// which bounds FP64 SpMV on this part.
 template <typename T, typename V>
 __device__ __forceinline__ V apply_blk(int r, int c, const T* b, const gath<V>& g, V* q, int lane) {
   V a0 = 0, a1 = 0, a2 = 0, part = 0;
@@ -573,15 +581,18 @@ __device__ __forceinline__ V apply_blk(int r, int c, const T* b, const gath<V>& 
     part = (V)2 * (xr0 * a0 + xr1 * a1 + xr2 * a2);
     q_add3(q, c, (V)b[0] * xr0 + (V)b[3] * xr1 + (V)b[6] * xr2, (V)b[1] * xr0 + (V)b[4] * xr1 + (V)b[7] * xr2,
            (V)b[2] * xr0 + (V)b[5] * xr1 + (V)b[8] * xr2);
+    if constexpr (sizeof(V) == 8) q_add3(q, r, a0, a1, a2);
   }
+  if constexpr (sizeof(V) == 4) {
 #pragma unroll
-  for (int off = 1; off < 32; off <<= 1) {
-    const int ro = __shfl_down_sync(0xffffffffu, r, off);
-    const V b0 = shfl_down_v(a0, off), b1 = shfl_down_v(a1, off), b2 = shfl_down_v(a2, off);
-    if (lane + off < 32 && ro == r) { a0 += b0; a1 += b1; a2 += b2; }
+    for (int off = 1; off < 32; off <<= 1) {
+      const int ro = __shfl_down_sync(0xffffffffu, r, off);
+      const V b0 = shfl_down_v(a0, off), b1 = shfl_down_v(a1, off), b2 = shfl_down_v(a2, off);
+      if (lane + off < 32 && ro == r) { a0 += b0; a1 += b1; a2 += b2; }
+    }
+    const int rp = __shfl_up_sync(0xffffffffu, r, 1);
+    if (r >= 0 && (lane == 0 || rp != r)) q_add3(q, r, a0, a1, a2);
   }
-  const int rp = __shfl_up_sync(0xffffffffu, r, 1);
-  if (r >= 0 && (lane == 0 || rp != r)) q_add3(q, r, a0, a1, a2);
   return part;
 }
 
