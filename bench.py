@@ -253,8 +253,11 @@ def native(args):
     world, rank, local = dist_setup(args.gpus)
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
-    scene = scenes.tori_scene()
+    L = args.lattice
+    scene = scenes.tori_scene(nx=L, ny=L, nz=L)
     n_tets = len(scene["tets"])
+    workload = WORKLOAD if L == 4 else (f"{L ** 3} Neo-Hookean tori on a {L}x{L}x{L} lattice (a small case of the "
+                                        f"64-tori workload for profiling; {n_tets} tets)")
     ntol = NEWTON_VEL_TOL * scene["dt"]
     common = dict(pcg_rel_tol=PCG_TOL, newton_tol=ntol, newton_max_iter=NEWTON_CAP)
     G = yb.System(scene, precision=1, **common)
@@ -356,7 +359,7 @@ def native(args):
         "warmup": args.warmup, "ms_per_step": mixed["ms_max"] / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32-mixed (f64 positions/gradients/energies)",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n_tets": n_tets, "n_nodes": G.n_nodes,
+        "config": {"workload": workload, "n_tets": n_tets, "n_nodes": G.n_nodes,
                    "preroll_steps": preroll, "timed_steps": f"{preroll + args.warmup}..{preroll + args.warmup + args.steps - 1}",
                    "newton_tol": "||dx||_inf/dt < 1e-2 m/s", "newton_max_iter": NEWTON_CAP, "pcg_rel_tol": PCG_TOL,
                    "pairs_at_start": {"pt": npt, "ee": nee, "pg": npg}, "newton_iters": mixed["newton"],
@@ -820,6 +823,8 @@ def main():
     ap.add_argument("--batch-steps", type=int, default=2)
     ap.add_argument("--save-state", default=None, help="write the post-pre-roll state (.npz) for --load-state")
     ap.add_argument("--load-state", default=None, help="start from a state written by --save-state")
+    ap.add_argument("--lattice", type=int, default=4,
+                    help="tori per lattice edge (4: the 64-tori workload; smaller: a small case for profiling)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -422,6 +422,128 @@ __device__ __forceinline__ bool sat_apart(int kind, d3 y0, d3 y1, d3 y2, d3 y3, 
   return surely_apart(sat_lb2(kind, y0, y1, y2, y3), sh);
 }
 
+// ---- single-precision prefilters of the candidate kernels
+// The tests above run on the FP64 pipe, which bounds the candidate kernels on
+// this part.  The candidate kernels therefore first run the same two bounds
+// in FP32 on single-precision copies of the vertex arrays (one rounding per
+// component), each reduced by a bound on every rounding involved, so that the
+// FP32 value never exceeds the exact bound.  A pair the FP32 test rejects is
+// one the FP64 test rejects too; only the others take the FP64 path.
+constexpr float kU32 = 5.9604645e-8f;  // 2^-24, the FP32 unit roundoff
+
+__device__ __forceinline__ float3 ldf3(const float4* p, int i) {
+  const float4 v = p[i];
+  return make_float3(v.x, v.y, v.z);
+}
+__device__ __forceinline__ float3 f3sub(float3 a, float3 b) { return make_float3(a.x - b.x, a.y - b.y, a.z - b.z); }
+__device__ __forceinline__ float f3dot(float3 a, float3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__device__ __forceinline__ float3 f3cross(float3 a, float3 b) {
+  return make_float3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+}
+__device__ __forceinline__ float f3amax(float3 a) { return fmaxf(fabsf(a.x), fmaxf(fabsf(a.y), fabsf(a.z))); }
+__device__ __forceinline__ float f3l1(float3 a) { return fabsf(a.x) + fabsf(a.y) + fabsf(a.z); }
+
+// FP32 copy of a 3-per-vertex FP64 array, 16 bytes per vertex
+__global__ void k_f32_copy(int n, const double* __restrict__ a, float4* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = make_float4((float)a[3 * i], (float)a[3 * i + 1], (float)a[3 * i + 2], 0.0f);
+}
+
+// A lower bound of the squared distance of a pair (kind and vertex order as
+// in pair_lb2) from the FP32 copies y of its vertices, valid for the exact
+// FP64 positions: the larger of the box bound and the separating-axis bound.
+// Every copied component is within u |y| of the exact one (u = 2^-24); the
+// box gaps lose that twice and one rounding of the subtraction; a projection
+// onto an axis a (any axis gives a valid bound, so a's own rounding does not
+// matter) is off by at most |a|_1 (2u X + u A) for the differences plus
+// 3u |a|_1 A for the dot product, where X bounds the coordinates and A the
+// differences; both bounds are taken twice over.  The result never exceeds
+// the exact bound.
+__device__ __forceinline__ float lb2_f32(int kind, float3 y0, float3 y1, float3 y2, float3 y3) {
+  const float u = kU32;
+  const float X = fmaxf(fmaxf(f3amax(y0), f3amax(y1)), fmaxf(f3amax(y2), f3amax(y3)));
+  const float dl = 2.0f * u * X;
+  float alo[3], ahi[3], blo[3], bhi[3];
+  const float a0[3] = {y0.x, y0.y, y0.z}, a1v[3] = {y1.x, y1.y, y1.z}, b0v[3] = {y2.x, y2.y, y2.z},
+              b1v[3] = {y3.x, y3.y, y3.z};
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    if (kind == 0) {
+      alo[c] = ahi[c] = a0[c];
+      blo[c] = fminf(a1v[c], fminf(b0v[c], b1v[c]));
+      bhi[c] = fmaxf(a1v[c], fmaxf(b0v[c], b1v[c]));
+    } else {
+      alo[c] = fminf(a0[c], a1v[c]);
+      ahi[c] = fmaxf(a0[c], a1v[c]);
+      blo[c] = fminf(b0v[c], b1v[c]);
+      bhi[c] = fmaxf(b0v[c], b1v[c]);
+    }
+  }
+  float sb = 0.0f;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    float g = fmaxf(alo[c] - bhi[c], blo[c] - ahi[c]);
+    g = g * (1.0f - 2.0f * u) - 2.0f * dl;
+    if (g > 0.0f) sb += g * g;
+  }
+  float best = sb * (1.0f - 8.0f * u);
+  const float3 a1 = f3sub(y1, y0), b0 = f3sub(y2, y0), b1 = f3sub(y3, y0);
+  const float A = fmaxf(f3amax(a1), fmaxf(f3amax(b0), f3amax(b1)));
+  float3 ax[2];
+  if (kind == 0) {
+    ax[0] = f3cross(f3sub(b0, a1), f3sub(b1, a1));
+    ax[1] = make_float3(a1.x + b0.x + b1.x, a1.y + b0.y + b1.y, a1.z + b0.z + b1.z);
+  } else {
+    ax[0] = f3cross(a1, f3sub(b1, b0));
+    ax[1] = make_float3(b0.x + b1.x - a1.x, b0.y + b1.y - a1.y, b0.z + b1.z - a1.z);
+  }
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const float3 w = ax[k];
+    const float n2 = f3dot(w, w);
+    if (!(n2 > 1e-30f)) continue;  // keeps the products out of the subnormal range
+    const float pa1 = f3dot(w, a1), pb0 = f3dot(w, b0), pb1 = f3dot(w, b1);
+    float lo_a, hi_a, lo_b, hi_b;
+    if (kind == 0) {
+      lo_a = hi_a = 0.0f;
+      lo_b = fminf(pa1, fminf(pb0, pb1));
+      hi_b = fmaxf(pa1, fmaxf(pb0, pb1));
+    } else {
+      lo_a = fminf(0.0f, pa1);
+      hi_a = fmaxf(0.0f, pa1);
+      lo_b = fminf(pb0, pb1);
+      hi_b = fmaxf(pb0, pb1);
+    }
+    const float E = f3l1(w) * (4.0f * u * X + 8.0f * u * A);
+    const float g = fmaxf(lo_b - hi_a, lo_a - hi_b) * (1.0f - 2.0f * u) - 2.0f * E;
+    if (g > 0.0f) best = fmaxf(best, (g * g) / (n2 * (1.0f + 8.0f * u)) * (1.0f - 4.0f * u));
+  }
+  return best;
+}
+__device__ __forceinline__ float lb2_f32(int kind, const float4* pf, const int* ids) {
+  return lb2_f32(kind, ldf3(pf, ids[0]), ldf3(pf, ids[1]), ldf3(pf, ids[2]), ldf3(pf, ids[3]));
+}
+// An upper bound of max_k |dx_k - m| (m the mean of the exact dx_k) from the
+// FP32 copies d_k: the copies, the mean and the differences add at most
+// 7 u Dm per component (Dm bounds the components), taken twice over.
+__device__ __forceinline__ float motion_hi_f32(const float3* d) {
+  const float u = kU32;
+  float Dm = 0.0f;
+  float3 m = make_float3(0.0f, 0.0f, 0.0f);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    Dm = fmaxf(Dm, f3amax(d[i]));
+    m.x += 0.25f * d[i].x; m.y += 0.25f * d[i].y; m.z += 0.25f * d[i].z;
+  }
+  float mx2 = 0.0f;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const float3 c = f3sub(d[i], m);
+    mx2 = fmaxf(mx2, f3dot(c, c));
+  }
+  return sqrtf(mx2) * (1.0f + 8.0f * u) + 1.7320508f * 16.0f * u * Dm;
+}
+
 // ---------------------------------------------------------------- barrier scalar
 struct bder {
   double b, db, d2b;
@@ -437,9 +559,11 @@ __host__ __device__ __forceinline__ bder barrier_fn(double s, double sh, int for
 
 // ---------------------------------------------------------------- detection
 // mode 0: count, mode 1: write + sort segment, mode 2: accumulate kappa * b(s)
-__global__ void k_pt_query(int total, int nsv, topo T, const double* __restrict__ P, grid_dev g, boxes A, double sh, int mode, int* __restrict__ cnt,
+__global__ void k_pt_query(int total, int nsv, topo T, const double* __restrict__ P, const float4* __restrict__ Pf,
+                           grid_dev g, boxes A, double sh, int mode, int* __restrict__ cnt,
                            const int* __restrict__ off, int* __restrict__ out, double kappa, int form,
                            ksum* __restrict__ part) {
+  const float shf = (float)sh * (1.0f + 1e-6f);
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   ksum acc{0.0, 0.0};
   if (i < nsv) {
@@ -451,6 +575,8 @@ __global__ void k_pt_query(int total, int nsv, topo T, const double* __restrict_
     grid_visit(g, A, i, [&](int t) {
       const int t0 = T.stri[3 * t], t1 = T.stri[3 * t + 1], t2 = T.stri[3 * t + 2];
       if (pt_excluded(T, v, t0, t1, t2)) return;
+      const int ids[4] = {v, t0, t1, t2};
+      if (Pf && lb2_f32(0, Pf, ids) > shf) return;  // FP32 prefilter
       const d3 q0 = ld3(P, t0), q1 = ld3(P, t1), q2 = ld3(P, t2);
       if (surely_apart(pair_lb2(0, p, q0, q1, q2), sh) || sat_apart(0, p, q0, q1, q2, sh)) return;
       double s;
@@ -488,9 +614,11 @@ __global__ void k_pt_query(int total, int nsv, topo T, const double* __restrict_
   }
 }
 
-__global__ void k_ee_query(int total, int nse, topo T, const double* __restrict__ P, grid_dev g, boxes A, double sh, int mode, int* __restrict__ cnt,
+__global__ void k_ee_query(int total, int nse, topo T, const double* __restrict__ P, const float4* __restrict__ Pf,
+                           grid_dev g, boxes A, double sh, int mode, int* __restrict__ cnt,
                            const int* __restrict__ off, int* __restrict__ out, double kappa, int form,
                            ksum* __restrict__ part) {
+  const float shf = (float)sh * (1.0f + 1e-6f);
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   ksum acc{0.0, 0.0};
   if (i < nse) {
@@ -503,6 +631,8 @@ __global__ void k_ee_query(int total, int nse, topo T, const double* __restrict_
       if (j <= i) return;
       const int f0 = T.sedge[2 * j], f1 = T.sedge[2 * j + 1];
       if (ee_excluded(T, e0, e1, f0, f1)) return;
+      const int ids[4] = {e0, e1, f0, f1};
+      if (Pf && lb2_f32(1, Pf, ids) > shf) return;  // FP32 prefilter
       const d3 b0 = ld3(P, f0), b1 = ld3(P, f1);
       if (surely_apart(pair_lb2(1, a0, a1, b0, b1), sh) || sat_apart(1, a0, a1, b0, b1, sh)) return;
       double s;
@@ -1373,13 +1503,27 @@ __device__ __forceinline__ int cand_first_vertex(int kind, const int* cand, size
 
 // additive CCD over the candidate list; one atomic min per block
 __global__ void k_ccd_cand(int kind, int n, const int* __restrict__ cand, topo T, const double* __restrict__ P0,
-                           const double* __restrict__ D, double gap, int max_iter, double* __restrict__ tmin, int* status) {
+                           const double* __restrict__ D, const float4* __restrict__ P0f, const float4* __restrict__ Df,
+                           double gap, int max_iter, double* __restrict__ tmin, int* status) {
   const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   double best = 1.0;
   bool capped = false;
-  if (k < n) {
-    int ids[4];
+  bool todo = k < n;
+  int ids[4];
+  if (todo) {
     cand_vertices(kind, cand, (size_t)k, T, ids);
+    // FP32 first: the full step already holds when (1 - gap)^2 lb^2 > lp^2
+    // with the conservative bounds of the copies (a 1e-6 relative margin on
+    // top covers ACCD's own FP64 rounding of its first advance)
+    float3 df[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) df[q] = ldf3(Df, ids[q]);
+    const float mh = motion_hi_f32(df);
+    const float om = 1.0f - (float)gap;
+    const float g1f = om * om * (1.0f - 8.0f * kU32);
+    if (g1f * lb2_f32(kind, P0f, ids) > 4.0f * mh * mh * (1.0f + 1e-6f)) todo = false;
+  }
+  if (todo) {
     d3 x[4], dx[4];
     for (int q = 0; q < 4; ++q) { x[q] = ld3(P0, ids[q]); dx[q] = ld3(D, ids[q]); }
     // ACCD's first advance is (1 - gap) d0 / lp with lp its bound on the
@@ -1429,8 +1573,9 @@ __global__ void k_ccd_cand(int kind, int n, const int* __restrict__ cand, topo T
 
 // barrier energy over the candidate list at positions P (fixed grid: deterministic)
 __global__ void k_energy_cand(int kind, int n, const int* __restrict__ cand, topo T, const double* __restrict__ P,
-                              double sh, double kappa, int form, ksum* __restrict__ part,
+                              const float4* __restrict__ Pf, double sh, double kappa, int form, ksum* __restrict__ part,
                               double* __restrict__ sacc = nullptr) {
+  const float shf = (float)sh * (1.0f + 1e-6f);
   ksum acc{0.0, 0.0};
   const int lane = threadIdx.x & 31;
   const long long stride = (long long)gridDim.x * blockDim.x;
@@ -1441,12 +1586,14 @@ __global__ void k_energy_cand(int kind, int n, const int* __restrict__ cand, top
     if (k < n) {
       int ids[4];
       cand_vertices(kind, cand, (size_t)k, T, ids);
-      const d3 y0 = ld3(P, ids[0]), y1 = ld3(P, ids[1]), y2 = ld3(P, ids[2]), y3 = ld3(P, ids[3]);
-      if (!surely_apart(pair_lb2(kind, y0, y1, y2, y3), sh) && !sat_apart(kind, y0, y1, y2, y3, sh)) {
-        double s;
-        if (kind == 0) dist::pt_classify(y0, y1, y2, y3, &s);
-        else dist::ee_classify(y0, y1, y2, y3, &s);
-        if (s < sh) e = kappa * barrier_fn(s, sh, form).b;
+      if (!(Pf && lb2_f32(kind, Pf, ids) > shf)) {  // FP32 prefilter, then the FP64 tests
+        const d3 y0 = ld3(P, ids[0]), y1 = ld3(P, ids[1]), y2 = ld3(P, ids[2]), y3 = ld3(P, ids[3]);
+        if (!surely_apart(pair_lb2(kind, y0, y1, y2, y3), sh) && !sat_apart(kind, y0, y1, y2, y3, sh)) {
+          double s;
+          if (kind == 0) dist::pt_classify(y0, y1, y2, y3, &s);
+          else dist::ee_classify(y0, y1, y2, y3, &s);
+          if (s < sh) e = kappa * barrier_fn(s, sh, form).b;
+        }
       }
       if (sacc) key = T.vscene[ids[0]];
     }
@@ -1462,11 +1609,16 @@ __global__ void k_energy_cand(int kind, int n, const int* __restrict__ cand, top
 
 // active pairs among the candidates at positions P: flag + subtype
 __global__ void k_filter_cand(int kind, int n, const int* __restrict__ cand, topo T, const double* __restrict__ P,
-                              double sh, int* __restrict__ flag, int* __restrict__ sub) {
+                              const float4* __restrict__ Pf, double sh, int* __restrict__ flag, int* __restrict__ sub) {
   const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= n) return;
   int ids[4];
   cand_vertices(kind, cand, (size_t)k, T, ids);
+  if (Pf && lb2_f32(kind, Pf, ids) > (float)sh * (1.0f + 1e-6f)) {  // FP32 prefilter
+    flag[k] = 0;
+    sub[k] = 0;
+    return;
+  }
   const d3 y0 = ld3(P, ids[0]), y1 = ld3(P, ids[1]), y2 = ld3(P, ids[2]), y3 = ld3(P, ids[3]);
   if (surely_apart(pair_lb2(kind, y0, y1, y2, y3), sh) || sat_apart(kind, y0, y1, y2, y3, sh)) {
     flag[k] = 0;
@@ -1719,6 +1871,13 @@ yasps_status detect_pairs(yasps_system* s, const double* P) {
   const topo Tp = make_topo(s);
   const double sh = s->prm.dhat * s->prm.dhat;
   s->npt = s->nee = s->npg = 0;
+  float4* Pf = nullptr;
+  if (s->nv > 0 && (s->nst > 0 || s->nse > 1)) {
+    ENSURE(s, s->pf32, sizeof(float4) * (2 * (size_t)s->nv + 1));
+    Pf = as<float4>(s->pf32);
+    k_f32_copy<<<blocks_for(s->nv, 256), 256, 0, s->stream>>>(s->nv, P, Pf);
+    LAUNCH_CHECK(s, "k_f32_copy");
+  }
   if (s->nsv > 0 && s->npl > 0) {
     RC(two_pass(s, s->nsv, [&](int mode, int total, int* cnt, const int* off, int* out) -> yasps_status {
       k_pg_query<<<blocks_for(s->nsv, 128), 128, 0, s->stream>>>(total, s->nsv, s->npl, Tp, P, as<double>(s->planes), sh, mode,
@@ -1738,7 +1897,7 @@ yasps_status detect_pairs(yasps_system* s, const double* P) {
     grid_dev g;
     RC(build_grid(s, s->nst, bb.b, &g));
     RC(two_pass(s, s->nsv, [&](int mode, int total, int* cnt, const int* off, int* out) -> yasps_status {
-      k_pt_query<<<blocks_for(s->nsv, 128), 128, 0, s->stream>>>(total, s->nsv, Tp, P, g, bb.a, sh, mode, cnt, off,
+      k_pt_query<<<blocks_for(s->nsv, 128), 128, 0, s->stream>>>(total, s->nsv, Tp, P, Pf, g, bb.a, sh, mode, cnt, off,
                                                                 out, 0.0, 0, nullptr);
       LAUNCH_CHECK(s, "k_pt_query");
       return YASPS_OK;
@@ -1753,7 +1912,7 @@ yasps_status detect_pairs(yasps_system* s, const double* P) {
     grid_dev g;
     RC(build_grid(s, s->nse, bb.b, &g));
     RC(two_pass(s, s->nse, [&](int mode, int total, int* cnt, const int* off, int* out) -> yasps_status {
-      k_ee_query<<<blocks_for(s->nse, 128), 128, 0, s->stream>>>(total, s->nse, Tp, P, g, bb.a, sh, mode, cnt, off,
+      k_ee_query<<<blocks_for(s->nse, 128), 128, 0, s->stream>>>(total, s->nse, Tp, P, Pf, g, bb.a, sh, mode, cnt, off,
                                                                 out, 0.0, 0, nullptr);
       LAUNCH_CHECK(s, "k_ee_query");
       return YASPS_OK;
@@ -1827,6 +1986,13 @@ yasps_status barrier_energy(yasps_system* s, const double* P, double* E_host) {
   ENSURE(s, pb, sizeof(ksum) * (npart + 4));
   ksum* part = as<ksum>(pb);
   CK(s, cudaMemsetAsync(part, 0, sizeof(ksum) * (npart + 4), s->stream));
+  float4* Pf = nullptr;
+  if (s->nv > 0 && (s->nst > 0 || s->nse > 1)) {
+    ENSURE(s, s->pf32, sizeof(float4) * (2 * (size_t)s->nv + 1));
+    Pf = as<float4>(s->pf32);
+    k_f32_copy<<<blocks_for(s->nv, 256), 256, 0, s->stream>>>(s->nv, P, Pf);
+    LAUNCH_CHECK(s, "k_f32_copy");
+  }
   if (s->nsv > 0 && s->npl > 0) {
     k_pg_query<<<nblk_v, 128, 0, s->stream>>>(0, s->nsv, s->npl, Tp, P, as<double>(s->planes), sh, 2, nullptr, nullptr,
                                               nullptr, s->prm.kappa, s->prm.barrier_form, part);
@@ -1842,7 +2008,7 @@ yasps_status barrier_energy(yasps_system* s, const double* P, double* E_host) {
     LAUNCH_CHECK(s, "k_boxes");
     grid_dev g;
     RC(build_grid(s, s->nst, bb.b, &g));
-    k_pt_query<<<nblk_v, 128, 0, s->stream>>>(0, s->nsv, Tp, P, g, bb.a, sh, 2, nullptr, nullptr, nullptr,
+    k_pt_query<<<nblk_v, 128, 0, s->stream>>>(0, s->nsv, Tp, P, Pf, g, bb.a, sh, 2, nullptr, nullptr, nullptr,
                                               s->prm.kappa, s->prm.barrier_form, part + nblk_v);
     LAUNCH_CHECK(s, "k_pt_query(E)");
   }
@@ -1854,7 +2020,7 @@ yasps_status barrier_energy(yasps_system* s, const double* P, double* E_host) {
     LAUNCH_CHECK(s, "k_boxes_self");
     grid_dev g;
     RC(build_grid(s, s->nse, bb.b, &g));
-    k_ee_query<<<nblk_e, 128, 0, s->stream>>>(0, s->nse, Tp, P, g, bb.a, sh, 2, nullptr, nullptr, nullptr,
+    k_ee_query<<<nblk_e, 128, 0, s->stream>>>(0, s->nse, Tp, P, Pf, g, bb.a, sh, 2, nullptr, nullptr, nullptr,
                                               s->prm.kappa, s->prm.barrier_form, part + 2 * nblk_v);
     LAUNCH_CHECK(s, "k_ee_query(E)");
   }
@@ -1951,6 +2117,15 @@ yasps_status ccd_candidates(yasps_system* s, double* alpha_host) {
   const std::vector<double> ones(nb_t, 1.0);
   CK(s, cudaMemcpyAsync(tmin, ones.data(), sizeof(double) * nb_t, cudaMemcpyHostToDevice, s->stream));
   int* st = as<int>(s->status);
+  // FP32 copies of the positions and displacements for the prefilter
+  ENSURE(s, s->pf32, sizeof(float4) * (2 * (size_t)s->nv + 1));
+  float4* P0f = as<float4>(s->pf32);
+  float4* Df = P0f + s->nv;
+  if (s->nv > 0 && (s->ncpt > 0 || s->ncee > 0)) {
+    k_f32_copy<<<blocks_for(s->nv, 256), 256, 0, s->stream>>>(s->nv, P0, P0f);
+    k_f32_copy<<<blocks_for(s->nv, 256), 256, 0, s->stream>>>(s->nv, D, Df);
+    LAUNCH_CHECK(s, "k_f32_copy");
+  }
   if (s->nsv > 0 && s->npl > 0) {
     k_ccd_pg<<<blocks_for(s->nsv, 128), 128, 0, s->stream>>>(s->nsv, s->npl, Tp, P0, D, as<double>(s->planes),
                                                             s->prm.ccd_gap, tmin);
@@ -1960,7 +2135,7 @@ yasps_status ccd_candidates(yasps_system* s, double* alpha_host) {
     const int n = kind == 0 ? s->ncpt : s->ncee;
     if (n == 0) continue;
     k_ccd_cand<<<blocks_for(n, 128), 128, 0, s->stream>>>(kind, n, as<int>(kind == 0 ? s->cpt : s->cee), Tp, P0, D,
-                                                         s->prm.ccd_gap, s->prm.ccd_max_iter, tmin, st);
+                                                         P0f, Df, s->prm.ccd_gap, s->prm.ccd_max_iter, tmin, st);
     LAUNCH_CHECK(s, "k_ccd_cand");
   }
   CK(s, cudaMemcpyAsync(alpha_host, tmin, sizeof(double) * nb_t, cudaMemcpyDeviceToHost, s->stream));
@@ -1983,10 +2158,17 @@ yasps_status barrier_energy_candidates(yasps_system* s, const double* P, double*
                                               nullptr, s->prm.kappa, s->prm.barrier_form, part, sacc);
     LAUNCH_CHECK(s, "k_pg_query(E)");
   }
+  float4* Pf = as<float4>(s->pf32);
+  if (s->ncpt > 0 || s->ncee > 0) {
+    ENSURE(s, s->pf32, sizeof(float4) * (2 * (size_t)s->nv + 1));
+    Pf = as<float4>(s->pf32);
+    k_f32_copy<<<blocks_for(s->nv, 256), 256, 0, s->stream>>>(s->nv, P, Pf);
+    LAUNCH_CHECK(s, "k_f32_copy");
+  }
   for (int kind = 0; kind < 2; ++kind) {
     const int n = kind == 0 ? s->ncpt : s->ncee;
     if (n == 0) continue;
-    k_energy_cand<<<nblk_c, 128, 0, s->stream>>>(kind, n, as<int>(kind == 0 ? s->cpt : s->cee), Tp, P, sh, s->prm.kappa,
+    k_energy_cand<<<nblk_c, 128, 0, s->stream>>>(kind, n, as<int>(kind == 0 ? s->cpt : s->cee), Tp, P, Pf, sh, s->prm.kappa,
                                                  s->prm.barrier_form, part + nblk_v + kind * nblk_c, sacc);
     LAUNCH_CHECK(s, "k_energy_cand");
   }
@@ -2011,6 +2193,13 @@ yasps_status detect_from_candidates(yasps_system* s, const double* P) {
       return YASPS_OK;
     }, s->pg, &s->npg));
   }
+  float4* Pf = nullptr;
+  if (s->ncpt > 0 || s->ncee > 0) {
+    ENSURE(s, s->pf32, sizeof(float4) * (2 * (size_t)s->nv + 1));
+    Pf = as<float4>(s->pf32);
+    k_f32_copy<<<blocks_for(s->nv, 256), 256, 0, s->stream>>>(s->nv, P, Pf);
+    LAUNCH_CHECK(s, "k_f32_copy");
+  }
   for (int kind = 0; kind < 2; ++kind) {
     const int n = kind == 0 ? s->ncpt : s->ncee;
     int& nout = kind == 0 ? s->npt : s->nee;
@@ -2022,7 +2211,7 @@ yasps_status detect_from_candidates(yasps_system* s, const double* P) {
     ENSURE(s, s->ws[2], sizeof(int) * (n + 1));
     int *flag = as<int>(s->ws[0]), *sub = as<int>(s->ws[1]), *off = as<int>(s->ws[2]);
     const int* cand = as<int>(kind == 0 ? s->cpt : s->cee);
-    k_filter_cand<<<blocks_for(n, 128), 128, 0, s->stream>>>(kind, n, cand, Tp, P, sh, flag, sub);
+    k_filter_cand<<<blocks_for(n, 128), 128, 0, s->stream>>>(kind, n, cand, Tp, P, Pf, sh, flag, sub);
     LAUNCH_CHECK(s, "k_filter_cand");
     int total = 0;
     RC(scan_exclusive(s, flag, off, n, &total));

@@ -107,6 +107,7 @@ struct yasps_system {
   gbuf pair_key_off;  // int [npt + nee + 1] offsets of each pair's dynamic keys
   gbuf dyn_slot;      // int [nkeys] dynamic BSR slot per key
   gbuf pcg_bt;        // per-block busy time of the PCG kernel's H d' phase (profiling)
+  gbuf pf32;          // FP32 copies of vertex arrays for the candidate prefilters
   gbuf bar_prep;      // per PT / EE pair: barrier derivatives (double2) then classification codes (int)
   int nkeys = 0;
 

@@ -505,6 +505,40 @@ def bw_cloth_scene(cloth_n=101, cloth_size=1.0, layers=1, blob_h=0.01, blob_radi
     return finalize_scene(parts, "bw_cloth", dt, dhat, kappa, n_steps, planes=[[0, 1, 0, 0]])
 
 
+def near_pairs_scene(n_pairs=2000, extent=1.0, size=0.005, dhat=1e-3, speed=0.05, seed=0, dt=0.01, kappa=1e4):
+    """Pairs of small free cloth triangles (edges of about `size`) at random
+    places up to `extent` from the origin, the second of each pair a slightly
+    rotated copy of the first moved by 0.5 to 2.5 dhat in a random direction,
+    with random velocities of about `speed`: point-triangle and edge-edge
+    distances spread on both sides of dhat at coordinates where single
+    precision rounds the most.  A stress input for the contact filters."""
+    rng = np.random.default_rng(seed)
+    parts = _empty_parts()
+    verts, tris, vel = [], [], []
+    R = random_rotations(rng, n_pairs)
+    for k in range(n_pairs):
+        c = rng.uniform(-extent, extent, 3)
+        base = np.array([[0.0, 0.0, 0.0], [1.0, 0.0, 0.0], [0.3, 0.9, 0.0]]) * size * rng.uniform(0.5, 1.5)
+        A = base @ R[k].T + c
+        ang = rng.uniform(0.0, 0.3)
+        ax = rng.normal(size=3)
+        ax /= np.linalg.norm(ax)
+        K = np.array([[0, -ax[2], ax[1]], [ax[2], 0, -ax[0]], [-ax[1], ax[0], 0]])
+        Q = np.eye(3) + np.sin(ang) * K + (1 - np.cos(ang)) * K @ K
+        o = rng.normal(size=3)
+        o *= dhat * rng.uniform(0.5, 2.5) / np.linalg.norm(o)
+        ctr = A.mean(0)
+        B = (A - ctr) @ Q.T + ctr + o
+        for T_ in (A, B):
+            tris.append(np.arange(3) + 3 * len(tris))
+            verts.append(T_)
+            vel.append(np.repeat(rng.normal(size=(1, 3)) * speed, 3, axis=0))
+    V = np.concatenate(verts)
+    off = _add_cloth(parts, V, np.array(tris), 1e5, 0.3, 1e-3, 1000.0, 0.0)
+    parts["vel"][-1] = np.concatenate(vel)
+    return finalize_scene(parts, "near_pairs", dt, dhat, kappa, 1, planes=np.zeros((0, 4)))
+
+
 def caged_blob_scene(blob_h=0.01, blob_radius=0.05, cage_h=0.025, E=3.17e4, nu=0.226, rho=1000.0, lift=3e-4,
                      with_box=True, seed=0, dt=0.01, dhat=1e-3, kappa=1e4, n_steps=150):
     """The cage example's shape (Sec. "Caged Bunny", Table "Caged Bunny"; the
