@@ -270,7 +270,8 @@ struct grid_dev {
 // queried against itself, each unordered pair once), skipped on the record's
 // id before its box is read.
 template <class F>
-__device__ __forceinline__ void grid_visit(const grid_dev& g, const boxes& A, int i, F&& f, bool upper = false) {
+__device__ __forceinline__ void grid_visit(const grid_dev& g, const boxes& A, int i, F&& f, bool upper = false,
+                                           int sub = 0, int gsz = 1) {
   // the query box in registers (f writes through pointers the compiler cannot
   // tell apart from it)
   float alf[3], ahf[3];
@@ -289,18 +290,19 @@ __device__ __forceinline__ void grid_visit(const grid_dev& g, const boxes& A, in
       for (int x = c0[0]; x <= c1[0]; ++x) {
         const long long id = ((long long)z * g.G.dim[1] + y) * g.G.dim[0] + x;
         const int qe = g.start[id + 1];
-        int q = g.start[id];
+        // records sub, sub + gsz, ... of the cell (a group of gsz lanes shares a query)
+        int q = g.start[id] + sub;
         // one record ahead: the next record's 32 bytes load while this one is tested
         float4 n0 = make_float4(0.f, 0.f, 0.f, 0.f), n1 = n0;
         if (q < qe) {
           n0 = g.pk[2 * (size_t)q];
           n1 = g.pk[2 * (size_t)q + 1];
         }
-        for (; q < qe; ++q) {
+        for (; q < qe; q += gsz) {
           const float4 r0 = n0, r1 = n1;
-          if (q + 1 < qe) {
-            n0 = g.pk[2 * (size_t)q + 2];
-            n1 = g.pk[2 * (size_t)q + 3];
+          if (q + gsz < qe) {
+            n0 = g.pk[2 * (size_t)(q + gsz)];
+            n1 = g.pk[2 * (size_t)(q + gsz) + 1];
           }
           const int j = __float_as_int(r0.w);
           if (upper && j <= i) continue;
@@ -1428,12 +1430,24 @@ __global__ void k_reduce_ksum(const ksum* __restrict__ part, int n, double* __re
 // and keeps the first kCandSlots partners in tmp[i][.]; k_cand_gather then
 // writes the queries that fit, and only overflowing queries run mode 1.
 constexpr int kCandSlots = 16;
+// A query's grid walk is shared by kQueryLanes lanes (records of each cell
+// interleaved over them): the longest walks, of the fastest-moving
+// primitives, set the kernel's duration.  The lanes of a query take output
+// positions from a shared-memory counter; each query's list is sorted by
+// partner afterwards, so the result does not depend on the order they find
+// them in.  128 threads per block.
+constexpr int kQueryLanes = 4;
+constexpr int kQueryThreads = 128;
 __global__ void k_cand_query(int total, int kind, int nA, topo T, grid_dev g, boxes A, int mode, int* __restrict__ cnt,
                              const int* __restrict__ off, int* __restrict__ out, int* __restrict__ tmp = nullptr) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= nA) return;
+  __shared__ int qc[kQueryThreads / kQueryLanes];
+  const int gq = threadIdx.x / kQueryLanes, sub = threadIdx.x % kQueryLanes;
+  const int i = blockIdx.x * (kQueryThreads / kQueryLanes) + gq;
+  if (sub == 0) qc[gq] = 0;
+  __syncwarp();
+  if (i >= nA) return;  // the whole group
   if (mode == 1 && tmp && off[i + 1] - off[i] <= kCandSlots) return;  // written by k_cand_gather
-  int c = 0;
+  const unsigned gmask = ((1u << kQueryLanes) - 1u) << (threadIdx.x & 31 & ~(kQueryLanes - 1));
   const int base = (mode == 1) ? off[i] : 0;
   const int lim = (mode == 1) ? ((i + 1 < nA) ? off[i + 1] : total) : 0;
   const int a = (kind == 0) ? T.svert[i] : i;
@@ -1444,6 +1458,7 @@ __global__ void k_cand_query(int total, int kind, int nA, topo T, grid_dev g, bo
       if (j <= i) return;
       if (ee_excluded(T, T.sedge[2 * i], T.sedge[2 * i + 1], T.sedge[2 * j], T.sedge[2 * j + 1])) return;
     }
+    const int c = atomicAdd(&qc[gq], 1);
     if (mode == 1) {
       if (base + c >= lim) { dev_flag(T.status, DEV_CAPACITY); return; }
       out[2 * (size_t)(base + c)] = a;
@@ -1451,8 +1466,10 @@ __global__ void k_cand_query(int total, int kind, int nA, topo T, grid_dev g, bo
     } else if (mode == 3 && c < kCandSlots) {
       tmp[(size_t)i * kCandSlots + c] = j;
     }
-    ++c;
-  }, kind == 1);
+  }, kind == 1, sub, kQueryLanes);
+  __syncwarp(gmask);  // the group's writes and count are complete
+  if (sub != 0) return;
+  int c = qc[gq];
   if (mode == 0 || mode == 3) cnt[i] = c;
   if (mode == 1) {
     c = min(c, lim - base);
@@ -2085,7 +2102,8 @@ yasps_status swept_candidates(yasps_system* s, const double* x, const double* p)
     int* cnt = as<int>(s->ws[2]);
     int* tmp = as<int>(s->ws[10]);
     // one traversal: exact counts, the first kCandSlots partners kept
-    k_cand_query<<<blocks_for(nA, 128), 128, 0, s->stream>>>(0, kind, nA, Tp, g, bb.a, 3, cnt, nullptr, nullptr, tmp);
+    const int qblk = blocks_for((long long)nA * kQueryLanes, kQueryThreads);
+    k_cand_query<<<qblk, kQueryThreads, 0, s->stream>>>(0, kind, nA, Tp, g, bb.a, 3, cnt, nullptr, nullptr, tmp);
     LAUNCH_CHECK(s, "k_cand_query");
     int total = 0;
     RC(scan_exclusive(s, cnt, cnt, nA, &total));
@@ -2096,7 +2114,7 @@ yasps_status swept_candidates(yasps_system* s, const double* x, const double* p)
       k_cand_gather<<<blocks_for(nA, 256), 256, 0, s->stream>>>(kind, nA, Tp, cnt, tmp, as<int>(out));
       LAUNCH_CHECK(s, "k_cand_gather");
       // queries with more partners than slots traverse again and write in place
-      k_cand_query<<<blocks_for(nA, 128), 128, 0, s->stream>>>(total, kind, nA, Tp, g, bb.a, 1, nullptr, cnt,
+      k_cand_query<<<qblk, kQueryThreads, 0, s->stream>>>(total, kind, nA, Tp, g, bb.a, 1, nullptr, cnt,
                                                                as<int>(out), tmp);
       LAUNCH_CHECK(s, "k_cand_query");
     }
