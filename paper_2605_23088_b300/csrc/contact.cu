@@ -1127,7 +1127,11 @@ __device__ void bar_reduced(int dtype, const d3* yl, double kappa, double db, do
   __syncwarp();
 }
 
-template <typename T>
+// STAGE 0: the whole pair in one pass (the warp projects K itself when
+// `project`); STAGE 1: up to K = L^T Hz L, which goes to kbuf[p] (R x R) with
+// g_z to gzbuf[p]; STAGE 2: K (projected by k_project_pairs) and g_z back from
+// there, then the position-space blocks, the gradient and the scatter.
+template <typename T, int STAGE>
 __global__ void __launch_bounds__(128) k_barrier_pair(int npairs, int npt, const int* __restrict__ pt,
                                                        const int* __restrict__ ee, topo Tp,
                                                        const double* __restrict__ vr, const double* __restrict__ P,
@@ -1135,7 +1139,8 @@ __global__ void __launch_bounds__(128) k_barrier_pair(int npairs, int npt, const
                                                        double kappa, int project, bar_tables tb,
                                                        const int* __restrict__ koff, const int* __restrict__ dslot,
                                                        double* __restrict__ g, T* __restrict__ diag,
-                                                       T* __restrict__ vals, int* status) {
+                                                       T* __restrict__ vals, int* status, T* __restrict__ kbuf,
+                                                       double* __restrict__ gzbuf) {
   __shared__ bar_ws<T> wsp[4];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int p = blockIdx.x * 4 + wid;
@@ -1152,9 +1157,37 @@ __global__ void __launch_bounds__(128) k_barrier_pair(int npairs, int npt, const
   d3 yl[4];
   for (int q = 0; q < 4; ++q) {
     loc[q] = (code >> (3 + 2 * q)) & 3;
-    yl[q] = ld3(P, ids[loc[q]]);
+    if (STAGE != 2) yl[q] = ld3(P, ids[loc[q]]);
   }
   const double2 b2 = bd[p];
+  const int k = tb.k[dtype], R = 3 * k, n3 = 3 * nloc;
+  if (STAGE != 2) {
+    bar_reduced<T>(dtype, yl, kappa, b2.x, b2.y, w, lane);
+    // K = L^T Hz L (R x R), into V as scratch, then back into Hz
+    for (int e = lane; e < R * R; e += 32) {
+      const int ra = e / R, ca = e % R, a = ra / 3, i = ra % 3, b = ca / 3, j = ca % 3;
+      T acc = 0;
+      for (int r = a; r < k; ++r)
+        for (int q = b; q < k; ++q) acc += tab_L(tb, T(), dtype, r, a) * tab_L(tb, T(), dtype, q, b) * w.Hz[R * (3 * r + i) + 3 * q + j];
+      w.V[e] = acc;
+    }
+    __syncwarp();
+    if (STAGE == 1) {
+      for (int e = lane; e < R * R; e += 32) kbuf[81 * (size_t)p + e] = w.V[e];
+      if (lane < R) gzbuf[9 * (size_t)p + lane] = w.gz[lane];
+      return;
+    }
+    for (int e = lane; e < R * R; e += 32) w.Hz[e] = w.V[e];
+    __syncwarp();
+    if (project) {
+      if (R == 9) warp_project<T, 9>(w.Hz, w.V, w.cs, w.sn, lane);
+      else if (R == 6) warp_project<T, 6>(w.Hz, w.V, w.cs, w.sn, lane);
+      else warp_project<T, 3>(w.Hz, w.V, w.cs, w.sn, lane);
+    }
+  } else {
+    for (int e = lane; e < R * R; e += 32) w.Hz[e] = kbuf[81 * (size_t)p + e];
+    if (lane < R) w.gz[lane] = gzbuf[9 * (size_t)p + lane];
+  }
   // merged node set and the UNION weights of the classified vertices (integer
   // work and loads; lane 0)
   if (lane == 0) {
@@ -1171,24 +1204,7 @@ __global__ void __launch_bounds__(128) k_barrier_pair(int npairs, int npt, const
       }
     }
   }
-  bar_reduced<T>(dtype, yl, kappa, b2.x, b2.y, w, lane);
-  const int k = tb.k[dtype], R = 3 * k, n3 = 3 * nloc;
-  // K = L^T Hz L (R x R), into V as scratch, then back into Hz
-  for (int e = lane; e < R * R; e += 32) {
-    const int ra = e / R, ca = e % R, a = ra / 3, i = ra % 3, b = ca / 3, j = ca % 3;
-    T acc = 0;
-    for (int r = a; r < k; ++r)
-      for (int q = b; q < k; ++q) acc += tab_L(tb, T(), dtype, r, a) * tab_L(tb, T(), dtype, q, b) * w.Hz[R * (3 * r + i) + 3 * q + j];
-    w.V[e] = acc;
-  }
   __syncwarp();
-  for (int e = lane; e < R * R; e += 32) w.Hz[e] = w.V[e];
-  __syncwarp();
-  if (project) {
-    if (R == 9) warp_project<T, 9>(w.Hz, w.V, w.cs, w.sn, lane);
-    else if (R == 6) warp_project<T, 6>(w.Hz, w.V, w.cs, w.sn, lane);
-    else warp_project<T, 3>(w.Hz, w.V, w.cs, w.sn, lane);
-  }
   // position space: Hy = Q^T K Q (n3 x n3)
   for (int e = lane; e < n3 * n3; e += 32) {
     const int row = e / n3, col = e % n3, v = row / 3, i = row % 3, u = col / 3, j = col % 3;
@@ -1245,6 +1261,34 @@ __global__ void __launch_bounds__(128) k_barrier_pair(int npairs, int npt, const
     }
     for (int t = 0; t < 9; ++t) atomicAdd(d + t, B[t]);
   }
+}
+
+// The projection of the stored K of every active PT / EE pair, one pair per
+// thread (cyclic Jacobi in registers, project_psd): a warp projects 32 pairs
+// at once, where the warp-parallel sweeps of k_barrier_pair<., 0> project one
+// with a long chain of dependent shared-memory steps.  Pairs of one warp with
+// different sizes (R = 3, 6, 9) take the branches in turn.
+template <typename T, int R>
+__device__ __forceinline__ void project_slot(T* __restrict__ kb) {
+  T A[R * R];
+#pragma unroll
+  for (int e = 0; e < R * R; ++e) A[e] = kb[e];
+  project_psd<R, T>(A);
+#pragma unroll
+  for (int e = 0; e < R * R; ++e) kb[e] = A[e];
+}
+template <typename T>
+__global__ void __launch_bounds__(128) k_project_pairs(int npairs, const int* __restrict__ info, bar_tables tb,
+                                                        T* __restrict__ kbuf) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= npairs) return;
+  const int code = info[p];
+  if (!(code & 1)) return;
+  const int R = 3 * tb.k[(code >> 1) & 3];
+  T* kb = kbuf + 81 * (size_t)p;
+  if (R == 9) project_slot<T, 9>(kb);
+  else if (R == 6) project_slot<T, 6>(kb);
+  else project_slot<T, 3>(kb);
 }
 
 // smallest squared distance over the PT, EE and PG pair lists (the adaptive
@@ -1830,10 +1874,32 @@ yasps_status eval_barrier_t(yasps_system* s, int project) {
     k_barrier_prep<<<blocks_for(np, 128), 128, 0, s->stream>>>(s->npt, s->nee, as<int>(s->pt), as<int>(s->ee), Tp, P,
                                                               sh, s->prm.barrier_form, info, bd);
     LAUNCH_CHECK(s, "k_barrier_prep");
-    k_barrier_pair<T><<<blocks_for(np, 4), 128, 0, s->stream>>>(np, s->npt, as<int>(s->pt), as<int>(s->ee), Tp,
-                                                               as<double>(s->vr), P, info, bd, s->prm.kappa, project,
-                                                               tb, koff, dslot, g, diag, vals, st);
-    LAUNCH_CHECK(s, "k_barrier_pair");
+    // FP64 Jacobi runs on the scarce FP64 pipe: a pair per thread puts 32
+    // pairs' sweeps on one SM sub-partition, which pays only once the pairs
+    // fill every sub-partition many times over; below that, a warp per pair
+    // spreads them.  FP32 projects a pair per thread at any count.
+    constexpr int kThreadProjMin64 = 16384;
+    if (!project || (sizeof(T) == 8 && np < kThreadProjMin64)) {
+      k_barrier_pair<T, 0><<<blocks_for(np, 4), 128, 0, s->stream>>>(np, s->npt, as<int>(s->pt), as<int>(s->ee), Tp,
+                                                                    as<double>(s->vr), P, info, bd, s->prm.kappa, project, tb,
+                                                                    koff, dslot, g, diag, vals, st, nullptr, nullptr);
+      LAUNCH_CHECK(s, "k_barrier_pair");
+    } else {
+      // K of every pair to scratch, projected a pair per thread, then the rest
+      ENSURE(s, s->bar_k, (sizeof(T) * 81 + sizeof(double) * 9) * ((size_t)np + 1));
+      double* gzb = as<double>(s->bar_k);
+      T* kb = reinterpret_cast<T*>(gzb + 9 * ((size_t)np + 1));
+      k_barrier_pair<T, 1><<<blocks_for(np, 4), 128, 0, s->stream>>>(np, s->npt, as<int>(s->pt), as<int>(s->ee), Tp,
+                                                                    as<double>(s->vr), P, info, bd, s->prm.kappa, 1, tb,
+                                                                    koff, dslot, g, diag, vals, st, kb, gzb);
+      LAUNCH_CHECK(s, "k_barrier_pair(1)");
+      k_project_pairs<T><<<blocks_for(np, 128), 128, 0, s->stream>>>(np, info, tb, kb);
+      LAUNCH_CHECK(s, "k_project_pairs");
+      k_barrier_pair<T, 2><<<blocks_for(np, 4), 128, 0, s->stream>>>(np, s->npt, as<int>(s->pt), as<int>(s->ee), Tp,
+                                                                    as<double>(s->vr), P, info, bd, s->prm.kappa, 1, tb,
+                                                                    koff, dslot, g, diag, vals, st, kb, gzb);
+      LAUNCH_CHECK(s, "k_barrier_pair(2)");
+    }
   }
   if (s->npg) {
     k_barrier_pg<T><<<blocks_for(s->npg, 128), 128, 0, s->stream>>>(s->npg, s->npt + s->nee, as<int>(s->pg), Tp,

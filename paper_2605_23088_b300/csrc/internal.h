@@ -108,6 +108,7 @@ struct yasps_system {
   gbuf dyn_slot;      // int [nkeys] dynamic BSR slot per key
   gbuf pcg_bt;        // per-block busy time of the PCG kernel's H d' phase (profiling)
   gbuf pf32;          // FP32 copies of vertex arrays for the candidate prefilters
+  gbuf bar_k;         // barrier pairs: g_z and K between the derivative and projection kernels
   gbuf bar_prep;      // per PT / EE pair: barrier derivatives (double2) then classification codes (int)
   int nkeys = 0;
 

@@ -64,7 +64,7 @@ static void all_bufs(yasps_system* s, std::vector<gbuf*>& v) {
                  &s->hinge_v, &s->hinge_n, &s->hinge_rest, &s->hinge_slot, &s->body_kv, &s->body_slot, &s->stri,
                  &s->sedge, &s->svert, &s->planes, &s->Hs.row_ptr, &s->Hs.col, &s->Hs.row, &s->Hs.vals,
                  &s->Hd.row_ptr, &s->Hd.col, &s->Hd.row, &s->Hd.vals, &s->diag, &s->grad, &s->minv, &s->dsym, &s->P, &s->pt,
-                 &s->ee, &s->pg, &s->cpt, &s->cee, &s->pair_key_off, &s->dyn_slot, &s->bar_prep, &s->pcg_bt, &s->pf32, &s->status, &s->scal, &s->red, &s->scan_tmp};
+                 &s->ee, &s->pg, &s->cpt, &s->cee, &s->pair_key_off, &s->dyn_slot, &s->bar_prep, &s->pcg_bt, &s->pf32, &s->bar_k, &s->status, &s->scal, &s->red, &s->scan_tmp};
   for (gbuf* b : one) v.push_back(b);
   for (auto& b : s->ws) v.push_back(&b);
   for (auto& b : s->vec) v.push_back(&b);
