@@ -368,7 +368,7 @@ __device__ __forceinline__ bool grid_reduce(pcg_bar* bar, unsigned& k, P partial
 
 // ---- shared-memory staging of the upper blocks (bulk async copies)
 //
-// Each block owns an even, 4-aligned share of the first 80% of the upper
+// Each block owns an even, 4-aligned share of the first 90% of the upper
 // blocks (static, then dynamic; share_cut) and then claims tiles of the rest
 // from a shared pool; tiles hold BPT blocks per thread.  A
 // tile's values, rows and columns are contiguous, so thread 0 moves them into
@@ -439,7 +439,7 @@ __device__ __forceinline__ void share_cut(long long n_s, long long n_d, long lon
 // of tiles that the blocks claim from a counter once their own share is done.
 // Pool tiles are full tiles (smaller ones leave lanes idle while costing a
 // tile's latency), the dynamic ones first (they take longest).
-constexpr int kPoolPct = 20;
+constexpr int kPoolPct = 10;
 template <typename T, typename V>
 __device__ __forceinline__ spmv_share share_of(const pcg_args<T, V>& a, int NT) {
   const long long G = gridDim.x, b = blockIdx.x;
