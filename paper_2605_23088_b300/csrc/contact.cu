@@ -1473,7 +1473,7 @@ __global__ void k_reduce_ksum(const ksum* __restrict__ part, int n, double* __re
 // mode 3: one traversal that counts every candidate of query i into cnt[i]
 // and keeps the first kCandSlots partners in tmp[i][.]; k_cand_gather then
 // writes the queries that fit, and only overflowing queries run mode 1.
-constexpr int kCandSlots = 16;
+constexpr int kCandSlots = 64;
 // A query's grid walk is shared by kQueryLanes lanes (records of each cell
 // interleaved over them): the longest walks, of the fastest-moving
 // primitives, set the kernel's duration.  The lanes of a query take output
