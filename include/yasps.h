@@ -471,8 +471,10 @@ yasps_status yasps_profile_get(yasps_system* sys, int stage, yasps_stage_stats* 
  * grid's d^T H d, out[3] the update + preconditioner phase, out[4] the wait
  * for the grid's r^T z; out[5], out[6] the mean and the largest over the
  * grid's blocks of a block's own-node + upper-block time (the load balance of
- * the H d phase); out[7] = 0.  Waits include the time the slowest block of
- * the grid needs beyond the first. */
+ * the H d phase); out[7] the wait at the extra grid barrier of the FP64
+ * form, after which the upper blocks read d' directly (0 in FP32 and in
+ * batches).  Waits include the time the slowest block of the grid needs
+ * beyond the first. */
 yasps_status yasps_pcg_phase_ms(const yasps_system* sys, double* out);
 
 /* Load balance of the PCG kernel, block by block: for each block of the grid

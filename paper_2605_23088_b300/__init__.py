@@ -37,7 +37,7 @@ SPMV_FORMATS = ["upper_bsr", "full_bsr", "full_bcoo", "upper_bcoo"]
 STAGE_SPMV, STAGE_TET, STAGE_BARRIER, STAGE_PCG, STAGE_DETECT, STAGE_EVAL, STAGE_CCD, STAGE_LS, STAGE_PCG_KERNEL = range(9)
 STAGE_NAMES = ["spmv", "tet", "barrier", "pcg", "detect", "eval", "ccd", "line_search", "pcg_kernel"]
 PCG_VARIANTS = 5  # YASPS_PCG_VARIANTS
-PCG_PHASES = ["own_nodes", "upper_blocks", "wait_dHd", "update", "wait_rz", "hd_busy_mean", "hd_busy_max", "unused7"]
+PCG_PHASES = ["own_nodes", "upper_blocks", "wait_dHd", "update", "wait_rz", "hd_busy_mean", "hd_busy_max", "wait_dn"]
 
 
 class YaspsError(RuntimeError):

@@ -530,6 +530,14 @@ __device__ __forceinline__ void gather_d(int r, int c, const V* z, const V* d, V
     g.r0 = dnew(zr0, beta, dr0); g.r1 = dnew(zr1, beta, dr1); g.r2 = dnew(zr2, beta, dr2);
   }
 }
+// the two d' segments read directly (d' of every node written before the tiles)
+template <typename V>
+__device__ __forceinline__ void gather_dn(int r, int c, const V* dn, gath<V>& g) {
+  if (r >= 0) {
+    g.c0 = dn[3 * c]; g.c1 = dn[3 * c + 1]; g.c2 = dn[3 * c + 2];
+    g.r0 = dn[3 * r]; g.r1 = dn[3 * r + 1]; g.r2 = dn[3 * r + 2];
+  }
+}
 // Layout of the product q = H d inside the PCG kernel: FP32 uses 16 bytes
 // per node, so a node's three contributions go in one vector atomic
 // (red.global.add.v4.f32); FP64 keeps 3 scalars per node.
@@ -786,11 +794,16 @@ __global__ void __launch_bounds__(CFG::NTHR, CFG::MINB) k_pcg_persistent(pcg_arg
   const bool clock0 = blockIdx.x == 0 && threadIdx.x == 0;
   // block 0's clock per iteration: 0 own nodes (d', D d'), 1 upper blocks,
   // 2 wait + d^T H d, 3 update, 4 wait + r^T z
-  __shared__ unsigned long long tph[5];
+  __shared__ unsigned long long tph[6];
+  // d' of every node first, behind one more grid barrier, then the tiles
+  // gather d' itself: in FP64 the on-the-fly z + beta d of every gathered
+  // node (six FMAs per upper block) costs the FP64 pipe, which bounds FP64
+  // SpMV on this part, more than the barrier does.  FP32 forms d' on the fly.
+  constexpr bool DPRE = !BATCH && sizeof(V) == 8;
   __shared__ int sh_active;
   __shared__ int s_tcnt[2];  // blocks in the tile requested into each buffer (0: none)
   unsigned long long tlast = 0, tbusy = 0, tbusy0 = 0;
-  if (threadIdx.x < 5) tph[threadIdx.x] = 0;
+  if (threadIdx.x < 6) tph[threadIdx.x] = 0;
   if constexpr (BATCH)
     for (int t = threadIdx.x; t < a.nscene; t += blockDim.x) shs[t] = 0.0;
   unsigned parity = 0u;    // bit b: phase parity of buffer b's next completion
@@ -969,6 +982,16 @@ __global__ void __launch_bounds__(CFG::NTHR, CFG::MINB) k_pcg_persistent(pcg_arg
       }
     }
     if (clock0) { const unsigned long long t = global_ns(); tph[0] += t - tlast; tlast = t; }
+    if constexpr (DPRE) {
+      if (a.bt && threadIdx.x == 0) tbusy += global_ns() - tbusy0;
+      double unused = 0.0;
+      if (!grid_reduce(a.bar, kbar, V(0), unused, a.spin_limit, a.unmet)) {
+        done = 3;
+        break;
+      }
+      if (clock0) { const unsigned long long t = global_ns(); tph[5] += t - tlast; tlast = t; }
+      if (a.bt && threadIdx.x == 0) tbusy0 = global_ns();
+    }
     // upper blocks, tile by tile from shared memory, until a buffer gets none
     bool ok = true;
     __syncthreads();  // s_tcnt of the first two tiles
@@ -1004,6 +1027,7 @@ __global__ void __launch_bounds__(CFG::NTHR, CFG::MINB) k_pcg_persistent(pcg_arg
 #pragma unroll
       for (int u = 0; u < BPT; ++u) {
         if constexpr (BATCH) gather_d(rr[u], cc[u], a.z, d, ss[u] >= 0 ? tab[ss[u]] : V(0), gg[u]);
+        else if constexpr (DPRE) gather_dn(rr[u], cc[u], dn, gg[u]);
         else gather_d(rr[u], cc[u], a.z, d, vb, gg[u]);
       }
 #pragma unroll
@@ -1157,7 +1181,7 @@ __global__ void __launch_bounds__(CFG::NTHR, CFG::MINB) k_pcg_persistent(pcg_arg
     a.sc->done = done;
     a.sc->iters = it;
 #pragma unroll
-    for (int k = 0; k < 8; ++k) a.sc->t_ns[k] = k < 5 ? tph[k] : 0ull;
+    for (int k = 0; k < 8; ++k) a.sc->t_ns[k] = k < 5 ? tph[k] : (k == 7 ? tph[5] : 0ull);
   }
   if (threadIdx.x == 0 && done == 3) dev_flag(a.status, DEV_TIMEOUT);
 }
@@ -1411,6 +1435,7 @@ yasps_status pcg_launch_cfg(yasps_system* s, const double* rhs, double* p, doubl
     sp.count += h.iters;
     sp.ms += (h.t_ns[0] + h.t_ns[1] + h.t_ns[2]) * 1e-6;
     for (int k = 0; k < 5; ++k) s->pcg_phase_ms[k] += h.t_ns[k] * 1e-6;
+    s->pcg_phase_ms[7] += h.t_ns[7] * 1e-6;
     sp.bytes += spmv_bytes * h.iters;
     // load balance of the H d' phase: mean and max over the blocks of their busy time
     std::vector<unsigned long long> bt(2 * (size_t)G);
