@@ -397,6 +397,7 @@ def native(args):
             line["fp64_plain"]["max_dx_vs_fp32_mixed_m"] = dx
     if not args.skip_spmv_study:
         line["spmv_study"] = spmv_study(G)
+        line["spmv_scaling"] = spmv_scaling()
         line["projection_study"] = projection_study()
     if not args.skip_batch:
         line["batch"] = batch_bench(args, dev)
@@ -440,7 +441,34 @@ def spmv_layouts(row_u, col_u, vals_u, diag, perm=None):
     return diag, {"upper_bsr": upper, "full_bsr": full, "full_bcoo": full, "upper_bcoo": upper}
 
 
-def spmv_study(G, reps=20):
+def spmv_scaling(lattices=(1, 2, 3, 4), reps=10):
+    """The shape of the paper's SpMV experiment (Sec. "Evaluation"): the
+    elastic (stable Neo-Hookean) Hessian of N objects, vertices randomly
+    renumbered, time per call of every layout as N grows; here N = 1, 8, 27,
+    64 tori of the workload's generator at rest (no contact), FP32 and FP64."""
+    import torch
+
+    import paper_2605_23088_b300 as yb
+    import scenes
+
+    out = {"tori": [], "upper_blocks": [], "us": {}}
+    for L in lattices:
+        sc = scenes.tori_scene(nx=L, ny=L, nz=L)
+        G = yb.System(sc, precision=1)
+        x, _ = G.initial_state()
+        G.eval_local(x, x, term_mask=yb.TERM_TET, project=True)
+        st = spmv_study(G, reps=reps, orders=("permuted",))
+        out["tori"].append(L ** 3)
+        out["upper_blocks"].append(st["upper_blocks"])
+        for k, v in st.items():
+            if isinstance(v, dict):
+                out["us"].setdefault(k, []).append(round(v["us"], 2))
+        G.close()
+        torch.cuda.synchronize()
+    return out
+
+
+def spmv_study(G, reps=20, orders=("natural", "permuted")):
     """Time y = A x on the system's current matrix in every layout and
     precision, natural node order and a seeded random renumbering, with L2
     flushed before every timed call; GB/s of algorithmic bytes (blocks and
@@ -468,7 +496,7 @@ def spmv_study(G, reps=20):
     out = {"n_nodes": n, "upper_blocks": int(len(row_u)), "peak_gbs": peak, "peak_kind": kind, "reps": reps,
            "l2": "flushed before every call (256 MB write)"}
     ref = None
-    for order in ("natural", "permuted"):
+    for order in orders:
         perm = None if order == "natural" else rng.permutation(n)
         d, lay = spmv_layouts(row_u, col_u, vals_u, diag, perm)
         xo = x64 if perm is None else x64[np.argsort(perm)]  # x in the new numbering: x'[perm[i]] = x[i]
@@ -483,7 +511,8 @@ def spmv_study(G, reps=20):
                 Y = torch.empty_like(X)
                 flag = torch.zeros(1, dtype=torch.int32, device="cuda")
                 fmt = yb.SPMV_FORMATS.index(name)
-                yb.spmv_format(fmt, n, R_, C_, V_, D, X, Y, flag)
+                for _ in range(3):  # untimed warm-up calls
+                    yb.spmv_format(fmt, n, R_, C_, V_, D, X, Y, flag)
                 ms = []
                 for _ in range(reps):
                     flush.zero_()
