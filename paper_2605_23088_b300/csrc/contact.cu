@@ -1874,12 +1874,14 @@ yasps_status eval_barrier_t(yasps_system* s, int project) {
     k_barrier_prep<<<blocks_for(np, 128), 128, 0, s->stream>>>(s->npt, s->nee, as<int>(s->pt), as<int>(s->ee), Tp, P,
                                                               sh, s->prm.barrier_form, info, bd);
     LAUNCH_CHECK(s, "k_barrier_prep");
-    // FP64 Jacobi runs on the scarce FP64 pipe: a pair per thread puts 32
-    // pairs' sweeps on one SM sub-partition, which pays only once the pairs
-    // fill every sub-partition many times over; below that, a warp per pair
-    // spreads them.  FP32 projects a pair per thread at any count.
-    constexpr int kThreadProjMin64 = 16384;
-    if (!project || (sizeof(T) == 8 && np < kThreadProjMin64)) {
+    // A pair per thread has a long latency per pair (one thread's sweeps,
+    // ~0.1 ms in FP32 measured) but a high throughput; a warp per pair has
+    // half the latency and spreads few pairs over every SM.  Below a few
+    // thousand pairs the warp projection is faster.  FP64 Jacobi also runs on
+    // the scarce FP64 pipe, where 32 pairs' sweeps on one SM sub-partition pay
+    // only once the pairs fill every sub-partition many times over.
+    constexpr int kThreadProjMin32 = 8192, kThreadProjMin64 = 16384;
+    if (!project || np < (sizeof(T) == 8 ? kThreadProjMin64 : kThreadProjMin32)) {
       k_barrier_pair<T, 0><<<blocks_for(np, 4), 128, 0, s->stream>>>(np, s->npt, as<int>(s->pt), as<int>(s->ee), Tp,
                                                                     as<double>(s->vr), P, info, bd, s->prm.kappa, project, tb,
                                                                     koff, dslot, g, diag, vals, st, nullptr, nullptr);

@@ -1,10 +1,10 @@
 """Both projection paths of the PT / EE barrier Hessians against the oracle.
 
 The barrier kernel projects the reduced Hessian K either inside the
-warp-per-pair kernel (warp-parallel Jacobi; FP64 below 16,384 pairs) or in a
-separate pass with one pair per thread (FP32 always; FP64 from 16,384 pairs
-on).  Scenes: 600 and 6000 near-contact triangle pairs (about 4k and 40k
-PT + EE pairs), so that FP64 takes each path once.  The assembled gradient
+warp-per-pair kernel (warp-parallel Jacobi; below 8,192 pairs in FP32 and
+16,384 in FP64) or in a separate pass with one pair per thread (above).
+Scenes: 600 and 6000 near-contact triangle pairs (about 4k and 40k PT + EE
+pairs), so that each precision takes each path once.  The assembled gradient
 and BSR (projected) match the oracle within 1e-10 per entry in FP64, as in
 test_gpu_parity; the FP32-mixed blocks within 2e-5 of the largest.
 """
@@ -32,7 +32,7 @@ def test_projected_barrier_assembly(n_pairs):
     x, v = O.initial_state()
     pt, ee, _ = O.pairs(x)
     npairs = len(pt) + len(ee)
-    assert (npairs >= 16384) == (n_pairs == 6000), npairs
+    assert (npairs >= 16384) == (n_pairs == 6000) and (npairs >= 8192) == (n_pairs == 6000), npairs
     G = yb.System(s)
     compare_assembly(G, O, x, v, project=True)
     # FP32-mixed: the same blocks in single precision
