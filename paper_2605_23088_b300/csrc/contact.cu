@@ -1172,17 +1172,18 @@ __global__ void __launch_bounds__(128) k_barrier_pair(int npairs, int npt, const
       w.V[e] = acc;
     }
     __syncwarp();
-    if (STAGE == 1) {
+    if constexpr (STAGE == 1) {
       for (int e = lane; e < R * R; e += 32) kbuf[81 * (size_t)p + e] = w.V[e];
       if (lane < R) gzbuf[9 * (size_t)p + lane] = w.gz[lane];
       return;
-    }
-    for (int e = lane; e < R * R; e += 32) w.Hz[e] = w.V[e];
-    __syncwarp();
-    if (project) {
-      if (R == 9) warp_project<T, 9>(w.Hz, w.V, w.cs, w.sn, lane);
-      else if (R == 6) warp_project<T, 6>(w.Hz, w.V, w.cs, w.sn, lane);
-      else warp_project<T, 3>(w.Hz, w.V, w.cs, w.sn, lane);
+    } else {
+      for (int e = lane; e < R * R; e += 32) w.Hz[e] = w.V[e];
+      __syncwarp();
+      if (project) {
+        if (R == 9) warp_project<T, 9>(w.Hz, w.V, w.cs, w.sn, lane);
+        else if (R == 6) warp_project<T, 6>(w.Hz, w.V, w.cs, w.sn, lane);
+        else warp_project<T, 3>(w.Hz, w.V, w.cs, w.sn, lane);
+      }
     }
   } else {
     for (int e = lane; e < R * R; e += 32) w.Hz[e] = kbuf[81 * (size_t)p + e];
