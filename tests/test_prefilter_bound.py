@@ -12,7 +12,9 @@ exact squared distance from the oracle's FP64 classification, on random
 point-triangle and edge-edge configurations far from the origin (where FP32
 rounds the most) and at distances from 1e-6 to 1e-2 m, including nearly
 parallel and nearly touching ones.  It also checks that the bound stays useful:
-for pairs more than 1.5 times dhat apart it rejects nearly all of them.
+for pairs more than 1.5 times dhat apart it rejects nearly all of them.  The
+CCD's bound on the relative motion, max_k |dx_k - mean|, is checked the same
+way against its exact value, with a common drift of up to 1 m.
 """
 import numpy as np
 
@@ -112,3 +114,23 @@ def test_bound_rejects_far_pairs():
             far += 1
             rejected += lb2_f32(kind, [np.asarray(v, f) for v in y]) > sh * (1 + 1e-6)
     assert far > 500 and rejected >= 0.9 * far, (far, rejected)
+
+
+def motion_hi_f32(d):
+    """The FP32 upper bound of max_k |dx_k - m| (m the mean of the exact dx_k)."""
+    d = [np.asarray(v, f) for v in d]
+    Dm = max(f(np.abs(v).max()) for v in d)
+    m = np.zeros(3, f)
+    for v in d:
+        m = (m + f(0.25) * v).astype(f)
+    mx2 = max(f(np.dot((v - m).astype(f), (v - m).astype(f))) for v in d)
+    return float(f(f(np.sqrt(mx2)) * f(1 + 8 * U)) + f(1.7320508) * f(16) * U * Dm)
+
+
+def test_motion_bound_covers_the_exact_relative_motion():
+    rng = np.random.default_rng(13)
+    for _ in range(4000):
+        common = rng.normal(size=3) * 10 ** rng.uniform(-4, 0)  # a shared drift, up to 1 m
+        dx = common + rng.normal(size=(4, 3)) * 10 ** rng.uniform(-9, -2)
+        exact = np.linalg.norm(dx - dx.mean(0), axis=1).max()
+        assert motion_hi_f32([np.asarray(v, f) for v in dx]) >= exact * (1 - 1e-12), (exact,)
